@@ -1,0 +1,316 @@
+"""Plain CPU oracle for full-RNS CKKS HE Mul -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+legs of ``bench.py`` may import this package.  The product library never does,
+and this package never imports the product.  The only module both sides use is
+``seeded_inputs`` (seeded synthetic messages and level draws), which holds none
+of the method's arithmetic.
+
+The arithmetic lives in ``oracle.c`` (uint64 residues, ``unsigned __int128``
+products, plain ``%`` reductions) and follows "HEAAN Demystified"
+(arXiv 2003.04510): NTT = Algo 3 with Algo 4's butterfly, iNTT as described
+beneath Algo 4, the HE Mul flow of Fig. 2 in its full-RNS form (Sec. 7,
+Table 11), encryption/decryption and rescale of Sec. 3.1.  Encoding and
+decoding (``oracle.encoding``) use numpy's FFT as a library primitive.
+
+Functions whose only pin is the decryption bound are marked "parity unpinned"
+in their docstrings; every other function is pinned by a closed form or a brute
+force check in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (plain gcc, no vector flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+             "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        u64, i64, i32, dbl = ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        P = ctypes.c_void_p
+        sig = {
+            "or_mulmod": (u64, [u64, u64, u64]),
+            "or_addmod": (u64, [u64, u64, u64]),
+            "or_submod": (u64, [u64, u64, u64]),
+            "or_powmod": (u64, [u64, u64, u64]),
+            "or_invmod": (u64, [u64, u64]),
+            "or_is_prime": (i32, [u64]),
+            "or_gen_primes": (i32, [i32, i32, i32, P, i32, P]),
+            "or_min_psi": (u64, [u64, i32]),
+            "or_ntt": (None, [P, i32, u64, u64]),
+            "or_intt": (None, [P, i32, u64, u64]),
+            "or_butterfly_count": (u64, []),
+            "or_reset_butterfly_count": (None, []),
+            "or_splitmix64": (u64, [u64, u64]),
+            "or_sample_gauss": (None, [u64, u64, dbl, i64, P]),
+            "or_sample_zo": (None, [u64, u64, i64, P]),
+            "or_sample_uniform": (None, [u64, u64, u64, i64, P]),
+            "or_keygen_sk": (None, [i32, i32, u64, P]),
+            "or_keygen_pk": (None, [i32, i32, P, P, dbl, P, u64, P]),
+            "or_keygen_evk": (None, [i32, i32, i32, i32, P, P, P, P, dbl, P, u64, P]),
+            "or_encrypt": (None, [i32, i32, P, P, dbl, P, P, i32, u64, P]),
+            "or_decrypt": (None, [i32, P, P, P, P, i32, P]),
+            "or_tensor": (None, [i32, i32, P, P, P, P, P, P]),
+            "or_modup_digit": (None, [i32, i32, i32, i32, P, P, i32, P, P]),
+            "or_inner_product": (None, [i32, i32, i32, i32, i32, P, P, P, P, P]),
+            "or_moddown": (None, [i32, i32, i32, P, P, P, P, P, P]),
+            "or_keyswitch": (None, [i32, i32, i32, i32, i32, P, P, P, P, P, P, P, P, P]),
+            "or_he_mul": (None, [i32, i32, i32, i32, i32, P, P, P, P, P, P, P, P]),
+            "or_rescale": (None, [i32, i32, P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _u64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint64))
+
+
+# --------------------------------------------------------------------------
+# Parameters (reading c-1: largest NTT-friendly primes, descending; smallest
+# primitive 2N-th root; specials exclude the ciphertext primes).
+# --------------------------------------------------------------------------
+@dataclass
+class Params:
+    logN: int
+    L: int
+    K: int
+    alpha: int
+    q_bits: int
+    p_bits: int
+    h: int = 64
+    sigma: float = 3.2
+    q: np.ndarray = field(default=None, repr=False)
+    p: np.ndarray = field(default=None, repr=False)
+    psi_q: np.ndarray = field(default=None, repr=False)
+    psi_p: np.ndarray = field(default=None, repr=False)
+
+    @property
+    def N(self) -> int:
+        return 1 << self.logN
+
+    @property
+    def dnum(self) -> int:
+        return -(-self.L // self.alpha)
+
+    def beta(self, l: int) -> int:
+        return -(-l // self.alpha)
+
+    def digit(self, j: int, l: int) -> range:
+        return range(j * self.alpha, min((j + 1) * self.alpha, l))
+
+    @property
+    def ext(self) -> list[int]:
+        """Moduli in ext order: K special primes first, then the L ciphertext primes."""
+        return [int(x) for x in self.p] + [int(x) for x in self.q]
+
+
+_param_cache: dict = {}
+
+
+def make_params(logN, L, K, alpha, q_bits, p_bits, h=64, sigma=3.2) -> Params:
+    key = (logN, L, K, alpha, q_bits, p_bits, h, sigma)
+    if key in _param_cache:
+        return _param_cache[key]
+    lb = lib()
+    q = np.zeros(L, dtype=np.uint64)
+    if lb.or_gen_primes(logN, q_bits, L, None, 0, _p(q)) != 0:
+        raise ValueError("not enough ciphertext primes")
+    p = np.zeros(max(K, 1), dtype=np.uint64)
+    if lb.or_gen_primes(logN, p_bits, K, _p(q), L, _p(p)) != 0:
+        raise ValueError("not enough special primes")
+    p = p[:K].copy()
+    psi_q = np.array([lb.or_min_psi(int(x), logN) for x in q], dtype=np.uint64)
+    psi_p = np.array([lb.or_min_psi(int(x), logN) for x in p], dtype=np.uint64)
+    prm = Params(logN, L, K, alpha, q_bits, p_bits, h, sigma, q, p, psi_q, psi_p)
+    _param_cache[key] = prm
+    return prm
+
+
+# Workload presets (the configurations the build is measured on).
+PRESETS = {
+    # N=2^12, 3 x 50-bit limbs + one 51-bit special prime, one limb per digit
+    "n12": dict(logN=12, L=3, K=1, alpha=1, q_bits=50, p_bits=51, h=64, scale_bits=40),
+    # N=2^15 serving preset: 16 limbs + 8 specials, alpha 8
+    "n15": dict(logN=15, L=16, K=8, alpha=8, q_bits=54, p_bits=55, h=192, scale_bits=50),
+    # N=2^16, 24 x 54-bit limbs + 8 x 55-bit specials, dnum 3
+    "n16": dict(logN=16, L=24, K=8, alpha=8, q_bits=54, p_bits=55, h=192, scale_bits=50),
+    # N=2^17, 44 x 54-bit limbs + 12 x 54-bit specials, dnum 4
+    "n17": dict(logN=17, L=44, K=12, alpha=11, q_bits=54, p_bits=54, h=192, scale_bits=50),
+}
+
+
+def preset(name: str) -> Params:
+    d = dict(PRESETS[name])
+    d.pop("scale_bits")
+    return make_params(**d)
+
+
+# --------------------------------------------------------------------------
+# Thin wrappers (allocation + argument marshalling only).
+# --------------------------------------------------------------------------
+def ntt(a, q: int, psi: int, logN: int) -> np.ndarray:
+    out = _u64(a).copy()
+    lib().or_ntt(_p(out), logN, q, psi)
+    return out
+
+
+def intt(a, q: int, psi: int, logN: int) -> np.ndarray:
+    out = _u64(a).copy()
+    lib().or_intt(_p(out), logN, q, psi)
+    return out
+
+
+def keygen_sk(prm: Params, seed: int) -> np.ndarray:
+    s = np.zeros(prm.N, dtype=np.int64)
+    lib().or_keygen_sk(prm.logN, prm.h, seed, _p(s))
+    return s
+
+
+def keygen_pk(prm: Params, sk: np.ndarray, seed: int) -> np.ndarray:
+    pk = np.zeros((2, prm.L, prm.N), dtype=np.uint64)
+    lib().or_keygen_pk(prm.logN, prm.L, _p(prm.q), _p(prm.psi_q), prm.sigma, _p(sk), seed, _p(pk))
+    return pk
+
+
+def keygen_evk(prm: Params, sk: np.ndarray, seed: int) -> np.ndarray:
+    evk = np.zeros((prm.dnum, 2, prm.K + prm.L, prm.N), dtype=np.uint64)
+    lib().or_keygen_evk(prm.logN, prm.L, prm.K, prm.alpha, _p(prm.q), _p(prm.psi_q), _p(prm.p),
+                        _p(prm.psi_p), prm.sigma, _p(sk), seed, _p(evk))
+    return evk
+
+
+def encrypt_poly(prm: Params, pk: np.ndarray, pt: np.ndarray, level: int, seed: int) -> np.ndarray:
+    pt = np.ascontiguousarray(pt, dtype=np.int64)
+    ct = np.zeros((2, level, prm.N), dtype=np.uint64)
+    lib().or_encrypt(prm.logN, prm.L, _p(prm.q), _p(prm.psi_q), prm.sigma, _p(_u64(pk)), _p(pt),
+                     level, seed, _p(ct))
+    return ct
+
+
+def decrypt_residues(prm: Params, sk: np.ndarray, ct: np.ndarray, level: int) -> np.ndarray:
+    m = np.zeros((level, prm.N), dtype=np.uint64)
+    lib().or_decrypt(prm.logN, _p(prm.q), _p(prm.psi_q), _p(np.ascontiguousarray(sk, dtype=np.int64)),
+                     _p(_u64(ct)), level, _p(m))
+    return m
+
+
+def tensor(prm: Params, ct1, ct2, level: int):
+    ct1, ct2 = _u64(ct1), _u64(ct2)
+    d = np.zeros((3, level, prm.N), dtype=np.uint64)
+    lib().or_tensor(prm.logN, level, _p(prm.q), _p(ct1), _p(ct2), _p(d[0]), _p(d[1]), _p(d[2]))
+    return d
+
+
+def modup_digit(prm: Params, x, level: int, j: int) -> np.ndarray:
+    U = np.zeros((prm.K + level, prm.N), dtype=np.uint64)
+    lib().or_modup_digit(prm.logN, level, prm.K, prm.alpha, _p(prm.q), _p(prm.p), j, _p(_u64(x)), _p(U))
+    return U
+
+
+def inner_product(prm: Params, U, evk, level: int) -> np.ndarray:
+    KS = np.zeros((2, prm.K + level, prm.N), dtype=np.uint64)
+    lib().or_inner_product(prm.logN, level, prm.L, prm.K, prm.alpha, _p(prm.q), _p(prm.p),
+                           _p(_u64(U)), _p(_u64(evk)), _p(KS))
+    return KS
+
+
+def moddown(prm: Params, X, level: int) -> np.ndarray:
+    out = np.zeros((level, prm.N), dtype=np.uint64)
+    lib().or_moddown(prm.logN, level, prm.K, _p(prm.q), _p(prm.psi_q), _p(prm.p), _p(prm.psi_p),
+                     _p(_u64(X)), _p(out))
+    return out
+
+
+def keyswitch(prm: Params, d2, evk, level: int, want_intermediates: bool = False):
+    E, beta = prm.K + level, prm.beta(level)
+    ks = np.zeros((2, level, prm.N), dtype=np.uint64)
+    U = np.zeros((beta, E, prm.N), dtype=np.uint64) if want_intermediates else None
+    KS = np.zeros((2, E, prm.N), dtype=np.uint64) if want_intermediates else None
+    lib().or_keyswitch(prm.logN, level, prm.L, prm.K, prm.alpha, _p(prm.q), _p(prm.psi_q), _p(prm.p),
+                       _p(prm.psi_p), _p(_u64(d2)), _p(_u64(evk)), _p(ks),
+                       _p(U) if U is not None else None, _p(KS) if KS is not None else None)
+    if want_intermediates:
+        return ks, U, KS
+    return ks
+
+
+def he_mul(prm: Params, ct1, ct2, evk, level: int) -> np.ndarray:
+    out = np.zeros((2, level, prm.N), dtype=np.uint64)
+    lib().or_he_mul(prm.logN, level, prm.L, prm.K, prm.alpha, _p(prm.q), _p(prm.psi_q), _p(prm.p),
+                    _p(prm.psi_p), _p(_u64(ct1)), _p(_u64(ct2)), _p(_u64(evk)), _p(out))
+    return out
+
+
+def rescale(prm: Params, ct, level: int) -> np.ndarray:
+    out = np.zeros((2, level - 1, prm.N), dtype=np.uint64)
+    lib().or_rescale(prm.logN, level, _p(prm.q), _p(prm.psi_q), _p(_u64(ct)), _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Big-integer helpers for decryption (Python ints are the big integers).
+# --------------------------------------------------------------------------
+def crt_centered(residues: np.ndarray, moduli) -> list[int]:
+    """CRT-reconstruct each column of residues[l][N] and centre it in (-Q/2, Q/2]."""
+    moduli = [int(m) for m in moduli]
+    Q = 1
+    for m in moduli:
+        Q *= m
+    coefs = []
+    for m in moduli:
+        Qh = Q // m
+        coefs.append(Qh * pow(Qh % m, -1, m))
+    l, N = residues.shape
+    cols = [residues[i].tolist() for i in range(l)]
+    out = []
+    for n in range(N):
+        v = 0
+        for i in range(l):
+            v += cols[i][n] * coefs[i]
+        v %= Q
+        if v > Q // 2:
+            v -= Q
+        out.append(v)
+    return out
+
+
+def decrypt(prm: Params, sk, ct, level: int, scale: float) -> np.ndarray:
+    """Decrypt and decode to N/2 complex slots (Sec. 3.1 decryption relation)."""
+    from .encoding import decode
+    m = decrypt_residues(prm, sk, ct, level)
+    coeffs = crt_centered(m, prm.q[:level])
+    return decode(np.array([float(c) for c in coeffs]) / scale, prm.logN)
