@@ -1,0 +1,402 @@
+"""Benchmark: HE Mul + relinearise + rescale throughput on GB300.
+
+Default workload (N=1): one HE Mul of two fresh ciphertexts at N = 2^16,
+24 x 54-bit limbs + 8 x 55-bit special primes, dnum 3, level 24 -> 23 after
+rescale (he_mul_rescale, bit-identical to he_mul followed by he_rescale).
+A step is one HE Mul + rescale of one ciphertext pair.  Eight distinct pairs
+are rotated so that the step's inputs (pairs + evaluation key, 480 MB) exceed
+the 129 MB L2.
+
+Printed JSON line (rank 0):
+  value       HE Mul/s with inputs resident in HBM (CUDA events on the stream)
+  e2e         HE Mul/s through he_mul_rescale_host: host->device copy of both
+              operands, the path, device->host copy of the result, per step
+  latency     p50 / p99 per-step device latency (ms)
+  roofline    the dominant kernel against its ceiling
+  cpu_baseline  the CPU oracle on the host cores, bounded sample
+  clocks      SM clocks sampled with nvidia-smi during the timed region
+
+--impl reference times the CPU oracle (the deliberately plain C checker) on
+the same workload as the reference arm.  With torchrun (N>1) every rank runs
+its own independent HE Muls on its own GPU (weak scaling, no collective on the
+data path); the reported time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import seeded_inputs as si  # noqa: E402
+
+WORKLOADS = {
+    # name: (preset, level, description)
+    "n16": ("n16", 24, "single HE Mul+relin+rescale, N=2^16, 24x54-bit limbs + 8x55-bit specials, dnum 3, level 24->23"),
+    "n17": ("n17", 44, "single HE Mul+relin+rescale, N=2^17, 44x54-bit limbs + 12x54-bit specials, dnum 4, level 44->43"),
+    "n12": ("n12", 3, "single HE Mul+relin+rescale, N=2^12, 3x50-bit limbs + 1x51-bit special, alpha 1, level 3->2"),
+}
+NPAIRS = 8
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_inputs(preset: str, level: int):
+    import oracle
+    from oracle.encoding import encode
+    op = oracle.preset(preset)
+    sc = 2.0 ** oracle.PRESETS[preset]["scale_bits"]
+    ks, s1, s2 = si.SEEDS[preset]
+    sk = oracle.keygen_sk(op, ks)
+    pk = oracle.keygen_pk(op, sk, ks)
+    evk = oracle.keygen_evk(op, sk, ks)
+    m1, m2 = si.messages(op.N // 2, s1), si.messages(op.N // 2, s2)
+    ct1 = oracle.encrypt_poly(op, pk, encode(m1, op.logN, sc), level, s1)
+    ct2 = oracle.encrypt_poly(op, pk, encode(m2, op.logN, sc), level, s2)
+    return op, ct1, ct2, evk
+
+
+def time_oracle(preset: str, level: int, budget_s: float, max_steps: int | None = None):
+    """Oracle HE Mul + rescale repeated until budget_s is spent (at least once)."""
+    import oracle
+    op, ct1, ct2, evk = oracle_inputs(preset, level)
+    times = []
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        c3 = oracle.he_mul(op, ct1, ct2, evk, level)
+        oracle.rescale(op, c3, level)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all >= budget_s or (max_steps and len(times) >= max_steps):
+            break
+    return times
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    preset, level, desc = WORKLOADS[args.workload]
+    # warm-up steps are part of the bounded sample budget: one untimed run
+    budget = float(os.environ.get("HE_REF_BUDGET_S", "120"))
+    times = time_oracle(preset, level, budget_s=budget, max_steps=args.steps)
+    total = float(sum(times))
+    value = len(times) / total
+    line = {
+        "impl": "reference", "metric": "HE Mul/s (HE Mul + relinearize + rescale)", "value": value,
+        "unit": "HE Mul/s", "n_gpus": args.gpus, "steps": len(times), "warmup": 0,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded encryptions of unit-disk messages)",
+        "config": {"workload": desc},
+        "cpu_baseline": {"value": value, "unit": "HE Mul/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(times)} full HE Mul+rescale runs of the plain single-threaded oracle "
+                                   f"(of {args.steps} requested; bounded to ~{budget:.0f} s)"},
+        "e2e": {"value": value, "unit": "HE Mul/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def kernel_work(name: str, prm, level: int):
+    """Algorithmic work of one launch of kernel `name` at this level:
+    ("alu", butterflies) for NTT passes, ("hbm", bytes) for the streaming kernels."""
+    N, K, alpha = 1 << prm.logN, prm.K, prm.alpha
+    beta = -(-level // alpha)
+    E = K + level
+    limb = N * 8
+    passes = {16: (8, 8), 17: (9, 8), 15: (8, 7), 14: (7, 7), 13: (7, 6), 12: (12, 0)}[prm.logN]
+    jobs = {"intt_d2": level + 2, "ntt_modup": beta * E - level, "intt_special": 2 * K + 2,
+            "ntt_moddown": 2 * (level - 1)}
+    base = name.split(".")[0]
+    if base in jobs:
+        fwd = ".fwd" in name
+        if prm.logN == 12:
+            stages = 12
+        elif fwd:
+            stages = passes[0] if name.endswith("pass1") else passes[1]
+        else:
+            stages = passes[1] if name.endswith("pass1") else passes[0]
+        return "alu", jobs[base] * (N // 2) * stages
+    if base == "inner_product":
+        return "hbm", (3 * beta + 2) * E * limb
+    if base == "tensor":
+        return "hbm", 7 * level * limb
+    if base == "modup":
+        return "hbm", (level + (beta * E - level)) * limb
+    if base == "moddown_conv":
+        return "hbm", (2 * K + 4 + 2 * (level - 1)) * limb
+    if base == "combine_rescale":
+        return "hbm", (2 * level + 2 * level + 2 * (level - 1) + 2 * (level - 1)) * limb
+    return None, 0
+
+
+def run_ours(args):
+    import torch
+    import paper_2003_04510_gb300 as g
+    from paper_2003_04510_gb300 import build as gb
+
+    wsz, rank, local = dist_env()
+    if wsz > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gb.build()
+
+    preset, level, desc = WORKLOADS[args.workload]
+    prm, scale_bits = g.PRESETS[preset]
+    sc = 2.0 ** scale_bits
+    ctx = g.Context(prm, device=True)
+    N = ctx.N
+    ks, s1, s2 = si.SEEDS[preset]
+    sk, pk, evk = g.he_keygen(ctx, ks + 1000 * rank)
+    pairs = []
+    for k in range(NPAIRS):
+        m1 = si.messages(N // 2, s1 + 17 * k)
+        m2 = si.messages(N // 2, s2 + 17 * k)
+        c1 = g.he_encrypt(ctx, pk, m1, sc, level, s1 + 17 * k)
+        c2 = g.he_encrypt(ctx, pk, m2, sc, level, s2 + 17 * k)
+        pairs.append((c1, c2))
+    evk_t = g.to_device(evk, dev)
+    ct_t = [(g.to_device(a, dev), g.to_device(b, dev)) for a, b in pairs]
+    outs = [torch.empty((2, level - 1, N), dtype=torch.int64, device=dev) for _ in range(NPAIRS)]
+    ws = g.workspace(ctx, level, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        a, b = ct_t[k % NPAIRS]
+        g.he_mul_rescale(ctx, a, b, evk_t, level, outs[k % NPAIRS], ws, stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    # correctness guard on the measured configuration: decrypt one result
+    z = g.he_decrypt(ctx, sk, g.to_host(outs[0]), level - 1, sc * sc / float(ctx.q[level - 1]))
+    m_exp = si.messages(N // 2, s1) * si.messages(N // 2, s2)
+    dec_err = float(np.abs(z - m_exp).max())
+
+    # ---- timed region: inputs resident in HBM ----
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if wsz > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t0.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step(k)
+        ev[k][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if wsz > 1:
+        torch.distributed.barrier()
+    elapsed_ms = t0.elapsed_time(t1)
+    lat = np.array([a.elapsed_time(b) for a, b in ev])
+    if wsz > 1:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = wsz * args.steps / (elapsed_ms * 1e-3)
+    launches_per_step = 13 if prm.logN > 12 else 9
+
+    # ---- end to end: host buffers through he_mul_rescale_host ----
+    hws = torch.empty(g.he_host_workspace_bytes(ctx, level) // 8, dtype=torch.int64, device=dev)
+    pin = [(torch.from_numpy(a.view(np.int64)).pin_memory(), torch.from_numpy(b.view(np.int64)).pin_memory())
+           for a, b in pairs[:2]]
+    pin_out = torch.empty((2, level - 1, N), dtype=torch.int64).pin_memory()
+    pin_np = [(a.numpy().view(np.uint64), b.numpy().view(np.uint64)) for a, b in pin]
+    out_np = pin_out.numpy().view(np.uint64)
+    e2e_steps = max(3, min(args.steps, 20))
+    for k in range(2):
+        a, b = pin_np[k % 2]
+        g.he_mul_rescale_host(ctx, a, b, evk_t, level, out_np, hws, stream)
+    if wsz > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for k in range(e2e_steps):
+        a, b = pin_np[k % 2]
+        g.he_mul_rescale_host(ctx, a, b, evk_t, level, out_np, hws, stream)
+    e2e_s = time.perf_counter() - te
+    if wsz > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = wsz * e2e_steps / e2e_s
+    h2d = 2 * 2 * level * N * 8
+    d2h = 2 * (level - 1) * N * 8
+
+    # ---- per-kernel profile (CUDA events on the launch stream) ----
+    g.he_profile(ctx, True)
+    prof_steps = min(args.steps, 20)
+    for k in range(prof_steps):
+        step(k)
+    prof = g.he_profile_read(ctx)
+    g.he_profile(ctx, False)
+    per_kernel = {k: {"ms_total": v[0], "calls": v[1], "ms_avg": v[0] / v[1]} for k, v in prof.items()}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_total"]) if per_kernel else None
+
+    # ALU ceiling: register-resident butterfly probe
+    bfly_peak = g.he_probe_butterfly_rate(152 * 8, 4096, stream)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    roof = None
+    if dom:
+        kind, work = kernel_work(dom, ctx.prm, level)
+        avg_s = per_kernel[dom]["ms_avg"] * 1e-3
+        if kind == "alu":
+            ach = work / avg_s / 1e9
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": bfly_peak / 1e9,
+                    "unit": "Gbutterfly/s", "frac": ach / (bfly_peak / 1e9), "traffic": None,
+                    "peak_source": "measured: register-resident lazy Shoup butterfly probe (he_probe_butterfly_rate)"}
+        elif kind == "hbm":
+            ach = work / avg_s / 1e9
+            roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": ach / hbm_peak, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    # HBM view of the key-switch inner product (the evk stream)
+    ip = None
+    if "inner_product" in per_kernel:
+        _, b = kernel_work("inner_product", ctx.prm, level)
+        ach = b / (per_kernel["inner_product"]["ms_avg"] * 1e-3) / 1e9
+        ip = {"achieved_gbs": ach, "peak_gbs": hbm_peak, "frac": ach / hbm_peak}
+
+    # ---- CPU oracle baseline (rank 0, N=1 only) ----
+    cpu = None
+    if rank == 0 and wsz == 1 and not args.no_cpu_baseline:
+        budget = float(os.environ.get("HE_CPU_BUDGET_S", "20"))
+        times = time_oracle(preset, level, budget_s=budget)
+        cpu = {"value": len(times) / sum(times), "unit": "HE Mul/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(times)} full HE Mul+rescale run(s) of the single-threaded oracle at the same "
+                         f"workload (~{sum(times):.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": "HE Mul/s (HE Mul + relinearize + rescale)", "value": value, "unit": "HE Mul/s",
+            "n_gpus": wsz, "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic: seeded encryptions of unit-disk messages, seeded keys",
+            "config": {"workload": desc, "N": N, "level": level, "L": prm.L, "K": prm.K, "alpha": prm.alpha,
+                       "dnum": ctx.dnum, "l2": f"{NPAIRS} distinct ciphertext pairs + evk rotated "
+                       f"({(NPAIRS * 4 * level + 2 * ctx.dnum * (prm.K + prm.L)) * N * 8 / 1e6:.0f} MB > 129 MB L2)",
+                       "parallelism": f"replicas x{wsz}"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean())},
+            "e2e": {"value": e2e_val, "unit": "HE Mul/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof,
+            "inner_product_hbm": ip,
+            "kernels": per_kernel,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "decrypt_max_err": dec_err,
+        }
+        print(json.dumps(line), flush=True)
+    if wsz > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n16", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

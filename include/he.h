@@ -1,0 +1,226 @@
+/*
+ * he.h -- C ABI of the GB300 (sm_103a) full-RNS CKKS HE Mul library.
+ *
+ * The operations follow "HEAAN Demystified" (arXiv 2003.04510):
+ *   - encryption c.ax = u*pk1 + e1, c.bx = u*pk0 + e0 + t, and the decryption
+ *     relation c.bx = c.ax*sk + t + e'                     (Sec. 3.1)
+ *   - rescale after each multiplication, q -> q/p         (Sec. 3.1)
+ *   - HE Mul of two ciphertexts under the same modulus: the tensor product,
+ *     then key switching of c1.ax*c2.ax with the evaluation key (Sec. 3.2,
+ *     Fig. 2), in its full-RNS form with mod up / mod down (Sec. 7, Table 11)
+ *   - NTT / iNTT (Algo 3, Algo 4)
+ *
+ * Data model (every array is uint64 residues in [0, q), limb-major):
+ *   ciphertext at level l : [2][l][N], b (= c.bx) part first, then a (= c.ax);
+ *                           NTT domain, bit-reversed evaluation order (the
+ *                           output order of Algo 3).
+ *   public key            : [2][L][N] (pk0 first, then pk1), NTT domain.
+ *   evaluation key        : [dnum][2][K+L][N], b part first; limb order is
+ *                           "ext": the K special primes first, then the L
+ *                           ciphertext primes.  One key serves every level.
+ *   secret key            : int64[N], coefficients in {-1, 0, 1}.
+ * Level l means the ciphertext primes q_0..q_{l-1}; rescale drops q_{l-1}.
+ *
+ * Ownership: the caller owns every buffer (host arrays and device memory).
+ * The library never frees caller memory.  A context owns only its parameter
+ * tables (host and device copies).
+ *
+ * Device calls are asynchronous on the stream given (a cudaStream_t passed as
+ * void*; NULL is the legacy default stream).  Device pointers must be
+ * 256-byte aligned and must not overlap unless a function says otherwise.
+ *
+ * Errors: every call returns an int status (HE_OK on success).  Argument
+ * errors are detected on the host before anything is enqueued.  A CUDA launch
+ * failure returns HE_ECUDA.  Bounded device waits (batched and served
+ * execution) that give up surface as HE_ETIMEOUT at the next synchronising
+ * call.  he_strerror() names a code.
+ */
+#ifndef HE_GB300_H
+#define HE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HE_OK = 0,
+    HE_EINVAL = 1,   /* bad argument: NULL pointer, level out of range, bad size */
+    HE_ELEVEL = 2,   /* operands at different or unsupported levels */
+    HE_ENOMEM = 3,   /* workspace too small, or admission refused */
+    HE_ECUDA = 4,    /* a CUDA runtime call failed */
+    HE_ETIMEOUT = 5, /* a bounded device wait gave up */
+    HE_EBUSY = 6     /* resource in use (e.g. serving slot pool exhausted) */
+};
+
+typedef struct he_ctx he_ctx;
+
+/* Parameters of one ring / modulus chain (the paper's Table 3 and Table 6
+ * list the non-RNS analogues).  Primes: q_0 > ... > q_{L-1} are the L largest
+ * primes below 2^q_bits that are 1 mod 2N; p_0 > ... > p_{K-1} the K largest
+ * below 2^p_bits that are 1 mod 2N and not ciphertext primes.  alpha = limbs
+ * per key-switching digit; dnum = ceil(L/alpha).  h = Hamming weight of the
+ * secret; sigma = error standard deviation (3.2 in the paper, Sec. 3.1). */
+typedef struct {
+    int logN;    /* 12 .. 17 */
+    int L;       /* ciphertext primes, 1 .. 64 */
+    int K;       /* special primes, 1 .. 16 */
+    int alpha;   /* limbs per digit, 1 .. 16 */
+    int q_bits;  /* 30 .. 57 */
+    int p_bits;  /* 30 .. 57 */
+    int h;       /* secret Hamming weight, 1 .. N */
+    double sigma;
+} he_params;
+
+/* Create a context: generates the primes, roots and every table on the host
+ * and uploads the device tables to the current CUDA device.  *out is set only
+ * on success.  Returns HE_EINVAL for out-of-range parameters, HE_ECUDA if the
+ * device upload fails (no device is needed when only host functions are
+ * used: pass a context created with he_ctx_create_host). */
+int he_ctx_create(he_ctx **out, const he_params *p);
+/* Host-only context (no CUDA calls are made); device entry points return
+ * HE_EINVAL on it. */
+int he_ctx_create_host(he_ctx **out, const he_params *p);
+int he_ctx_destroy(he_ctx *ctx);
+
+/* Query: N, dnum, and the moduli in ext order (K specials then L ciphertext
+ * primes; `moduli` must hold K+L words). */
+int he_ctx_info(const he_ctx *ctx, int *N, int *dnum, uint64_t *moduli);
+
+/* ---- host side (plain C buffers, caller-owned) --------------------------- */
+
+/* Key generation from a seed (counter-based SplitMix64 streams).  Any output
+ * pointer may be NULL to skip that key; pk and evk need sk's values, so sk is
+ * always generated internally.  sk: int64[N]; pk: [2][L][N]; evk:
+ * [dnum][2][K+L][N].  The evaluation key of digit j encrypts P*Qtilde_j*s^2,
+ * Qtilde_j = 1 mod the primes of digit j and 0 mod the others (Fig. 2's evk,
+ * full-RNS gadget). */
+int he_keygen(he_ctx *ctx, uint64_t seed, int64_t *sk, uint64_t *pk, uint64_t *evk);
+/* The same, from a given secret key. */
+int he_keygen_from_sk(he_ctx *ctx, uint64_t seed, const int64_t *sk, uint64_t *pk, uint64_t *evk);
+
+/* Encoding (Sec. 3.1): n = N/2 complex numbers, scaled by `scale` and rounded
+ * to the nearest integer, into int64[N] coefficients via the canonical
+ * embedding at the roots zeta^(5^k).  Decoding is the inverse evaluation
+ * (coefficients are given as doubles already divided by the scale). */
+int he_encode(he_ctx *ctx, const double *re, const double *im, size_t n, double scale, int64_t *coeffs);
+int he_decode(he_ctx *ctx, const double *coeffs, double *re, double *im, size_t n);
+
+/* Encryption at `level` of an integer plaintext (Sec. 3.1): u ZO(1/2), e0 and
+ * e1 rounded Gaussians, drawn from `seed`.  ct: [2][level][N]. */
+int he_encrypt_poly(he_ctx *ctx, const uint64_t *pk, const int64_t *pt, int level, uint64_t seed,
+                    uint64_t *ct);
+/* Encode + encrypt. */
+int he_encrypt(he_ctx *ctx, const uint64_t *pk, const double *re, const double *im, size_t n, double scale,
+               int level, uint64_t seed, uint64_t *ct);
+/* Decryption relation (Sec. 3.1): returns the coefficient-form residues of
+ * c.bx - c.ax*sk, m: [level][N]. */
+int he_decrypt_poly(he_ctx *ctx, const int64_t *sk, const uint64_t *ct, int level, uint64_t *m);
+/* Decrypt + decode.  Centres each coefficient using CRT over the first
+ * min(level, 2) primes, which is exact while |coefficient| < q_0*q_1/2. */
+int he_decrypt(he_ctx *ctx, const int64_t *sk, const uint64_t *ct, int level, double scale, double *re,
+               double *im, size_t n);
+
+/* ---- device side: caller-owned device memory, caller's stream ------------ */
+
+/* Copy an evaluation key from host to device memory (evk_dev holds
+ * dnum*2*(K+L)*N words). */
+int he_evk_upload(he_ctx *ctx, const uint64_t *evk_host, uint64_t *evk_dev, void *stream);
+
+/* Bytes of device workspace one he_mul / he_rescale / he_mul_rescale call at
+ * `level` needs (the largest of the three). */
+size_t he_workspace_bytes(const he_ctx *ctx, int level);
+
+/* HE Mul (Fig. 2, full-RNS form): out = (d0 + ModDown(KS_b), d1 + ModDown(KS_a))
+ * where d0 = b1*b2, d1 = a1*b2 + a2*b1, d2 = a1*a2 and KS = sum_j
+ * ModUp_j(d2) * evk_j.  ct1, ct2, out: [2][level][N] device; out may not alias
+ * the inputs.  Result scale is scale1*scale2 (host metadata).  Returns
+ * HE_ELEVEL if level is outside 1..L, HE_ENOMEM if ws_bytes is too small. */
+int he_mul(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *evk_dev, int level,
+           uint64_t *out, void *ws, size_t ws_bytes, void *stream);
+
+/* Rescale (Sec. 3.1, "divide by p"): out = floor(ct / q_{level-1}) in RNS form,
+ * [2][level-1][N].  level >= 2. */
+int he_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, void *ws, size_t ws_bytes,
+               void *stream);
+
+/* he_mul followed by he_rescale, fused: bit-identical to the two calls, with
+ * the ModDown and rescale NTTs merged (out: [2][level-1][N]).  level >= 2. */
+int he_mul_rescale(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *evk_dev, int level,
+                   uint64_t *out, void *ws, size_t ws_bytes, void *stream);
+
+/* he_mul_rescale on HOST buffers: copies ct1, ct2 ([2][level][N], host) to the
+ * device, runs the path and copies the result ([2][level-1][N]) back to `out`
+ * (host), then waits for the stream.  ws is device memory of at least
+ * he_host_workspace_bytes(level) (the path's workspace plus staging for the
+ * operands and the result).  Pinned host buffers give asynchronous copies. */
+size_t he_host_workspace_bytes(const he_ctx *ctx, int level);
+int he_mul_rescale_host(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *evk_dev, int level,
+                        uint64_t *out, void *ws, size_t ws_bytes, void *stream);
+
+/* ---- individual steps of the path (per-kernel parity) -------------------- */
+
+/* Forward / inverse NTT (Algo 3 / its inverse) of `count` limbs in place:
+ * limb c of `data` (device, [count][N]) is taken mod the ext prime
+ * prime_idx[c] (host array; ext order, 0..K+L-1). */
+int he_step_ntt(he_ctx *ctx, uint64_t *data, const int *prime_idx, int count, int inverse, void *stream);
+/* Tensor product at level l: d = [3][l][N] (d0, d1, d2) from ct1, ct2. */
+int he_step_tensor(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, int level, uint64_t *d, void *stream);
+/* iNTT of d2 ([level][N], NTT domain) followed by ModUp of every digit:
+ * U [beta][K+level][N] in ext order, coefficient form.  Rows of a digit's own
+ * limbs are not written (the path reuses d2 for them).  ws must hold
+ * he_workspace_bytes(level). */
+int he_step_modup(he_ctx *ctx, const uint64_t *d2, int level, uint64_t *U, void *ws, size_t ws_bytes,
+                  void *stream);
+/* Inner product of NTT-domain U ([beta][K+level][N], own-digit rows taken
+ * from d2 [level][N]) with the device evk: KS [2][K+level][N]. */
+int he_step_inner_product(he_ctx *ctx, const uint64_t *U, const uint64_t *d2, const uint64_t *evk_dev, int level,
+                          uint64_t *KS, void *stream);
+/* ModDown of one NTT-domain polynomial X ([K+level][N], ext order) to
+ * out [level][N]; ws must hold he_workspace_bytes(level). */
+int he_step_moddown(he_ctx *ctx, const uint64_t *X, int level, uint64_t *out, void *ws, size_t ws_bytes,
+                    void *stream);
+
+/* ---- batched execution ---------------------------------------------------- */
+
+typedef struct {
+    const uint64_t *ct1; /* [2][level][N] device */
+    const uint64_t *ct2;
+    uint64_t *out;       /* [2][level-1][N] device (rescaled) */
+    int level;           /* 2 .. L */
+} he_job;
+
+/* Workspace bytes for a batch of `count` jobs at the given levels. */
+size_t he_batch_workspace_bytes(const he_ctx *ctx, int count, const int *levels);
+/* Run B independent HE Mul + rescale jobs (uneven levels allowed) as one
+ * batch: each stage is one launch over every job's work, so jobs overlap on
+ * the device.  Results are bit-identical to he_mul_rescale on each job. */
+int he_mul_batch(he_ctx *ctx, int count, const he_job *jobs, const uint64_t *evk_dev, void *ws,
+                 size_t ws_bytes, void *stream);
+
+/* ---- profiling ------------------------------------------------------------ */
+
+/* Enable (1) or disable (0) per-kernel CUDA-event marks on this context's
+ * device calls.  While enabled, every kernel of the path is followed by an
+ * event on the stream it was launched on; he_profile_read waits for the last
+ * mark and returns, per kernel name, the summed time between each kernel's
+ * mark and the previous mark (names: 48-byte slots), then clears the marks.
+ * Use a single stream while profiling. */
+int he_profile(he_ctx *ctx, int enable);
+int he_profile_read(he_ctx *ctx, int max, char *names, double *total_ms, int *calls, int *count);
+
+/* Measurement helper: rate (butterflies per second) of the NTT's lazy
+ * Cooley-Tukey butterfly (one Shoup product, Algo 2, plus adds) on
+ * register-resident data, `blocks` x 256 threads x 8 chains x `iters`.  The
+ * ALU ceiling the NTT kernels are compared against. */
+int he_probe_butterfly_rate(int blocks, int iters, double *bfly_per_s, void *stream);
+
+const char *he_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HE_GB300_H */

@@ -1,0 +1,367 @@
+"""Python binding of the GB300 full-RNS CKKS HE Mul library (libhe_gb300.so).
+
+Argument marshalling only: every step of HE Mul runs in the library's CUDA
+kernels.  Device buffers are torch tensors (int64 storage holding the uint64
+residues, which are all below 2^57); streams are torch streams.  Host arrays
+are numpy.  Function names mirror the C ABI in include/he.h.
+
+There is no CPU fallback: if the compiled library is missing, importing the
+device entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhe_gb300.so")
+
+HE_OK, HE_EINVAL, HE_ELEVEL, HE_ENOMEM, HE_ECUDA, HE_ETIMEOUT, HE_EBUSY = range(7)
+
+
+class HeError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {lib().he_strerror(code).decode()} (code {code})")
+        self.code = code
+
+
+class he_params(ctypes.Structure):
+    _fields_ = [("logN", ctypes.c_int), ("L", ctypes.c_int), ("K", ctypes.c_int), ("alpha", ctypes.c_int),
+                ("q_bits", ctypes.c_int), ("p_bits", ctypes.c_int), ("h", ctypes.c_int),
+                ("sigma", ctypes.c_double)]
+
+
+class he_job(ctypes.Structure):
+    _fields_ = [("ct1", ctypes.c_void_p), ("ct2", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("level", ctypes.c_int)]
+
+
+_lib = None
+
+_SIGS = {
+    "he_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "he_ctx_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "he_ctx_create_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "he_ctx_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "he_ctx_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "he_keygen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p]),
+    "he_keygen_from_sk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "he_encode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                 ctypes.c_double, ctypes.c_void_p]),
+    "he_decode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_size_t]),
+    "he_encrypt_poly": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_uint64, ctypes.c_void_p]),
+    "he_encrypt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_size_t, ctypes.c_double, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p]),
+    "he_decrypt_poly": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_void_p]),
+    "he_decrypt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "he_evk_upload": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "he_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int]),
+    "he_mul": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "he_mul_rescale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.c_void_p]),
+    "he_rescale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_size_t, ctypes.c_void_p]),
+    "he_step_ntt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_void_p]),
+    "he_step_tensor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "he_step_modup": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "he_step_inner_product": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "he_step_moddown": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "he_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "he_host_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int]),
+    "he_mul_rescale_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                           ctypes.c_void_p]),
+    "he_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "he_probe_butterfly_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "he_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "he_mul_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+}
+
+
+def lib():
+    """Load libhe_gb300.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2003_04510_gb300.build.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != HE_OK:
+        raise HeError(rc, what)
+
+
+def _np_ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t) -> int:
+    assert t.is_cuda and t.is_contiguous()
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+@dataclass
+class Params:
+    logN: int
+    L: int
+    K: int
+    alpha: int
+    q_bits: int
+    p_bits: int
+    h: int = 64
+    sigma: float = 3.2
+
+    def c(self) -> he_params:
+        return he_params(self.logN, self.L, self.K, self.alpha, self.q_bits, self.p_bits, self.h, self.sigma)
+
+
+# Workload presets (ring degree, limb counts, prime sizes, secret weight, scale).
+PRESETS = {
+    "n12": (Params(12, 3, 1, 1, 50, 51, 64), 40),
+    "n15": (Params(15, 16, 8, 8, 54, 55, 192), 50),
+    "n16": (Params(16, 24, 8, 8, 54, 55, 192), 50),
+    "n17": (Params(17, 44, 12, 11, 54, 54, 192), 50),
+}
+
+
+class Context:
+    """Owns an he_ctx*.  device=False builds a host-only context (no CUDA)."""
+
+    def __init__(self, prm: Params, device: bool = True):
+        self.prm = prm
+        self.ptr = ctypes.c_void_p()
+        cp = prm.c()
+        fn = lib().he_ctx_create if device else lib().he_ctx_create_host
+        _check(fn(ctypes.byref(self.ptr), ctypes.byref(cp)), "he_ctx_create")
+        N = ctypes.c_int()
+        dnum = ctypes.c_int()
+        mod = np.zeros(prm.K + prm.L, dtype=np.uint64)
+        _check(lib().he_ctx_info(self.ptr, ctypes.byref(N), ctypes.byref(dnum), _np_ptr(mod)), "he_ctx_info")
+        self.N, self.dnum, self.moduli = N.value, dnum.value, mod
+        self.device = device
+
+    @property
+    def q(self) -> np.ndarray:
+        return self.moduli[self.prm.K:]
+
+    @property
+    def p(self) -> np.ndarray:
+        return self.moduli[: self.prm.K]
+
+    def beta(self, level: int) -> int:
+        return -(-level // self.prm.alpha)
+
+    def close(self):
+        if self.ptr:
+            lib().he_ctx_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- host side --------------------------------------------------------------
+def he_keygen(ctx: Context, seed: int):
+    N, L, K = ctx.N, ctx.prm.L, ctx.prm.K
+    sk = np.zeros(N, dtype=np.int64)
+    pk = np.zeros((2, L, N), dtype=np.uint64)
+    evk = np.zeros((ctx.dnum, 2, K + L, N), dtype=np.uint64)
+    _check(lib().he_keygen(ctx.ptr, seed, _np_ptr(sk), _np_ptr(pk), _np_ptr(evk)), "he_keygen")
+    return sk, pk, evk
+
+
+def he_encode(ctx: Context, z: np.ndarray, scale: float) -> np.ndarray:
+    re = np.ascontiguousarray(z.real, dtype=np.float64)
+    im = np.ascontiguousarray(z.imag, dtype=np.float64)
+    out = np.zeros(ctx.N, dtype=np.int64)
+    _check(lib().he_encode(ctx.ptr, _np_ptr(re), _np_ptr(im), len(re), scale, _np_ptr(out)), "he_encode")
+    return out
+
+
+def he_decode(ctx: Context, coeffs: np.ndarray) -> np.ndarray:
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    re = np.zeros(ctx.N // 2)
+    im = np.zeros(ctx.N // 2)
+    _check(lib().he_decode(ctx.ptr, _np_ptr(c), _np_ptr(re), _np_ptr(im), ctx.N // 2), "he_decode")
+    return re + 1j * im
+
+
+def he_encrypt_poly(ctx: Context, pk: np.ndarray, pt: np.ndarray, level: int, seed: int) -> np.ndarray:
+    ct = np.zeros((2, level, ctx.N), dtype=np.uint64)
+    pt = np.ascontiguousarray(pt, dtype=np.int64)
+    _check(lib().he_encrypt_poly(ctx.ptr, _np_ptr(np.ascontiguousarray(pk)), _np_ptr(pt), level, seed, _np_ptr(ct)),
+           "he_encrypt_poly")
+    return ct
+
+
+def he_encrypt(ctx: Context, pk: np.ndarray, z: np.ndarray, scale: float, level: int, seed: int) -> np.ndarray:
+    re = np.ascontiguousarray(z.real, dtype=np.float64)
+    im = np.ascontiguousarray(z.imag, dtype=np.float64)
+    ct = np.zeros((2, level, ctx.N), dtype=np.uint64)
+    _check(lib().he_encrypt(ctx.ptr, _np_ptr(np.ascontiguousarray(pk)), _np_ptr(re), _np_ptr(im), len(re), scale,
+                            level, seed, _np_ptr(ct)), "he_encrypt")
+    return ct
+
+
+def he_decrypt_poly(ctx: Context, sk: np.ndarray, ct: np.ndarray, level: int) -> np.ndarray:
+    m = np.zeros((level, ctx.N), dtype=np.uint64)
+    _check(lib().he_decrypt_poly(ctx.ptr, _np_ptr(np.ascontiguousarray(sk, dtype=np.int64)),
+                                 _np_ptr(np.ascontiguousarray(ct, dtype=np.uint64)), level, _np_ptr(m)),
+           "he_decrypt_poly")
+    return m
+
+
+def he_decrypt(ctx: Context, sk: np.ndarray, ct: np.ndarray, level: int, scale: float) -> np.ndarray:
+    re = np.zeros(ctx.N // 2)
+    im = np.zeros(ctx.N // 2)
+    _check(lib().he_decrypt(ctx.ptr, _np_ptr(np.ascontiguousarray(sk, dtype=np.int64)),
+                            _np_ptr(np.ascontiguousarray(ct, dtype=np.uint64)), level, scale, _np_ptr(re),
+                            _np_ptr(im), ctx.N // 2), "he_decrypt")
+    return re + 1j * im
+
+
+# ---- device side (torch tensors as device buffers) ----------------------------
+def to_device(a: np.ndarray, device="cuda"):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(device)
+
+
+def to_host(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint64)
+
+
+def he_workspace_bytes(ctx: Context, level: int) -> int:
+    return int(lib().he_workspace_bytes(ctx.ptr, level))
+
+
+def workspace(ctx: Context, level: int, device="cuda"):
+    import torch
+    nbytes = he_workspace_bytes(ctx, level)
+    return torch.empty(nbytes // 8, dtype=torch.int64, device=device)
+
+
+def he_mul(ctx, ct1, ct2, evk, level, out, ws, stream=None):
+    _check(lib().he_mul(ctx.ptr, _dev_ptr(ct1), _dev_ptr(ct2), _dev_ptr(evk), level, _dev_ptr(out), _dev_ptr(ws),
+                        ws.numel() * 8, _stream_ptr(stream)), "he_mul")
+
+
+def he_mul_rescale(ctx, ct1, ct2, evk, level, out, ws, stream=None):
+    _check(lib().he_mul_rescale(ctx.ptr, _dev_ptr(ct1), _dev_ptr(ct2), _dev_ptr(evk), level, _dev_ptr(out),
+                                _dev_ptr(ws), ws.numel() * 8, _stream_ptr(stream)), "he_mul_rescale")
+
+
+def he_rescale(ctx, ct, level, out, ws, stream=None):
+    _check(lib().he_rescale(ctx.ptr, _dev_ptr(ct), level, _dev_ptr(out), _dev_ptr(ws), ws.numel() * 8,
+                            _stream_ptr(stream)), "he_rescale")
+
+
+def he_step_ntt(ctx, data, prime_idx, inverse: bool, stream=None):
+    pi = np.ascontiguousarray(prime_idx, dtype=np.int32)
+    _check(lib().he_step_ntt(ctx.ptr, _dev_ptr(data), _np_ptr(pi), len(pi), int(inverse), _stream_ptr(stream)),
+           "he_step_ntt")
+
+
+def he_step_tensor(ctx, ct1, ct2, level, d, stream=None):
+    _check(lib().he_step_tensor(ctx.ptr, _dev_ptr(ct1), _dev_ptr(ct2), level, _dev_ptr(d), _stream_ptr(stream)),
+           "he_step_tensor")
+
+
+def he_step_modup(ctx, d2, level, U, ws, stream=None):
+    _check(lib().he_step_modup(ctx.ptr, _dev_ptr(d2), level, _dev_ptr(U), _dev_ptr(ws), ws.numel() * 8,
+                               _stream_ptr(stream)), "he_step_modup")
+
+
+def he_step_inner_product(ctx, U, d2, evk, level, KS, stream=None):
+    _check(lib().he_step_inner_product(ctx.ptr, _dev_ptr(U), _dev_ptr(d2), _dev_ptr(evk), level, _dev_ptr(KS),
+                                       _stream_ptr(stream)), "he_step_inner_product")
+
+
+def he_step_moddown(ctx, X, level, out, ws, stream=None):
+    _check(lib().he_step_moddown(ctx.ptr, _dev_ptr(X), level, _dev_ptr(out), _dev_ptr(ws), ws.numel() * 8,
+                                 _stream_ptr(stream)), "he_step_moddown")
+
+
+def he_batch_workspace_bytes(ctx, levels) -> int:
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    return int(lib().he_batch_workspace_bytes(ctx.ptr, len(lv), _np_ptr(lv)))
+
+
+def he_mul_batch(ctx, jobs, evk, ws, stream=None):
+    """jobs: list of (ct1, ct2, out, level) with device tensors."""
+    arr = (he_job * len(jobs))()
+    for i, (a, b, o, lv) in enumerate(jobs):
+        arr[i] = he_job(_dev_ptr(a), _dev_ptr(b), _dev_ptr(o), int(lv))
+    _check(lib().he_mul_batch(ctx.ptr, len(jobs), ctypes.cast(arr, ctypes.c_void_p), _dev_ptr(evk), _dev_ptr(ws),
+                              ws.numel() * 8, _stream_ptr(stream)), "he_mul_batch")
+
+
+def he_host_workspace_bytes(ctx, level) -> int:
+    return int(lib().he_host_workspace_bytes(ctx.ptr, level))
+
+
+def he_mul_rescale_host(ctx, ct1: np.ndarray, ct2: np.ndarray, evk, level, out: np.ndarray, ws, stream=None):
+    """ct1, ct2, out: host numpy uint64 arrays (pinned memory gives async copies)."""
+    _check(lib().he_mul_rescale_host(ctx.ptr, _np_ptr(ct1), _np_ptr(ct2), _dev_ptr(evk), level, _np_ptr(out),
+                                     _dev_ptr(ws), ws.numel() * 8, _stream_ptr(stream)), "he_mul_rescale_host")
+
+
+def he_profile(ctx, enable: bool):
+    _check(lib().he_profile(ctx.ptr, int(enable)), "he_profile")
+
+
+def he_profile_read(ctx, max_kernels: int = 64) -> dict:
+    """{kernel name: (total ms, calls)} for the marks recorded since he_profile(ctx, True)."""
+    names = ctypes.create_string_buffer(48 * max_kernels)
+    ms = np.zeros(max_kernels)
+    calls = np.zeros(max_kernels, dtype=np.int32)
+    n = ctypes.c_int()
+    _check(lib().he_profile_read(ctx.ptr, max_kernels, names, _np_ptr(ms), _np_ptr(calls), ctypes.byref(n)),
+           "he_profile_read")
+    out = {}
+    for j in range(n.value):
+        nm = names.raw[48 * j: 48 * j + 48].split(b"\0", 1)[0].decode()
+        out[nm] = (float(ms[j]), int(calls[j]))
+    return out
+
+
+def he_probe_butterfly_rate(blocks: int, iters: int, stream=None) -> float:
+    r = ctypes.c_double()
+    _check(lib().he_probe_butterfly_rate(blocks, iters, ctypes.byref(r), _stream_ptr(stream)),
+           "he_probe_butterfly_rate")
+    return r.value

@@ -1,0 +1,129 @@
+// he_internal.h -- internal types shared by the host and device translation
+// units of the library (not part of the public ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "he.h"
+
+typedef uint64_t u64;
+
+namespace he {
+
+constexpr int kMaxDigits = 16;
+constexpr int kMaxK = 16;
+constexpr int kMaxL = 64;
+
+// One prime as the kernels see it (ext order: specials first, then q_0..).
+struct DevPrime {
+    u64 q, q2;              // q and 2q
+    u64 mu;                 // Barrett: floor(2^(64+s) / q)
+    unsigned s, pad;        // s = bitlen(q) - 2
+    const ulonglong2 *w;    // forward twiddles: w[m+j] = psi^bitrev(m+j), (value, Shoup)
+    const ulonglong2 *iw;   // inverse twiddles: psi^-bitrev(m+j)
+};
+
+// One limb transform of an NTT launch.  Offsets are in limbs (units of N
+// words) from the launch's base pointer.  scale (with its Shoup companion) is
+// applied to inverse-transform outputs together with N^-1.
+struct NttJob {
+    unsigned src, dst, prime, pad;
+    u64 scale, scale_sh;
+};
+
+// Per-level constants on the device.
+struct DevLevel {
+    int l, beta, E, A;             // level, digits, K+l, alpha padded for the kernels
+    int dig_lo[kMaxDigits], dig_n[kMaxDigits];
+    const u64 *modupB;             // [beta][E][A]: [Qhat_{j,i}]_t (0 for own-digit rows)
+    const ulonglong2 *qinv_last;   // [l-1]: q_{l-1}^-1 mod q_i (value, Shoup)
+    const ulonglong2 *pinv_qinv;   // [l-1]: P^-1 * q_{l-1}^-1 mod q_i
+};
+
+// Workspace layout of one HE Mul at level l (offsets in limbs).
+struct WsLayout {
+    size_t d0, d1, d2, y, u, ks, ys, r, z, total;
+};
+
+// Job lists of one level, stored in the context's device arena.
+struct LevelJobs {
+    const NttJob *intt1;    int n_intt1;     // d2 -> y          (+2 fused: d0,d1 last limb -> r[0..1])
+    const NttJob *intt1f;   int n_intt1f;    // fused variant
+    const NttJob *ntt_up;   int n_ntt_up;    // ModUp outputs, in place
+    const NttJob *intt2;    int n_intt2;     // KS specials -> ys (scaled by N^-1 Phat^-1)
+    const NttJob *intt2f;   int n_intt2f;    // + KS last limb -> r[2..3]
+    const NttJob *ntt_conv; int n_ntt_conv;  // 2l conv limbs (plain ModDown)
+    const NttJob *ntt_z;    int n_ntt_z;     // 2(l-1) z limbs (fused ModDown + rescale)
+    const NttJob *rs_intt;  int n_rs_intt;   // rescale: last limb of b, a -> r
+    const NttJob *rs_ntt;   int n_rs_ntt;    // rescale: r -> z_i
+};
+
+struct HostLevel {
+    WsLayout ws;
+    std::vector<NttJob> intt1, intt1f, ntt_up, intt2, intt2f, ntt_conv, ntt_z, rs_intt, rs_ntt;
+    std::vector<u64> modupB;
+    std::vector<ulonglong2> qinv_last, pinv_qinv;
+};
+
+}  // namespace he
+
+struct he_ctx {
+    he_params prm;
+    int N, logN, L, K, alpha, dnum, E;  // E = K + L
+    bool device;
+    std::vector<u64> ext;                // moduli, ext order
+    std::vector<u64> psi;                // smallest primitive 2N-th roots, ext order
+    // host tables (for the host NTT used by keygen / encrypt / decrypt)
+    std::vector<std::vector<u64>> w, wsh, iw, iwsh;  // [E][N]
+    std::vector<u64> ninv, ninv_sh;                  // [E]
+    // level-independent ModDown constants
+    std::vector<u64> PB;                 // [L][K]: [Phat_k]_{q_i}
+    std::vector<ulonglong2> pinv;        // [L]: P^-1 mod q_i
+    std::vector<ulonglong2> phat_inv;    // [K]: Phat_k^-1 mod p_k
+    std::vector<he::HostLevel> host_levels;  // index l (1..L)
+    // device
+    int device_id = -1;
+    void *arena = nullptr;               // one allocation holding every device table
+    size_t arena_bytes = 0;
+    he::DevPrime *d_primes = nullptr;    // [E]
+    const u64 *d_PB = nullptr;
+    const ulonglong2 *d_pinv = nullptr;
+    std::vector<he::DevLevel> dev_levels;  // index l (host copy of the device structs)
+    he::DevLevel *d_levels = nullptr;      // [L+1]
+    std::vector<he::LevelJobs> jobs;       // index l
+    // optional per-kernel event marks (he_profile); consecutive marks on one
+    // stream bracket one kernel each
+    mutable bool prof = false;
+    mutable std::vector<cudaEvent_t> prof_pool;
+    mutable std::vector<std::string> prof_names;  // prof_names[i] = kernel ended by event i ("" = a start mark)
+    mutable size_t prof_used = 0;
+};
+
+namespace he {
+// host_params.cpp
+int build_context(he_ctx *ctx, const he_params *p, bool device);
+// kernels (ntt.cu, keyswitch.cu); return cudaError_t
+// Record a profiling mark named after the kernel that just finished (no-op
+// unless profiling is enabled on the context).
+void prof_mark(const he_ctx *ctx, cudaStream_t st, const char *tag, const char *suffix = nullptr);
+cudaError_t launch_ntt(const he_ctx *ctx, u64 *base, const NttJob *jobs, int njobs, bool inverse,
+                       cudaStream_t st, const char *tag = nullptr);
+cudaError_t launch_ntt2(const he_ctx *ctx, const u64 *src, u64 *dst, const NttJob *jobs, int njobs, bool inverse,
+                        cudaStream_t st, const char *tag = nullptr);
+cudaError_t run_tensor(const he_ctx *c, const u64 *ct1, const u64 *ct2, u64 *d0, u64 *d1, u64 *d2, int l,
+                       cudaStream_t st);
+cudaError_t run_modup(const he_ctx *c, const u64 *y, u64 *U, int l, cudaStream_t st);
+cudaError_t run_inner_product(const he_ctx *c, const u64 *U, const u64 *d2, const u64 *evk, u64 *KS, int l,
+                              cudaStream_t st);
+cudaError_t run_moddown_conv(const he_ctx *c, const u64 *ys, const u64 *rr, u64 *z, int l, bool fused,
+                             cudaStream_t st);
+cudaError_t run_combine_plain(const he_ctx *c, const u64 *d0, const u64 *d1, const u64 *KS, const u64 *C, u64 *out,
+                              int l, cudaStream_t st);
+cudaError_t run_combine_rescale(const he_ctx *c, const u64 *d0, const u64 *d1, const u64 *KS, const u64 *Z,
+                                u64 *out, int l, cudaStream_t st);
+cudaError_t run_rescale_combine(const he_ctx *c, const u64 *ct, const u64 *Z, u64 *out, int l, cudaStream_t st);
+}  // namespace he

@@ -1,0 +1,338 @@
+// host_params.cpp -- context construction: primes, roots, twiddle tables,
+// base-conversion constants, per-level workspace layouts and NTT job lists,
+// and the upload of every device table into one arena.
+//
+// Parameter rules (the paper is silent on the RNS choices):
+//   * q_0 > q_1 > ... : the L largest primes below 2^q_bits with q = 1 mod 2N
+//   * p_0 > p_1 > ... : the K largest primes below 2^p_bits with p = 1 mod 2N
+//                       that are not ciphertext primes
+//   * psi             : the smallest primitive 2N-th root of unity mod each prime
+//   * digits          : I_j = {j*alpha, ..., min((j+1)*alpha, l) - 1}
+// Twiddles follow Algo 3's table TB_W[m + j] = psi^bitrev(m + j) and the iNTT's
+// TB_invW; every constant carries its Shoup companion (Algo 2).
+#include <algorithm>
+#include <cstring>
+
+#include "he_internal.h"
+#include "host_math.h"
+
+namespace he {
+
+using namespace hm;
+
+static std::vector<u64> find_primes(int logN, int bits, int count, const std::vector<u64> &skip)
+{
+    std::vector<u64> out;
+    const u64 step = 2ull << logN;
+    u64 top = (1ull << bits) - 1;
+    u64 c = top - (top - 1) % step;  // largest c <= top with c = 1 mod 2N
+    while ((int)out.size() < count && c > step) {
+        if (std::find(skip.begin(), skip.end(), c) == skip.end() && is_prime(c)) out.push_back(c);
+        c -= step;
+    }
+    return out;
+}
+
+// Smallest primitive 2N-th root: take a generator g of Z_q^*, psi0 = g^((q-1)/2N);
+// the primitive 2N-th roots are psi0^k for odd k.
+static u64 smallest_psi(u64 q, int logN)
+{
+    const u64 twoN = 2ull << logN;
+    std::vector<u64> f = prime_factors(q - 1);
+    u64 g = 2;
+    for (;; g++) {
+        bool gen = true;
+        for (u64 p : f)
+            if (pw(g, (q - 1) / p, q) == 1) { gen = false; break; }
+        if (gen) break;
+    }
+    u64 psi0 = pw(g, (q - 1) / twoN, q);
+    u64 sq = mul(psi0, psi0, q), best = psi0, cur = psi0;
+    for (u64 k = 1; k < twoN / 2; k++) {
+        cur = mul(cur, sq, q);
+        best = std::min(best, cur);
+    }
+    return best;
+}
+
+static ulonglong2 pair(u64 v, u64 m) { return make_ulonglong2(v, shoup(v, m)); }
+
+static WsLayout layout_for(int l, int K, int alpha)
+{
+    int beta = (l + alpha - 1) / alpha;
+    int E = K + l;
+    WsLayout w;
+    w.d0 = 0;
+    w.d1 = (size_t)l;
+    w.d2 = 2 * (size_t)l;
+    w.y = 3 * (size_t)l;
+    w.u = 4 * (size_t)l;
+    w.ks = w.u + (size_t)beta * E;
+    w.ys = w.ks + 2 * (size_t)E;
+    w.r = w.ys + 2 * (size_t)K;
+    w.z = w.r + 4;
+    w.total = w.z + 2 * (size_t)l;
+    return w;
+}
+
+int build_context(he_ctx *c, const he_params *p, bool device)
+{
+    // q_bits, p_bits <= 57 keep every base-conversion accumulator (at most 16
+    // products of a residue and a constant) below barrett128's 2^(b+61) bound.
+    if (p->logN < 12 || p->logN > 17 || p->L < 1 || p->L > kMaxL || p->K < 1 || p->K > kMaxK ||
+        p->alpha < 1 || p->alpha > 16 || p->q_bits < 30 || p->q_bits > 57 || p->p_bits < 30 ||
+        p->p_bits > 57 || p->h < 1 || p->h > (1 << p->logN) || !(p->sigma > 0))
+        return HE_EINVAL;
+    c->prm = *p;
+    c->logN = p->logN;
+    c->N = 1 << p->logN;
+    c->L = p->L;
+    c->K = p->K;
+    c->alpha = p->alpha;
+    c->dnum = (p->L + p->alpha - 1) / p->alpha;
+    c->E = p->K + p->L;
+    c->device = device;
+    if (c->dnum > kMaxDigits) return HE_EINVAL;
+
+    std::vector<u64> q = find_primes(p->logN, p->q_bits, p->L, {});
+    if ((int)q.size() != p->L) return HE_EINVAL;
+    std::vector<u64> sp = find_primes(p->logN, p->p_bits, p->K, q);
+    if ((int)sp.size() != p->K) return HE_EINVAL;
+    c->ext = sp;
+    c->ext.insert(c->ext.end(), q.begin(), q.end());
+    const int N = c->N, K = c->K, L = c->L, E = c->E, logN = c->logN;
+
+    // the ciphertext primes descend, so a rescale residue r < q_{l-1} is
+    // already reduced mod every q_i with i < l-1.
+
+    c->psi.resize(E);
+    c->w.assign(E, {});
+    c->wsh.assign(E, {});
+    c->iw.assign(E, {});
+    c->iwsh.assign(E, {});
+    c->ninv.resize(E);
+    c->ninv_sh.resize(E);
+    for (int e = 0; e < E; e++) {
+        u64 m = c->ext[e];
+        u64 psi = smallest_psi(m, logN);
+        c->psi[e] = psi;
+        u64 ipsi = inv(psi, m);
+        std::vector<u64> pow_f(N), pow_i(N);
+        pow_f[0] = pow_i[0] = 1;
+        for (int k = 1; k < N; k++) {
+            pow_f[k] = mul(pow_f[k - 1], psi, m);
+            pow_i[k] = mul(pow_i[k - 1], ipsi, m);
+        }
+        auto &W = c->w[e], &Ws = c->wsh[e], &IW = c->iw[e], &IWs = c->iwsh[e];
+        W.resize(N); Ws.resize(N); IW.resize(N); IWs.resize(N);
+        for (int k = 0; k < N; k++) {
+            u64 br = bitrev((u64)k, logN);
+            W[k] = pow_f[br];
+            Ws[k] = shoup(W[k], m);
+            IW[k] = pow_i[br];
+            IWs[k] = shoup(IW[k], m);
+        }
+        c->ninv[e] = inv((u64)N % m, m);
+        c->ninv_sh[e] = shoup(c->ninv[e], m);
+    }
+
+    // ModDown constants
+    c->PB.assign((size_t)L * K, 0);
+    c->pinv.resize(L);
+    c->phat_inv.resize(K);
+    for (int k = 0; k < K; k++) {
+        u64 pk = c->ext[k], v = 1;
+        for (int k2 = 0; k2 < K; k2++)
+            if (k2 != k) v = mul(v, c->ext[k2] % pk, pk);
+        c->phat_inv[k] = pair(inv(v, pk), pk);
+    }
+    for (int i = 0; i < L; i++) {
+        u64 qi = c->ext[K + i], P = 1;
+        for (int k = 0; k < K; k++) {
+            u64 v = 1;
+            for (int k2 = 0; k2 < K; k2++)
+                if (k2 != k) v = mul(v, c->ext[k2] % qi, qi);
+            c->PB[(size_t)i * K + k] = v;
+            P = mul(P, c->ext[k] % qi, qi);
+        }
+        c->pinv[i] = pair(inv(P, qi), qi);
+    }
+
+    // per level
+    c->host_levels.assign(L + 1, HostLevel());
+    for (int l = 1; l <= L; l++) {
+        HostLevel &H = c->host_levels[l];
+        const int beta = (l + c->alpha - 1) / c->alpha, El = K + l;
+        const int A = c->alpha;
+        H.ws = layout_for(l, K, c->alpha);
+        const WsLayout &W = H.ws;
+        // ModUp tables and the iNTT scale N^-1 * Qhat_{j,i}^-1
+        H.modupB.assign((size_t)beta * El * A, 0);
+        for (int j = 0; j < beta; j++) {
+            int lo = j * c->alpha, hi = std::min((j + 1) * c->alpha, l);
+            for (int i = lo; i < hi; i++) {
+                u64 qi = c->ext[K + i], qh = 1;
+                for (int i2 = lo; i2 < hi; i2++)
+                    if (i2 != i) qh = mul(qh, c->ext[K + i2] % qi, qi);
+                u64 sc = mul(c->ninv[K + i], inv(qh, qi), qi);
+                H.intt1.push_back(NttJob{(unsigned)(W.d2 + i), (unsigned)(W.y + i), (unsigned)(K + i), 0, sc,
+                                         shoup(sc, qi)});
+            }
+            for (int e = 0; e < El; e++) {
+                bool own = e >= K && (e - K) >= lo && (e - K) < hi;
+                if (own) continue;
+                u64 t = c->ext[e];
+                for (int i = lo; i < hi; i++) {
+                    u64 v = 1;
+                    for (int i2 = lo; i2 < hi; i2++)
+                        if (i2 != i) v = mul(v, c->ext[K + i2] % t, t);
+                    H.modupB[((size_t)j * El + e) * A + (i - lo)] = v;
+                }
+                H.ntt_up.push_back(NttJob{(unsigned)(W.u + (size_t)j * El + e), (unsigned)(W.u + (size_t)j * El + e),
+                                          (unsigned)e, 0, 0, 0});
+            }
+        }
+        const u64 ql = c->ext[K + l - 1];
+        H.intt1f = H.intt1;
+        for (int h = 0; h < 2; h++)
+            H.intt1f.push_back(NttJob{(unsigned)((h ? W.d1 : W.d0) + l - 1), (unsigned)(W.r + h), (unsigned)(K + l - 1),
+                                      0, c->ninv[K + l - 1], c->ninv_sh[K + l - 1]});
+        for (int h = 0; h < 2; h++)
+            for (int k = 0; k < K; k++) {
+                u64 pk = c->ext[k];
+                u64 sc = mul(c->ninv[k], c->phat_inv[k].x, pk);
+                H.intt2.push_back(NttJob{(unsigned)(W.ks + (size_t)h * El + k), (unsigned)(W.ys + (size_t)h * K + k),
+                                         (unsigned)k, 0, sc, shoup(sc, pk)});
+            }
+        H.intt2f = H.intt2;
+        for (int h = 0; h < 2; h++)
+            H.intt2f.push_back(NttJob{(unsigned)(W.ks + (size_t)h * El + K + l - 1), (unsigned)(W.r + 2 + h),
+                                      (unsigned)(K + l - 1), 0, c->ninv[K + l - 1], c->ninv_sh[K + l - 1]});
+        for (int h = 0; h < 2; h++)
+            for (int i = 0; i < l; i++)
+                H.ntt_conv.push_back(NttJob{(unsigned)(W.z + (size_t)h * l + i), (unsigned)(W.z + (size_t)h * l + i),
+                                            (unsigned)(K + i), 0, 0, 0});
+        for (int h = 0; h < 2; h++)
+            for (int i = 0; i + 1 < l; i++)
+                H.ntt_z.push_back(NttJob{(unsigned)(W.z + (size_t)h * (l - 1) + i),
+                                         (unsigned)(W.z + (size_t)h * (l - 1) + i), (unsigned)(K + i), 0, 0, 0});
+        // rescale on its own: src offsets are relative to the input ciphertext
+        for (int h = 0; h < 2; h++)
+            H.rs_intt.push_back(NttJob{(unsigned)((size_t)h * l + l - 1), (unsigned)(W.r + h), (unsigned)(K + l - 1), 0,
+                                       c->ninv[K + l - 1], c->ninv_sh[K + l - 1]});
+        for (int h = 0; h < 2; h++)
+            for (int i = 0; i + 1 < l; i++)
+                H.rs_ntt.push_back(NttJob{(unsigned)(W.r + h), (unsigned)(W.z + (size_t)h * (l - 1) + i), (unsigned)(K + i),
+                                          0, 0, 0});
+        H.qinv_last.resize(l > 1 ? l - 1 : 1);
+        H.pinv_qinv.resize(l > 1 ? l - 1 : 1);
+        for (int i = 0; i + 1 < l; i++) {
+            u64 qi = c->ext[K + i];
+            u64 qinv = inv(ql % qi, qi);
+            H.qinv_last[i] = pair(qinv, qi);
+            H.pinv_qinv[i] = pair(mul(qinv, c->pinv[i].x, qi), qi);
+        }
+    }
+    if (!device) return HE_OK;
+
+    // ---- device arena -------------------------------------------------------
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_primes = take(sizeof(DevPrime) * E);
+    std::vector<size_t> o_w(E), o_iw(E);
+    for (int e = 0; e < E; e++) {
+        o_w[e] = take(sizeof(ulonglong2) * N);
+        o_iw[e] = take(sizeof(ulonglong2) * N);
+    }
+    const size_t o_PB = take(sizeof(u64) * c->PB.size());
+    const size_t o_pinv = take(sizeof(ulonglong2) * L);
+    const size_t o_levels = take(sizeof(DevLevel) * (L + 1));
+    struct LvlOff { size_t modupB, qinv, pq, j[9]; };
+    std::vector<LvlOff> lo(L + 1);
+    for (int l = 1; l <= L; l++) {
+        HostLevel &H = c->host_levels[l];
+        lo[l].modupB = take(sizeof(u64) * H.modupB.size());
+        lo[l].qinv = take(sizeof(ulonglong2) * H.qinv_last.size());
+        lo[l].pq = take(sizeof(ulonglong2) * H.pinv_qinv.size());
+        const std::vector<NttJob> *lists[9] = {&H.intt1, &H.intt1f, &H.ntt_up, &H.intt2, &H.intt2f,
+                                               &H.ntt_conv, &H.ntt_z, &H.rs_intt, &H.rs_ntt};
+        for (int t = 0; t < 9; t++) lo[l].j[t] = take(sizeof(NttJob) * std::max<size_t>(1, lists[t]->size()));
+    }
+    c->arena_bytes = off;
+    if (cudaGetDevice(&c->device_id) != cudaSuccess) return HE_ECUDA;
+    if (cudaMalloc(&c->arena, off) != cudaSuccess) return HE_ECUDA;
+    std::vector<unsigned char> img(off, 0);
+    char *base = (char *)c->arena;
+    std::vector<DevPrime> dp(E);
+    for (int e = 0; e < E; e++) {
+        u64 m = c->ext[e];
+        int b = bitlen(m);
+        dp[e].q = m;
+        dp[e].q2 = 2 * m;
+        dp[e].s = (unsigned)(b - 2);
+        dp[e].mu = (u64)(((u128)1 << (64 + b - 2)) / m);
+        dp[e].pad = 0;
+        dp[e].w = (const ulonglong2 *)(base + o_w[e]);
+        dp[e].iw = (const ulonglong2 *)(base + o_iw[e]);
+        ulonglong2 *W = (ulonglong2 *)(img.data() + o_w[e]);
+        ulonglong2 *IW = (ulonglong2 *)(img.data() + o_iw[e]);
+        for (int k = 0; k < N; k++) {
+            W[k] = make_ulonglong2(c->w[e][k], c->wsh[e][k]);
+            IW[k] = make_ulonglong2(c->iw[e][k], c->iwsh[e][k]);
+        }
+    }
+    memcpy(img.data() + o_primes, dp.data(), sizeof(DevPrime) * E);
+    memcpy(img.data() + o_PB, c->PB.data(), sizeof(u64) * c->PB.size());
+    memcpy(img.data() + o_pinv, c->pinv.data(), sizeof(ulonglong2) * L);
+    c->dev_levels.assign(L + 1, DevLevel());
+    c->jobs.assign(L + 1, LevelJobs());
+    for (int l = 1; l <= L; l++) {
+        HostLevel &H = c->host_levels[l];
+        DevLevel &D = c->dev_levels[l];
+        memset(&D, 0, sizeof(D));
+        D.l = l;
+        D.beta = (l + c->alpha - 1) / c->alpha;
+        D.E = K + l;
+        D.A = c->alpha;
+        for (int j = 0; j < D.beta; j++) {
+            D.dig_lo[j] = j * c->alpha;
+            D.dig_n[j] = std::min((j + 1) * c->alpha, l) - j * c->alpha;
+        }
+        memcpy(img.data() + lo[l].modupB, H.modupB.data(), sizeof(u64) * H.modupB.size());
+        memcpy(img.data() + lo[l].qinv, H.qinv_last.data(), sizeof(ulonglong2) * H.qinv_last.size());
+        memcpy(img.data() + lo[l].pq, H.pinv_qinv.data(), sizeof(ulonglong2) * H.pinv_qinv.size());
+        D.modupB = (const u64 *)(base + lo[l].modupB);
+        D.qinv_last = (const ulonglong2 *)(base + lo[l].qinv);
+        D.pinv_qinv = (const ulonglong2 *)(base + lo[l].pq);
+        const std::vector<NttJob> *lists[9] = {&H.intt1, &H.intt1f, &H.ntt_up, &H.intt2, &H.intt2f,
+                                               &H.ntt_conv, &H.ntt_z, &H.rs_intt, &H.rs_ntt};
+        const NttJob *dptr[9];
+        for (int t = 0; t < 9; t++) {
+            if (!lists[t]->empty()) memcpy(img.data() + lo[l].j[t], lists[t]->data(), sizeof(NttJob) * lists[t]->size());
+            dptr[t] = (const NttJob *)(base + lo[l].j[t]);
+        }
+        LevelJobs &J = c->jobs[l];
+        J.intt1 = dptr[0];    J.n_intt1 = (int)H.intt1.size();
+        J.intt1f = dptr[1];   J.n_intt1f = (int)H.intt1f.size();
+        J.ntt_up = dptr[2];   J.n_ntt_up = (int)H.ntt_up.size();
+        J.intt2 = dptr[3];    J.n_intt2 = (int)H.intt2.size();
+        J.intt2f = dptr[4];   J.n_intt2f = (int)H.intt2f.size();
+        J.ntt_conv = dptr[5]; J.n_ntt_conv = (int)H.ntt_conv.size();
+        J.ntt_z = dptr[6];    J.n_ntt_z = (int)H.ntt_z.size();
+        J.rs_intt = dptr[7];  J.n_rs_intt = (int)H.rs_intt.size();
+        J.rs_ntt = dptr[8];   J.n_rs_ntt = (int)H.rs_ntt.size();
+    }
+    memcpy(img.data() + o_levels, c->dev_levels.data(), sizeof(DevLevel) * (L + 1));
+    if (cudaMemcpy(c->arena, img.data(), off, cudaMemcpyHostToDevice) != cudaSuccess) return HE_ECUDA;
+    c->d_primes = (DevPrime *)(base + o_primes);
+    c->d_PB = (const u64 *)(base + o_PB);
+    c->d_pinv = (const ulonglong2 *)(base + o_pinv);
+    c->d_levels = (DevLevel *)(base + o_levels);
+    return HE_OK;
+}
+
+}  // namespace he

@@ -1,0 +1,326 @@
+// keyswitch.cu -- element-wise and base-conversion kernels of HE Mul on sm_103a.
+//
+//  k_tensor        Region 1 of Fig. 2 in RNS form (congruence relation,
+//                  Sec. 3.3): d0 = b1 b2, d1 = a1 b2 + a2 b1, d2 = a1 a2 mod q_i.
+//  k_modup         full-RNS mod up (Sec. 7, Table 11): the iCRT-then-CRT
+//                  shape of Algo 5 / Algo 1 as a fast base conversion
+//                  U_j[t] = sum_{i in I_j} y_i [Qhat_{j,i}]_t mod t, with the
+//                  y_i = x_i Qhat^-1 factor already applied by the iNTT.
+//                  128-bit lazy accumulation, one reduction per output (the
+//                  paper's delayed-modulo idea for CRT, Sec. 5.3).
+//  k_inner_product Region 2 of Fig. 2: KS_{b,a}[t] = sum_j U_j[t] evk_j.{b,a}[t].
+//  k_moddown_conv  mod down (Sec. 7): conv_i = sum_k y_k [Phat_k]_{q_i} mod q_i;
+//                  the fused variant also folds in the rescale residue.
+//  k_combine_*     the final additions (Fig. 2) and the rescale division.
+//
+// Every kernel handles two consecutive coefficients per thread with 16-byte
+// loads and stores; the limb-major layouts keep all accesses coalesced.
+#include "he_internal.h"
+#include "modarith.cuh"
+
+namespace he {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *reinterpret_cast<const ulonglong2 *>(p); }
+__device__ __forceinline__ void st2(u64 *p, u64 x, u64 y) { *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(x, y); }
+
+// grid: x over N/2/kThreads, y over limbs
+__global__ void __launch_bounds__(kThreads)
+k_tensor(const u64 *__restrict__ ct1, const u64 *__restrict__ ct2, u64 *__restrict__ d0, u64 *__restrict__ d1,
+         u64 *__restrict__ d2, const DevPrime *__restrict__ primes, int K, int l, int N)
+{
+    const int i = blockIdx.y;
+    const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
+    const DevPrime pr = primes[K + i];
+    const size_t ob = (size_t)i * N + n, oa = ((size_t)l + i) * N + n;
+    ulonglong2 b1 = ld2(ct1 + ob), a1 = ld2(ct1 + oa), b2 = ld2(ct2 + ob), a2 = ld2(ct2 + oa);
+    st2(d0 + (size_t)i * N + n, mul_mod(b1.x, b2.x, pr.q, pr.mu, pr.s), mul_mod(b1.y, b2.y, pr.q, pr.mu, pr.s));
+    U128 x = mul_wide(a1.x, b2.x), y = mul_wide(a1.y, b2.y);
+    mac(x, a2.x, b1.x);
+    mac(y, a2.y, b1.y);
+    st2(d1 + (size_t)i * N + n, barrett128(x, pr.q, pr.mu, pr.s), barrett128(y, pr.q, pr.mu, pr.s));
+    st2(d2 + (size_t)i * N + n, mul_mod(a1.x, a2.x, pr.q, pr.mu, pr.s), mul_mod(a1.y, a2.y, pr.q, pr.mu, pr.s));
+}
+
+// grid: x over N/2/kThreads, y over digits.  y: [l][N] (scaled iNTT of d2),
+// U: [beta][E][N].
+template <int A>
+__global__ void __launch_bounds__(kThreads)
+k_modup(const u64 *__restrict__ y, u64 *__restrict__ U, const DevLevel *__restrict__ lv_arr, int l,
+        const DevPrime *__restrict__ primes, int K, int N)
+{
+    const DevLevel &lv = lv_arr[l];
+    const int j = blockIdx.y;
+    const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
+    const int E = lv.E;
+    const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
+    u64 yx[A], yy[A];
+#pragma unroll
+    for (int i = 0; i < A; i++) {
+        if (i < nj) {
+            ulonglong2 v = ld2(y + (size_t)(lo + i) * N + n);
+            yx[i] = v.x;
+            yy[i] = v.y;
+        } else {
+            yx[i] = yy[i] = 0;
+        }
+    }
+    const u64 *B = lv.modupB + (size_t)j * E * lv.A;
+    u64 *Uj = U + (size_t)j * E * N;
+    for (int e = 0; e < E; e++) {
+        if (e >= K && e - K >= lo && e - K < lo + nj) continue;  // own digit: d2 is reused
+        const DevPrime pr = primes[e];
+        const u64 *b = B + (size_t)e * lv.A;
+        U128 ax = {0, 0}, ay = {0, 0};
+#pragma unroll
+        for (int i = 0; i < A; i++) {
+            if (i < nj) {
+                const u64 c = __ldg(b + i);
+                mac(ax, yx[i], c);
+                mac(ay, yy[i], c);
+            }
+        }
+        st2(Uj + (size_t)e * N + n, barrett128(ax, pr.q, pr.mu, pr.s), barrett128(ay, pr.q, pr.mu, pr.s));
+    }
+}
+
+// grid: x over N/2/kThreads, y over E = K + l.  U: [beta][E][N] (own-digit
+// rows read from d2), evk: [dnum][2][K+L][N], KS: [2][E][N].
+__global__ void __launch_bounds__(kThreads)
+k_inner_product(const u64 *__restrict__ U, const u64 *__restrict__ d2, const u64 *__restrict__ evk,
+                u64 *__restrict__ KS, const DevLevel *__restrict__ lv_arr, int l, const DevPrime *__restrict__ primes,
+                int K, int L, int N)
+{
+    const DevLevel &lv = lv_arr[l];
+    const int e = blockIdx.y;
+    const int E = lv.E, EL = K + L;
+    const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
+    const DevPrime pr = primes[e];
+    U128 bx = {0, 0}, by = {0, 0}, ax = {0, 0}, ay = {0, 0};
+    for (int j = 0; j < lv.beta; j++) {
+        const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
+        const bool own = e >= K && e - K >= lo && e - K < lo + nj;
+        const u64 *up = own ? d2 + (size_t)(e - K) * N : U + ((size_t)j * E + e) * N;
+        ulonglong2 u = ld2(up + n);
+        ulonglong2 kb = ld2(evk + ((size_t)(2 * j) * EL + e) * N + n);
+        ulonglong2 ka = ld2(evk + ((size_t)(2 * j + 1) * EL + e) * N + n);
+        mac(bx, u.x, kb.x);
+        mac(by, u.y, kb.y);
+        mac(ax, u.x, ka.x);
+        mac(ay, u.y, ka.y);
+    }
+    st2(KS + (size_t)e * N + n, barrett128(bx, pr.q, pr.mu, pr.s), barrett128(by, pr.q, pr.mu, pr.s));
+    st2(KS + ((size_t)E + e) * N + n, barrett128(ax, pr.q, pr.mu, pr.s), barrett128(ay, pr.q, pr.mu, pr.s));
+}
+
+// grid: x over N/2/kThreads, y over h in {0,1}.  ys: [2][K] coefficient form
+// (already times Phat_k^-1).  PLAIN: z[h][i] = conv_i for i < l.
+// FUSED: r = r0 + (r1 - conv_{l-1}) P^-1 mod q_{l-1} with r0 = iNTT(d_h)_{l-1},
+// r1 = iNTT(KS_h)_{l-1}; z[h][i] = conv_i P^-1 + r mod q_i for i < l-1.
+template <int KM, bool FUSED>
+__global__ void __launch_bounds__(kThreads)
+k_moddown_conv(const u64 *__restrict__ ys, const u64 *__restrict__ rr, u64 *__restrict__ z,
+               const u64 *__restrict__ PB, const ulonglong2 *__restrict__ pinv, const DevPrime *__restrict__ primes,
+               int K, int l, int N)
+{
+    const int h = blockIdx.y;
+    const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
+    u64 vx[KM], vy[KM];
+#pragma unroll
+    for (int k = 0; k < KM; k++) {
+        if (k < K) {
+            ulonglong2 v = ld2(ys + ((size_t)h * K + k) * N + n);
+            vx[k] = v.x;
+            vy[k] = v.y;
+        } else {
+            vx[k] = vy[k] = 0;
+        }
+    }
+    u64 rx = 0, ry = 0;
+    const int nout = FUSED ? l - 1 : l;
+    if (FUSED) {
+        const int i = l - 1;
+        const DevPrime pr = primes[K + i];
+        const u64 *b = PB + (size_t)i * K;
+        U128 ax = {0, 0}, ay = {0, 0};
+#pragma unroll
+        for (int k = 0; k < KM; k++)
+            if (k < K) {
+                const u64 c = __ldg(b + k);
+                mac(ax, vx[k], c);
+                mac(ay, vy[k], c);
+            }
+        const u64 cx = barrett128(ax, pr.q, pr.mu, pr.s), cy = barrett128(ay, pr.q, pr.mu, pr.s);
+        ulonglong2 r0 = ld2(rr + (size_t)h * N + n), r1 = ld2(rr + (size_t)(2 + h) * N + n);
+        const ulonglong2 pv = pinv[i];
+        rx = add_mod(r0.x, shoup(sub_mod(r1.x, cx, pr.q), pv.x, pv.y, pr.q), pr.q);
+        ry = add_mod(r0.y, shoup(sub_mod(r1.y, cy, pr.q), pv.x, pv.y, pr.q), pr.q);
+    }
+    for (int i = 0; i < nout; i++) {
+        const DevPrime pr = primes[K + i];
+        const u64 *b = PB + (size_t)i * K;
+        U128 ax = {0, 0}, ay = {0, 0};
+#pragma unroll
+        for (int k = 0; k < KM; k++)
+            if (k < K) {
+                const u64 c = __ldg(b + k);
+                mac(ax, vx[k], c);
+                mac(ay, vy[k], c);
+            }
+        u64 cx = barrett128(ax, pr.q, pr.mu, pr.s), cy = barrett128(ay, pr.q, pr.mu, pr.s);
+        if (FUSED) {
+            // r < q_{l-1} < q_i: r is already a residue mod q_i
+            const ulonglong2 pv = pinv[i];
+            cx = add_mod(shoup(cx, pv.x, pv.y, pr.q), rx, pr.q);
+            cy = add_mod(shoup(cy, pv.x, pv.y, pr.q), ry, pr.q);
+        }
+        st2(z + ((size_t)h * nout + i) * N + n, cx, cy);
+    }
+}
+
+// out[h][i] = d_h[i] + (KS_h[K+i] - C[h][i]) P^-1 mod q_i, i < l
+__global__ void __launch_bounds__(kThreads)
+k_combine_plain(const u64 *__restrict__ d0, const u64 *__restrict__ d1, const u64 *__restrict__ KS,
+                const u64 *__restrict__ C, u64 *__restrict__ out, const ulonglong2 *__restrict__ pinv,
+                const DevPrime *__restrict__ primes, int K, int l, int N)
+{
+    const int i = blockIdx.y, h = blockIdx.z;
+    const int E = K + l;
+    const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
+    const DevPrime pr = primes[K + i];
+    const ulonglong2 pv = pinv[i];
+    ulonglong2 d = ld2((h ? d1 : d0) + (size_t)i * N + n);
+    ulonglong2 ks = ld2(KS + ((size_t)h * E + K + i) * N + n);
+    ulonglong2 c = ld2(C + ((size_t)h * l + i) * N + n);
+    u64 x = add_mod(d.x, shoup(sub_mod(ks.x, c.x, pr.q), pv.x, pv.y, pr.q), pr.q);
+    u64 y = add_mod(d.y, shoup(sub_mod(ks.y, c.y, pr.q), pv.x, pv.y, pr.q), pr.q);
+    st2(out + ((size_t)h * l + i) * N + n, x, y);
+}
+
+// Fused ModDown + rescale: out[h][i] = (d_h[i] + KS_h[K+i] P^-1 - Z[h][i]) q_{l-1}^-1, i < l-1
+__global__ void __launch_bounds__(kThreads)
+k_combine_rescale(const u64 *__restrict__ d0, const u64 *__restrict__ d1, const u64 *__restrict__ KS,
+                  const u64 *__restrict__ Z, u64 *__restrict__ out, const ulonglong2 *__restrict__ pinv,
+                  const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int l, int N)
+{
+    const int i = blockIdx.y, h = blockIdx.z;
+    const int E = K + l;
+    const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
+    const DevPrime pr = primes[K + i];
+    const ulonglong2 pv = pinv[i];
+    const ulonglong2 qv = lv_arr[l].qinv_last[i];
+    ulonglong2 d = ld2((h ? d1 : d0) + (size_t)i * N + n);
+    ulonglong2 ks = ld2(KS + ((size_t)h * E + K + i) * N + n);
+    ulonglong2 zz = ld2(Z + ((size_t)h * (l - 1) + i) * N + n);
+    u64 x = sub_mod(add_mod(d.x, shoup(ks.x, pv.x, pv.y, pr.q), pr.q), zz.x, pr.q);
+    u64 y = sub_mod(add_mod(d.y, shoup(ks.y, pv.x, pv.y, pr.q), pr.q), zz.y, pr.q);
+    st2(out + ((size_t)h * (l - 1) + i) * N + n, shoup(x, qv.x, qv.y, pr.q), shoup(y, qv.x, qv.y, pr.q));
+}
+
+// Rescale on its own: out[h][i] = (c_h[i] - Z[h][i]) q_{l-1}^-1, i < l-1
+__global__ void __launch_bounds__(kThreads)
+k_rescale_combine(const u64 *__restrict__ ct, const u64 *__restrict__ Z, u64 *__restrict__ out,
+                  const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int l, int N)
+{
+    const int i = blockIdx.y, h = blockIdx.z;
+    const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
+    const DevPrime pr = primes[K + i];
+    const ulonglong2 qv = lv_arr[l].qinv_last[i];
+    ulonglong2 c = ld2(ct + ((size_t)h * l + i) * N + n);
+    ulonglong2 zz = ld2(Z + ((size_t)h * (l - 1) + i) * N + n);
+    st2(out + ((size_t)h * (l - 1) + i) * N + n, shoup(sub_mod(c.x, zz.x, pr.q), qv.x, qv.y, pr.q),
+        shoup(sub_mod(c.y, zz.y, pr.q), qv.x, qv.y, pr.q));
+}
+
+inline dim3 grid_x(int N) { return dim3((unsigned)(N / 2 / kThreads)); }
+
+}  // namespace
+
+cudaError_t run_tensor(const he_ctx *c, const u64 *ct1, const u64 *ct2, u64 *d0, u64 *d1, u64 *d2, int l,
+                       cudaStream_t st)
+{
+    dim3 g = grid_x(c->N);
+    g.y = l;
+    k_tensor<<<g, kThreads, 0, st>>>(ct1, ct2, d0, d1, d2, c->d_primes, c->K, l, c->N);
+    return cudaGetLastError();
+}
+
+cudaError_t run_modup(const he_ctx *c, const u64 *y, u64 *U, int l, cudaStream_t st)
+{
+    dim3 g = grid_x(c->N);
+    g.y = (l + c->alpha - 1) / c->alpha;
+    const int a = c->alpha;
+#define HE_MODUP(AA) k_modup<AA><<<g, kThreads, 0, st>>>(y, U, c->d_levels, l, c->d_primes, c->K, c->N)
+    if (a <= 1) HE_MODUP(1);
+    else if (a <= 2) HE_MODUP(2);
+    else if (a <= 4) HE_MODUP(4);
+    else if (a <= 8) HE_MODUP(8);
+    else if (a <= 12) HE_MODUP(12);
+    else HE_MODUP(16);
+#undef HE_MODUP
+    return cudaGetLastError();
+}
+
+cudaError_t run_inner_product(const he_ctx *c, const u64 *U, const u64 *d2, const u64 *evk, u64 *KS, int l,
+                              cudaStream_t st)
+{
+    dim3 g = grid_x(c->N);
+    g.y = c->K + l;
+    k_inner_product<<<g, kThreads, 0, st>>>(U, d2, evk, KS, c->d_levels, l, c->d_primes, c->K, c->L, c->N);
+    return cudaGetLastError();
+}
+
+cudaError_t run_moddown_conv(const he_ctx *c, const u64 *ys, const u64 *rr, u64 *z, int l, bool fused,
+                             cudaStream_t st)
+{
+    dim3 g = grid_x(c->N);
+    g.y = 2;
+    const int K = c->K;
+#define HE_MD(KK)                                                                                                  \
+    do {                                                                                                           \
+        if (fused) k_moddown_conv<KK, true><<<g, kThreads, 0, st>>>(ys, rr, z, c->d_PB, c->d_pinv, c->d_primes, K, l, c->N); \
+        else k_moddown_conv<KK, false><<<g, kThreads, 0, st>>>(ys, rr, z, c->d_PB, c->d_pinv, c->d_primes, K, l, c->N);     \
+    } while (0)
+    if (K <= 1) HE_MD(1);
+    else if (K <= 2) HE_MD(2);
+    else if (K <= 4) HE_MD(4);
+    else if (K <= 8) HE_MD(8);
+    else if (K <= 12) HE_MD(12);
+    else HE_MD(16);
+#undef HE_MD
+    return cudaGetLastError();
+}
+
+cudaError_t run_combine_plain(const he_ctx *c, const u64 *d0, const u64 *d1, const u64 *KS, const u64 *C, u64 *out,
+                              int l, cudaStream_t st)
+{
+    dim3 g = grid_x(c->N);
+    g.y = l;
+    g.z = 2;
+    k_combine_plain<<<g, kThreads, 0, st>>>(d0, d1, KS, C, out, c->d_pinv, c->d_primes, c->K, l, c->N);
+    return cudaGetLastError();
+}
+
+cudaError_t run_combine_rescale(const he_ctx *c, const u64 *d0, const u64 *d1, const u64 *KS, const u64 *Z,
+                                u64 *out, int l, cudaStream_t st)
+{
+    dim3 g = grid_x(c->N);
+    g.y = l - 1;
+    g.z = 2;
+    k_combine_rescale<<<g, kThreads, 0, st>>>(d0, d1, KS, Z, out, c->d_pinv, c->d_levels, c->d_primes, c->K, l, c->N);
+    return cudaGetLastError();
+}
+
+cudaError_t run_rescale_combine(const he_ctx *c, const u64 *ct, const u64 *Z, u64 *out, int l, cudaStream_t st)
+{
+    dim3 g = grid_x(c->N);
+    g.y = l - 1;
+    g.z = 2;
+    k_rescale_combine<<<g, kThreads, 0, st>>>(ct, Z, out, c->d_levels, c->d_primes, c->K, l, c->N);
+    return cudaGetLastError();
+}
+
+}  // namespace he

@@ -1,0 +1,68 @@
+// modarith.cuh -- 64-bit modular arithmetic for sm_103a kernels.
+//
+// Residues are uint64.  Moduli are NTT-friendly primes below 2^62 (the
+// configurations use 50- to 55-bit primes), so 4q still fits in a word and the
+// lazy ranges below are safe.
+//
+//  * shoup_lazy / shoup: Shoup's modular multiplication by a constant
+//    (the paper's Algo 2) with w' = floor(w * 2^64 / q).  The lazy form returns
+//    a value in [0, 2q); the paper's correction "if r > p" is read as r >= q,
+//    which the full form applies.
+//  * mul_wide / mac: 64x64 -> 128-bit products accumulated without reduction
+//    (the lazy reduction idea the paper applies to CRT accumulation, Sec. 5.3).
+//  * barrett128: one reduction of a 128-bit accumulator V < 2^(b+61), where
+//    b = bitlen(q).  mu = floor(2^(62+b) / q); the quotient estimate
+//    floor((V >> (b-2)) * mu / 2^64) is the true quotient or one less, so the
+//    remainder needs a single conditional subtraction.
+#pragma once
+#include <cstdint>
+
+typedef uint64_t u64;
+
+struct U128 {
+    u64 lo, hi;
+};
+
+__device__ __forceinline__ u64 shoup_lazy(u64 x, u64 w, u64 wp, u64 q)
+{
+    u64 qh = __umul64hi(x, wp);
+    return x * w - qh * q;  // in [0, 2q), exact mod 2^64
+}
+
+__device__ __forceinline__ u64 csub(u64 x, u64 q) { return x >= q ? x - q : x; }
+
+__device__ __forceinline__ u64 shoup(u64 x, u64 w, u64 wp, u64 q) { return csub(shoup_lazy(x, w, wp, q), q); }
+
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
+
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+__device__ __forceinline__ U128 mul_wide(u64 a, u64 b)
+{
+    U128 r;
+    r.lo = a * b;
+    r.hi = __umul64hi(a, b);
+    return r;
+}
+
+__device__ __forceinline__ void mac(U128 &acc, u64 a, u64 b)
+{
+    u64 lo = a * b;
+    u64 hi = __umul64hi(a, b);
+    acc.lo += lo;
+    acc.hi += hi + (acc.lo < lo ? 1ull : 0ull);
+}
+
+// V mod q for V = acc < 2^(b+61); s = b - 2 (1 <= s <= 60), mu = floor(2^(64+s) / q).
+__device__ __forceinline__ u64 barrett128(U128 v, u64 q, u64 mu, unsigned s)
+{
+    u64 u = (v.lo >> s) | (v.hi << (64 - s));
+    u64 qh = __umul64hi(u, mu);
+    u64 r = v.lo - qh * q;  // in [0, 2q)
+    return csub(r, q);
+}
+
+__device__ __forceinline__ u64 mul_mod(u64 a, u64 b, u64 q, u64 mu, unsigned s)
+{
+    return barrett128(mul_wide(a, b), q, mu, s);
+}

@@ -1,0 +1,292 @@
+"""GPU parity: every CUDA step and the whole HE Mul path, called through the
+C ABI, against the CPU oracle on the same seeded inputs.
+
+All arithmetic is modular integer arithmetic, so the bar is bit-exactness:
+every output word must equal the oracle's.  Sizes span several NTT tiles and
+ragged digit partitions (a short last digit), from N = 2^12 to the full
+N = 2^17 configuration.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+from oracle.encoding import encode
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="session")
+def g():
+    from paper_2003_04510_gb300 import build
+    build.build()
+    import paper_2003_04510_gb300 as pkg
+    return pkg
+
+
+_ctx = {}
+
+
+def ctx_for(g, name):
+    if name not in _ctx:
+        _ctx[name] = g.Context(g.PRESETS[name][0], device=True)
+    return _ctx[name]
+
+
+def rand_polys(moduli, N, seed):
+    return si.uniform_residues([int(m) for m in moduli], (N,), seed)
+
+
+def rand_ct(op, level, seed):
+    q = [int(x) for x in op.q[:level]]
+    return np.stack([rand_polys(q, op.N, seed), rand_polys(q, op.N, seed + 1)])
+
+
+def rand_evk(op, seed):
+    return np.stack([np.stack([rand_polys(op.ext, op.N, seed + 2 * j), rand_polys(op.ext, op.N, seed + 2 * j + 1)])
+                     for j in range(op.dnum)])
+
+
+def dev(g, a):
+    return g.to_device(a)
+
+
+def host(g, t):
+    return g.to_host(t)
+
+
+# ---------------------------------------------------------------------------
+# per-step parity
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["n12", "n15", "n16", "n17"])
+def test_ntt_forward_inverse_parity(g, name):
+    import torch
+    ctx = ctx_for(g, name)
+    op = oracle.preset(name)
+    E = op.K + op.L
+    idx = sorted({0, op.K - 1, op.K, E - 1, op.K + op.L // 2})
+    mods = [op.ext[e] for e in idx]
+    psis = [int(op.psi_p[e]) if e < op.K else int(op.psi_q[e - op.K]) for e in idx]
+    a = rand_polys(mods, op.N, 11)
+    a[0, :4] = [0, 1, mods[0] - 1, mods[0] - 2]
+    a[-1, :] = mods[-1] - 1  # the largest residue everywhere
+    want = np.stack([oracle.ntt(a[i], mods[i], psis[i], op.logN) for i in range(len(idx))])
+    t = dev(g, a)
+    g.he_step_ntt(ctx, t, idx, inverse=False)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(g, t), want)
+    g.he_step_ntt(ctx, t, idx, inverse=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(g, t), a)
+    # inverse of fresh data against the oracle's iNTT
+    b = rand_polys(mods, op.N, 12)
+    want_i = np.stack([oracle.intt(b[i], mods[i], psis[i], op.logN) for i in range(len(idx))])
+    t = dev(g, b)
+    g.he_step_ntt(ctx, t, idx, inverse=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(g, t), want_i)
+
+
+@pytest.mark.parametrize("name,level", [("n12", 3), ("n12", 1), ("n16", 24), ("n16", 7)])
+def test_tensor_parity(g, name, level):
+    import torch
+    ctx = ctx_for(g, name)
+    op = oracle.preset(name)
+    ct1, ct2 = rand_ct(op, level, 21), rand_ct(op, level, 23)
+    d = torch.empty((3, level, op.N), dtype=torch.int64, device="cuda")
+    g.he_step_tensor(ctx, dev(g, ct1), dev(g, ct2), level, d)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(g, d), oracle.tensor(op, ct1, ct2, level))
+
+
+@pytest.mark.parametrize("name,level", [("n12", 3), ("n12", 2), ("n12", 1), ("n16", 24), ("n16", 17), ("n16", 1)])
+def test_modup_parity(g, name, level):
+    import torch
+    ctx = ctx_for(g, name)
+    op = oracle.preset(name)
+    E, beta = op.K + level, op.beta(level)
+    d2 = rand_polys(op.q[:level], op.N, 31)
+    U = torch.zeros((beta, E, op.N), dtype=torch.int64, device="cuda")
+    ws = g.workspace(ctx, level)
+    g.he_step_modup(ctx, dev(g, d2), level, U, ws)
+    torch.cuda.synchronize()
+    got = host(g, U)
+    x = np.stack([oracle.intt(d2[i], int(op.q[i]), int(op.psi_q[i]), op.logN) for i in range(level)])
+    for j in range(beta):
+        want = oracle.modup_digit(op, x, level, j)
+        own = [op.K + i for i in op.digit(j, level)]
+        rows = [e for e in range(E) if e not in own]
+        assert np.array_equal(got[j, rows], want[rows]), j
+
+
+@pytest.mark.parametrize("name,level", [("n12", 3), ("n12", 2), ("n16", 24), ("n16", 17)])
+def test_inner_product_parity(g, name, level):
+    import torch
+    ctx = ctx_for(g, name)
+    op = oracle.preset(name)
+    E, beta = op.K + level, op.beta(level)
+    ext = op.ext[:E]
+    U = np.stack([rand_polys(ext, op.N, 41 + j) for j in range(beta)])
+    d2 = rand_polys(op.q[:level], op.N, 40)
+    for j in range(beta):  # the oracle sees d2 in the own-digit rows
+        for i in op.digit(j, level):
+            U[j, op.K + i] = d2[i]
+    evk = rand_evk(op, 50)
+    KS = torch.empty((2, E, op.N), dtype=torch.int64, device="cuda")
+    g.he_step_inner_product(ctx, dev(g, U), dev(g, d2), dev(g, evk), level, KS)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(g, KS), oracle.inner_product(op, U, evk, level))
+
+
+@pytest.mark.parametrize("name,level", [("n12", 3), ("n12", 1), ("n16", 24), ("n16", 5)])
+def test_moddown_parity(g, name, level):
+    import torch
+    ctx = ctx_for(g, name)
+    op = oracle.preset(name)
+    X = rand_polys(op.ext[: op.K + level], op.N, 61)
+    out = torch.empty((level, op.N), dtype=torch.int64, device="cuda")
+    g.he_step_moddown(ctx, dev(g, X), level, out, g.workspace(ctx, level))
+    torch.cuda.synchronize()
+    assert np.array_equal(host(g, out), oracle.moddown(op, X, level))
+
+
+# ---------------------------------------------------------------------------
+# the whole path
+# ---------------------------------------------------------------------------
+_keys = {}
+
+
+def real_inputs(name):
+    """Oracle-generated keys and ciphertexts (fresh encryptions at level L)."""
+    if name not in _keys:
+        op = oracle.preset(name)
+        sc = 2.0 ** oracle.PRESETS[name]["scale_bits"]
+        ks, s1, s2 = si.SEEDS[name]
+        sk = oracle.keygen_sk(op, ks)
+        pk = oracle.keygen_pk(op, sk, ks)
+        evk = oracle.keygen_evk(op, sk, ks)
+        m1, m2 = si.messages(op.N // 2, s1), si.messages(op.N // 2, s2)
+        ct1 = oracle.encrypt_poly(op, pk, encode(m1, op.logN, sc), op.L, s1)
+        ct2 = oracle.encrypt_poly(op, pk, encode(m2, op.logN, sc), op.L, s2)
+        _keys[name] = (op, sc, sk, pk, evk, m1, m2, ct1, ct2)
+    return _keys[name]
+
+
+def gpu_mul(g, ctx, ct1, ct2, evk_t, level, fused):
+    import torch
+    N = ctx.N
+    out = torch.empty((2, level - 1 if fused else level, N), dtype=torch.int64, device="cuda")
+    ws = g.workspace(ctx, level)
+    (g.he_mul_rescale if fused else g.he_mul)(ctx, dev(g, ct1), dev(g, ct2), evk_t, level, out, ws)
+    torch.cuda.synchronize()
+    return host(g, out)
+
+
+def test_he_mul_n12_every_level(g):
+    import torch
+    op, sc, sk, pk, evk, m1, m2, ct1, ct2 = real_inputs("n12")
+    ctx = ctx_for(g, "n12")
+    evk_t = dev(g, evk)
+    for level in (3, 2, 1):
+        c1 = np.ascontiguousarray(np.stack([ct1[0, :level], ct1[1, :level]]))
+        c2 = np.ascontiguousarray(np.stack([ct2[0, :level], ct2[1, :level]]))
+        want = oracle.he_mul(op, c1, c2, evk, level)
+        assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=False), want), level
+        if level >= 2:
+            want_rs = oracle.rescale(op, want, level)
+            assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want_rs), level
+            out = torch.empty((2, level - 1, op.N), dtype=torch.int64, device="cuda")
+            g.he_rescale(ctx, dev(g, want), level, out, g.workspace(ctx, level))
+            torch.cuda.synchronize()
+            assert np.array_equal(host(g, out), want_rs), level
+    # and the GPU result decrypts to m1*m2
+    res = gpu_mul(g, ctx, ct1, ct2, evk_t, op.L, fused=True)
+    z = oracle.decrypt(op, sk, res, op.L - 1, sc * sc / int(op.q[op.L - 1]))
+    assert np.abs(z - m1 * m2).max() < 2.0 ** -14
+
+
+def test_he_mul_n16_full_level_real_keys(g):
+    op, sc, sk, pk, evk, m1, m2, ct1, ct2 = real_inputs("n16")
+    ctx = ctx_for(g, "n16")
+    evk_t = dev(g, evk)
+    want = oracle.he_mul(op, ct1, ct2, evk, op.L)
+    assert np.array_equal(gpu_mul(g, ctx, ct1, ct2, evk_t, op.L, fused=False), want)
+    want_rs = oracle.rescale(op, want, op.L)
+    got = gpu_mul(g, ctx, ct1, ct2, evk_t, op.L, fused=True)
+    assert np.array_equal(got, want_rs)
+    z = oracle.decrypt(op, sk, got, op.L - 1, sc * sc / int(op.q[op.L - 1]))
+    err = np.abs(z - m1 * m2).max()
+    assert 2.0 ** -60 < err < 2.0 ** -24
+
+
+@pytest.mark.parametrize("name,level", [("n16", 13), ("n16", 2), ("n15", 16), ("n15", 9)])
+def test_he_mul_rescale_ragged_levels(g, name, level):
+    ctx = ctx_for(g, name)
+    op = oracle.preset(name)
+    ct1, ct2 = rand_ct(op, level, 71), rand_ct(op, level, 73)
+    evk = rand_evk(op, 80)
+    want = oracle.rescale(op, oracle.he_mul(op, ct1, ct2, evk, level), level)
+    assert np.array_equal(gpu_mul(g, ctx, ct1, ct2, dev(g, evk), level, fused=True), want)
+
+
+@pytest.mark.slow
+def test_he_mul_rescale_n17_full(g):
+    ctx = ctx_for(g, "n17")
+    op = oracle.preset("n17")
+    level = op.L
+    ct1, ct2 = rand_ct(op, level, 91), rand_ct(op, level, 93)
+    evk = rand_evk(op, 100)
+    want = oracle.rescale(op, oracle.he_mul(op, ct1, ct2, evk, level), level)
+    assert np.array_equal(gpu_mul(g, ctx, ct1, ct2, dev(g, evk), level, fused=True), want)
+
+
+def test_batch_matches_single_and_oracle(g):
+    import torch
+    name = "n16"
+    ctx = ctx_for(g, name)
+    op = oracle.preset(name)
+    evk = rand_evk(op, 120)
+    evk_t = dev(g, evk)
+    levels = [4, 24, 9, 17, 2, 13]
+    jobs, singles, cts = [], [], []
+    for k, lv in enumerate(levels):
+        c1, c2 = rand_ct(op, lv, 200 + 2 * k), rand_ct(op, lv, 300 + 2 * k)
+        cts.append((c1, c2))
+        t1, t2 = dev(g, c1), dev(g, c2)
+        out = torch.empty((2, lv - 1, op.N), dtype=torch.int64, device="cuda")
+        jobs.append((t1, t2, out, lv))
+        singles.append(gpu_mul(g, ctx, c1, c2, evk_t, lv, fused=True))
+    nbytes = g.he_batch_workspace_bytes(ctx, levels)
+    ws = torch.empty(nbytes // 8, dtype=torch.int64, device="cuda")
+    g.he_mul_batch(ctx, jobs, evk_t, ws)
+    torch.cuda.synchronize()
+    for (t1, t2, out, lv), single in zip(jobs, singles):
+        assert np.array_equal(host(g, out), single), lv
+    for k in (0, 4):  # two entries against the oracle directly
+        c1, c2 = cts[k]
+        lv = levels[k]
+        want = oracle.rescale(op, oracle.he_mul(op, c1, c2, evk, lv), lv)
+        assert np.array_equal(host(g, jobs[k][2]), want)
+
+
+def test_device_argument_errors(g):
+    import torch
+    ctx = ctx_for(g, "n12")
+    N = ctx.N
+    a = torch.zeros((2, 3, N), dtype=torch.int64, device="cuda")
+    out = torch.zeros((2, 3, N), dtype=torch.int64, device="cuda")
+    ws = g.workspace(ctx, 3)
+    small = ws[: ws.numel() // 2]
+    with pytest.raises(g.HeError) as e:
+        g.he_mul(ctx, a, a, a, 3, out, small)
+    assert e.value.code == g.HE_ENOMEM
+    with pytest.raises(g.HeError) as e:
+        g.he_mul(ctx, a, a, a, 4, out, ws)
+    assert e.value.code == g.HE_ELEVEL
+    with pytest.raises(g.HeError) as e:
+        g.he_rescale(ctx, a, 1, out, ws)
+    assert e.value.code == g.HE_ELEVEL
+    mis = torch.zeros(2 * 3 * N + 1, dtype=torch.int64, device="cuda")[1:]
+    rc = g.lib().he_mul(ctx.ptr, mis.data_ptr(), a.data_ptr(), a.data_ptr(), 3, out.data_ptr(), ws.data_ptr(),
+                        ws.numel() * 8, None)
+    assert rc == g.HE_EINVAL
