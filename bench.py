@@ -71,7 +71,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -195,10 +195,10 @@ def kernel_work(name: str, prm, level: int):
         return "hbm", (3 * beta + 2) * E * limb
     if base == "tensor":
         return "hbm", 7 * level * limb
-    if base == "modup":
-        return "hbm", (level + (beta * E - level)) * limb
+    if base == "modup":  # 64x64-bit multiply-accumulates
+        return "mac", (beta * E - level) * N * alpha
     if base == "moddown_conv":
-        return "hbm", (2 * K + 4 + 2 * (level - 1)) * limb
+        return "mac", 2 * level * N * K
     if base == "combine_rescale":
         return "hbm", (2 * level + 2 * level + 2 * (level - 1) + 2 * (level - 1)) * limb
     return None, 0
@@ -315,11 +315,22 @@ def run_ours(args):
         step(k)
     prof = g.he_profile_read(ctx)
     g.he_profile(ctx, False)
-    per_kernel = {k: {"ms_total": v[0], "calls": v[1], "ms_avg": v[0] / v[1]} for k, v in prof.items()}
+    per_kernel = {}
+    for k, v in prof.items():
+        kind, work = kernel_work(k, ctx.prm, level)
+        d = {"ms_total": v[0], "calls": v[1], "ms_avg": v[0] / v[1], "kind": kind}
+        if kind == "alu":
+            d["Gbutterfly_s"] = work / (d["ms_avg"] * 1e-3) / 1e9
+        elif kind == "hbm":
+            d["GB_s"] = work / (d["ms_avg"] * 1e-3) / 1e9
+        elif kind == "mac":
+            d["GMAC_s"] = work / (d["ms_avg"] * 1e-3) / 1e9
+        per_kernel[k] = d
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_total"]) if per_kernel else None
 
     # ALU ceiling: register-resident butterfly probe
     bfly_peak = g.he_probe_butterfly_rate(152 * 8, 4096, stream)
+    probe = {"butterfly_per_s": bfly_peak}
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -335,6 +346,13 @@ def run_ours(args):
             roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": bfly_peak / 1e9,
                     "unit": "Gbutterfly/s", "frac": ach / (bfly_peak / 1e9), "traffic": None,
                     "peak_source": "measured: register-resident lazy Shoup butterfly probe (he_probe_butterfly_rate)"}
+        elif kind == "mac":
+            # one base-conversion MAC is four 32x32->64 multiply-adds; the
+            # butterfly probe's Shoup product is ten multiplies
+            ach = work / avg_s / 1e9
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": 2.5 * bfly_peak / 1e9,
+                    "unit": "GMAC/s", "frac": ach / (2.5 * bfly_peak / 1e9), "traffic": None,
+                    "peak_source": "derived: 2.5 x measured butterfly probe rate (multiply count ratio 10:4)"}
         elif kind == "hbm":
             ach = work / avg_s / 1e9
             roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
@@ -371,6 +389,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof,
             "inner_product_hbm": ip,
+            "probe": probe,
             "kernels": per_kernel,
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -384,8 +403,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n16", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")

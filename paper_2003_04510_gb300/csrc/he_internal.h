@@ -39,7 +39,7 @@ struct NttJob {
 struct DevLevel {
     int l, beta, E, A;             // level, digits, K+l, alpha padded for the kernels
     int dig_lo[kMaxDigits], dig_n[kMaxDigits];
-    const u64 *modupB;             // [beta][E][A]: [Qhat_{j,i}]_t (0 for own-digit rows)
+    const u64 *modupB;             // [beta][E][A]: [Qhat_{j,i}]_t split at bit 28 (0 for own-digit rows)
     const ulonglong2 *qinv_last;   // [l-1]: q_{l-1}^-1 mod q_i (value, Shoup)
     const ulonglong2 *pinv_qinv;   // [l-1]: P^-1 * q_{l-1}^-1 mod q_i
 };
@@ -81,7 +81,7 @@ struct he_ctx {
     std::vector<std::vector<u64>> w, wsh, iw, iwsh;  // [E][N]
     std::vector<u64> ninv, ninv_sh;                  // [E]
     // level-independent ModDown constants
-    std::vector<u64> PB;                 // [L][K]: [Phat_k]_{q_i}
+    std::vector<u64> PB;                 // [L][K]: [Phat_k]_{q_i}, split at bit 28
     std::vector<ulonglong2> pinv;        // [L]: P^-1 mod q_i
     std::vector<ulonglong2> phat_inv;    // [K]: Phat_k^-1 mod p_k
     std::vector<he::HostLevel> host_levels;  // index l (1..L)

@@ -57,6 +57,9 @@ static u64 smallest_psi(u64 q, int logN)
 
 static ulonglong2 pair(u64 v, u64 m) { return make_ulonglong2(v, shoup(v, m)); }
 
+// base-conversion constant stored split at bit 28 for the kernels' lazy MACs
+static u64 split28(u64 b) { return (b & 0xFFFFFFFull) | ((b >> 28) << 32); }
+
 static WsLayout layout_for(int l, int K, int alpha)
 {
     int beta = (l + alpha - 1) / alpha;
@@ -152,7 +155,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
             u64 v = 1;
             for (int k2 = 0; k2 < K; k2++)
                 if (k2 != k) v = mul(v, c->ext[k2] % qi, qi);
-            c->PB[(size_t)i * K + k] = v;
+            c->PB[(size_t)i * K + k] = split28(v);
             P = mul(P, c->ext[k] % qi, qi);
         }
         c->pinv[i] = pair(inv(P, qi), qi);
@@ -186,7 +189,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
                     u64 v = 1;
                     for (int i2 = lo; i2 < hi; i2++)
                         if (i2 != i) v = mul(v, c->ext[K + i2] % t, t);
-                    H.modupB[((size_t)j * El + e) * A + (i - lo)] = v;
+                    H.modupB[((size_t)j * El + e) * A + (i - lo)] = split28(v);
                 }
                 H.ntt_up.push_back(NttJob{(unsigned)(W.u + (size_t)j * El + e), (unsigned)(W.u + (size_t)j * El + e),
                                           (unsigned)e, 0, 0, 0});

@@ -6,8 +6,9 @@
 //                  shape of Algo 5 / Algo 1 as a fast base conversion
 //                  U_j[t] = sum_{i in I_j} y_i [Qhat_{j,i}]_t mod t, with the
 //                  y_i = x_i Qhat^-1 factor already applied by the iNTT.
-//                  128-bit lazy accumulation, one reduction per output (the
-//                  paper's delayed-modulo idea for CRT, Sec. 5.3).
+//                  Lazy accumulation (the paper's delayed-modulo idea for
+//                  CRT, Sec. 5.3): operands split at bit 28, four 32x32->64
+//                  multiply-adds per term, one Barrett reduction per output.
 //  k_inner_product Region 2 of Fig. 2: KS_{b,a}[t] = sum_j U_j[t] evk_j.{b,a}[t].
 //  k_moddown_conv  mod down (Sec. 7): conv_i = sum_k y_k [Phat_k]_{q_i} mod q_i;
 //                  the fused variant also folds in the rescale residue.
@@ -15,6 +16,8 @@
 //
 // Every kernel handles two consecutive coefficients per thread with 16-byte
 // loads and stores; the limb-major layouts keep all accesses coalesced.
+#include <algorithm>
+
 #include "he_internal.h"
 #include "modarith.cuh"
 
@@ -45,8 +48,11 @@ k_tensor(const u64 *__restrict__ ct1, const u64 *__restrict__ ct2, u64 *__restri
     st2(d2 + (size_t)i * N + n, mul_mod(a1.x, a2.x, pr.q, pr.mu, pr.s), mul_mod(a1.y, a2.y, pr.q, pr.mu, pr.s));
 }
 
-// grid: x over N/2/kThreads, y over digits.  y: [l][N] (scaled iNTT of d2),
-// U: [beta][E][N].
+// grid: x over N/2/kThreads, y over digits, z over chunks of kModupChunk
+// targets.  y: [l][N] (scaled iNTT of d2), U: [beta][E][N].  Target u of
+// digit j (u < E - n_j) is ext limb u below the digit's own limbs, u + n_j above.
+constexpr int kModupChunk = 8;
+
 template <int A>
 __global__ void __launch_bounds__(kThreads)
 k_modup(const u64 *__restrict__ y, u64 *__restrict__ U, const DevLevel *__restrict__ lv_arr, int l,
@@ -56,34 +62,39 @@ k_modup(const u64 *__restrict__ y, u64 *__restrict__ U, const DevLevel *__restri
     const int j = blockIdx.y;
     const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
     const int E = lv.E;
+    const int u0 = blockIdx.z * kModupChunk;
+    const int u1 = min(u0 + kModupChunk, E - nj);
+    if (u0 >= u1) return;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
-    u64 yx[A], yy[A];
+    uint32_t x0[A], x1[A], z0[A], z1[A];
 #pragma unroll
     for (int i = 0; i < A; i++) {
+        u64 vx = 0, vy = 0;
         if (i < nj) {
             ulonglong2 v = ld2(y + (size_t)(lo + i) * N + n);
-            yx[i] = v.x;
-            yy[i] = v.y;
-        } else {
-            yx[i] = yy[i] = 0;
+            vx = v.x;
+            vy = v.y;
         }
+        split28(vx, x0[i], x1[i]);
+        split28(vy, z0[i], z1[i]);
     }
     const u64 *B = lv.modupB + (size_t)j * E * lv.A;
     u64 *Uj = U + (size_t)j * E * N;
-    for (int e = 0; e < E; e++) {
-        if (e >= K && e - K >= lo && e - K < lo + nj) continue;  // own digit: d2 is reused
+    for (int u = u0; u < u1; u++) {
+        const int e = u < K + lo ? u : u + nj;
         const DevPrime pr = primes[e];
         const u64 *b = B + (size_t)e * lv.A;
-        U128 ax = {0, 0}, ay = {0, 0};
+        Acc3 ax = {0, 0, 0}, ay = {0, 0, 0};
 #pragma unroll
         for (int i = 0; i < A; i++) {
             if (i < nj) {
                 const u64 c = __ldg(b + i);
-                mac(ax, yx[i], c);
-                mac(ay, yy[i], c);
+                mac28(ax, x0[i], x1[i], c);
+                mac28(ay, z0[i], z1[i], c);
             }
         }
-        st2(Uj + (size_t)e * N + n, barrett128(ax, pr.q, pr.mu, pr.s), barrett128(ay, pr.q, pr.mu, pr.s));
+        st2(Uj + (size_t)e * N + n, barrett128(acc3_value(ax), pr.q, pr.mu, pr.s),
+            barrett128(acc3_value(ay), pr.q, pr.mu, pr.s));
     }
 }
 
@@ -116,10 +127,30 @@ k_inner_product(const u64 *__restrict__ U, const u64 *__restrict__ d2, const u64
     st2(KS + ((size_t)E + e) * N + n, barrett128(ax, pr.q, pr.mu, pr.s), barrett128(ay, pr.q, pr.mu, pr.s));
 }
 
-// grid: x over N/2/kThreads, y over h in {0,1}.  ys: [2][K] coefficient form
-// (already times Phat_k^-1).  PLAIN: z[h][i] = conv_i for i < l.
+// grid: x over N/2/kThreads, y over h in {0,1}, z over chunks of
+// kModdownChunk outputs.  ys: [2][K] coefficient form (already times
+// Phat_k^-1).  PLAIN: z[h][i] = conv_i for i < l.
 // FUSED: r = r0 + (r1 - conv_{l-1}) P^-1 mod q_{l-1} with r0 = iNTT(d_h)_{l-1},
 // r1 = iNTT(KS_h)_{l-1}; z[h][i] = conv_i P^-1 + r mod q_i for i < l-1.
+constexpr int kModdownChunk = 8;
+
+template <int KM>
+__device__ __forceinline__ void conv_one(const uint32_t *x0, const uint32_t *x1, const uint32_t *z0,
+                                         const uint32_t *z1, const u64 *__restrict__ b, int K, const DevPrime &pr,
+                                         u64 &cx, u64 &cy)
+{
+    Acc3 ax = {0, 0, 0}, ay = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < KM; k++)
+        if (k < K) {
+            const u64 c = __ldg(b + k);
+            mac28(ax, x0[k], x1[k], c);
+            mac28(ay, z0[k], z1[k], c);
+        }
+    cx = barrett128(acc3_value(ax), pr.q, pr.mu, pr.s);
+    cy = barrett128(acc3_value(ay), pr.q, pr.mu, pr.s);
+}
+
 template <int KM, bool FUSED>
 __global__ void __launch_bounds__(kThreads)
 k_moddown_conv(const u64 *__restrict__ ys, const u64 *__restrict__ rr, u64 *__restrict__ z,
@@ -127,50 +158,38 @@ k_moddown_conv(const u64 *__restrict__ ys, const u64 *__restrict__ rr, u64 *__re
                int K, int l, int N)
 {
     const int h = blockIdx.y;
+    const int nout = FUSED ? l - 1 : l;
+    const int i0 = blockIdx.z * kModdownChunk;
+    const int i1 = min(i0 + kModdownChunk, nout);
+    if (i0 >= i1) return;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
-    u64 vx[KM], vy[KM];
+    uint32_t x0[KM], x1[KM], z0[KM], z1[KM];
 #pragma unroll
     for (int k = 0; k < KM; k++) {
+        u64 vx = 0, vy = 0;
         if (k < K) {
             ulonglong2 v = ld2(ys + ((size_t)h * K + k) * N + n);
-            vx[k] = v.x;
-            vy[k] = v.y;
-        } else {
-            vx[k] = vy[k] = 0;
+            vx = v.x;
+            vy = v.y;
         }
+        split28(vx, x0[k], x1[k]);
+        split28(vy, z0[k], z1[k]);
     }
     u64 rx = 0, ry = 0;
-    const int nout = FUSED ? l - 1 : l;
     if (FUSED) {
         const int i = l - 1;
         const DevPrime pr = primes[K + i];
-        const u64 *b = PB + (size_t)i * K;
-        U128 ax = {0, 0}, ay = {0, 0};
-#pragma unroll
-        for (int k = 0; k < KM; k++)
-            if (k < K) {
-                const u64 c = __ldg(b + k);
-                mac(ax, vx[k], c);
-                mac(ay, vy[k], c);
-            }
-        const u64 cx = barrett128(ax, pr.q, pr.mu, pr.s), cy = barrett128(ay, pr.q, pr.mu, pr.s);
+        u64 cx, cy;
+        conv_one<KM>(x0, x1, z0, z1, PB + (size_t)i * K, K, pr, cx, cy);
         ulonglong2 r0 = ld2(rr + (size_t)h * N + n), r1 = ld2(rr + (size_t)(2 + h) * N + n);
         const ulonglong2 pv = pinv[i];
         rx = add_mod(r0.x, shoup(sub_mod(r1.x, cx, pr.q), pv.x, pv.y, pr.q), pr.q);
         ry = add_mod(r0.y, shoup(sub_mod(r1.y, cy, pr.q), pv.x, pv.y, pr.q), pr.q);
     }
-    for (int i = 0; i < nout; i++) {
+    for (int i = i0; i < i1; i++) {
         const DevPrime pr = primes[K + i];
-        const u64 *b = PB + (size_t)i * K;
-        U128 ax = {0, 0}, ay = {0, 0};
-#pragma unroll
-        for (int k = 0; k < KM; k++)
-            if (k < K) {
-                const u64 c = __ldg(b + k);
-                mac(ax, vx[k], c);
-                mac(ay, vy[k], c);
-            }
-        u64 cx = barrett128(ax, pr.q, pr.mu, pr.s), cy = barrett128(ay, pr.q, pr.mu, pr.s);
+        u64 cx, cy;
+        conv_one<KM>(x0, x1, z0, z1, PB + (size_t)i * K, K, pr, cx, cy);
         if (FUSED) {
             // r < q_{l-1} < q_i: r is already a residue mod q_i
             const ulonglong2 pv = pinv[i];
@@ -252,6 +271,9 @@ cudaError_t run_modup(const he_ctx *c, const u64 *y, u64 *U, int l, cudaStream_t
 {
     dim3 g = grid_x(c->N);
     g.y = (l + c->alpha - 1) / c->alpha;
+    const int beta = (l + c->alpha - 1) / c->alpha;
+    const int ntarget = c->K + (beta - 1) * c->alpha;  // targets of the shortest (last) digit: the most
+    g.z = (ntarget + kModupChunk - 1) / kModupChunk;
     const int a = c->alpha;
 #define HE_MODUP(AA) k_modup<AA><<<g, kThreads, 0, st>>>(y, U, c->d_levels, l, c->d_primes, c->K, c->N)
     if (a <= 1) HE_MODUP(1);
@@ -278,6 +300,7 @@ cudaError_t run_moddown_conv(const he_ctx *c, const u64 *ys, const u64 *rr, u64 
 {
     dim3 g = grid_x(c->N);
     g.y = 2;
+    g.z = ((fused ? l - 1 : l) + kModdownChunk - 1) / kModdownChunk;
     const int K = c->K;
 #define HE_MD(KK)                                                                                                  \
     do {                                                                                                           \

@@ -66,3 +66,40 @@ __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, u64 q, u64 mu, unsigned s)
 {
     return barrett128(mul_wide(a, b), q, mu, s);
 }
+
+// Lazy dot products of a residue vector with constant vectors (base
+// conversion).  Operands are split at bit 28: x = x1*2^28 + x0, and the
+// constant is stored pre-split as b0 | (b1 << 32).  Each term is four
+// 32x32 -> 64-bit multiply-adds into three 64-bit accumulators with no carry
+// handling: for x, b < 2^57 and at most 16 terms every accumulator stays below
+// 2^63.  The 128-bit value is assembled once per output.
+struct Acc3 {
+    u64 a0, a1, a2;  // weights 1, 2^28, 2^56
+};
+
+__device__ __forceinline__ void split28(u64 x, uint32_t &x0, uint32_t &x1)
+{
+    x0 = (uint32_t)(x & 0xFFFFFFFull);
+    x1 = (uint32_t)(x >> 28);
+}
+
+__device__ __forceinline__ void mac28(Acc3 &s, uint32_t x0, uint32_t x1, u64 bpacked)
+{
+    const uint32_t b0 = (uint32_t)bpacked, b1 = (uint32_t)(bpacked >> 32);
+    s.a0 += (u64)x0 * b0;
+    s.a1 += (u64)x0 * b1;
+    s.a1 += (u64)x1 * b0;
+    s.a2 += (u64)x1 * b1;
+}
+
+__device__ __forceinline__ U128 acc3_value(const Acc3 &s)
+{
+    U128 v;
+    const u64 t1 = s.a1 << 28, t2 = s.a2 << 56;
+    v.lo = s.a0 + t1;
+    u64 c = v.lo < t1 ? 1ull : 0ull;
+    v.lo += t2;
+    c += v.lo < t2 ? 1ull : 0ull;
+    v.hi = (s.a1 >> 36) + (s.a2 >> 8) + c;
+    return v;
+}
