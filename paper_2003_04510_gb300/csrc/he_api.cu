@@ -41,13 +41,13 @@ size_t ws_bytes_for(const he_ctx *c, int l) { return c->host_levels[l].ws.total 
 int check_dev(const he_ctx *c) { return (c && c->device) ? HE_OK : HE_EINVAL; }
 
 // Upload a small job list for the per-step entry points (test helpers).
-int with_jobs(const std::vector<NttJob> &jobs, cudaStream_t st, NttJob **out)
+int with_jobs(const std::vector<NttGroup> &jobs, cudaStream_t st, NttGroup **out)
 {
     void *p = nullptr;
-    if (cudaMallocAsync(&p, sizeof(NttJob) * jobs.size(), st) != cudaSuccess) return HE_ECUDA;
-    if (cudaMemcpyAsync(p, jobs.data(), sizeof(NttJob) * jobs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    if (cudaMallocAsync(&p, sizeof(NttGroup) * jobs.size(), st) != cudaSuccess) return HE_ECUDA;
+    if (cudaMemcpyAsync(p, jobs.data(), sizeof(NttGroup) * jobs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return HE_ECUDA;
-    *out = (NttJob *)p;
+    *out = (NttGroup *)p;
     return HE_OK;
 }
 
@@ -202,10 +202,11 @@ int he_step_ntt(he_ctx *c, uint64_t *data, const int *prime_idx, int count, int 
         jobs[i] = NttJob{(unsigned)i, (unsigned)i, (unsigned)e, 0, c->ninv[e], c->ninv_sh[e]};
     }
     cudaStream_t st = S(stream);
-    NttJob *dj = nullptr;
-    int rc = with_jobs(jobs, st, &dj);
+    std::vector<NttGroup> groups = group_jobs(jobs);
+    NttGroup *dj = nullptr;
+    int rc = with_jobs(groups, st, &dj);
     if (rc) return rc;
-    cudaError_t e = launch_ntt(c, (u64 *)data, dj, count, inverse != 0, st);
+    cudaError_t e = launch_ntt(c, (u64 *)data, dj, (int)groups.size(), inverse != 0, st);
     cudaFreeAsync(dj, st);
     return e == cudaSuccess ? HE_OK : HE_ECUDA;
 }

@@ -35,6 +35,18 @@ struct NttJob {
     u64 scale, scale_sh;
 };
 
+// What the NTT kernels consume: up to kGroupMax limb transforms that share a
+// prime, so one CTA stages that prime's twiddles once and reuses them.
+constexpr int kGroupMax = 4;
+struct NttGroup {
+    unsigned prime, nl, pad0, pad1;
+    unsigned src[kGroupMax], dst[kGroupMax];
+    u64 scale[kGroupMax], scale_sh[kGroupMax];
+};
+
+// Group single-limb jobs by prime (order within a prime is kept).
+std::vector<NttGroup> group_jobs(const std::vector<NttJob> &jobs);
+
 // Per-level constants on the device.
 struct DevLevel {
     int l, beta, E, A;             // level, digits, K+l, alpha padded for the kernels
@@ -51,15 +63,15 @@ struct WsLayout {
 
 // Job lists of one level, stored in the context's device arena.
 struct LevelJobs {
-    const NttJob *intt1;    int n_intt1;     // d2 -> y          (+2 fused: d0,d1 last limb -> r[0..1])
-    const NttJob *intt1f;   int n_intt1f;    // fused variant
-    const NttJob *ntt_up;   int n_ntt_up;    // ModUp outputs, in place
-    const NttJob *intt2;    int n_intt2;     // KS specials -> ys (scaled by N^-1 Phat^-1)
-    const NttJob *intt2f;   int n_intt2f;    // + KS last limb -> r[2..3]
-    const NttJob *ntt_conv; int n_ntt_conv;  // 2l conv limbs (plain ModDown)
-    const NttJob *ntt_z;    int n_ntt_z;     // 2(l-1) z limbs (fused ModDown + rescale)
-    const NttJob *rs_intt;  int n_rs_intt;   // rescale: last limb of b, a -> r
-    const NttJob *rs_ntt;   int n_rs_ntt;    // rescale: r -> z_i
+    const NttGroup *intt1;    int n_intt1;     // d2 -> y          (+2 fused: d0,d1 last limb -> r[0..1])
+    const NttGroup *intt1f;   int n_intt1f;    // fused variant
+    const NttGroup *ntt_up;   int n_ntt_up;    // ModUp outputs, in place
+    const NttGroup *intt2;    int n_intt2;     // KS specials -> ys (scaled by N^-1 Phat^-1)
+    const NttGroup *intt2f;   int n_intt2f;    // + KS last limb -> r[2..3]
+    const NttGroup *ntt_conv; int n_ntt_conv;  // 2l conv limbs (plain ModDown)
+    const NttGroup *ntt_z;    int n_ntt_z;     // 2(l-1) z limbs (fused ModDown + rescale)
+    const NttGroup *rs_intt;  int n_rs_intt;   // rescale: last limb of b, a -> r
+    const NttGroup *rs_ntt;   int n_rs_ntt;    // rescale: r -> z_i
 };
 
 struct HostLevel {
@@ -110,10 +122,10 @@ int build_context(he_ctx *ctx, const he_params *p, bool device);
 // Record a profiling mark named after the kernel that just finished (no-op
 // unless profiling is enabled on the context).
 void prof_mark(const he_ctx *ctx, cudaStream_t st, const char *tag, const char *suffix = nullptr);
-cudaError_t launch_ntt(const he_ctx *ctx, u64 *base, const NttJob *jobs, int njobs, bool inverse,
+cudaError_t launch_ntt(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, bool inverse,
                        cudaStream_t st, const char *tag = nullptr);
-cudaError_t launch_ntt2(const he_ctx *ctx, const u64 *src, u64 *dst, const NttJob *jobs, int njobs, bool inverse,
-                        cudaStream_t st, const char *tag = nullptr);
+cudaError_t launch_ntt2(const he_ctx *ctx, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups,
+                        bool inverse, cudaStream_t st, const char *tag = nullptr);
 cudaError_t run_tensor(const he_ctx *c, const u64 *ct1, const u64 *ct2, u64 *d0, u64 *d1, u64 *d2, int l,
                        cudaStream_t st);
 cudaError_t run_modup(const he_ctx *c, const u64 *y, u64 *U, int l, cudaStream_t st);

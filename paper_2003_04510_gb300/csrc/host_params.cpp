@@ -60,6 +60,31 @@ static ulonglong2 pair(u64 v, u64 m) { return make_ulonglong2(v, shoup(v, m)); }
 // base-conversion constant stored split at bit 28 for the kernels' lazy MACs
 static u64 split28(u64 b) { return (b & 0xFFFFFFFull) | ((b >> 28) << 32); }
 
+std::vector<NttGroup> group_jobs(const std::vector<NttJob> &jobs)
+{
+    std::vector<NttGroup> out;
+    std::vector<int> open_for_prime;  // index into out of the group being filled, per prime
+    for (const NttJob &j : jobs) {
+        if (j.prime >= open_for_prime.size()) open_for_prime.resize(j.prime + 1, -1);
+        int g = open_for_prime[j.prime];
+        if (g < 0 || out[g].nl == (unsigned)kGroupMax) {
+            NttGroup ng;
+            memset(&ng, 0, sizeof(ng));
+            ng.prime = j.prime;
+            out.push_back(ng);
+            g = (int)out.size() - 1;
+            open_for_prime[j.prime] = g;
+        }
+        NttGroup &G = out[g];
+        G.src[G.nl] = j.src;
+        G.dst[G.nl] = j.dst;
+        G.scale[G.nl] = j.scale;
+        G.scale_sh[G.nl] = j.scale_sh;
+        G.nl++;
+    }
+    return out;
+}
+
 static WsLayout layout_for(int l, int K, int alpha)
 {
     int beta = (l + alpha - 1) / alpha;
@@ -256,6 +281,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
     const size_t o_levels = take(sizeof(DevLevel) * (L + 1));
     struct LvlOff { size_t modupB, qinv, pq, j[9]; };
     std::vector<LvlOff> lo(L + 1);
+    std::vector<std::vector<std::vector<NttGroup>>> gl(L + 1, std::vector<std::vector<NttGroup>>(9));
     for (int l = 1; l <= L; l++) {
         HostLevel &H = c->host_levels[l];
         lo[l].modupB = take(sizeof(u64) * H.modupB.size());
@@ -263,7 +289,10 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         lo[l].pq = take(sizeof(ulonglong2) * H.pinv_qinv.size());
         const std::vector<NttJob> *lists[9] = {&H.intt1, &H.intt1f, &H.ntt_up, &H.intt2, &H.intt2f,
                                                &H.ntt_conv, &H.ntt_z, &H.rs_intt, &H.rs_ntt};
-        for (int t = 0; t < 9; t++) lo[l].j[t] = take(sizeof(NttJob) * std::max<size_t>(1, lists[t]->size()));
+        for (int t = 0; t < 9; t++) {
+            gl[l][t] = group_jobs(*lists[t]);
+            lo[l].j[t] = take(sizeof(NttGroup) * std::max<size_t>(1, gl[l][t].size()));
+        }
     }
     c->arena_bytes = off;
     if (cudaGetDevice(&c->device_id) != cudaSuccess) return HE_ECUDA;
@@ -311,23 +340,24 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         D.modupB = (const u64 *)(base + lo[l].modupB);
         D.qinv_last = (const ulonglong2 *)(base + lo[l].qinv);
         D.pinv_qinv = (const ulonglong2 *)(base + lo[l].pq);
-        const std::vector<NttJob> *lists[9] = {&H.intt1, &H.intt1f, &H.ntt_up, &H.intt2, &H.intt2f,
-                                               &H.ntt_conv, &H.ntt_z, &H.rs_intt, &H.rs_ntt};
-        const NttJob *dptr[9];
+        const NttGroup *dptr[9];
+        int cnt[9];
         for (int t = 0; t < 9; t++) {
-            if (!lists[t]->empty()) memcpy(img.data() + lo[l].j[t], lists[t]->data(), sizeof(NttJob) * lists[t]->size());
-            dptr[t] = (const NttJob *)(base + lo[l].j[t]);
+            const std::vector<NttGroup> &G = gl[l][t];
+            if (!G.empty()) memcpy(img.data() + lo[l].j[t], G.data(), sizeof(NttGroup) * G.size());
+            dptr[t] = (const NttGroup *)(base + lo[l].j[t]);
+            cnt[t] = (int)G.size();
         }
         LevelJobs &J = c->jobs[l];
-        J.intt1 = dptr[0];    J.n_intt1 = (int)H.intt1.size();
-        J.intt1f = dptr[1];   J.n_intt1f = (int)H.intt1f.size();
-        J.ntt_up = dptr[2];   J.n_ntt_up = (int)H.ntt_up.size();
-        J.intt2 = dptr[3];    J.n_intt2 = (int)H.intt2.size();
-        J.intt2f = dptr[4];   J.n_intt2f = (int)H.intt2f.size();
-        J.ntt_conv = dptr[5]; J.n_ntt_conv = (int)H.ntt_conv.size();
-        J.ntt_z = dptr[6];    J.n_ntt_z = (int)H.ntt_z.size();
-        J.rs_intt = dptr[7];  J.n_rs_intt = (int)H.rs_intt.size();
-        J.rs_ntt = dptr[8];   J.n_rs_ntt = (int)H.rs_ntt.size();
+        J.intt1 = dptr[0];    J.n_intt1 = cnt[0];
+        J.intt1f = dptr[1];   J.n_intt1f = cnt[1];
+        J.ntt_up = dptr[2];   J.n_ntt_up = cnt[2];
+        J.intt2 = dptr[3];    J.n_intt2 = cnt[3];
+        J.intt2f = dptr[4];   J.n_intt2f = cnt[4];
+        J.ntt_conv = dptr[5]; J.n_ntt_conv = cnt[5];
+        J.ntt_z = dptr[6];    J.n_ntt_z = cnt[6];
+        J.rs_intt = dptr[7];  J.n_rs_intt = cnt[7];
+        J.rs_ntt = dptr[8];   J.n_rs_ntt = cnt[8];
     }
     memcpy(img.data() + o_levels, c->dev_levels.data(), sizeof(DevLevel) * (L + 1));
     if (cudaMemcpy(c->arena, img.data(), off, cudaMemcpyHostToDevice) != cudaSuccess) return HE_ECUDA;

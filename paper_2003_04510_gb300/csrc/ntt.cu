@@ -4,18 +4,29 @@
 // TB_W[m + j] = psi^bitrev(m + j), bit-reversed output) with Algo 4's
 // butterfly, and its inverse (Gentleman-Sande with TB_invW, then N^-1).
 // GPU mapping (the paper's high-radix idea, Sec. 5.3, rebuilt for 64-bit
-// words): log N stages are split into two passes over HBM (one for N = 2^12);
-// a pass works on 4096-element tiles held in shared memory and runs its
-// stages as rounds of radix-2^r butterflies in registers, one shared-memory
-// exchange per round.  Butterflies are Harvey's lazy forms: forward values
-// stay in [0, 4q), inverse values in [0, 2q); the last pass reduces to
-// [0, q) and, for the inverse, multiplies by N^-1 times a per-limb constant.
+// words): the log N stages are split into two passes over memory (one for
+// N = 2^12).  A pass works on tiles of TE elements held in shared memory and
+// runs its stages as rounds of radix-2^r butterflies in registers, one
+// shared-memory exchange per round.  Butterflies are Harvey's lazy forms:
+// forward values stay in [0, 4q), inverse values in [0, 2q); the last pass
+// reduces to [0, q) and, for the inverse, multiplies by N^-1 times a per-limb
+// constant.
+//
+// Memory side: a CTA takes one tile position of a group of up to four limbs
+// that share a prime.  The tile's twiddles are copied into shared memory once
+// (cp.async) and reused for every limb of the group; the limbs' data tiles are
+// double-buffered with cp.async so the next limb loads while this one computes.
 //
 // Stage / twiddle indexing.  Global stage sigma (m = 2^sigma) pairs j and
 // j + N/2^(sigma+1) and uses twiddle m + floor(j / 2^(logN - sigma)).  A pass
 // covering stages [s0, s0 + M) sees element j = G * 2^(logN - s0) + k * C + c
 // (k < 2^M the in-group index, c < C the column, G the group's high bits); at
 // local stage l the twiddle index is 2^(s0+l) + (G << l) + (k >> (M - l)).
+// In the strided (first forward / last inverse) pass s0 = 0 and G = 0, so
+// every tile uses twiddles [1, 2^M); in the contiguous pass the tile's groups
+// [g0, g0 + NG) use, per stage l, the run [2^(s0+l) + g0 2^l, + NG 2^l).
+#include <cuda_pipeline_primitives.h>
+
 #include "he_internal.h"
 #include "modarith.cuh"
 
@@ -23,18 +34,15 @@ namespace he {
 
 namespace {
 
-constexpr int kTE = 4096;                  // elements per tile
-constexpr int kSmem = kTE + kTE / 16;      // one pad word every 16 elements
-
 __device__ __forceinline__ int padi(int e) { return e + (e >> 4); }
 
 struct NttArgs {
-    const u64 *src;      // base of job.src offsets
-    u64 *dst;            // base of job.dst offsets
-    const NttJob *jobs;
+    const u64 *src;  // base of group.src offsets
+    u64 *dst;        // base of group.dst offsets
+    const NttGroup *groups;
     const DevPrime *primes;
     int logN;
-    int tiles;           // tiles per job
+    int tiles;       // tiles per limb
 };
 
 __device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, ulonglong2 w, u64 q, u64 q2)
@@ -54,14 +62,32 @@ __device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, ulonglong2 w, u64 q, u64
     x = s;
 }
 
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+template <int LOGM, int TE, bool STRIDED>
+struct Geometry {
+    static constexpr int M = 1 << LOGM;
+    static constexpr int NG = TE / M;                           // groups (or columns) per tile
+    static constexpr int TWN = STRIDED ? M - 1 : NG * (M - 1);  // twiddle pairs staged per tile
+    static constexpr int DATA = TE + TE / 16;                   // padded words per data buffer
+    static constexpr size_t SMEM = sizeof(ulonglong2) * TWN + sizeof(u64) * 2 * DATA;
+};
+
+// Shared-memory twiddle slot of local stage l, group grp, offset x.
+template <int LOGM, int TE, bool STRIDED>
+__device__ __forceinline__ int tw_slot(int l, int grp, int x)
+{
+    if (STRIDED) return (1 << l) - 1 + x;
+    return Geometry<LOGM, TE, STRIDED>::NG * ((1 << l) - 1) + (grp << l) + x;
+}
+
 // One round of R stages [l0, l0 + R) on every register set of the tile.
-template <int LOGM, int R, bool STRIDED, bool INV, int NT>
-__device__ __forceinline__ void ntt_round(u64 *sm, int l0, int s0, int gbase, const ulonglong2 *__restrict__ tw,
-                                          u64 q, u64 q2)
+template <int LOGM, int TE, int R, bool STRIDED, bool INV, int NT>
+__device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *tw, int l0, u64 q, u64 q2)
 {
     constexpr int M = 1 << LOGM;
-    constexpr int NG = kTE / M;
-    constexpr int SETS = kTE >> R;
+    constexpr int NG = TE / M;
+    constexpr int SETS = TE >> R;
     const int lo_bits = LOGM - l0 - R;
     for (int s = threadIdx.x; s < SETS; s += NT) {
         int grp, khi, klo;
@@ -85,31 +111,28 @@ __device__ __forceinline__ void ntt_round(u64 *sm, int l0, int s0, int gbase, co
             int e = STRIDED ? k * NG + grp : grp * M + k;
             a[v] = sm[padi(e)];
         }
-        const int G = STRIDED ? 0 : gbase + grp;
         if (!INV) {
 #pragma unroll
             for (int lp = 0; lp < R; lp++) {
                 const int l = l0 + lp;
-                const int tb = (1 << (s0 + l)) + (G << l) + (khi << lp);
+                const int tb = tw_slot<LOGM, TE, STRIDED>(l, grp, khi << lp);
                 const int h = 1 << (R - 1 - lp);
 #pragma unroll
                 for (int v = 0; v < (1 << R); v++) {
                     if (v & h) continue;
-                    ulonglong2 w = __ldg(&tw[tb + (v >> (R - lp))]);
-                    ct_bfly(a[v], a[v + h], w, q, q2);
+                    ct_bfly(a[v], a[v + h], tw[tb + (v >> (R - lp))], q, q2);
                 }
             }
         } else {
 #pragma unroll
             for (int lp = R - 1; lp >= 0; lp--) {
                 const int l = l0 + lp;
-                const int tb = (1 << (s0 + l)) + (G << l) + (khi << lp);
+                const int tb = tw_slot<LOGM, TE, STRIDED>(l, grp, khi << lp);
                 const int h = 1 << (R - 1 - lp);
 #pragma unroll
                 for (int v = 0; v < (1 << R); v++) {
                     if (v & h) continue;
-                    ulonglong2 w = __ldg(&tw[tb + (v >> (R - lp))]);
-                    gs_bfly(a[v], a[v + h], w, q, q2);
+                    gs_bfly(a[v], a[v + h], tw[tb + (v >> (R - lp))], q, q2);
                 }
             }
         }
@@ -122,152 +145,187 @@ __device__ __forceinline__ void ntt_round(u64 *sm, int l0, int s0, int gbase, co
     }
 }
 
-__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+// global index of tile element e
+template <int LOGM, int TE, bool STRIDED>
+__device__ __forceinline__ size_t tile_gi(int e, int tile, int stride)
+{
+    constexpr int NG = TE / (1 << LOGM);
+    if (STRIDED) return (size_t)(e / NG) * stride + (size_t)tile * NG + (e % NG);
+    return (size_t)tile * TE + e;
+}
 
-// One pass of LOGM stages.  Rounds RA, RB, RC (RC may be 0) in forward order;
-// the inverse runs them in reverse.  FIRST: read job.src (else job.dst);
-// LAST: apply the output reduction / scaling.
-template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST>
-__global__ void __launch_bounds__(kTE >> cmax(RA, cmax(RB, RC)))
+// One pass of LOGM stages over a group of limbs.  Rounds RA, RB, RC (RC may
+// be 0) in forward order; the inverse runs them in reverse.  FIRST: read
+// group.src (else group.dst); LAST: apply the output reduction / scaling.
+template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE>
+__global__ void __launch_bounds__(TE >> cmax(RA, cmax(RB, RC)))
 k_ntt_pass(const NttArgs P)
 {
-    constexpr int NT = kTE >> cmax(RA, cmax(RB, RC));
-    constexpr int M = 1 << LOGM;
-    constexpr int NG = kTE / M;
+    constexpr int NT = TE >> cmax(RA, cmax(RB, RC));
+    using Gm = Geometry<LOGM, TE, STRIDED>;
+    constexpr int NG = Gm::NG;
     static_assert(RA + RB + RC == LOGM, "rounds must cover the pass");
-    __shared__ u64 sm[kSmem];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ulonglong2 *tw = reinterpret_cast<ulonglong2 *>(smem_raw);
+    u64 *buf = reinterpret_cast<u64 *>(smem_raw + sizeof(ulonglong2) * Gm::TWN);
 
-    const int job = blockIdx.x / P.tiles;
-    const int tile = blockIdx.x - job * P.tiles;
-    const NttJob J = P.jobs[job];
-    const DevPrime pr = P.primes[J.prime];
+    const int gidx = blockIdx.x / P.tiles;
+    const int tile = blockIdx.x - gidx * P.tiles;
+    const NttGroup &G = P.groups[gidx];
+    const int nl = (int)G.nl;
+    const DevPrime pr = P.primes[G.prime];
     const int N = 1 << P.logN;
-    const u64 *src = (FIRST ? P.src + (size_t)J.src * N : P.dst + (size_t)J.dst * N);
-    u64 *dst = P.dst + (size_t)J.dst * N;
-    const int stride = N >> LOGM;  // columns (strided) -- element k of column c at k*stride + c
-    const int col0 = tile * NG;    // strided: first column of the tile
-    const int g0 = tile * NG;      // contiguous: first group of the tile
+    const int stride = N >> LOGM;
     const int s0 = STRIDED ? 0 : P.logN - LOGM;
 
-    // HBM -> shared memory, coalesced 16-byte loads
-    for (int i = threadIdx.x; i < kTE / 2; i += NT) {
-        const int e = 2 * i;
-        size_t gi;
-        if (STRIDED) gi = (size_t)(e / NG) * stride + col0 + (e % NG);
-        else gi = (size_t)g0 * M + e;
-        ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(src + gi);
-        sm[padi(e)] = v.x;
-        sm[padi(e + 1)] = v.y;
-    }
-    __syncthreads();
-
-    const ulonglong2 *tw = INV ? pr.iw : pr.w;
-    if (!INV) {
-        ntt_round<LOGM, RA, STRIDED, false, NT>(sm, 0, s0, g0, tw, pr.q, pr.q2);
-        __syncthreads();
-        ntt_round<LOGM, RB, STRIDED, false, NT>(sm, RA, s0, g0, tw, pr.q, pr.q2);
-        __syncthreads();
-        if (RC) {
-            ntt_round<LOGM, (RC ? RC : 1), STRIDED, false, NT>(sm, RA + RB, s0, g0, tw, pr.q, pr.q2);
-            __syncthreads();
+    // twiddles of this tile -> shared memory (16-byte async copies)
+    const ulonglong2 *twg = INV ? pr.iw : pr.w;
+    for (int f = threadIdx.x; f < Gm::TWN; f += NT) {
+        int gsrc;
+        if (STRIDED) {
+            gsrc = 1 + f;
+        } else {
+            const int l = 31 - __clz(f / NG + 1);  // NG (2^l - 1) <= f < NG (2^(l+1) - 1)
+            const int x = f - NG * ((1 << l) - 1);
+            gsrc = (1 << (s0 + l)) + tile * NG * (1 << l) + x;
         }
-    } else {
-        if (RC) {
-            ntt_round<LOGM, (RC ? RC : 1), STRIDED, true, NT>(sm, RA + RB, s0, g0, tw, pr.q, pr.q2);
-            __syncthreads();
-        }
-        ntt_round<LOGM, RB, STRIDED, true, NT>(sm, RA, s0, g0, tw, pr.q, pr.q2);
-        __syncthreads();
-        ntt_round<LOGM, RA, STRIDED, true, NT>(sm, 0, s0, g0, tw, pr.q, pr.q2);
-        __syncthreads();
+        __pipeline_memcpy_async(&tw[f], &twg[gsrc], 16);
     }
+    // data tile of limb i of the group -> shared memory (8-byte async copies)
+    auto load_tile = [&](int i, u64 *b) {
+        const u64 *src = FIRST ? P.src + (size_t)G.src[i] * N : P.dst + (size_t)G.dst[i] * N;
+        for (int e = threadIdx.x; e < TE; e += NT)
+            __pipeline_memcpy_async(&b[padi(e)], src + tile_gi<LOGM, TE, STRIDED>(e, tile, stride), 8);
+    };
+    load_tile(0, buf);
+    __pipeline_commit();
 
-    // shared memory -> HBM, with the output reduction on the last pass
-    for (int i = threadIdx.x; i < kTE / 2; i += NT) {
-        const int e = 2 * i;
-        u64 x = sm[padi(e)], y = sm[padi(e + 1)];
-        if (LAST) {
-            if (!INV) {
-                x = csub(x >= pr.q2 ? x - pr.q2 : x, pr.q);
-                y = csub(y >= pr.q2 ? y - pr.q2 : y, pr.q);
-            } else {
-                x = shoup(x, J.scale, J.scale_sh, pr.q);
-                y = shoup(y, J.scale, J.scale_sh, pr.q);
+    for (int i = 0; i < nl; i++) {
+        u64 *sm = buf + (i & 1) * Gm::DATA;
+        if (i + 1 < nl) {
+            load_tile(i + 1, buf + ((i + 1) & 1) * Gm::DATA);
+            __pipeline_commit();
+            __pipeline_wait_prior(1);
+        } else {
+            __pipeline_wait_prior(0);
+        }
+        __syncthreads();
+        if (!INV) {
+            ntt_round<LOGM, TE, RA, STRIDED, false, NT>(sm, tw, 0, pr.q, pr.q2);
+            __syncthreads();
+            ntt_round<LOGM, TE, RB, STRIDED, false, NT>(sm, tw, RA, pr.q, pr.q2);
+            __syncthreads();
+            if (RC) {
+                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, false, NT>(sm, tw, RA + RB, pr.q, pr.q2);
+                __syncthreads();
             }
+        } else {
+            if (RC) {
+                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, true, NT>(sm, tw, RA + RB, pr.q, pr.q2);
+                __syncthreads();
+            }
+            ntt_round<LOGM, TE, RB, STRIDED, true, NT>(sm, tw, RA, pr.q, pr.q2);
+            __syncthreads();
+            ntt_round<LOGM, TE, RA, STRIDED, true, NT>(sm, tw, 0, pr.q, pr.q2);
+            __syncthreads();
         }
-        size_t gi;
-        if (STRIDED) gi = (size_t)(e / NG) * stride + col0 + (e % NG);
-        else gi = (size_t)g0 * M + e;
-        *reinterpret_cast<ulonglong2 *>(dst + gi) = make_ulonglong2(x, y);
+        // shared memory -> HBM, 16-byte stores, output reduction on the last pass
+        u64 *dst = P.dst + (size_t)G.dst[i] * N;
+        const u64 sc = G.scale[i], scs = G.scale_sh[i];
+        for (int h = threadIdx.x; h < TE / 2; h += NT) {
+            const int e = 2 * h;
+            u64 x = sm[padi(e)], y = sm[padi(e + 1)];
+            if (LAST) {
+                if (!INV) {
+                    x = csub(x >= pr.q2 ? x - pr.q2 : x, pr.q);
+                    y = csub(y >= pr.q2 ? y - pr.q2 : y, pr.q);
+                } else {
+                    x = shoup(x, sc, scs, pr.q);
+                    y = shoup(y, sc, scs, pr.q);
+                }
+            }
+            *reinterpret_cast<ulonglong2 *>(dst + tile_gi<LOGM, TE, STRIDED>(e, tile, stride)) =
+                make_ulonglong2(x, y);
+        }
+        __syncthreads();  // the next prefetch reuses this buffer
     }
 }
 
-template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST>
-cudaError_t run_pass(const NttArgs &a, int njobs, cudaStream_t st)
+template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE>
+cudaError_t run_pass(const NttArgs &a, int ngroups, cudaStream_t st)
 {
-    constexpr int NT = kTE >> cmax(RA, cmax(RB, RC));
-    k_ntt_pass<LOGM, RA, RB, RC, STRIDED, INV, FIRST, LAST><<<njobs * a.tiles, NT, 0, st>>>(a);
+    constexpr int NT = TE >> cmax(RA, cmax(RB, RC));
+    constexpr size_t smem = Geometry<LOGM, TE, STRIDED>::SMEM;
+    auto kern = k_ntt_pass<LOGM, RA, RB, RC, STRIDED, INV, FIRST, LAST, TE>;
+    static bool configured = false;  // once per instantiation
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    kern<<<ngroups * a.tiles, NT, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 // Two-pass transform: the strided pass covers the first S1 stages (forward
 // order), the contiguous pass the last S2.
 template <int S1, int A1, int B1, int C1, int S2, int A2, int B2, int C2>
-cudaError_t two_pass(const he_ctx *c, NttArgs a, int njobs, bool inverse, cudaStream_t st, const char *tag)
+cudaError_t two_pass(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag)
 {
-    a.tiles = (1 << (S1 + S2)) / kTE;
+    constexpr int TE = 2048;
+    a.tiles = (1 << (S1 + S2)) / TE;
     cudaError_t e;
     const char *t1 = inverse ? ".inv_pass1" : ".fwd_pass1";
     const char *t2 = inverse ? ".inv_pass2" : ".fwd_pass2";
     if (!inverse) {
-        e = run_pass<S1, A1, B1, C1, true, false, true, false>(a, njobs, st);
+        e = run_pass<S1, A1, B1, C1, true, false, true, false, TE>(a, ngroups, st);
         if (e != cudaSuccess) return e;
         prof_mark(c, st, tag, t1);
-        e = run_pass<S2, A2, B2, C2, false, false, false, true>(a, njobs, st);
+        e = run_pass<S2, A2, B2, C2, false, false, false, true, TE>(a, ngroups, st);
         prof_mark(c, st, tag, t2);
         return e;
     }
-    e = run_pass<S2, A2, B2, C2, false, true, true, false>(a, njobs, st);
+    e = run_pass<S2, A2, B2, C2, false, true, true, false, TE>(a, ngroups, st);
     if (e != cudaSuccess) return e;
     prof_mark(c, st, tag, t1);
-    e = run_pass<S1, A1, B1, C1, true, true, false, true>(a, njobs, st);
+    e = run_pass<S1, A1, B1, C1, true, true, false, true, TE>(a, ngroups, st);
     prof_mark(c, st, tag, t2);
     return e;
 }
 
 }  // namespace
 
-cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttJob *jobs, int njobs, bool inverse,
+cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups, bool inverse,
                         cudaStream_t st, const char *tag)
 {
-    if (njobs <= 0) return cudaSuccess;
+    if (ngroups <= 0) return cudaSuccess;
     NttArgs a;
     a.src = src;
     a.dst = dst;
-    a.jobs = jobs;
+    a.groups = groups;
     a.primes = c->d_primes;
     a.logN = c->logN;
     a.tiles = 1;
     switch (c->logN) {
     case 12: {
-        cudaError_t e = inverse ? run_pass<12, 4, 4, 4, false, true, true, true>(a, njobs, st)
-                                : run_pass<12, 4, 4, 4, false, false, true, true>(a, njobs, st);
+        cudaError_t e = inverse ? run_pass<12, 4, 4, 4, false, true, true, true, 4096>(a, ngroups, st)
+                                : run_pass<12, 4, 4, 4, false, false, true, true, 4096>(a, ngroups, st);
         prof_mark(c, st, tag, inverse ? ".inv" : ".fwd");
         return e;
     }
-    case 13: return two_pass<7, 4, 3, 0, 6, 3, 3, 0>(c, a, njobs, inverse, st, tag);
-    case 14: return two_pass<7, 4, 3, 0, 7, 4, 3, 0>(c, a, njobs, inverse, st, tag);
-    case 15: return two_pass<8, 4, 4, 0, 7, 4, 3, 0>(c, a, njobs, inverse, st, tag);
-    case 16: return two_pass<8, 4, 4, 0, 8, 4, 4, 0>(c, a, njobs, inverse, st, tag);
-    case 17: return two_pass<9, 3, 3, 3, 8, 4, 4, 0>(c, a, njobs, inverse, st, tag);
+    case 13: return two_pass<7, 4, 3, 0, 6, 3, 3, 0>(c, a, ngroups, inverse, st, tag);
+    case 14: return two_pass<7, 4, 3, 0, 7, 4, 3, 0>(c, a, ngroups, inverse, st, tag);
+    case 15: return two_pass<8, 4, 4, 0, 7, 4, 3, 0>(c, a, ngroups, inverse, st, tag);
+    case 16: return two_pass<8, 4, 4, 0, 8, 4, 4, 0>(c, a, ngroups, inverse, st, tag);
+    case 17: return two_pass<9, 3, 3, 3, 8, 4, 4, 0>(c, a, ngroups, inverse, st, tag);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_ntt(const he_ctx *c, u64 *base, const NttJob *jobs, int njobs, bool inverse, cudaStream_t st,
+cudaError_t launch_ntt(const he_ctx *c, u64 *base, const NttGroup *groups, int ngroups, bool inverse, cudaStream_t st,
                        const char *tag)
 {
-    return launch_ntt2(c, base, base, jobs, njobs, inverse, st, tag);
+    return launch_ntt2(c, base, base, groups, ngroups, inverse, st, tag);
 }
 
 }  // namespace he
