@@ -20,7 +20,8 @@ constexpr int kMaxL = 64;
 
 // One prime as the kernels see it (ext order: specials first, then q_0..).
 struct DevPrime {
-    u64 q, q2;              // q and 2q
+    u64 q, q2, q4;          // q, 2q, 4q
+    u64 r64;                // floor(2^64 / q): Shoup companion of 1, for final reductions
     u64 mu;                 // Barrett: floor(2^(64+s) / q)
     unsigned s, pad;        // s = bitlen(q) - 2
     const ulonglong2 *w;    // forward twiddles: w[m+j] = psi^bitrev(m+j), (value, Shoup)

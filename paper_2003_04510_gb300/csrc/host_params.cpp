@@ -305,6 +305,8 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         int b = bitlen(m);
         dp[e].q = m;
         dp[e].q2 = 2 * m;
+        dp[e].q4 = 4 * m;
+        dp[e].r64 = (u64)((((u128)1) << 64) / m);
         dp[e].s = (unsigned)(b - 2);
         dp[e].mu = (u64)(((u128)1 << (64 + b - 2)) / m);
         dp[e].pad = 0;

@@ -31,6 +31,34 @@ __device__ __forceinline__ u64 shoup_lazy(u64 x, u64 w, u64 wp, u64 q)
 
 __device__ __forceinline__ u64 csub(u64 x, u64 q) { return x >= q ? x - q : x; }
 
+// 32x32 -> 64-bit multiply-add and 32x32 -> high-32 multiply, written as PTX
+// so each is one integer multiply-add instruction.
+__device__ __forceinline__ u64 mad_wide(uint32_t a, uint32_t b, u64 c)
+{
+    u64 d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t mul_hi32(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// The paper's modified Shoup multiplication (Sec. 5.2): the quotient
+// floor(x * w' / 2^64) is estimated from three 32-bit partial products only
+// (x1 w'1, hi(x1 w'0), hi(x0 w'1)); the dropped terms are each below one
+// unit, so the estimate is the exact quotient minus 0, 1 or 2 and the
+// remainder x*w - qh*q lies in [0, 4q).  Valid for any x < 2^64, w < q < 2^62.
+__device__ __forceinline__ u64 shoup_approx(u64 x, u64 w, u64 wp, u64 q)
+{
+    const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
+    const uint32_t p0 = (uint32_t)wp, p1 = (uint32_t)(wp >> 32);
+    const u64 qh = mad_wide(x1, p1, (u64)mul_hi32(x1, p0) + mul_hi32(x0, p1));
+    return x * w - qh * q;
+}
+
 __device__ __forceinline__ u64 shoup(u64 x, u64 w, u64 wp, u64 q) { return csub(shoup_lazy(x, w, wp, q), q); }
 
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
@@ -86,10 +114,10 @@ __device__ __forceinline__ void split28(u64 x, uint32_t &x0, uint32_t &x1)
 __device__ __forceinline__ void mac28(Acc3 &s, uint32_t x0, uint32_t x1, u64 bpacked)
 {
     const uint32_t b0 = (uint32_t)bpacked, b1 = (uint32_t)(bpacked >> 32);
-    s.a0 += (u64)x0 * b0;
-    s.a1 += (u64)x0 * b1;
-    s.a1 += (u64)x1 * b0;
-    s.a2 += (u64)x1 * b1;
+    s.a0 = mad_wide(x0, b0, s.a0);
+    s.a1 = mad_wide(x0, b1, s.a1);
+    s.a1 = mad_wide(x1, b0, s.a1);
+    s.a2 = mad_wide(x1, b1, s.a2);
 }
 
 __device__ __forceinline__ U128 acc3_value(const Acc3 &s)

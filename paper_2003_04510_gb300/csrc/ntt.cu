@@ -7,10 +7,11 @@
 // words): the log N stages are split into two passes over memory (one for
 // N = 2^12).  A pass works on tiles of TE elements held in shared memory and
 // runs its stages as rounds of radix-2^r butterflies in registers, one
-// shared-memory exchange per round.  Butterflies are Harvey's lazy forms:
-// forward values stay in [0, 4q), inverse values in [0, 2q); the last pass
-// reduces to [0, q) and, for the inverse, multiplies by N^-1 times a per-limb
-// constant.
+// shared-memory exchange per round.  Butterflies are lazy: forward values
+// grow by at most 4q per stage with no correction step, inverse values stay in
+// [0, 4q); the paper's modified Shoup product (Sec. 5.2) supplies the twiddle
+// multiplications.  The last pass reduces to [0, q) and, for the inverse,
+// multiplies by N^-1 times a per-limb constant.
 //
 // Memory side: a CTA takes one tile position of a group of up to four limbs
 // that share a prime.  The tile's twiddles are copied into shared memory once
@@ -45,20 +46,26 @@ struct NttArgs {
     int tiles;       // tiles per limb
 };
 
-__device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, ulonglong2 w, u64 q, u64 q2)
+// Forward (Cooley-Tukey) butterfly with no correction step: the modified
+// Shoup product t lies in [0, 4q), so each stage adds at most 4q to the
+// range.  From canonical inputs, values stay below (1 + 4 log N) q < 2^64 for
+// q < 2^57.9 and are reduced once, on the final store.
+__device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, ulonglong2 w, u64 q, u64 q4)
 {
-    u64 a = x >= q2 ? x - q2 : x;
-    u64 t = shoup_lazy(y, w.x, w.y, q);
-    x = a + t;
-    y = a - t + q2;
+    const u64 t = shoup_approx(y, w.x, w.y, q);
+    y = x + q4 - t;
+    x = x + t;
 }
 
-__device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, ulonglong2 w, u64 q, u64 q2)
+// Inverse (Gentleman-Sande) butterfly on values in [0, 4q): the sum is
+// brought back below 4q with one conditional subtraction, the difference
+// goes through the modified Shoup product, which lands in [0, 4q).
+__device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, ulonglong2 w, u64 q, u64 q4)
 {
     u64 s = x + y;
-    s = s >= q2 ? s - q2 : s;
-    u64 d = x - y + q2;
-    y = shoup_lazy(d, w.x, w.y, q);
+    s = s >= q4 ? s - q4 : s;
+    const u64 d = x + q4 - y;
+    y = shoup_approx(d, w.x, w.y, q);
     x = s;
 }
 
@@ -82,12 +89,17 @@ __device__ __forceinline__ int tw_slot(int l, int grp, int x)
 }
 
 // One round of R stages [l0, l0 + R) on every register set of the tile.
+// The 2^R elements of a set sit at shared-memory word padi(e0) + c + (c >> 4)
+// with c = v * 2^lo_bits * (STRIDED ? NG : 1): for every configuration used
+// (R >= 3) the low four bits of e0 plus those of c never carry, so the
+// padding of e0 + c splits into padi(e0) plus a compile-time offset.
 template <int LOGM, int TE, int R, bool STRIDED, bool INV, int NT>
-__device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *tw, int l0, u64 q, u64 q2)
+__device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *tw, int l0, u64 q, u64 q4)
 {
     constexpr int M = 1 << LOGM;
     constexpr int NG = TE / M;
     constexpr int SETS = TE >> R;
+    constexpr int CSTEP = STRIDED ? NG : 1;
     const int lo_bits = LOGM - l0 - R;
     for (int s = threadIdx.x; s < SETS; s += NT) {
         int grp, khi, klo;
@@ -104,43 +116,42 @@ __device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *tw, int l0,
             grp = rest / nhi;
         }
         const int kbase = (khi << (LOGM - l0)) | klo;
+        u64 *base = sm + padi(STRIDED ? kbase * NG + grp : grp * M + kbase);
         u64 a[1 << R];
 #pragma unroll
         for (int v = 0; v < (1 << R); v++) {
-            int k = kbase + (v << lo_bits);
-            int e = STRIDED ? k * NG + grp : grp * M + k;
-            a[v] = sm[padi(e)];
+            const int c = (v << lo_bits) * CSTEP;
+            a[v] = base[c + (c >> 4)];
         }
         if (!INV) {
 #pragma unroll
             for (int lp = 0; lp < R; lp++) {
                 const int l = l0 + lp;
-                const int tb = tw_slot<LOGM, TE, STRIDED>(l, grp, khi << lp);
+                const ulonglong2 *t = tw + tw_slot<LOGM, TE, STRIDED>(l, grp, khi << lp);
                 const int h = 1 << (R - 1 - lp);
 #pragma unroll
                 for (int v = 0; v < (1 << R); v++) {
                     if (v & h) continue;
-                    ct_bfly(a[v], a[v + h], tw[tb + (v >> (R - lp))], q, q2);
+                    ct_bfly(a[v], a[v + h], t[v >> (R - lp)], q, q4);
                 }
             }
         } else {
 #pragma unroll
             for (int lp = R - 1; lp >= 0; lp--) {
                 const int l = l0 + lp;
-                const int tb = tw_slot<LOGM, TE, STRIDED>(l, grp, khi << lp);
+                const ulonglong2 *t = tw + tw_slot<LOGM, TE, STRIDED>(l, grp, khi << lp);
                 const int h = 1 << (R - 1 - lp);
 #pragma unroll
                 for (int v = 0; v < (1 << R); v++) {
                     if (v & h) continue;
-                    gs_bfly(a[v], a[v + h], tw[tb + (v >> (R - lp))], q, q2);
+                    gs_bfly(a[v], a[v + h], t[v >> (R - lp)], q, q4);
                 }
             }
         }
 #pragma unroll
         for (int v = 0; v < (1 << R); v++) {
-            int k = kbase + (v << lo_bits);
-            int e = STRIDED ? k * NG + grp : grp * M + k;
-            sm[padi(e)] = a[v];
+            const int c = (v << lo_bits) * CSTEP;
+            base[c + (c >> 4)] = a[v];
         }
     }
 }
@@ -211,22 +222,22 @@ k_ntt_pass(const NttArgs P)
         }
         __syncthreads();
         if (!INV) {
-            ntt_round<LOGM, TE, RA, STRIDED, false, NT>(sm, tw, 0, pr.q, pr.q2);
+            ntt_round<LOGM, TE, RA, STRIDED, false, NT>(sm, tw, 0, pr.q, pr.q4);
             __syncthreads();
-            ntt_round<LOGM, TE, RB, STRIDED, false, NT>(sm, tw, RA, pr.q, pr.q2);
+            ntt_round<LOGM, TE, RB, STRIDED, false, NT>(sm, tw, RA, pr.q, pr.q4);
             __syncthreads();
             if (RC) {
-                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, false, NT>(sm, tw, RA + RB, pr.q, pr.q2);
+                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, false, NT>(sm, tw, RA + RB, pr.q, pr.q4);
                 __syncthreads();
             }
         } else {
             if (RC) {
-                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, true, NT>(sm, tw, RA + RB, pr.q, pr.q2);
+                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, true, NT>(sm, tw, RA + RB, pr.q, pr.q4);
                 __syncthreads();
             }
-            ntt_round<LOGM, TE, RB, STRIDED, true, NT>(sm, tw, RA, pr.q, pr.q2);
+            ntt_round<LOGM, TE, RB, STRIDED, true, NT>(sm, tw, RA, pr.q, pr.q4);
             __syncthreads();
-            ntt_round<LOGM, TE, RA, STRIDED, true, NT>(sm, tw, 0, pr.q, pr.q2);
+            ntt_round<LOGM, TE, RA, STRIDED, true, NT>(sm, tw, 0, pr.q, pr.q4);
             __syncthreads();
         }
         // shared memory -> HBM, 16-byte stores, output reduction on the last pass
@@ -236,9 +247,9 @@ k_ntt_pass(const NttArgs P)
             const int e = 2 * h;
             u64 x = sm[padi(e)], y = sm[padi(e + 1)];
             if (LAST) {
-                if (!INV) {
-                    x = csub(x >= pr.q2 ? x - pr.q2 : x, pr.q);
-                    y = csub(y >= pr.q2 ? y - pr.q2 : y, pr.q);
+                if (!INV) {  // x < (1 + 4 log N) q: one Shoup product by 1 reduces it
+                    x = shoup(x, 1, pr.r64, pr.q);
+                    y = shoup(y, 1, pr.r64, pr.q);
                 } else {
                     x = shoup(x, sc, scs, pr.q);
                     y = shoup(y, sc, scs, pr.q);
