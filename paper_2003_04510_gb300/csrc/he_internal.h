@@ -52,7 +52,7 @@ std::vector<NttGroup> group_jobs(const std::vector<NttJob> &jobs);
 struct DevLevel {
     int l, beta, E, A;             // level, digits, K+l, alpha padded for the kernels
     int dig_lo[kMaxDigits], dig_n[kMaxDigits];
-    const u64 *modupB;             // [beta][E][A]: [Qhat_{j,i}]_t split at bit 28 (0 for own-digit rows)
+    const u64 *modupB;             // [beta][E][A]: [Qhat_{j,i}]_t split at bit 28, zero-padded
     const ulonglong2 *qinv_last;   // [l-1]: q_{l-1}^-1 mod q_i (value, Shoup)
     const ulonglong2 *pinv_qinv;   // [l-1]: P^-1 * q_{l-1}^-1 mod q_i
 };
@@ -87,6 +87,7 @@ struct HostLevel {
 struct he_ctx {
     he_params prm;
     int N, logN, L, K, alpha, dnum, E;  // E = K + L
+    int AP, KP;                          // alpha and K padded to a kernel width (1,2,4,8,12,16)
     bool device;
     std::vector<u64> ext;                // moduli, ext order
     std::vector<u64> psi;                // smallest primitive 2N-th roots, ext order
@@ -94,7 +95,7 @@ struct he_ctx {
     std::vector<std::vector<u64>> w, wsh, iw, iwsh;  // [E][N]
     std::vector<u64> ninv, ninv_sh;                  // [E]
     // level-independent ModDown constants
-    std::vector<u64> PB;                 // [L][K]: [Phat_k]_{q_i}, split at bit 28
+    std::vector<u64> PB;                 // [L][KP]: [Phat_k]_{q_i} split at bit 28, zero-padded
     std::vector<ulonglong2> pinv;        // [L]: P^-1 mod q_i
     std::vector<ulonglong2> phat_inv;    // [K]: Phat_k^-1 mod p_k
     std::vector<he::HostLevel> host_levels;  // index l (1..L)

@@ -121,6 +121,9 @@ int build_context(he_ctx *c, const he_params *p, bool device)
     c->E = p->K + p->L;
     c->device = device;
     if (c->dnum > kMaxDigits) return HE_EINVAL;
+    auto pad_width = [](int v) { return v <= 2 ? v : v <= 4 ? 4 : v <= 8 ? 8 : v <= 12 ? 12 : 16; };
+    c->AP = pad_width(p->alpha);
+    c->KP = pad_width(p->K);
 
     std::vector<u64> q = find_primes(p->logN, p->q_bits, p->L, {});
     if ((int)q.size() != p->L) return HE_EINVAL;
@@ -165,7 +168,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
     }
 
     // ModDown constants
-    c->PB.assign((size_t)L * K, 0);
+    c->PB.assign((size_t)L * c->KP, 0);
     c->pinv.resize(L);
     c->phat_inv.resize(K);
     for (int k = 0; k < K; k++) {
@@ -180,7 +183,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
             u64 v = 1;
             for (int k2 = 0; k2 < K; k2++)
                 if (k2 != k) v = mul(v, c->ext[k2] % qi, qi);
-            c->PB[(size_t)i * K + k] = split28(v);
+            c->PB[(size_t)i * c->KP + k] = split28(v);
             P = mul(P, c->ext[k] % qi, qi);
         }
         c->pinv[i] = pair(inv(P, qi), qi);
@@ -191,7 +194,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
     for (int l = 1; l <= L; l++) {
         HostLevel &H = c->host_levels[l];
         const int beta = (l + c->alpha - 1) / c->alpha, El = K + l;
-        const int A = c->alpha;
+        const int A = c->AP;
         H.ws = layout_for(l, K, c->alpha);
         const WsLayout &W = H.ws;
         // ModUp tables and the iNTT scale N^-1 * Qhat_{j,i}^-1
@@ -331,7 +334,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         D.l = l;
         D.beta = (l + c->alpha - 1) / c->alpha;
         D.E = K + l;
-        D.A = c->alpha;
+        D.A = c->AP;
         for (int j = 0; j < D.beta; j++) {
             D.dig_lo[j] = j * c->alpha;
             D.dig_n[j] = std::min((j + 1) * c->alpha, l) - j * c->alpha;

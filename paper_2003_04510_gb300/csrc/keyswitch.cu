@@ -51,6 +51,9 @@ k_tensor(const u64 *__restrict__ ct1, const u64 *__restrict__ ct2, u64 *__restri
 // grid: x over N/2/kThreads, y over digits, z over chunks of kModupChunk
 // targets.  y: [l][N] (scaled iNTT of d2), U: [beta][E][N].  Target u of
 // digit j (u < E - n_j) is ext limb u below the digit's own limbs, u + n_j above.
+// Digits are padded to A limbs with zero constants (the padding loads reread a
+// real limb, whose value is multiplied by zero), so the MAC loop has no
+// predicates; the chunk's constants and prime parameters sit in shared memory.
 constexpr int kModupChunk = 8;
 
 template <int A>
@@ -63,38 +66,47 @@ k_modup(const u64 *__restrict__ y, u64 *__restrict__ U, const DevLevel *__restri
     const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
     const int E = lv.E;
     const int u0 = blockIdx.z * kModupChunk;
-    const int u1 = min(u0 + kModupChunk, E - nj);
-    if (u0 >= u1) return;
+    const int cnt = min(kModupChunk, E - nj - u0);
+    if (cnt <= 0) return;
+    __shared__ u64 sB[kModupChunk][A];
+    __shared__ u64 sq[kModupChunk], smu[kModupChunk];
+    __shared__ unsigned ss[kModupChunk];
+    __shared__ int se[kModupChunk];
+    const u64 *B = lv.modupB + (size_t)j * E * A;
+    for (int t = threadIdx.x; t < cnt * A; t += kThreads) {
+        const int u = u0 + t / A;
+        const int e = u < K + lo ? u : u + nj;
+        sB[t / A][t % A] = B[(size_t)e * A + t % A];
+    }
+    if (threadIdx.x < cnt) {
+        const int u = u0 + threadIdx.x;
+        const int e = u < K + lo ? u : u + nj;
+        se[threadIdx.x] = e;
+        sq[threadIdx.x] = primes[e].q;
+        smu[threadIdx.x] = primes[e].mu;
+        ss[threadIdx.x] = primes[e].s;
+    }
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     uint32_t x0[A], x1[A], z0[A], z1[A];
 #pragma unroll
     for (int i = 0; i < A; i++) {
-        u64 vx = 0, vy = 0;
-        if (i < nj) {
-            ulonglong2 v = ld2(y + (size_t)(lo + i) * N + n);
-            vx = v.x;
-            vy = v.y;
-        }
-        split28(vx, x0[i], x1[i]);
-        split28(vy, z0[i], z1[i]);
+        const ulonglong2 v = ld2(y + (size_t)(lo + min(i, nj - 1)) * N + n);
+        split28(v.x, x0[i], x1[i]);
+        split28(v.y, z0[i], z1[i]);
     }
-    const u64 *B = lv.modupB + (size_t)j * E * lv.A;
+    __syncthreads();
     u64 *Uj = U + (size_t)j * E * N;
-    for (int u = u0; u < u1; u++) {
-        const int e = u < K + lo ? u : u + nj;
-        const DevPrime pr = primes[e];
-        const u64 *b = B + (size_t)e * lv.A;
+    for (int u = 0; u < cnt; u++) {
         Acc3 ax = {0, 0, 0}, ay = {0, 0, 0};
 #pragma unroll
         for (int i = 0; i < A; i++) {
-            if (i < nj) {
-                const u64 c = __ldg(b + i);
-                mac28(ax, x0[i], x1[i], c);
-                mac28(ay, z0[i], z1[i], c);
-            }
+            const u64 c = sB[u][i];
+            mac28(ax, x0[i], x1[i], c);
+            mac28(ay, z0[i], z1[i], c);
         }
-        st2(Uj + (size_t)e * N + n, barrett128(acc3_value(ax), pr.q, pr.mu, pr.s),
-            barrett128(acc3_value(ay), pr.q, pr.mu, pr.s));
+        const u64 q = sq[u], mu = smu[u];
+        const unsigned sh = ss[u];
+        st2(Uj + (size_t)se[u] * N + n, barrett128(acc3_value(ax), q, mu, sh), barrett128(acc3_value(ay), q, mu, sh));
     }
 }
 
@@ -132,23 +144,23 @@ k_inner_product(const u64 *__restrict__ U, const u64 *__restrict__ d2, const u64
 // Phat_k^-1).  PLAIN: z[h][i] = conv_i for i < l.
 // FUSED: r = r0 + (r1 - conv_{l-1}) P^-1 mod q_{l-1} with r0 = iNTT(d_h)_{l-1},
 // r1 = iNTT(KS_h)_{l-1}; z[h][i] = conv_i P^-1 + r mod q_i for i < l-1.
+// PB rows are zero-padded to KM constants, so the MAC loop has no predicates.
 constexpr int kModdownChunk = 8;
 
 template <int KM>
 __device__ __forceinline__ void conv_one(const uint32_t *x0, const uint32_t *x1, const uint32_t *z0,
-                                         const uint32_t *z1, const u64 *__restrict__ b, int K, const DevPrime &pr,
-                                         u64 &cx, u64 &cy)
+                                         const uint32_t *z1, const u64 *b, u64 q, u64 mu, unsigned sh, u64 &cx,
+                                         u64 &cy)
 {
     Acc3 ax = {0, 0, 0}, ay = {0, 0, 0};
 #pragma unroll
-    for (int k = 0; k < KM; k++)
-        if (k < K) {
-            const u64 c = __ldg(b + k);
-            mac28(ax, x0[k], x1[k], c);
-            mac28(ay, z0[k], z1[k], c);
-        }
-    cx = barrett128(acc3_value(ax), pr.q, pr.mu, pr.s);
-    cy = barrett128(acc3_value(ay), pr.q, pr.mu, pr.s);
+    for (int k = 0; k < KM; k++) {
+        const u64 c = b[k];
+        mac28(ax, x0[k], x1[k], c);
+        mac28(ay, z0[k], z1[k], c);
+    }
+    cx = barrett128(acc3_value(ax), q, mu, sh);
+    cy = barrett128(acc3_value(ay), q, mu, sh);
 }
 
 template <int KM, bool FUSED>
@@ -160,43 +172,59 @@ k_moddown_conv(const u64 *__restrict__ ys, const u64 *__restrict__ rr, u64 *__re
     const int h = blockIdx.y;
     const int nout = FUSED ? l - 1 : l;
     const int i0 = blockIdx.z * kModdownChunk;
-    const int i1 = min(i0 + kModdownChunk, nout);
-    if (i0 >= i1) return;
+    const int cnt = min(kModdownChunk, nout - i0);
+    if (cnt <= 0) return;
+    // rows 0..cnt-1: this chunk's outputs; row kModdownChunk: q_{l-1} (fused)
+    __shared__ u64 sB[kModdownChunk + 1][KM];
+    __shared__ u64 sq[kModdownChunk + 1], smu[kModdownChunk + 1];
+    __shared__ unsigned ss[kModdownChunk + 1];
+    __shared__ ulonglong2 spv[kModdownChunk + 1];
+    for (int t = threadIdx.x; t < (kModdownChunk + 1) * KM; t += kThreads) {
+        const int r = t / KM, k = t % KM;
+        const int i = r < kModdownChunk ? i0 + r : l - 1;
+        if (r < cnt || (FUSED && r == kModdownChunk)) sB[r][k] = PB[(size_t)i * KM + k];
+    }
+    if (threadIdx.x <= kModdownChunk) {
+        const int r = threadIdx.x;
+        const int i = r < kModdownChunk ? i0 + r : l - 1;
+        if (r < cnt || (FUSED && r == kModdownChunk)) {
+            sq[r] = primes[K + i].q;
+            smu[r] = primes[K + i].mu;
+            ss[r] = primes[K + i].s;
+            spv[r] = pinv[i];
+        }
+    }
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     uint32_t x0[KM], x1[KM], z0[KM], z1[KM];
 #pragma unroll
     for (int k = 0; k < KM; k++) {
-        u64 vx = 0, vy = 0;
-        if (k < K) {
-            ulonglong2 v = ld2(ys + ((size_t)h * K + k) * N + n);
-            vx = v.x;
-            vy = v.y;
-        }
-        split28(vx, x0[k], x1[k]);
-        split28(vy, z0[k], z1[k]);
+        const ulonglong2 v = ld2(ys + ((size_t)h * K + min(k, K - 1)) * N + n);
+        split28(v.x, x0[k], x1[k]);
+        split28(v.y, z0[k], z1[k]);
     }
+    __syncthreads();
     u64 rx = 0, ry = 0;
     if (FUSED) {
-        const int i = l - 1;
-        const DevPrime pr = primes[K + i];
+        const int r = kModdownChunk;
+        const u64 q = sq[r];
         u64 cx, cy;
-        conv_one<KM>(x0, x1, z0, z1, PB + (size_t)i * K, K, pr, cx, cy);
-        ulonglong2 r0 = ld2(rr + (size_t)h * N + n), r1 = ld2(rr + (size_t)(2 + h) * N + n);
-        const ulonglong2 pv = pinv[i];
-        rx = add_mod(r0.x, shoup(sub_mod(r1.x, cx, pr.q), pv.x, pv.y, pr.q), pr.q);
-        ry = add_mod(r0.y, shoup(sub_mod(r1.y, cy, pr.q), pv.x, pv.y, pr.q), pr.q);
+        conv_one<KM>(x0, x1, z0, z1, sB[r], q, smu[r], ss[r], cx, cy);
+        const ulonglong2 r0 = ld2(rr + (size_t)h * N + n), r1 = ld2(rr + (size_t)(2 + h) * N + n);
+        const ulonglong2 pv = spv[r];
+        rx = add_mod(r0.x, shoup(sub_mod(r1.x, cx, q), pv.x, pv.y, q), q);
+        ry = add_mod(r0.y, shoup(sub_mod(r1.y, cy, q), pv.x, pv.y, q), q);
     }
-    for (int i = i0; i < i1; i++) {
-        const DevPrime pr = primes[K + i];
+    for (int r = 0; r < cnt; r++) {
+        const u64 q = sq[r];
         u64 cx, cy;
-        conv_one<KM>(x0, x1, z0, z1, PB + (size_t)i * K, K, pr, cx, cy);
+        conv_one<KM>(x0, x1, z0, z1, sB[r], q, smu[r], ss[r], cx, cy);
         if (FUSED) {
             // r < q_{l-1} < q_i: r is already a residue mod q_i
-            const ulonglong2 pv = pinv[i];
-            cx = add_mod(shoup(cx, pv.x, pv.y, pr.q), rx, pr.q);
-            cy = add_mod(shoup(cy, pv.x, pv.y, pr.q), ry, pr.q);
+            const ulonglong2 pv = spv[r];
+            cx = add_mod(shoup(cx, pv.x, pv.y, q), rx, q);
+            cy = add_mod(shoup(cy, pv.x, pv.y, q), ry, q);
         }
-        st2(z + ((size_t)h * nout + i) * N + n, cx, cy);
+        st2(z + ((size_t)h * nout + i0 + r) * N + n, cx, cy);
     }
 }
 
@@ -274,13 +302,13 @@ cudaError_t run_modup(const he_ctx *c, const u64 *y, u64 *U, int l, cudaStream_t
     const int beta = (l + c->alpha - 1) / c->alpha;
     const int ntarget = c->K + (beta - 1) * c->alpha;  // targets of the shortest (last) digit: the most
     g.z = (ntarget + kModupChunk - 1) / kModupChunk;
-    const int a = c->alpha;
+    const int a = c->AP;
 #define HE_MODUP(AA) k_modup<AA><<<g, kThreads, 0, st>>>(y, U, c->d_levels, l, c->d_primes, c->K, c->N)
-    if (a <= 1) HE_MODUP(1);
-    else if (a <= 2) HE_MODUP(2);
-    else if (a <= 4) HE_MODUP(4);
-    else if (a <= 8) HE_MODUP(8);
-    else if (a <= 12) HE_MODUP(12);
+    if (a == 1) HE_MODUP(1);
+    else if (a == 2) HE_MODUP(2);
+    else if (a == 4) HE_MODUP(4);
+    else if (a == 8) HE_MODUP(8);
+    else if (a == 12) HE_MODUP(12);
     else HE_MODUP(16);
 #undef HE_MODUP
     return cudaGetLastError();
@@ -307,11 +335,12 @@ cudaError_t run_moddown_conv(const he_ctx *c, const u64 *ys, const u64 *rr, u64 
         if (fused) k_moddown_conv<KK, true><<<g, kThreads, 0, st>>>(ys, rr, z, c->d_PB, c->d_pinv, c->d_primes, K, l, c->N); \
         else k_moddown_conv<KK, false><<<g, kThreads, 0, st>>>(ys, rr, z, c->d_PB, c->d_pinv, c->d_primes, K, l, c->N);     \
     } while (0)
-    if (K <= 1) HE_MD(1);
-    else if (K <= 2) HE_MD(2);
-    else if (K <= 4) HE_MD(4);
-    else if (K <= 8) HE_MD(8);
-    else if (K <= 12) HE_MD(12);
+    const int kp = c->KP;
+    if (kp == 1) HE_MD(1);
+    else if (kp == 2) HE_MD(2);
+    else if (kp == 4) HE_MD(4);
+    else if (kp == 8) HE_MD(8);
+    else if (kp == 12) HE_MD(12);
     else HE_MD(16);
 #undef HE_MD
     return cudaGetLastError();
