@@ -14,13 +14,12 @@
 // multiplies by N^-1 times a per-limb constant.
 //
 // Memory side: a CTA takes one tile position of a group of up to four limbs
-// that share a prime, so each twiddle fetched serves every limb of the group.
-// Strided passes use the same twiddles TB_W[1, M) in every tile and copy them
-// into shared memory once; contiguous passes read their per-group twiddle runs
-// straight from the (L2-resident) table with coalesced loads, which keeps the
-// shared-memory footprint, and so the occupancy, of those passes low/high.
-// The limbs' data tiles are double-buffered with cp.async so the next limb
-// loads while this one computes.
+// that share a prime.  The tile's twiddles are copied into shared memory once
+// (cp.async) and reused for every limb of the group.  Strided passes (whose
+// twiddles, TB_W[1, M), are few) double-buffer the limbs' data tiles so the
+// next limb loads while this one computes; contiguous passes stage a 32 KB
+// twiddle run per tile and keep a single data buffer, which holds occupancy
+// at four CTAs per SM.
 //
 // Stage / twiddle indexing.  Global stage sigma (m = 2^sigma) pairs j and
 // j + N/2^(sigma+1) and uses twiddle m + floor(j / 2^(logN - sigma)).  A pass
@@ -79,19 +78,18 @@ template <int LOGM, int TE, bool STRIDED>
 struct Geometry {
     static constexpr int M = 1 << LOGM;
     static constexpr int NG = TE / M;                           // groups (or columns) per tile
-    static constexpr int TWN = STRIDED ? M - 1 : 0;  // twiddle pairs staged in shared memory
+    static constexpr int TWN = STRIDED ? M - 1 : NG * (M - 1);  // twiddle pairs staged per tile
     static constexpr int DATA = TE + TE / 16;                   // padded words per data buffer
-    static constexpr size_t SMEM = sizeof(ulonglong2) * TWN + sizeof(u64) * 2 * DATA;
+    static constexpr int NBUF = STRIDED ? 2 : 1;                // data buffers (double-buffered if strided)
+    static constexpr size_t SMEM = sizeof(ulonglong2) * TWN + sizeof(u64) * NBUF * DATA;
 };
 
-// Twiddle slot of local stage l, group grp, offset x.  Strided passes read
-// the shared-memory copy of TB_W[1, M); contiguous passes read the global
-// table at 2^(s0+l) + (G << l) + x, G = g0 + grp (coalesced across a warp).
+// Shared-memory twiddle slot of local stage l, group grp, offset x.
 template <int LOGM, int TE, bool STRIDED>
-__device__ __forceinline__ int tw_slot(int l, int s0, int G, int x)
+__device__ __forceinline__ int tw_slot(int l, int grp, int x)
 {
     if (STRIDED) return (1 << l) - 1 + x;
-    return (1 << (s0 + l)) + (G << l) + x;
+    return Geometry<LOGM, TE, STRIDED>::NG * ((1 << l) - 1) + (grp << l) + x;
 }
 
 // One round of R stages [l0, l0 + R) on every register set of the tile.
@@ -100,8 +98,7 @@ __device__ __forceinline__ int tw_slot(int l, int s0, int G, int x)
 // (R >= 3) the low four bits of e0 plus those of c never carry, so the
 // padding of e0 + c splits into padi(e0) plus a compile-time offset.
 template <int LOGM, int TE, int R, bool STRIDED, bool INV, int NT>
-__device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *__restrict__ tw, int l0, int s0, int g0, u64 q,
-                                          u64 q4)
+__device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *tw, int l0, u64 q, u64 q4)
 {
     constexpr int M = 1 << LOGM;
     constexpr int NG = TE / M;
@@ -134,24 +131,24 @@ __device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *__restrict_
 #pragma unroll
             for (int lp = 0; lp < R; lp++) {
                 const int l = l0 + lp;
-                const ulonglong2 *t = tw + tw_slot<LOGM, TE, STRIDED>(l, s0, g0 + grp, khi << lp);
+                const ulonglong2 *t = tw + tw_slot<LOGM, TE, STRIDED>(l, grp, khi << lp);
                 const int h = 1 << (R - 1 - lp);
 #pragma unroll
                 for (int v = 0; v < (1 << R); v++) {
                     if (v & h) continue;
-                    ct_bfly(a[v], a[v + h], STRIDED ? t[v >> (R - lp)] : __ldg(&t[v >> (R - lp)]), q, q4);
+                    ct_bfly(a[v], a[v + h], t[v >> (R - lp)], q, q4);
                 }
             }
         } else {
 #pragma unroll
             for (int lp = R - 1; lp >= 0; lp--) {
                 const int l = l0 + lp;
-                const ulonglong2 *t = tw + tw_slot<LOGM, TE, STRIDED>(l, s0, g0 + grp, khi << lp);
+                const ulonglong2 *t = tw + tw_slot<LOGM, TE, STRIDED>(l, grp, khi << lp);
                 const int h = 1 << (R - 1 - lp);
 #pragma unroll
                 for (int v = 0; v < (1 << R); v++) {
                     if (v & h) continue;
-                    gs_bfly(a[v], a[v + h], STRIDED ? t[v >> (R - lp)] : __ldg(&t[v >> (R - lp)]), q, q4);
+                    gs_bfly(a[v], a[v + h], t[v >> (R - lp)], q, q4);
                 }
             }
         }
@@ -196,11 +193,19 @@ k_ntt_pass(const NttArgs P)
     const int stride = N >> LOGM;
     const int s0 = STRIDED ? 0 : P.logN - LOGM;
 
-    // strided pass: the tile-independent twiddles TB_W[1, M) -> shared memory
+    // twiddles of this tile -> shared memory (16-byte async copies)
     const ulonglong2 *twg = INV ? pr.iw : pr.w;
-    for (int f = threadIdx.x; f < Gm::TWN; f += NT) __pipeline_memcpy_async(&tw[f], &twg[1 + f], 16);
-    const ulonglong2 *twr = STRIDED ? tw : twg;  // where the rounds read twiddles
-    const int g0 = tile * NG;
+    for (int f = threadIdx.x; f < Gm::TWN; f += NT) {
+        int gsrc;
+        if (STRIDED) {
+            gsrc = 1 + f;
+        } else {
+            const int l = 31 - __clz(f / NG + 1);  // NG (2^l - 1) <= f < NG (2^(l+1) - 1)
+            const int x = f - NG * ((1 << l) - 1);
+            gsrc = (1 << (s0 + l)) + tile * NG * (1 << l) + x;
+        }
+        __pipeline_memcpy_async(&tw[f], &twg[gsrc], 16);
+    }
     // data tile of limb i of the group -> shared memory (8-byte async copies)
     auto load_tile = [&](int i, u64 *b) {
         const u64 *src = FIRST ? P.src + (size_t)G.src[i] * N : P.dst + (size_t)G.dst[i] * N;
@@ -211,32 +216,36 @@ k_ntt_pass(const NttArgs P)
     __pipeline_commit();
 
     for (int i = 0; i < nl; i++) {
-        u64 *sm = buf + (i & 1) * Gm::DATA;
-        if (i + 1 < nl) {
+        u64 *sm = buf + (Gm::NBUF == 2 ? (i & 1) * Gm::DATA : 0);
+        if (Gm::NBUF == 2 && i + 1 < nl) {
             load_tile(i + 1, buf + ((i + 1) & 1) * Gm::DATA);
             __pipeline_commit();
             __pipeline_wait_prior(1);
         } else {
+            if (Gm::NBUF == 1 && i > 0) {  // single buffer: load this limb now
+                load_tile(i, buf);
+                __pipeline_commit();
+            }
             __pipeline_wait_prior(0);
         }
         __syncthreads();
         if (!INV) {
-            ntt_round<LOGM, TE, RA, STRIDED, false, NT>(sm, twr, 0, s0, g0, pr.q, pr.q4);
+            ntt_round<LOGM, TE, RA, STRIDED, false, NT>(sm, tw, 0, pr.q, pr.q4);
             __syncthreads();
-            ntt_round<LOGM, TE, RB, STRIDED, false, NT>(sm, twr, RA, s0, g0, pr.q, pr.q4);
+            ntt_round<LOGM, TE, RB, STRIDED, false, NT>(sm, tw, RA, pr.q, pr.q4);
             __syncthreads();
             if (RC) {
-                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, false, NT>(sm, twr, RA + RB, s0, g0, pr.q, pr.q4);
+                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, false, NT>(sm, tw, RA + RB, pr.q, pr.q4);
                 __syncthreads();
             }
         } else {
             if (RC) {
-                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, true, NT>(sm, twr, RA + RB, s0, g0, pr.q, pr.q4);
+                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, true, NT>(sm, tw, RA + RB, pr.q, pr.q4);
                 __syncthreads();
             }
-            ntt_round<LOGM, TE, RB, STRIDED, true, NT>(sm, twr, RA, s0, g0, pr.q, pr.q4);
+            ntt_round<LOGM, TE, RB, STRIDED, true, NT>(sm, tw, RA, pr.q, pr.q4);
             __syncthreads();
-            ntt_round<LOGM, TE, RA, STRIDED, true, NT>(sm, twr, 0, s0, g0, pr.q, pr.q4);
+            ntt_round<LOGM, TE, RA, STRIDED, true, NT>(sm, tw, 0, pr.q, pr.q4);
             __syncthreads();
         }
         // shared memory -> HBM, 16-byte stores, output reduction on the last pass
