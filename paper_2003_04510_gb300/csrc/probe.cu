@@ -1,10 +1,12 @@
 // probe.cu -- throughput probe for the ALU roofline of the NTT kernels.
 //
 // The NTT kernels are bound by 64-bit integer multiply work, not by HBM: each
-// butterfly is one Shoup product (Algo 2) plus a few adds.  This kernel runs
-// the same lazy Cooley-Tukey butterfly as ntt.cu on register-resident data
-// with no memory traffic and many independent chains per thread, so its rate
-// is the practical ceiling for butterflies per second on this GPU.
+// butterfly is one Shoup product (the paper's modified Shoup of Sec. 5.2)
+// plus adds.  This kernel issues exactly the forward butterfly of ntt.cu
+// (ct_bfly: no correction step) on register-resident data with no memory
+// traffic and eight independent chains per thread, so its rate is the
+// practical ceiling for butterflies per second on this GPU.  The values are
+// not kept reduced (they wrap), which changes no instruction.
 #include "he_internal.h"
 #include "modarith.cuh"
 
@@ -21,13 +23,13 @@ __global__ void __launch_bounds__(256) k_probe_bfly(u64 *out, u64 q, u64 w, u64 
         x[c] = (threadIdx.x * 7919ull + c * 104729ull + blockIdx.x) % q;
         y[c] = (threadIdx.x * 15485863ull + c * 32452843ull + blockIdx.x) % q;
     }
+    const u64 q4 = 2 * q2;
     for (int it = 0; it < iters; it++) {
 #pragma unroll
         for (int c = 0; c < kChains; c++) {
-            u64 a = x[c] >= q2 ? x[c] - q2 : x[c];
-            u64 t = shoup_lazy(y[c], w, wp, q);
-            x[c] = a + t;
-            y[c] = a - t + q2;
+            const u64 t = shoup_approx(y[c], w, wp, q);
+            y[c] = x[c] + q4 - t;
+            x[c] = x[c] + t;
         }
     }
     u64 acc = 0;
