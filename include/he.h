@@ -175,9 +175,10 @@ int he_step_tensor(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, int le
 int he_step_modup(he_ctx *ctx, const uint64_t *d2, int level, uint64_t *U, void *ws, size_t ws_bytes,
                   void *stream);
 /* Inner product of NTT-domain U ([beta][K+level][N], own-digit rows taken
- * from d2 [level][N]) with the device evk: KS [2][K+level][N]. */
+ * from d2 [level][N]) with the device evk: KS [2][K+level][N].  ws must hold
+ * he_workspace_bytes(level). */
 int he_step_inner_product(he_ctx *ctx, const uint64_t *U, const uint64_t *d2, const uint64_t *evk_dev, int level,
-                          uint64_t *KS, void *stream);
+                          uint64_t *KS, void *ws, size_t ws_bytes, void *stream);
 /* ModDown of one NTT-domain polynomial X ([K+level][N], ext order) to
  * out [level][N]; ws must hold he_workspace_bytes(level). */
 int he_step_moddown(he_ctx *ctx, const uint64_t *X, int level, uint64_t *out, void *ws, size_t ws_bytes,
@@ -195,8 +196,12 @@ typedef struct {
 /* Workspace bytes for a batch of `count` jobs at the given levels. */
 size_t he_batch_workspace_bytes(const he_ctx *ctx, int count, const int *levels);
 /* Run B independent HE Mul + rescale jobs (uneven levels allowed) as one
- * batch: each stage is one launch over every job's work, so jobs overlap on
- * the device.  Results are bit-identical to he_mul_rescale on each job. */
+ * batch: each stage is one launch over every job's work (grid.z = job), and
+ * each NTT launch groups the limbs of all jobs by prime so that one staged
+ * twiddle tile serves limbs of several jobs.  The first bytes of ws receive
+ * the batch's job table and NTT job lists (one host-to-device copy on the
+ * stream); the rest holds the jobs' workspaces.  Results are bit-identical
+ * to he_mul_rescale on each job.  count <= 65535. */
 int he_mul_batch(he_ctx *ctx, int count, const he_job *jobs, const uint64_t *evk_dev, void *ws,
                  size_t ws_bytes, void *stream);
 

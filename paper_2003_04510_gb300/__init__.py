@@ -79,7 +79,8 @@ _SIGS = {
     "he_step_modup": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "he_step_inner_product": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+                                             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                             ctypes.c_void_p]),
     "he_step_moddown": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "he_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -307,9 +308,9 @@ def he_step_modup(ctx, d2, level, U, ws, stream=None):
                                _stream_ptr(stream)), "he_step_modup")
 
 
-def he_step_inner_product(ctx, U, d2, evk, level, KS, stream=None):
+def he_step_inner_product(ctx, U, d2, evk, level, KS, ws, stream=None):
     _check(lib().he_step_inner_product(ctx.ptr, _dev_ptr(U), _dev_ptr(d2), _dev_ptr(evk), level, _dev_ptr(KS),
-                                       _stream_ptr(stream)), "he_step_inner_product")
+                                       _dev_ptr(ws), ws.numel() * 8, _stream_ptr(stream)), "he_step_inner_product")
 
 
 def he_step_moddown(ctx, X, level, out, ws, stream=None):

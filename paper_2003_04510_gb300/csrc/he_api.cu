@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "he_internal.h"
 
@@ -51,40 +52,102 @@ int with_jobs(const std::vector<NttGroup> &jobs, cudaStream_t st, NttGroup **out
     return HE_OK;
 }
 
-// The HE Mul pipeline at level l.  fused = ModDown and rescale merged (out is
-// [2][l-1][N]); otherwise out is the level-l product ([2][l][N]).
-int hemul_pipeline(he_ctx *c, const u64 *ct1, const u64 *ct2, const u64 *evk, int l, u64 *out, u64 *ws,
-                   bool fused, cudaStream_t st)
+// NTT job lists of one launch sequence.
+struct Stages {
+    const NttGroup *intt1;    int n_intt1;     // iNTT of d2 (+ d0/d1 last limb when fused)
+    const NttGroup *ntt_up;   int n_ntt_up;    // NTT of the ModUp outputs
+    const NttGroup *intt2;    int n_intt2;     // iNTT of the special limbs (+ KS last limb when fused)
+    const NttGroup *ntt_last; int n_ntt_last;  // NTT of the ModDown (fused: ModDown + rescale) limbs
+};
+
+// The HE Mul pipeline for one job or a batch (JobRef).  fused = ModDown and
+// rescale merged (out is [2][l-1][N]); otherwise out is the level-l product.
+// NTT group offsets are relative to ntt_base.
+int run_pipeline(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, bool fused,
+                 cudaStream_t st)
 {
-    const WsLayout &W = c->host_levels[l].ws;
-    const LevelJobs &J = c->jobs[l];
-    const size_t N = (size_t)c->N;
-    u64 *d0 = ws + W.d0 * N, *d1 = ws + W.d1 * N, *d2 = ws + W.d2 * N;
     prof_mark(c, st, "");
     // Region 1: tensor product
-    HE_TRY(run_tensor(c, ct1, ct2, d0, d1, d2, l, st));
+    HE_TRY(run_tensor(c, R, st));
     prof_mark(c, st, "tensor");
     // key switching: iNTT(d2) (times N^-1 Qhat^-1), ModUp, NTT, inner product
-    HE_TRY(launch_ntt(c, ws, fused ? J.intt1f : J.intt1, fused ? J.n_intt1f : J.n_intt1, true, st, "intt_d2"));
-    HE_TRY(run_modup(c, ws + W.y * N, ws + W.u * N, l, st));
+    HE_TRY(launch_ntt(c, ntt_base, S.intt1, S.n_intt1, true, st, "intt_d2"));
+    HE_TRY(run_modup(c, R, st));
     prof_mark(c, st, "modup");
-    HE_TRY(launch_ntt(c, ws, J.ntt_up, J.n_ntt_up, false, st, "ntt_modup"));
-    HE_TRY(run_inner_product(c, ws + W.u * N, d2, evk, ws + W.ks * N, l, st));
+    HE_TRY(launch_ntt(c, ntt_base, S.ntt_up, S.n_ntt_up, false, st, "ntt_modup"));
+    HE_TRY(run_inner_product(c, R, evk, st));
     prof_mark(c, st, "inner_product");
     // ModDown: iNTT of the special limbs (times N^-1 Phat^-1), conversion, NTT
-    HE_TRY(launch_ntt(c, ws, fused ? J.intt2f : J.intt2, fused ? J.n_intt2f : J.n_intt2, true, st, "intt_special"));
-    HE_TRY(run_moddown_conv(c, ws + W.ys * N, ws + W.r * N, ws + W.z * N, l, fused, st));
+    HE_TRY(launch_ntt(c, ntt_base, S.intt2, S.n_intt2, true, st, "intt_special"));
+    HE_TRY(run_moddown_conv(c, R, fused, st));
     prof_mark(c, st, "moddown_conv");
+    HE_TRY(launch_ntt(c, ntt_base, S.ntt_last, S.n_ntt_last, false, st, "ntt_moddown"));
     if (fused) {
-        HE_TRY(launch_ntt(c, ws, J.ntt_z, J.n_ntt_z, false, st, "ntt_moddown"));
-        HE_TRY(run_combine_rescale(c, d0, d1, ws + W.ks * N, ws + W.z * N, out, l, st));
+        HE_TRY(run_combine_rescale(c, R, st));
         prof_mark(c, st, "combine_rescale");
     } else {
-        HE_TRY(launch_ntt(c, ws, J.ntt_conv, J.n_ntt_conv, false, st, "ntt_moddown"));
-        HE_TRY(run_combine_plain(c, d0, d1, ws + W.ks * N, ws + W.z * N, out, l, st));
+        HE_TRY(run_combine_plain(c, R, st));
         prof_mark(c, st, "combine");
     }
     return HE_OK;
+}
+
+JobRef single_job(const u64 *ct1, const u64 *ct2, u64 *out, u64 *ws, int l)
+{
+    JobRef R;
+    R.items = nullptr;
+    R.one.ct1 = ct1;
+    R.one.ct2 = ct2;
+    R.one.out = out;
+    R.one.ws = ws;
+    R.one.level = l;
+    R.one.pad = 0;
+    R.B = 1;
+    R.lmax = l;
+    return R;
+}
+
+Stages level_stages(const he_ctx *c, int l, bool fused)
+{
+    const LevelJobs &J = c->jobs[l];
+    Stages S;
+    S.intt1 = fused ? J.intt1f : J.intt1;
+    S.n_intt1 = fused ? J.n_intt1f : J.n_intt1;
+    S.ntt_up = J.ntt_up;
+    S.n_ntt_up = J.n_ntt_up;
+    S.intt2 = fused ? J.intt2f : J.intt2;
+    S.n_intt2 = fused ? J.n_intt2f : J.n_intt2;
+    S.ntt_last = fused ? J.ntt_z : J.ntt_conv;
+    S.n_ntt_last = fused ? J.n_ntt_z : J.n_ntt_conv;
+    return S;
+}
+
+int hemul_pipeline(he_ctx *c, const u64 *ct1, const u64 *ct2, const u64 *evk, int l, u64 *out, u64 *ws,
+                   bool fused, cudaStream_t st)
+{
+    return run_pipeline(c, single_job(ct1, ct2, out, ws, l), ws, level_stages(c, l, fused), evk, fused, st);
+}
+
+// ---- batches -------------------------------------------------------------
+// Batch workspace: [header: items | four NTT group lists] [job 0 ws] [job 1 ws] ...
+// Group offsets are relative to the first job's ws.
+size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t batch_header_bytes(const he_ctx *c, int count, const int *levels)
+{
+    size_t limbs = 0;
+    for (int i = 0; i < count; i++) {
+        const HostLevel &H = c->host_levels[levels[i]];
+        limbs += H.intt1f.size() + H.ntt_up.size() + H.intt2f.size() + H.ntt_z.size();
+    }
+    return round_up(sizeof(BatchItem) * count) + round_up(sizeof(NttGroup) * limbs);
+}
+
+size_t batch_bytes(const he_ctx *c, int count, const int *levels)
+{
+    size_t total = batch_header_bytes(c, count, levels);
+    for (int i = 0; i < count; i++) total += ws_bytes_for(c, levels[i]);
+    return total;
 }
 
 }  // namespace
@@ -215,8 +278,8 @@ int he_step_tensor(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, int leve
 {
     if (check_dev(c) || !ct1 || !ct2 || !d) return HE_EINVAL;
     if (level < 1 || level > c->L) return HE_ELEVEL;
-    const size_t lN = (size_t)level * c->N;
-    HE_TRY(run_tensor(c, ct1, ct2, d, d + lN, d + 2 * lN, level, S(stream)));
+    // d0, d1, d2 sit at limb offsets 0, l, 2l of a workspace: d serves as one
+    HE_TRY(run_tensor(c, single_job(ct1, ct2, nullptr, (u64 *)d, level), S(stream)));
     return HE_OK;
 }
 
@@ -228,20 +291,32 @@ int he_step_modup(he_ctx *c, const uint64_t *d2, int level, uint64_t *U, void *w
     const WsLayout &W = c->host_levels[level].ws;
     const LevelJobs &J = c->jobs[level];
     const size_t N = (size_t)c->N;
+    const size_t E = (size_t)c->K + level, beta = (size_t)(level + c->alpha - 1) / c->alpha;
     u64 *w = (u64 *)ws;
     cudaStream_t st = S(stream);
     HE_TRY(cudaMemcpyAsync(w + W.d2 * N, d2, (size_t)level * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+    HE_TRY(cudaMemcpyAsync(w + W.u * N, U, beta * E * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
     HE_TRY(launch_ntt(c, w, J.intt1, J.n_intt1, true, st));
-    HE_TRY(run_modup(c, w + W.y * N, (u64 *)U, level, st));
+    HE_TRY(run_modup(c, single_job(nullptr, nullptr, nullptr, w, level), st));
+    HE_TRY(cudaMemcpyAsync(U, w + W.u * N, beta * E * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
     return HE_OK;
 }
 
 int he_step_inner_product(he_ctx *c, const uint64_t *U, const uint64_t *d2, const uint64_t *evk, int level,
-                          uint64_t *KS, void *stream)
+                          uint64_t *KS, void *ws, size_t ws_bytes, void *stream)
 {
-    if (check_dev(c) || !U || !d2 || !evk || !KS) return HE_EINVAL;
+    if (check_dev(c) || !U || !d2 || !evk || !KS || !ws) return HE_EINVAL;
     if (level < 1 || level > c->L) return HE_ELEVEL;
-    HE_TRY(run_inner_product(c, U, d2, evk, KS, level, S(stream)));
+    if (ws_bytes < ws_bytes_for(c, level)) return HE_ENOMEM;
+    const WsLayout &W = c->host_levels[level].ws;
+    const size_t N = (size_t)c->N;
+    const size_t E = (size_t)c->K + level, beta = (size_t)(level + c->alpha - 1) / c->alpha;
+    u64 *w = (u64 *)ws;
+    cudaStream_t st = S(stream);
+    HE_TRY(cudaMemcpyAsync(w + W.d2 * N, d2, (size_t)level * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+    HE_TRY(cudaMemcpyAsync(w + W.u * N, U, beta * E * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+    HE_TRY(run_inner_product(c, single_job(nullptr, nullptr, nullptr, w, level), evk, st));
+    HE_TRY(cudaMemcpyAsync(KS, w + W.ks * N, 2 * E * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
     return HE_OK;
 }
 
@@ -261,10 +336,10 @@ int he_step_moddown(he_ctx *c, const uint64_t *X, int level, uint64_t *out, void
     HE_TRY(cudaMemsetAsync(w + (W.ks + E) * N, 0, (size_t)E * N * sizeof(u64), st));
     HE_TRY(cudaMemsetAsync(w + W.d0 * N, 0, 2 * (size_t)level * N * sizeof(u64), st));
     HE_TRY(launch_ntt(c, w, J.intt2, J.n_intt2, true, st));
-    HE_TRY(run_moddown_conv(c, w + W.ys * N, w + W.r * N, w + W.z * N, level, false, st));
+    const JobRef R = single_job(nullptr, nullptr, w + W.y * N, w, level);  // both halves land at y, u
+    HE_TRY(run_moddown_conv(c, R, false, st));
     HE_TRY(launch_ntt(c, w, J.ntt_conv, J.n_ntt_conv, false, st));
-    // the combine writes both halves; the b half is the answer
-    HE_TRY(run_combine_plain(c, w + W.d0 * N, w + W.d1 * N, w + W.ks * N, w + W.z * N, w + W.y * N, level, st));
+    HE_TRY(run_combine_plain(c, R, st));
     HE_TRY(cudaMemcpyAsync(out, w + W.y * N, (size_t)level * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
     return HE_OK;
 }
@@ -276,34 +351,84 @@ extern "C" {
 size_t he_batch_workspace_bytes(const he_ctx *c, int count, const int *levels)
 {
     if (!c || count < 1 || !levels) return 0;
-    size_t total = 0;
-    for (int i = 0; i < count; i++) {
+    for (int i = 0; i < count; i++)
         if (levels[i] < 2 || levels[i] > c->L) return 0;
-        total += (ws_bytes_for(c, levels[i]) + 255) & ~(size_t)255;
-    }
-    return total;
+    return batch_bytes(c, count, levels);
 }
 
 int he_mul_batch(he_ctx *c, int count, const he_job *jobs, const uint64_t *evk, void *ws, size_t ws_bytes,
                  void *stream)
 {
-    if (check_dev(c) || count < 1 || !jobs || !evk || !ws) return HE_EINVAL;
-    size_t need = 0;
+    if (check_dev(c) || count < 1 || count > 65535 || !jobs || !evk || !ws || !aligned(ws) || !aligned(evk))
+        return HE_EINVAL;
+    std::vector<int> levels(count);
+    int lmax = 0;
     for (int i = 0; i < count; i++) {
         const he_job &j = jobs[i];
         if (!j.ct1 || !j.ct2 || !j.out) return HE_EINVAL;
+        if (!aligned(j.ct1) || !aligned(j.ct2) || !aligned(j.out)) return HE_EINVAL;
         if (j.level < 2 || j.level > c->L) return HE_ELEVEL;
-        need += (ws_bytes_for(c, j.level) + 255) & ~(size_t)255;
+        levels[i] = j.level;
+        lmax = std::max(lmax, j.level);
     }
-    if (ws_bytes < need) return HE_ENOMEM;
-    char *w = (char *)ws;
+    if (ws_bytes < batch_bytes(c, count, levels.data())) return HE_ENOMEM;
+    const size_t N = (size_t)c->N;
+    const size_t hdr = batch_header_bytes(c, count, levels.data());
+    char *wsb = (char *)ws;
+    u64 *data = (u64 *)(wsb + hdr);
+    // items, and every job's single-limb NTT jobs shifted to its ws slice
+    std::vector<BatchItem> items(count);
+    std::vector<NttJob> l1, l2, l3, l4;
+    size_t off = 0;  // limbs
     for (int i = 0; i < count; i++) {
-        const he_job &j = jobs[i];
-        int rc = hemul_pipeline(c, j.ct1, j.ct2, evk, j.level, j.out, (u64 *)w, true, S(stream));
-        if (rc) return rc;
-        w += (ws_bytes_for(c, j.level) + 255) & ~(size_t)255;
+        const HostLevel &H = c->host_levels[levels[i]];
+        items[i].ct1 = jobs[i].ct1;
+        items[i].ct2 = jobs[i].ct2;
+        items[i].out = jobs[i].out;
+        items[i].ws = data + off * N;
+        items[i].level = levels[i];
+        items[i].pad = 0;
+        auto add = [&](const std::vector<NttJob> &src, std::vector<NttJob> &dst) {
+            for (NttJob j : src) {
+                j.src += (unsigned)off;
+                j.dst += (unsigned)off;
+                dst.push_back(j);
+            }
+        };
+        add(H.intt1f, l1);
+        add(H.ntt_up, l2);
+        add(H.intt2f, l3);
+        add(H.ntt_z, l4);
+        off += H.ws.total;
     }
-    return HE_OK;
+    if (off * N >= ((size_t)1 << 32) * N) return HE_EINVAL;  // offsets are 32-bit limb counts
+    // regroup by prime across jobs: limbs of different jobs share a twiddle tile
+    std::vector<NttGroup> g1 = group_jobs(l1), g2 = group_jobs(l2), g3 = group_jobs(l3), g4 = group_jobs(l4);
+    std::vector<unsigned char> head(hdr, 0);
+    const size_t items_bytes = round_up(sizeof(BatchItem) * count);
+    memcpy(head.data(), items.data(), sizeof(BatchItem) * count);
+    NttGroup *gdst = (NttGroup *)(head.data() + items_bytes);
+    const NttGroup *gdev = (const NttGroup *)(wsb + items_bytes);
+    size_t gi = 0;
+    Stages Sg;
+    auto put = [&](const std::vector<NttGroup> &g, const NttGroup *&p, int &n) {
+        memcpy(gdst + gi, g.data(), sizeof(NttGroup) * g.size());
+        p = gdev + gi;
+        n = (int)g.size();
+        gi += g.size();
+    };
+    put(g1, Sg.intt1, Sg.n_intt1);
+    put(g2, Sg.ntt_up, Sg.n_ntt_up);
+    put(g3, Sg.intt2, Sg.n_intt2);
+    put(g4, Sg.ntt_last, Sg.n_ntt_last);
+    cudaStream_t st = S(stream);
+    HE_TRY(cudaMemcpyAsync(ws, head.data(), hdr, cudaMemcpyHostToDevice, st));
+    JobRef R;
+    R.items = (const BatchItem *)ws;
+    memset(&R.one, 0, sizeof(R.one));
+    R.B = count;
+    R.lmax = lmax;
+    return run_pipeline(c, R, data, Sg, evk, true, st);
 }
 
 }  // extern "C"

@@ -52,9 +52,26 @@ std::vector<NttGroup> group_jobs(const std::vector<NttJob> &jobs);
 struct DevLevel {
     int l, beta, E, A;             // level, digits, K+l, alpha padded for the kernels
     int dig_lo[kMaxDigits], dig_n[kMaxDigits];
+    // workspace layout of one HE Mul at this level (limb offsets from the job's ws)
+    unsigned o_d0, o_d1, o_d2, o_y, o_u, o_ks, o_ys, o_r, o_z, o_total;
     const u64 *modupB;             // [beta][E][A]: [Qhat_{j,i}]_t split at bit 28, zero-padded
     const ulonglong2 *qinv_last;   // [l-1]: q_{l-1}^-1 mod q_i (value, Shoup)
     const ulonglong2 *pinv_qinv;   // [l-1]: P^-1 * q_{l-1}^-1 mod q_i
+};
+
+// One HE Mul of a launch: its operands, output, workspace base and level.
+// Kernels take a JobRef: either a device array of items (batched execution,
+// item = blockIdx.z) or one item by value (a single HE Mul).
+struct BatchItem {
+    const u64 *ct1, *ct2;
+    u64 *out, *ws;
+    int level, pad;
+};
+struct JobRef {
+    const BatchItem *items;  // device array, or nullptr to use `one`
+    BatchItem one;
+    int B;                   // number of jobs
+    int lmax;                // largest level among them
 };
 
 // Workspace layout of one HE Mul at level l (offsets in limbs).
@@ -128,16 +145,11 @@ cudaError_t launch_ntt(const he_ctx *ctx, u64 *base, const NttGroup *groups, int
                        cudaStream_t st, const char *tag = nullptr);
 cudaError_t launch_ntt2(const he_ctx *ctx, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups,
                         bool inverse, cudaStream_t st, const char *tag = nullptr);
-cudaError_t run_tensor(const he_ctx *c, const u64 *ct1, const u64 *ct2, u64 *d0, u64 *d1, u64 *d2, int l,
-                       cudaStream_t st);
-cudaError_t run_modup(const he_ctx *c, const u64 *y, u64 *U, int l, cudaStream_t st);
-cudaError_t run_inner_product(const he_ctx *c, const u64 *U, const u64 *d2, const u64 *evk, u64 *KS, int l,
-                              cudaStream_t st);
-cudaError_t run_moddown_conv(const he_ctx *c, const u64 *ys, const u64 *rr, u64 *z, int l, bool fused,
-                             cudaStream_t st);
-cudaError_t run_combine_plain(const he_ctx *c, const u64 *d0, const u64 *d1, const u64 *KS, const u64 *C, u64 *out,
-                              int l, cudaStream_t st);
-cudaError_t run_combine_rescale(const he_ctx *c, const u64 *d0, const u64 *d1, const u64 *KS, const u64 *Z,
-                                u64 *out, int l, cudaStream_t st);
+cudaError_t run_tensor(const he_ctx *c, const JobRef &R, cudaStream_t st);
+cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st);
+cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st);
+cudaError_t run_moddown_conv(const he_ctx *c, const JobRef &R, bool fused, cudaStream_t st);
+cudaError_t run_combine_plain(const he_ctx *c, const JobRef &R, cudaStream_t st);
+cudaError_t run_combine_rescale(const he_ctx *c, const JobRef &R, cudaStream_t st);
 cudaError_t run_rescale_combine(const he_ctx *c, const u64 *ct, const u64 *Z, u64 *out, int l, cudaStream_t st);
 }  // namespace he

@@ -335,6 +335,10 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         D.beta = (l + c->alpha - 1) / c->alpha;
         D.E = K + l;
         D.A = c->AP;
+        const WsLayout &Wl = H.ws;
+        D.o_d0 = (unsigned)Wl.d0; D.o_d1 = (unsigned)Wl.d1; D.o_d2 = (unsigned)Wl.d2; D.o_y = (unsigned)Wl.y;
+        D.o_u = (unsigned)Wl.u; D.o_ks = (unsigned)Wl.ks; D.o_ys = (unsigned)Wl.ys; D.o_r = (unsigned)Wl.r;
+        D.o_z = (unsigned)Wl.z; D.o_total = (unsigned)Wl.total;
         for (int j = 0; j < D.beta; j++) {
             D.dig_lo[j] = j * c->alpha;
             D.dig_n[j] = std::min((j + 1) * c->alpha, l) - j * c->alpha;

@@ -15,7 +15,10 @@
 //  k_combine_*     the final additions (Fig. 2) and the rescale division.
 //
 // Every kernel handles two consecutive coefficients per thread with 16-byte
-// loads and stores; the limb-major layouts keep all accesses coalesced.
+// loads and stores; the limb-major layouts keep all accesses coalesced.  A
+// launch serves one HE Mul or a batch of them (grid.z = job), each job
+// bringing its own operands, workspace and level (JobRef); blocks beyond a
+// job's level exit at once.
 #include <algorithm>
 
 #include "he_internal.h"
@@ -30,16 +33,21 @@ constexpr int kThreads = 256;
 __device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *reinterpret_cast<const ulonglong2 *>(p); }
 __device__ __forceinline__ void st2(u64 *p, u64 x, u64 y) { *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(x, y); }
 
-// grid: x over N/2/kThreads, y over limbs
+__device__ __forceinline__ BatchItem job_of(const JobRef &R, int z) { return R.items ? R.items[z] : R.one; }
+
+// grid: x over N/2/kThreads, y over limbs (up to the largest level), z over jobs
 __global__ void __launch_bounds__(kThreads)
-k_tensor(const u64 *__restrict__ ct1, const u64 *__restrict__ ct2, u64 *__restrict__ d0, u64 *__restrict__ d1,
-         u64 *__restrict__ d2, const DevPrime *__restrict__ primes, int K, int l, int N)
+k_tensor(const JobRef R, const DevPrime *__restrict__ primes, const DevLevel *__restrict__ lv_arr, int K, int N)
 {
-    const int i = blockIdx.y;
+    const BatchItem it = job_of(R, blockIdx.z);
+    const int l = it.level, i = blockIdx.y;
+    if (i >= l) return;
+    const DevLevel &lv = lv_arr[l];
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[K + i];
     const size_t ob = (size_t)i * N + n, oa = ((size_t)l + i) * N + n;
-    ulonglong2 b1 = ld2(ct1 + ob), a1 = ld2(ct1 + oa), b2 = ld2(ct2 + ob), a2 = ld2(ct2 + oa);
+    const ulonglong2 b1 = ld2(it.ct1 + ob), a1 = ld2(it.ct1 + oa), b2 = ld2(it.ct2 + ob), a2 = ld2(it.ct2 + oa);
+    u64 *d0 = it.ws + (size_t)lv.o_d0 * N, *d1 = it.ws + (size_t)lv.o_d1 * N, *d2 = it.ws + (size_t)lv.o_d2 * N;
     st2(d0 + (size_t)i * N + n, mul_mod(b1.x, b2.x, pr.q, pr.mu, pr.s), mul_mod(b1.y, b2.y, pr.q, pr.mu, pr.s));
     U128 x = mul_wide(a1.x, b2.x), y = mul_wide(a1.y, b2.y);
     mac(x, a2.x, b1.x);
@@ -48,24 +56,27 @@ k_tensor(const u64 *__restrict__ ct1, const u64 *__restrict__ ct2, u64 *__restri
     st2(d2 + (size_t)i * N + n, mul_mod(a1.x, a2.x, pr.q, pr.mu, pr.s), mul_mod(a1.y, a2.y, pr.q, pr.mu, pr.s));
 }
 
-// grid: x over N/2/kThreads, y over digits, z over chunks of kModupChunk
-// targets.  y: [l][N] (scaled iNTT of d2), U: [beta][E][N].  Target u of
-// digit j (u < E - n_j) is ext limb u below the digit's own limbs, u + n_j above.
-// Digits are padded to A limbs with zero constants (the padding loads reread a
-// real limb, whose value is multiplied by zero), so the MAC loop has no
-// predicates; the chunk's constants and prime parameters sit in shared memory.
+// grid: x over N/2/kThreads, y over (digit, chunk of kModupChunk targets),
+// z over jobs.  Input: the scaled iNTT of d2 (y region), output U: [beta][E][N].
+// Target u of digit j (u < E - n_j) is ext limb u below the digit's own limbs,
+// u + n_j above.  Digits are padded to A limbs with zero constants (the padding
+// loads reread a real limb, whose value is multiplied by zero), so the MAC loop
+// has no predicates; the chunk's constants and prime parameters sit in shared
+// memory.
 constexpr int kModupChunk = 8;
 
 template <int A>
 __global__ void __launch_bounds__(kThreads)
-k_modup(const u64 *__restrict__ y, u64 *__restrict__ U, const DevLevel *__restrict__ lv_arr, int l,
-        const DevPrime *__restrict__ primes, int K, int N)
+k_modup(const JobRef R, const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int N,
+        int chunks)
 {
-    const DevLevel &lv = lv_arr[l];
-    const int j = blockIdx.y;
+    const BatchItem it = job_of(R, blockIdx.z);
+    const DevLevel &lv = lv_arr[it.level];
+    const int j = blockIdx.y / chunks;
+    if (j >= lv.beta) return;
     const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
     const int E = lv.E;
-    const int u0 = blockIdx.z * kModupChunk;
+    const int u0 = (blockIdx.y - j * chunks) * kModupChunk;
     const int cnt = min(kModupChunk, E - nj - u0);
     if (cnt <= 0) return;
     __shared__ u64 sB[kModupChunk][A];
@@ -86,6 +97,7 @@ k_modup(const u64 *__restrict__ y, u64 *__restrict__ U, const DevLevel *__restri
         smu[threadIdx.x] = primes[e].mu;
         ss[threadIdx.x] = primes[e].s;
     }
+    const u64 *y = it.ws + (size_t)lv.o_y * N;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     uint32_t x0[A], x1[A], z0[A], z1[A];
 #pragma unroll
@@ -95,7 +107,7 @@ k_modup(const u64 *__restrict__ y, u64 *__restrict__ U, const DevLevel *__restri
         split28(v.y, z0[i], z1[i]);
     }
     __syncthreads();
-    u64 *Uj = U + (size_t)j * E * N;
+    u64 *Uj = it.ws + ((size_t)lv.o_u + (size_t)j * E) * N;
     for (int u = 0; u < cnt; u++) {
         Acc3 ax = {0, 0, 0}, ay = {0, 0, 0};
 #pragma unroll
@@ -110,37 +122,41 @@ k_modup(const u64 *__restrict__ y, u64 *__restrict__ U, const DevLevel *__restri
     }
 }
 
-// grid: x over N/2/kThreads, y over E = K + l.  U: [beta][E][N] (own-digit
-// rows read from d2), evk: [dnum][2][K+L][N], KS: [2][E][N].
+// grid: x over N/2/kThreads, y over ext limbs (up to K + lmax), z over jobs.
+// U: [beta][E][N] (own-digit rows read from d2), evk: [dnum][2][K+L][N],
+// KS: [2][E][N].
 __global__ void __launch_bounds__(kThreads)
-k_inner_product(const u64 *__restrict__ U, const u64 *__restrict__ d2, const u64 *__restrict__ evk,
-                u64 *__restrict__ KS, const DevLevel *__restrict__ lv_arr, int l, const DevPrime *__restrict__ primes,
-                int K, int L, int N)
+k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__restrict__ lv_arr,
+                const DevPrime *__restrict__ primes, int K, int L, int N)
 {
-    const DevLevel &lv = lv_arr[l];
+    const BatchItem it = job_of(R, blockIdx.z);
+    const DevLevel &lv = lv_arr[it.level];
     const int e = blockIdx.y;
     const int E = lv.E, EL = K + L;
+    if (e >= E) return;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[e];
+    const u64 *U = it.ws + (size_t)lv.o_u * N, *d2 = it.ws + (size_t)lv.o_d2 * N;
     U128 bx = {0, 0}, by = {0, 0}, ax = {0, 0}, ay = {0, 0};
     for (int j = 0; j < lv.beta; j++) {
         const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
         const bool own = e >= K && e - K >= lo && e - K < lo + nj;
         const u64 *up = own ? d2 + (size_t)(e - K) * N : U + ((size_t)j * E + e) * N;
-        ulonglong2 u = ld2(up + n);
-        ulonglong2 kb = ld2(evk + ((size_t)(2 * j) * EL + e) * N + n);
-        ulonglong2 ka = ld2(evk + ((size_t)(2 * j + 1) * EL + e) * N + n);
+        const ulonglong2 u = ld2(up + n);
+        const ulonglong2 kb = ld2(evk + ((size_t)(2 * j) * EL + e) * N + n);
+        const ulonglong2 ka = ld2(evk + ((size_t)(2 * j + 1) * EL + e) * N + n);
         mac(bx, u.x, kb.x);
         mac(by, u.y, kb.y);
         mac(ax, u.x, ka.x);
         mac(ay, u.y, ka.y);
     }
+    u64 *KS = it.ws + (size_t)lv.o_ks * N;
     st2(KS + (size_t)e * N + n, barrett128(bx, pr.q, pr.mu, pr.s), barrett128(by, pr.q, pr.mu, pr.s));
     st2(KS + ((size_t)E + e) * N + n, barrett128(ax, pr.q, pr.mu, pr.s), barrett128(ay, pr.q, pr.mu, pr.s));
 }
 
-// grid: x over N/2/kThreads, y over h in {0,1}, z over chunks of
-// kModdownChunk outputs.  ys: [2][K] coefficient form (already times
+// grid: x over N/2/kThreads, y over (h in {0,1}, chunk of kModdownChunk
+// outputs), z over jobs.  ys: [2][K] coefficient form (already times
 // Phat_k^-1).  PLAIN: z[h][i] = conv_i for i < l.
 // FUSED: r = r0 + (r1 - conv_{l-1}) P^-1 mod q_{l-1} with r0 = iNTT(d_h)_{l-1},
 // r1 = iNTT(KS_h)_{l-1}; z[h][i] = conv_i P^-1 + r mod q_i for i < l-1.
@@ -165,13 +181,15 @@ __device__ __forceinline__ void conv_one(const uint32_t *x0, const uint32_t *x1,
 
 template <int KM, bool FUSED>
 __global__ void __launch_bounds__(kThreads)
-k_moddown_conv(const u64 *__restrict__ ys, const u64 *__restrict__ rr, u64 *__restrict__ z,
-               const u64 *__restrict__ PB, const ulonglong2 *__restrict__ pinv, const DevPrime *__restrict__ primes,
-               int K, int l, int N)
+k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__restrict__ pinv,
+               const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int N, int chunks)
 {
-    const int h = blockIdx.y;
+    const BatchItem it = job_of(R, blockIdx.z);
+    const int l = it.level;
+    const DevLevel &lv = lv_arr[l];
+    const int h = blockIdx.y / chunks;
     const int nout = FUSED ? l - 1 : l;
-    const int i0 = blockIdx.z * kModdownChunk;
+    const int i0 = (blockIdx.y - h * chunks) * kModdownChunk;
     const int cnt = min(kModdownChunk, nout - i0);
     if (cnt <= 0) return;
     // rows 0..cnt-1: this chunk's outputs; row kModdownChunk: q_{l-1} (fused)
@@ -194,6 +212,8 @@ k_moddown_conv(const u64 *__restrict__ ys, const u64 *__restrict__ rr, u64 *__re
             spv[r] = pinv[i];
         }
     }
+    const u64 *ys = it.ws + (size_t)lv.o_ys * N, *rr = it.ws + (size_t)lv.o_r * N;
+    u64 *z = it.ws + (size_t)lv.o_z * N;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     uint32_t x0[KM], x1[KM], z0[KM], z1[KM];
 #pragma unroll
@@ -228,43 +248,53 @@ k_moddown_conv(const u64 *__restrict__ ys, const u64 *__restrict__ rr, u64 *__re
     }
 }
 
+// grid: x over N/2/kThreads, y over limbs, z over 2 * jobs (h = z & 1).
 // out[h][i] = d_h[i] + (KS_h[K+i] - C[h][i]) P^-1 mod q_i, i < l
 __global__ void __launch_bounds__(kThreads)
-k_combine_plain(const u64 *__restrict__ d0, const u64 *__restrict__ d1, const u64 *__restrict__ KS,
-                const u64 *__restrict__ C, u64 *__restrict__ out, const ulonglong2 *__restrict__ pinv,
-                const DevPrime *__restrict__ primes, int K, int l, int N)
+k_combine_plain(const JobRef R, const ulonglong2 *__restrict__ pinv, const DevLevel *__restrict__ lv_arr,
+                const DevPrime *__restrict__ primes, int K, int N)
 {
-    const int i = blockIdx.y, h = blockIdx.z;
+    const BatchItem it = job_of(R, blockIdx.z >> 1);
+    const int h = blockIdx.z & 1, l = it.level, i = blockIdx.y;
+    if (i >= l) return;
+    const DevLevel &lv = lv_arr[l];
     const int E = K + l;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[K + i];
     const ulonglong2 pv = pinv[i];
-    ulonglong2 d = ld2((h ? d1 : d0) + (size_t)i * N + n);
-    ulonglong2 ks = ld2(KS + ((size_t)h * E + K + i) * N + n);
-    ulonglong2 c = ld2(C + ((size_t)h * l + i) * N + n);
-    u64 x = add_mod(d.x, shoup(sub_mod(ks.x, c.x, pr.q), pv.x, pv.y, pr.q), pr.q);
-    u64 y = add_mod(d.y, shoup(sub_mod(ks.y, c.y, pr.q), pv.x, pv.y, pr.q), pr.q);
-    st2(out + ((size_t)h * l + i) * N + n, x, y);
+    const u64 *d = it.ws + (size_t)(h ? lv.o_d1 : lv.o_d0) * N;
+    const u64 *KS = it.ws + (size_t)lv.o_ks * N, *C = it.ws + (size_t)lv.o_z * N;
+    const ulonglong2 dv = ld2(d + (size_t)i * N + n);
+    const ulonglong2 ks = ld2(KS + ((size_t)h * E + K + i) * N + n);
+    const ulonglong2 c = ld2(C + ((size_t)h * l + i) * N + n);
+    const u64 x = add_mod(dv.x, shoup(sub_mod(ks.x, c.x, pr.q), pv.x, pv.y, pr.q), pr.q);
+    const u64 y = add_mod(dv.y, shoup(sub_mod(ks.y, c.y, pr.q), pv.x, pv.y, pr.q), pr.q);
+    st2(it.out + ((size_t)h * l + i) * N + n, x, y);
 }
 
 // Fused ModDown + rescale: out[h][i] = (d_h[i] + KS_h[K+i] P^-1 - Z[h][i]) q_{l-1}^-1, i < l-1
+// grid: x over N/2/kThreads, y over limbs, z over 2 * jobs (h = z & 1).
 __global__ void __launch_bounds__(kThreads)
-k_combine_rescale(const u64 *__restrict__ d0, const u64 *__restrict__ d1, const u64 *__restrict__ KS,
-                  const u64 *__restrict__ Z, u64 *__restrict__ out, const ulonglong2 *__restrict__ pinv,
-                  const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int l, int N)
+k_combine_rescale(const JobRef R, const ulonglong2 *__restrict__ pinv, const DevLevel *__restrict__ lv_arr,
+                  const DevPrime *__restrict__ primes, int K, int N)
 {
-    const int i = blockIdx.y, h = blockIdx.z;
+    const BatchItem it = job_of(R, blockIdx.z >> 1);
+    const int h = blockIdx.z & 1, l = it.level, i = blockIdx.y;
+    if (i >= l - 1) return;
+    const DevLevel &lv = lv_arr[l];
     const int E = K + l;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[K + i];
     const ulonglong2 pv = pinv[i];
-    const ulonglong2 qv = lv_arr[l].qinv_last[i];
-    ulonglong2 d = ld2((h ? d1 : d0) + (size_t)i * N + n);
-    ulonglong2 ks = ld2(KS + ((size_t)h * E + K + i) * N + n);
-    ulonglong2 zz = ld2(Z + ((size_t)h * (l - 1) + i) * N + n);
-    u64 x = sub_mod(add_mod(d.x, shoup(ks.x, pv.x, pv.y, pr.q), pr.q), zz.x, pr.q);
-    u64 y = sub_mod(add_mod(d.y, shoup(ks.y, pv.x, pv.y, pr.q), pr.q), zz.y, pr.q);
-    st2(out + ((size_t)h * (l - 1) + i) * N + n, shoup(x, qv.x, qv.y, pr.q), shoup(y, qv.x, qv.y, pr.q));
+    const ulonglong2 qv = lv.qinv_last[i];
+    const u64 *d = it.ws + (size_t)(h ? lv.o_d1 : lv.o_d0) * N;
+    const u64 *KS = it.ws + (size_t)lv.o_ks * N, *Z = it.ws + (size_t)lv.o_z * N;
+    const ulonglong2 dv = ld2(d + (size_t)i * N + n);
+    const ulonglong2 ks = ld2(KS + ((size_t)h * E + K + i) * N + n);
+    const ulonglong2 zz = ld2(Z + ((size_t)h * (l - 1) + i) * N + n);
+    const u64 x = sub_mod(add_mod(dv.x, shoup(ks.x, pv.x, pv.y, pr.q), pr.q), zz.x, pr.q);
+    const u64 y = sub_mod(add_mod(dv.y, shoup(ks.y, pv.x, pv.y, pr.q), pr.q), zz.y, pr.q);
+    st2(it.out + ((size_t)h * (l - 1) + i) * N + n, shoup(x, qv.x, qv.y, pr.q), shoup(y, qv.x, qv.y, pr.q));
 }
 
 // Rescale on its own: out[h][i] = (c_h[i] - Z[h][i]) q_{l-1}^-1, i < l-1
@@ -276,8 +306,8 @@ k_rescale_combine(const u64 *__restrict__ ct, const u64 *__restrict__ Z, u64 *__
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[K + i];
     const ulonglong2 qv = lv_arr[l].qinv_last[i];
-    ulonglong2 c = ld2(ct + ((size_t)h * l + i) * N + n);
-    ulonglong2 zz = ld2(Z + ((size_t)h * (l - 1) + i) * N + n);
+    const ulonglong2 c = ld2(ct + ((size_t)h * l + i) * N + n);
+    const ulonglong2 zz = ld2(Z + ((size_t)h * (l - 1) + i) * N + n);
     st2(out + ((size_t)h * (l - 1) + i) * N + n, shoup(sub_mod(c.x, zz.x, pr.q), qv.x, qv.y, pr.q),
         shoup(sub_mod(c.y, zz.y, pr.q), qv.x, qv.y, pr.q));
 }
@@ -286,24 +316,25 @@ inline dim3 grid_x(int N) { return dim3((unsigned)(N / 2 / kThreads)); }
 
 }  // namespace
 
-cudaError_t run_tensor(const he_ctx *c, const u64 *ct1, const u64 *ct2, u64 *d0, u64 *d1, u64 *d2, int l,
-                       cudaStream_t st)
+cudaError_t run_tensor(const he_ctx *c, const JobRef &R, cudaStream_t st)
 {
     dim3 g = grid_x(c->N);
-    g.y = l;
-    k_tensor<<<g, kThreads, 0, st>>>(ct1, ct2, d0, d1, d2, c->d_primes, c->K, l, c->N);
+    g.y = R.lmax;
+    g.z = R.B;
+    k_tensor<<<g, kThreads, 0, st>>>(R, c->d_primes, c->d_levels, c->K, c->N);
     return cudaGetLastError();
 }
 
-cudaError_t run_modup(const he_ctx *c, const u64 *y, u64 *U, int l, cudaStream_t st)
+cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st)
 {
+    // the most targets any digit of any level up to lmax has: K + (beta - 1) alpha
+    const int beta = (R.lmax + c->alpha - 1) / c->alpha;
+    const int chunks = (c->K + (beta - 1) * c->alpha + kModupChunk - 1) / kModupChunk;
     dim3 g = grid_x(c->N);
-    g.y = (l + c->alpha - 1) / c->alpha;
-    const int beta = (l + c->alpha - 1) / c->alpha;
-    const int ntarget = c->K + (beta - 1) * c->alpha;  // targets of the shortest (last) digit: the most
-    g.z = (ntarget + kModupChunk - 1) / kModupChunk;
+    g.y = beta * chunks;
+    g.z = R.B;
     const int a = c->AP;
-#define HE_MODUP(AA) k_modup<AA><<<g, kThreads, 0, st>>>(y, U, c->d_levels, l, c->d_primes, c->K, c->N)
+#define HE_MODUP(AA) k_modup<AA><<<g, kThreads, 0, st>>>(R, c->d_levels, c->d_primes, c->K, c->N, chunks)
     if (a == 1) HE_MODUP(1);
     else if (a == 2) HE_MODUP(2);
     else if (a == 4) HE_MODUP(4);
@@ -314,26 +345,30 @@ cudaError_t run_modup(const he_ctx *c, const u64 *y, u64 *U, int l, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t run_inner_product(const he_ctx *c, const u64 *U, const u64 *d2, const u64 *evk, u64 *KS, int l,
-                              cudaStream_t st)
+cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st)
 {
     dim3 g = grid_x(c->N);
-    g.y = c->K + l;
-    k_inner_product<<<g, kThreads, 0, st>>>(U, d2, evk, KS, c->d_levels, l, c->d_primes, c->K, c->L, c->N);
+    g.y = c->K + R.lmax;
+    g.z = R.B;
+    k_inner_product<<<g, kThreads, 0, st>>>(R, evk, c->d_levels, c->d_primes, c->K, c->L, c->N);
     return cudaGetLastError();
 }
 
-cudaError_t run_moddown_conv(const he_ctx *c, const u64 *ys, const u64 *rr, u64 *z, int l, bool fused,
-                             cudaStream_t st)
+cudaError_t run_moddown_conv(const he_ctx *c, const JobRef &R, bool fused, cudaStream_t st)
 {
+    const int chunks = (R.lmax + kModdownChunk - 1) / kModdownChunk;
     dim3 g = grid_x(c->N);
-    g.y = 2;
-    g.z = ((fused ? l - 1 : l) + kModdownChunk - 1) / kModdownChunk;
+    g.y = 2 * chunks;
+    g.z = R.B;
     const int K = c->K;
-#define HE_MD(KK)                                                                                                  \
-    do {                                                                                                           \
-        if (fused) k_moddown_conv<KK, true><<<g, kThreads, 0, st>>>(ys, rr, z, c->d_PB, c->d_pinv, c->d_primes, K, l, c->N); \
-        else k_moddown_conv<KK, false><<<g, kThreads, 0, st>>>(ys, rr, z, c->d_PB, c->d_pinv, c->d_primes, K, l, c->N);     \
+#define HE_MD(KK)                                                                                                   \
+    do {                                                                                                            \
+        if (fused)                                                                                                  \
+            k_moddown_conv<KK, true><<<g, kThreads, 0, st>>>(R, c->d_PB, c->d_pinv, c->d_levels, c->d_primes, K,   \
+                                                             c->N, chunks);                                         \
+        else                                                                                                        \
+            k_moddown_conv<KK, false><<<g, kThreads, 0, st>>>(R, c->d_PB, c->d_pinv, c->d_levels, c->d_primes, K,  \
+                                                              c->N, chunks);                                        \
     } while (0)
     const int kp = c->KP;
     if (kp == 1) HE_MD(1);
@@ -346,23 +381,21 @@ cudaError_t run_moddown_conv(const he_ctx *c, const u64 *ys, const u64 *rr, u64 
     return cudaGetLastError();
 }
 
-cudaError_t run_combine_plain(const he_ctx *c, const u64 *d0, const u64 *d1, const u64 *KS, const u64 *C, u64 *out,
-                              int l, cudaStream_t st)
+cudaError_t run_combine_plain(const he_ctx *c, const JobRef &R, cudaStream_t st)
 {
     dim3 g = grid_x(c->N);
-    g.y = l;
-    g.z = 2;
-    k_combine_plain<<<g, kThreads, 0, st>>>(d0, d1, KS, C, out, c->d_pinv, c->d_primes, c->K, l, c->N);
+    g.y = R.lmax;
+    g.z = 2 * R.B;
+    k_combine_plain<<<g, kThreads, 0, st>>>(R, c->d_pinv, c->d_levels, c->d_primes, c->K, c->N);
     return cudaGetLastError();
 }
 
-cudaError_t run_combine_rescale(const he_ctx *c, const u64 *d0, const u64 *d1, const u64 *KS, const u64 *Z,
-                                u64 *out, int l, cudaStream_t st)
+cudaError_t run_combine_rescale(const he_ctx *c, const JobRef &R, cudaStream_t st)
 {
     dim3 g = grid_x(c->N);
-    g.y = l - 1;
-    g.z = 2;
-    k_combine_rescale<<<g, kThreads, 0, st>>>(d0, d1, KS, Z, out, c->d_pinv, c->d_levels, c->d_primes, c->K, l, c->N);
+    g.y = R.lmax - 1;
+    g.z = 2 * R.B;
+    k_combine_rescale<<<g, kThreads, 0, st>>>(R, c->d_pinv, c->d_levels, c->d_primes, c->K, c->N);
     return cudaGetLastError();
 }
 

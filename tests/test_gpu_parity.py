@@ -133,7 +133,7 @@ def test_inner_product_parity(g, name, level):
             U[j, op.K + i] = d2[i]
     evk = rand_evk(op, 50)
     KS = torch.empty((2, E, op.N), dtype=torch.int64, device="cuda")
-    g.he_step_inner_product(ctx, dev(g, U), dev(g, d2), dev(g, evk), level, KS)
+    g.he_step_inner_product(ctx, dev(g, U), dev(g, d2), dev(g, evk), level, KS, g.workspace(ctx, level))
     torch.cuda.synchronize()
     assert np.array_equal(host(g, KS), oracle.inner_product(op, U, evk, level))
 
