@@ -247,8 +247,13 @@ def run_batched(g, ctx, evk_t, dev, stream, wsz, count=64, reps=20):
         for a, b, o, lv in jobs:
             g.he_mul_rescale(ctx, a, b, evk_t, lv, o, ws1, stream)
 
+    graph = g.BatchGraph(ctx, count, evk_t, stream, device=dev)
+
+    def graphed():
+        graph.launch(jobs, stream)
+
     res = {}
-    for name, fn in (("batched", batch), ("single_path", singles)):
+    for name, fn in (("batched", batch), ("batched_graph", graphed), ("single_path", singles)):
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
@@ -266,6 +271,7 @@ def run_batched(g, ctx, evk_t, dev, stream, wsz, count=64, reps=20):
         res[name] = {"HE_Mul_per_s": wsz * count * reps / (ms * 1e-3), "ms_per_batch": ms / reps,
                      "batch_latency_ms_p50": float(np.percentile(lat, 50)),
                      "batch_latency_ms_p99": float(np.percentile(lat, 99))}
+    graph.close()
     res["config"] = {"jobs": count, "N": N, "levels": "uniform 4..24 (seed 1604)", "mean_level": float(np.mean(levels)),
                      "operands": "uniform residues"}
     return res

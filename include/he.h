@@ -205,6 +205,23 @@ size_t he_batch_workspace_bytes(const he_ctx *ctx, int count, const int *levels)
 int he_mul_batch(he_ctx *ctx, int count, const he_job *jobs, const uint64_t *evk_dev, void *ws,
                  size_t ws_bytes, void *stream);
 
+/* The batched path captured once in a CUDA graph for up to max_jobs jobs:
+ * every launch is sized for max_jobs jobs at level L and reads the job table
+ * and NTT job lists (and their counts) that the graph's first node copies from
+ * a pinned host buffer, so he_batch_graph_launch with any batch of at most
+ * max_jobs jobs (levels 2..L) is one graph launch.  ws (device, at least
+ * he_batch_graph_workspace_bytes(max_jobs)) and evk_dev are bound at
+ * creation and must outlive the graph.  Creation captures `stream` (no work
+ * runs).  A launch waits on the host for the previous launch of the same graph
+ * to finish before it rewrites the pinned table.  Results are bit-identical to
+ * he_mul_rescale per job. */
+typedef struct he_batch_graph he_batch_graph;
+size_t he_batch_graph_workspace_bytes(const he_ctx *ctx, int max_jobs);
+int he_batch_graph_create(he_ctx *ctx, int max_jobs, const uint64_t *evk_dev, void *ws, size_t ws_bytes,
+                          void *stream, he_batch_graph **out);
+int he_batch_graph_launch(he_batch_graph *g, int count, const he_job *jobs, void *stream);
+int he_batch_graph_destroy(he_batch_graph *g);
+
 /* ---- profiling ------------------------------------------------------------ */
 
 /* Enable (1) or disable (0) per-kernel CUDA-event marks on this context's

@@ -89,6 +89,11 @@ _SIGS = {
                                            ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                            ctypes.c_void_p]),
     "he_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "he_batch_graph_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int]),
+    "he_batch_graph_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
+    "he_batch_graph_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "he_batch_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "he_probe_butterfly_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "he_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
@@ -366,3 +371,35 @@ def he_probe_butterfly_rate(blocks: int, iters: int, stream=None) -> float:
     _check(lib().he_probe_butterfly_rate(blocks, iters, ctypes.byref(r), _stream_ptr(stream)),
            "he_probe_butterfly_rate")
     return r.value
+
+
+class BatchGraph:
+    """he_batch_graph: the batched path captured once in a CUDA graph."""
+
+    def __init__(self, ctx, max_jobs: int, evk, stream=None, device="cuda"):
+        import torch
+        self.ctx = ctx
+        nbytes = int(lib().he_batch_graph_workspace_bytes(ctx.ptr, max_jobs))
+        self.ws = torch.empty(nbytes // 8, dtype=torch.int64, device=device)
+        self.evk = evk
+        self.ptr = ctypes.c_void_p()
+        _check(lib().he_batch_graph_create(ctx.ptr, max_jobs, _dev_ptr(evk), _dev_ptr(self.ws), nbytes,
+                                           _stream_ptr(stream), ctypes.byref(self.ptr)), "he_batch_graph_create")
+
+    def launch(self, jobs, stream=None):
+        arr = (he_job * len(jobs))()
+        for i, (a, b, o, lv) in enumerate(jobs):
+            arr[i] = he_job(_dev_ptr(a), _dev_ptr(b), _dev_ptr(o), int(lv))
+        _check(lib().he_batch_graph_launch(self.ptr, len(jobs), ctypes.cast(arr, ctypes.c_void_p),
+                                           _stream_ptr(stream)), "he_batch_graph_launch")
+
+    def close(self):
+        if self.ptr:
+            lib().he_batch_graph_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -58,6 +58,7 @@ struct Stages {
     const NttGroup *ntt_up;   int n_ntt_up;    // NTT of the ModUp outputs
     const NttGroup *intt2;    int n_intt2;     // iNTT of the special limbs (+ KS last limb when fused)
     const NttGroup *ntt_last; int n_ntt_last;  // NTT of the ModDown (fused: ModDown + rescale) limbs
+    const int *counts = nullptr;               // optional device-side counts of the four lists
 };
 
 // The HE Mul pipeline for one job or a batch (JobRef).  fused = ModDown and
@@ -71,17 +72,18 @@ int run_pipeline(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, con
     HE_TRY(run_tensor(c, R, st));
     prof_mark(c, st, "tensor");
     // key switching: iNTT(d2) (times N^-1 Qhat^-1), ModUp, NTT, inner product
-    HE_TRY(launch_ntt(c, ntt_base, S.intt1, S.n_intt1, true, st, "intt_d2"));
+    const int *cnt = S.counts;
+    HE_TRY(launch_ntt(c, ntt_base, S.intt1, S.n_intt1, true, st, "intt_d2", cnt ? cnt + 0 : nullptr));
     HE_TRY(run_modup(c, R, st));
     prof_mark(c, st, "modup");
-    HE_TRY(launch_ntt(c, ntt_base, S.ntt_up, S.n_ntt_up, false, st, "ntt_modup"));
+    HE_TRY(launch_ntt(c, ntt_base, S.ntt_up, S.n_ntt_up, false, st, "ntt_modup", cnt ? cnt + 1 : nullptr));
     HE_TRY(run_inner_product(c, R, evk, st));
     prof_mark(c, st, "inner_product");
     // ModDown: iNTT of the special limbs (times N^-1 Phat^-1), conversion, NTT
-    HE_TRY(launch_ntt(c, ntt_base, S.intt2, S.n_intt2, true, st, "intt_special"));
+    HE_TRY(launch_ntt(c, ntt_base, S.intt2, S.n_intt2, true, st, "intt_special", cnt ? cnt + 2 : nullptr));
     HE_TRY(run_moddown_conv(c, R, fused, st));
     prof_mark(c, st, "moddown_conv");
-    HE_TRY(launch_ntt(c, ntt_base, S.ntt_last, S.n_ntt_last, false, st, "ntt_moddown"));
+    HE_TRY(launch_ntt(c, ntt_base, S.ntt_last, S.n_ntt_last, false, st, "ntt_moddown", cnt ? cnt + 3 : nullptr));
     if (fused) {
         HE_TRY(run_combine_rescale(c, R, st));
         prof_mark(c, st, "combine_rescale");
@@ -506,6 +508,182 @@ int he_mul_rescale_host(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, con
     if (rc) return rc;
     HE_TRY(cudaMemcpyAsync(out, dout, 2 * (size_t)(level - 1) * limb, cudaMemcpyDeviceToHost, st));
     HE_TRY(cudaStreamSynchronize(st));
+    return HE_OK;
+}
+
+}  // extern "C"
+
+// ---- batch graphs ----------------------------------------------------------
+// The batched pipeline captured once in a CUDA graph for up to max_jobs jobs:
+// every grid is sized for max_jobs jobs at level L, the job table and NTT
+// group lists (and their counts) live at the head of the workspace and are
+// refreshed from a pinned host copy by the graph's first node, so a replay
+// with a different batch (count, levels, operands) is one graph launch.
+// Unused job slots carry level 0, for which every kernel block exits.
+struct he_batch_graph {
+    he_ctx *c = nullptr;
+    int max_jobs = 0;
+    const u64 *evk = nullptr;
+    char *ws = nullptr;
+    size_t hdr = 0, slot_limbs = 0;
+    size_t items_bytes = 0, counts_off = 0, lists_off[4] = {0, 0, 0, 0};
+    int list_max[4] = {0, 0, 0, 0};
+    unsigned char *pinned = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    bool launched = false;
+};
+
+namespace {
+
+void graph_layout(const he_ctx *c, int max_jobs, he_batch_graph *g)
+{
+    int mx[4] = {0, 0, 0, 0};
+    for (int l = 2; l <= c->L; l++) {
+        const HostLevel &H = c->host_levels[l];
+        mx[0] = std::max(mx[0], (int)H.intt1f.size());
+        mx[1] = std::max(mx[1], (int)H.ntt_up.size());
+        mx[2] = std::max(mx[2], (int)H.intt2f.size());
+        mx[3] = std::max(mx[3], (int)H.ntt_z.size());
+    }
+    g->items_bytes = round_up(sizeof(BatchItem) * max_jobs);
+    g->counts_off = g->items_bytes;
+    size_t off = g->counts_off + 256;
+    for (int t = 0; t < 4; t++) {
+        g->list_max[t] = mx[t] * max_jobs;  // one group per limb at worst
+        g->lists_off[t] = off;
+        off += round_up(sizeof(NttGroup) * (size_t)g->list_max[t]);
+    }
+    g->hdr = off;
+    size_t slot = 0;
+    for (int l = 2; l <= c->L; l++) slot = std::max(slot, c->host_levels[l].ws.total);
+    g->slot_limbs = slot;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t he_batch_graph_workspace_bytes(const he_ctx *c, int max_jobs)
+{
+    if (!c || max_jobs < 1 || max_jobs > 65535 || c->L < 2) return 0;
+    he_batch_graph g;
+    graph_layout(c, max_jobs, &g);
+    return g.hdr + (size_t)max_jobs * g.slot_limbs * c->N * sizeof(u64);
+}
+
+int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws, size_t ws_bytes, void *stream,
+                          he_batch_graph **out)
+{
+    if (check_dev(c) || !evk || !ws || !out || !aligned(ws) || !aligned(evk)) return HE_EINVAL;
+    if (max_jobs < 1 || max_jobs > 65535 || c->L < 2) return HE_EINVAL;
+    if (ws_bytes < he_batch_graph_workspace_bytes(c, max_jobs)) return HE_ENOMEM;
+    he_batch_graph *g = new (std::nothrow) he_batch_graph();
+    if (!g) return HE_ENOMEM;
+    g->c = c;
+    g->max_jobs = max_jobs;
+    g->evk = evk;
+    g->ws = (char *)ws;
+    graph_layout(c, max_jobs, g);
+    cudaStream_t st = S(stream);
+    auto fail = [&](int rc) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        if (g->done) cudaEventDestroy(g->done);
+        if (g->pinned) cudaFreeHost(g->pinned);
+        delete g;
+        return rc;
+    };
+    if (cudaMallocHost((void **)&g->pinned, g->hdr) != cudaSuccess) return fail(HE_ENOMEM);
+    memset(g->pinned, 0, g->hdr);  // level-0 items: every block exits
+    if (cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess) return fail(HE_ECUDA);
+    const bool prof = c->prof;
+    c->prof = false;
+    JobRef R;
+    R.items = (const BatchItem *)g->ws;
+    memset(&R.one, 0, sizeof(R.one));
+    R.B = max_jobs;
+    R.lmax = c->L;
+    Stages Sg;
+    const NttGroup **lp[4] = {&Sg.intt1, &Sg.ntt_up, &Sg.intt2, &Sg.ntt_last};
+    int *np[4] = {&Sg.n_intt1, &Sg.n_ntt_up, &Sg.n_intt2, &Sg.n_ntt_last};
+    for (int t = 0; t < 4; t++) {
+        *lp[t] = (const NttGroup *)(g->ws + g->lists_off[t]);
+        *np[t] = g->list_max[t];
+    }
+    Sg.counts = (const int *)(g->ws + g->counts_off);
+    u64 *data = (u64 *)(g->ws + g->hdr);
+    int rc = HE_OK;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        c->prof = prof;
+        return fail(HE_ECUDA);
+    }
+    if (cudaMemcpyAsync(g->ws, g->pinned, g->hdr, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = HE_ECUDA;
+    if (rc == HE_OK) rc = run_pipeline(c, R, data, Sg, evk, true, st);
+    cudaError_t ce = cudaStreamEndCapture(st, &g->graph);
+    c->prof = prof;
+    if (rc != HE_OK || ce != cudaSuccess) return fail(rc != HE_OK ? rc : HE_ECUDA);
+    if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) return fail(HE_ECUDA);
+    *out = g;
+    return HE_OK;
+}
+
+int he_batch_graph_launch(he_batch_graph *g, int count, const he_job *jobs, void *stream)
+{
+    if (!g || !jobs || count < 1 || count > g->max_jobs) return HE_EINVAL;
+    he_ctx *c = g->c;
+    for (int i = 0; i < count; i++) {
+        const he_job &j = jobs[i];
+        if (!j.ct1 || !j.ct2 || !j.out || !aligned(j.ct1) || !aligned(j.ct2) || !aligned(j.out)) return HE_EINVAL;
+        if (j.level < 2 || j.level > c->L) return HE_ELEVEL;
+    }
+    // the previous replay must have consumed the pinned header
+    if (g->launched && cudaEventSynchronize(g->done) != cudaSuccess) return HE_ECUDA;
+    const size_t N = (size_t)c->N;
+    u64 *data = (u64 *)(g->ws + g->hdr);
+    BatchItem *items = (BatchItem *)g->pinned;
+    memset(items, 0, sizeof(BatchItem) * g->max_jobs);
+    std::vector<NttJob> lists[4];
+    for (int i = 0; i < count; i++) {
+        const HostLevel &H = c->host_levels[jobs[i].level];
+        const size_t off = (size_t)i * g->slot_limbs;
+        items[i].ct1 = jobs[i].ct1;
+        items[i].ct2 = jobs[i].ct2;
+        items[i].out = jobs[i].out;
+        items[i].ws = data + off * N;
+        items[i].level = jobs[i].level;
+        const std::vector<NttJob> *src[4] = {&H.intt1f, &H.ntt_up, &H.intt2f, &H.ntt_z};
+        for (int t = 0; t < 4; t++)
+            for (NttJob j : *src[t]) {
+                j.src += (unsigned)off;
+                j.dst += (unsigned)off;
+                lists[t].push_back(j);
+            }
+    }
+    int *counts = (int *)(g->pinned + g->counts_off);
+    for (int t = 0; t < 4; t++) {
+        std::vector<NttGroup> grp = group_jobs(lists[t]);
+        if ((int)grp.size() > g->list_max[t]) return HE_EINVAL;
+        memcpy(g->pinned + g->lists_off[t], grp.data(), sizeof(NttGroup) * grp.size());
+        counts[t] = (int)grp.size();
+    }
+    cudaStream_t st = S(stream);
+    if (cudaGraphLaunch(g->exec, st) != cudaSuccess) return HE_ECUDA;
+    if (cudaEventRecord(g->done, st) != cudaSuccess) return HE_ECUDA;
+    g->launched = true;
+    return HE_OK;
+}
+
+int he_batch_graph_destroy(he_batch_graph *g)
+{
+    if (!g) return HE_EINVAL;
+    if (g->launched) cudaEventSynchronize(g->done);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->done) cudaEventDestroy(g->done);
+    if (g->pinned) cudaFreeHost(g->pinned);
+    delete g;
     return HE_OK;
 }
 

@@ -141,10 +141,12 @@ int build_context(he_ctx *ctx, const he_params *p, bool device);
 // Record a profiling mark named after the kernel that just finished (no-op
 // unless profiling is enabled on the context).
 void prof_mark(const he_ctx *ctx, cudaStream_t st, const char *tag, const char *suffix = nullptr);
+// ngroups > 0 launches; dev_count (optional) bounds the groups on the device.
 cudaError_t launch_ntt(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, bool inverse,
-                       cudaStream_t st, const char *tag = nullptr);
+                       cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr);
 cudaError_t launch_ntt2(const he_ctx *ctx, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups,
-                        bool inverse, cudaStream_t st, const char *tag = nullptr);
+                        bool inverse, cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr);
+cudaError_t configure_ntt(const he_ctx *ctx);
 cudaError_t run_tensor(const he_ctx *c, const JobRef &R, cudaStream_t st);
 cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st);
 cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st);

@@ -374,6 +374,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
     c->d_PB = (const u64 *)(base + o_PB);
     c->d_pinv = (const ulonglong2 *)(base + o_pinv);
     c->d_levels = (DevLevel *)(base + o_levels);
+    if (configure_ntt(c) != cudaSuccess) return HE_ECUDA;
     return HE_OK;
 }
 

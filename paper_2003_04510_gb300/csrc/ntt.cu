@@ -47,6 +47,7 @@ struct NttArgs {
     const DevPrime *primes;
     int logN;
     int tiles;       // tiles per limb
+    const int *count;  // optional device-side group count (grids sized for a maximum)
 };
 
 // Forward (Cooley-Tukey) butterfly with no correction step: the modified
@@ -186,6 +187,7 @@ k_ntt_pass(const NttArgs P)
 
     const int gidx = blockIdx.x / P.tiles;
     const int tile = blockIdx.x - gidx * P.tiles;
+    if (P.count && gidx >= *P.count) return;
     const NttGroup &G = P.groups[gidx];
     const int nl = (int)G.nl;
     const DevPrime pr = P.primes[G.prime];
@@ -270,6 +272,7 @@ k_ntt_pass(const NttArgs P)
     }
 }
 
+// ngroups == 0 only sets the kernel's shared-memory limit (no launch).
 template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE>
 cudaError_t run_pass(const NttArgs &a, int ngroups, cudaStream_t st)
 {
@@ -282,6 +285,7 @@ cudaError_t run_pass(const NttArgs &a, int ngroups, cudaStream_t st)
         if (e != cudaSuccess) return e;
         configured = true;
     }
+    if (ngroups == 0) return cudaSuccess;
     kern<<<ngroups * a.tiles, NT, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -296,6 +300,13 @@ cudaError_t two_pass(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cuda
     cudaError_t e;
     const char *t1 = inverse ? ".inv_pass1" : ".fwd_pass1";
     const char *t2 = inverse ? ".inv_pass2" : ".fwd_pass2";
+    if (ngroups == 0) {  // configure only
+        e = run_pass<S1, A1, B1, C1, true, false, true, false, TE>(a, 0, st);
+        if (e == cudaSuccess) e = run_pass<S2, A2, B2, C2, false, false, false, true, TE>(a, 0, st);
+        if (e == cudaSuccess) e = run_pass<S2, A2, B2, C2, false, true, true, false, TE>(a, 0, st);
+        if (e == cudaSuccess) e = run_pass<S1, A1, B1, C1, true, true, false, true, TE>(a, 0, st);
+        return e;
+    }
     if (!inverse) {
         e = run_pass<S1, A1, B1, C1, true, false, true, false, TE>(a, ngroups, st);
         if (e != cudaSuccess) return e;
@@ -315,9 +326,9 @@ cudaError_t two_pass(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cuda
 }  // namespace
 
 cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups, bool inverse,
-                        cudaStream_t st, const char *tag)
+                        cudaStream_t st, const char *tag, const int *dev_count)
 {
-    if (ngroups <= 0) return cudaSuccess;
+    if (ngroups < 0) return cudaSuccess;  // ngroups == 0: configure the kernels only
     NttArgs a;
     a.src = src;
     a.dst = dst;
@@ -325,8 +336,13 @@ cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGrou
     a.primes = c->d_primes;
     a.logN = c->logN;
     a.tiles = 1;
+    a.count = dev_count;
     switch (c->logN) {
     case 12: {
+        if (ngroups == 0) {
+            cudaError_t e = run_pass<12, 4, 4, 4, false, true, true, true, 4096>(a, 0, st);
+            return e == cudaSuccess ? run_pass<12, 4, 4, 4, false, false, true, true, 4096>(a, 0, st) : e;
+        }
         cudaError_t e = inverse ? run_pass<12, 4, 4, 4, false, true, true, true, 4096>(a, ngroups, st)
                                 : run_pass<12, 4, 4, 4, false, false, true, true, 4096>(a, ngroups, st);
         prof_mark(c, st, tag, inverse ? ".inv" : ".fwd");
@@ -342,9 +358,13 @@ cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGrou
 }
 
 cudaError_t launch_ntt(const he_ctx *c, u64 *base, const NttGroup *groups, int ngroups, bool inverse, cudaStream_t st,
-                       const char *tag)
+                       const char *tag, const int *dev_count)
 {
-    return launch_ntt2(c, base, base, groups, ngroups, inverse, st, tag);
+    return launch_ntt2(c, base, base, groups, ngroups, inverse, st, tag, dev_count);
 }
+
+// Set the dynamic shared-memory limit of every NTT pass this ring size uses
+// (done once per context, before any launch or stream capture).
+cudaError_t configure_ntt(const he_ctx *c) { return launch_ntt2(c, nullptr, nullptr, nullptr, 0, false, nullptr); }
 
 }  // namespace he

@@ -269,6 +269,31 @@ def test_batch_matches_single_and_oracle(g):
         assert np.array_equal(host(g, jobs[k][2]), want)
 
 
+def test_batch_graph_replays_match_single(g):
+    """One captured graph, replayed with two different batches (sizes, levels,
+    operands): every result equals he_mul_rescale on the job alone."""
+    import torch
+    name = "n16"
+    ctx = ctx_for(g, name)
+    op = oracle.preset(name)
+    evk_t = dev(g, rand_evk(op, 130))
+    graph = g.BatchGraph(ctx, 8, evk_t)
+    for rnd, levels in enumerate([[24, 5, 13, 2, 18, 9], [3, 24, 11]]):
+        jobs, singles = [], []
+        for k, lv in enumerate(levels):
+            c1, c2 = rand_ct(op, lv, 400 + 10 * rnd + 2 * k), rand_ct(op, lv, 500 + 10 * rnd + 2 * k)
+            out = torch.full((2, lv - 1, op.N), -1, dtype=torch.int64, device="cuda")
+            jobs.append((dev(g, c1), dev(g, c2), out, lv))
+            singles.append(gpu_mul(g, ctx, c1, c2, evk_t, lv, fused=True))
+        graph.launch(jobs)
+        torch.cuda.synchronize()
+        for (t1, t2, out, lv), single in zip(jobs, singles):
+            assert np.array_equal(host(g, out), single), (rnd, lv)
+    with pytest.raises(g.HeError):
+        graph.launch([jobs[0]] * 9)  # more jobs than captured
+    graph.close()
+
+
 def test_device_argument_errors(g):
     import torch
     ctx = ctx_for(g, "n12")
