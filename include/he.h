@@ -240,6 +240,8 @@ int he_profile_read(he_ctx *ctx, int max, char *names, double *total_ms, int *ca
 int he_probe_butterfly_rate(int blocks, int iters, double *bfly_per_s, void *stream);
 
 const char *he_strerror(int code);
+/* Name of the CUDA error behind the calling thread's last HE_ECUDA. */
+const char *he_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,10 @@ HE_OK, HE_EINVAL, HE_ELEVEL, HE_ENOMEM, HE_ECUDA, HE_ETIMEOUT, HE_EBUSY = range(
 
 class HeError(RuntimeError):
     def __init__(self, code: int, what: str):
-        super().__init__(f"{what}: {lib().he_strerror(code).decode()} (code {code})")
+        msg = f"{what}: {lib().he_strerror(code).decode()} (code {code})"
+        if code == HE_ECUDA:
+            msg += f" [{lib().he_last_cuda_error().decode()}]"
+        super().__init__(msg)
         self.code = code
 
 
@@ -43,6 +46,7 @@ _lib = None
 
 _SIGS = {
     "he_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "he_last_cuda_error": (ctypes.c_char_p, []),
     "he_ctx_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "he_ctx_create_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "he_ctx_destroy": (ctypes.c_int, [ctypes.c_void_p]),

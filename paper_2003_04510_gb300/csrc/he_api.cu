@@ -29,10 +29,15 @@ namespace {
 
 inline cudaStream_t S(void *s) { return (cudaStream_t)s; }
 
-#define HE_TRY(x)                                  \
-    do {                                           \
-        cudaError_t e_ = (x);                      \
-        if (e_ != cudaSuccess) return HE_ECUDA;    \
+thread_local const char *g_last_cuda_error = "no error";
+
+#define HE_TRY(x)                                           \
+    do {                                                    \
+        cudaError_t e_ = (x);                               \
+        if (e_ != cudaSuccess) {                            \
+            g_last_cuda_error = cudaGetErrorName(e_);       \
+            return HE_ECUDA;                                \
+        }                                                   \
     } while (0)
 
 bool aligned(const void *p) { return ((uintptr_t)p & 255) == 0; }
@@ -155,6 +160,8 @@ size_t batch_bytes(const he_ctx *c, int count, const int *levels)
 }  // namespace
 
 extern "C" {
+
+const char *he_last_cuda_error(void) { return g_last_cuda_error; }
 
 const char *he_strerror(int code)
 {
@@ -586,8 +593,12 @@ int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws
     g->evk = evk;
     g->ws = (char *)ws;
     graph_layout(c, max_jobs, g);
-    cudaStream_t st = S(stream);
+    // capture runs nothing, so it uses a private stream: capture is not
+    // permitted on the legacy default stream the caller may be using
+    (void)stream;
+    cudaStream_t st = nullptr;
     auto fail = [&](int rc) {
+        if (st) cudaStreamDestroy(st);
         if (g->exec) cudaGraphExecDestroy(g->exec);
         if (g->graph) cudaGraphDestroy(g->graph);
         if (g->done) cudaEventDestroy(g->done);
@@ -595,6 +606,7 @@ int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws
         delete g;
         return rc;
     };
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return fail(HE_ECUDA);
     if (cudaMallocHost((void **)&g->pinned, g->hdr) != cudaSuccess) return fail(HE_ENOMEM);
     memset(g->pinned, 0, g->hdr);  // level-0 items: every block exits
     if (cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess) return fail(HE_ECUDA);
@@ -615,16 +627,28 @@ int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws
     Sg.counts = (const int *)(g->ws + g->counts_off);
     u64 *data = (u64 *)(g->ws + g->hdr);
     int rc = HE_OK;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) {
         c->prof = prof;
+        g_last_cuda_error = cudaGetErrorName(ce);
         return fail(HE_ECUDA);
     }
-    if (cudaMemcpyAsync(g->ws, g->pinned, g->hdr, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = HE_ECUDA;
+    ce = cudaMemcpyAsync(g->ws, g->pinned, g->hdr, cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) {
+        g_last_cuda_error = cudaGetErrorName(ce);
+        rc = HE_ECUDA;
+    }
     if (rc == HE_OK) rc = run_pipeline(c, R, data, Sg, evk, true, st);
-    cudaError_t ce = cudaStreamEndCapture(st, &g->graph);
+    ce = cudaStreamEndCapture(st, &g->graph);
     c->prof = prof;
+    if (ce != cudaSuccess) g_last_cuda_error = cudaGetErrorName(ce);
     if (rc != HE_OK || ce != cudaSuccess) return fail(rc != HE_OK ? rc : HE_ECUDA);
-    if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) return fail(HE_ECUDA);
+    ce = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (ce != cudaSuccess) {
+        g_last_cuda_error = cudaGetErrorName(ce);
+        return fail(HE_ECUDA);
+    }
+    cudaStreamDestroy(st);
     *out = g;
     return HE_OK;
 }
