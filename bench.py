@@ -277,6 +277,53 @@ def run_batched(g, ctx, evk_t, dev, stream, wsz, count=64, reps=20):
     return res
 
 
+def run_serving(g, dev, rate_hz=2000.0, duration_s=10.0, streams=4, max_batch=64):
+    """Poisson stream of HE Mul + rescale requests: 70% N=2^15 (levels 2..16),
+    30% N=2^16 (levels 4..24), both rings' evaluation keys resident; operands
+    are uniform residues (one pair per ring and level), outputs rotate over a
+    pool.  Reports throughput and p50/p99 latency (submit -> completion)."""
+    import torch
+    rings = ["n15", "n16"]
+    ctxs = [g.Context(g.PRESETS[r][0], device=True) for r in rings]
+    evks, pairs, pools = [], [], []
+    for ri, ctx in enumerate(ctxs):
+        ext = [int(x) for x in ctx.moduli]
+        evk = np.stack([np.stack([si.uniform_residues(ext, (ctx.N,), 9000 + 10 * ri + 2 * j + h) for h in range(2)])
+                        for j in range(ctx.dnum)])
+        evks.append(g.to_device(evk, dev))
+        pr = {}
+        lo, hi = (2, 16) if ri == 0 else (4, 24)
+        for lv in range(lo, hi + 1):
+            q = [int(x) for x in ctx.q[:lv]]
+            pr[lv] = tuple(g.to_device(np.stack([si.uniform_residues(q, (ctx.N,), 9500 + 100 * ri + 4 * lv + 2 * k + h)
+                                                  for h in range(2)]), dev) for k in range(2))
+        pairs.append(pr)
+        L = ctx.prm.L
+        pools.append(torch.empty((256, 2 * (L - 1) * ctx.N), dtype=torch.int64, device=dev))
+    arrivals = si.poisson_arrivals(rate_hz, duration_s)
+    mix = si.serving_mix(len(arrivals))
+    budget = 16 << 30
+    srv = g.Server(ctxs, evks, hbm_budget=budget, max_batch=max_batch, streams=streams)
+    tickets = []
+    t0 = time.perf_counter()
+    for k, (ta, (logN, lv)) in enumerate(zip(arrivals, mix)):
+        ri = 0 if logN == 15 else 1
+        while time.perf_counter() - t0 < ta:
+            pass
+        a, b = pairs[ri][lv]
+        out = pools[ri][k % 256][: 2 * (lv - 1) * ctxs[ri].N]
+        tickets.append(srv.submit(ri, lv, a, b, out))
+    for tk in tickets:
+        srv.wait(tk, 600000)
+    st = srv.stats()
+    srv.close()
+    return {"requests": len(tickets), "rate_hz": rate_hz, "duration_s": duration_s,
+            "throughput_req_s": st["throughput"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "max_ms": st["max_ms"], "batches": st["batches"], "mean_batch": st["mean_batch"],
+            "mix": "70% N=2^15 levels 2..16, 30% N=2^16 levels 4..24", "streams": streams, "max_batch": max_batch,
+            "hbm_budget_bytes": budget}
+
+
 def run_ours(args):
     import torch
     import paper_2003_04510_gb300 as g
@@ -443,6 +490,10 @@ def run_ours(args):
     if preset == "n16" and not args.no_batch:
         batched = run_batched(g, ctx, evk_t, dev, stream, wsz)
 
+    serving = None
+    if preset == "n16" and not args.no_serve:
+        serving = run_serving(g, dev)
+
     # ---- CPU oracle baseline (rank 0, N=1 only) ----
     cpu = None
     if rank == 0 and wsz == 1 and not args.no_cpu_baseline:
@@ -471,6 +522,7 @@ def run_ours(args):
             "probe": probe,
             "kernels": per_kernel,
             "batched": batched,
+            "serving": serving,
             "cpu_baseline": cpu,
             "clocks": clk,
             "decrypt_max_err": dec_err,
@@ -489,6 +541,7 @@ def main():
     ap.add_argument("--workload", default="n16", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

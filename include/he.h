@@ -222,6 +222,52 @@ int he_batch_graph_create(he_ctx *ctx, int max_jobs, const uint64_t *evk_dev, vo
 int he_batch_graph_launch(he_batch_graph *g, int count, const he_job *jobs, void *stream);
 int he_batch_graph_destroy(he_batch_graph *g);
 
+/* ---- serving (continuous batching) ------------------------------------------ */
+
+/* A served request: HE Mul + rescale of device-resident operands on ring
+ * ctx_index of the server (ct1, ct2: [2][level][N]; out: [2][level-1][N]). */
+typedef struct {
+    int ctx_index;
+    int level;
+    const uint64_t *ct1;
+    const uint64_t *ct2;
+    uint64_t *out;
+} he_request;
+
+typedef struct {
+    uint64_t completed, pending, batches;
+    double mean_batch;   /* requests per launched batch */
+    double p50_ms, p99_ms, max_ms;  /* submit -> completion observed */
+    double throughput;   /* completed requests per second, first submit to last completion */
+} he_server_report;
+
+typedef struct he_server he_server;
+
+/* Create a server over nctx rings (contexts) with their device-resident
+ * evaluation keys.  It allocates one device arena of hbm_budget bytes for
+ * request workspaces and `streams` CUDA streams, and starts a scheduler
+ * thread.  The scheduler admits queued requests in arrival order as arena
+ * space and streams free up, groups admitted requests of one ring into a
+ * batch of at most max_batch (one launch per stage, as he_mul_batch) and runs
+ * it on a free stream, so batches formed while others run overlap on the
+ * device.  Completion is detected by polling CUDA events on the host.
+ * Results are bit-identical to he_mul_rescale per request.  The operand and
+ * output buffers of a request must stay valid until it completes. */
+int he_server_create(he_server **out, he_ctx *const *ctxs, const uint64_t *const *evk_devs, int nctx,
+                     size_t hbm_budget, int max_batch, int streams);
+/* Queue a request (non-blocking).  HE_ENOMEM if its workspace exceeds the
+ * whole budget (it could never be admitted), HE_ELEVEL / HE_EINVAL for bad
+ * arguments. */
+int he_server_submit(he_server *s, const he_request *r, uint64_t *ticket);
+/* done = 1 once the request completed; returns its error code if it failed. */
+int he_server_poll(he_server *s, uint64_t ticket, int *done);
+/* Wait up to timeout_ms for a request; HE_ETIMEOUT if it has not completed. */
+int he_server_wait(he_server *s, uint64_t ticket, int timeout_ms);
+int he_server_stats(he_server *s, he_server_report *stats);
+/* Stops the scheduler after the batches in flight finish; queued requests
+ * that were never launched are dropped. */
+int he_server_destroy(he_server *s);
+
 /* ---- profiling ------------------------------------------------------------ */
 
 /* Enable (1) or disable (0) per-kernel CUDA-event marks on this context's

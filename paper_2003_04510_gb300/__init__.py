@@ -37,6 +37,17 @@ class he_params(ctypes.Structure):
                 ("sigma", ctypes.c_double)]
 
 
+class he_request(ctypes.Structure):
+    _fields_ = [("ctx_index", ctypes.c_int), ("level", ctypes.c_int), ("ct1", ctypes.c_void_p),
+                ("ct2", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class he_server_report(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("pending", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("mean_batch", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("throughput", ctypes.c_double)]
+
+
 class he_job(ctypes.Structure):
     _fields_ = [("ct1", ctypes.c_void_p), ("ct2", ctypes.c_void_p), ("out", ctypes.c_void_p),
                 ("level", ctypes.c_int)]
@@ -93,6 +104,13 @@ _SIGS = {
                                            ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                            ctypes.c_void_p]),
     "he_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "he_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
+    "he_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "he_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
+    "he_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int]),
+    "he_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "he_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "he_batch_graph_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int]),
     "he_batch_graph_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
@@ -400,6 +418,49 @@ class BatchGraph:
     def close(self):
         if self.ptr:
             lib().he_batch_graph_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """he_server: continuous-batching HE Mul server over several rings."""
+
+    def __init__(self, ctxs, evks, hbm_budget: int, max_batch: int = 64, streams: int = 4):
+        n = len(ctxs)
+        self._ctxs = (ctypes.c_void_p * n)(*[c.ptr.value for c in ctxs])
+        self._evks = (ctypes.c_void_p * n)(*[_dev_ptr(e) for e in evks])
+        self._keep = (list(ctxs), list(evks))
+        self.ptr = ctypes.c_void_p()
+        _check(lib().he_server_create(ctypes.byref(self.ptr), self._ctxs, self._evks, n, hbm_budget, max_batch,
+                                      streams), "he_server_create")
+
+    def submit(self, ctx_index: int, level: int, ct1, ct2, out) -> int:
+        r = he_request(ctx_index, level, _dev_ptr(ct1), _dev_ptr(ct2), _dev_ptr(out))
+        t = ctypes.c_uint64()
+        _check(lib().he_server_submit(self.ptr, ctypes.byref(r), ctypes.byref(t)), "he_server_submit")
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int()
+        _check(lib().he_server_poll(self.ptr, ticket, ctypes.byref(d)), "he_server_poll")
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        _check(lib().he_server_wait(self.ptr, ticket, timeout_ms), "he_server_wait")
+
+    def stats(self) -> dict:
+        st = he_server_report()
+        _check(lib().he_server_stats(self.ptr, ctypes.byref(st)), "he_server_stats")
+        return {f: getattr(st, f) for f, _ in he_server_report._fields_}
+
+    def close(self):
+        if self.ptr:
+            lib().he_server_destroy(self.ptr)
             self.ptr = ctypes.c_void_p()
 
     def __del__(self):

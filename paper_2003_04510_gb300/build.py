@@ -70,7 +70,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc: list[str] | No
     for src in cpp:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         objs.append(obj)
-        cmds.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", *common_inc,
+        cmds.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-pthread", *common_inc,
                      "-I", os.path.join(cuda, "include"), "-c", src, "-o", obj])
 
     def run(cmd):
@@ -86,7 +86,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc: list[str] | No
             if lg.strip():
                 print(lg)
     tmp = LIB + f".tmp{os.getpid()}"
-    run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
+    run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-Xcompiler", "-pthread", "-o", tmp, *objs])
     os.replace(tmp, LIB)
     with open(stamp_file, "w") as f:
         f.write(stamp)

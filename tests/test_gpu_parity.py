@@ -294,6 +294,68 @@ def test_batch_graph_replays_match_single(g):
     graph.close()
 
 
+def test_server_continuous_batching_matches_single(g):
+    """Requests of two rings and many levels, submitted while earlier ones run,
+    under an HBM budget that admits only a few at a time: every result is the
+    same as the request run alone."""
+    import torch
+    rings = ["n15", "n16"]
+    ctxs = [ctx_for(g, r) for r in rings]
+    ops = [oracle.preset(r) for r in rings]
+    evks = [dev(g, rand_evk(op, 140 + i)) for i, op in enumerate(ops)]
+    # room for roughly four level-16 N=2^16 requests at once
+    budget = 4 * g.he_batch_workspace_bytes(ctxs[1], [16])
+    srv = g.Server(ctxs, evks, hbm_budget=budget, max_batch=8, streams=3)
+    rng = np.random.default_rng(9)
+    reqs = []
+    for k in range(40):
+        ri = int(rng.random() < 0.3)
+        op = ops[ri]
+        lv = int(rng.integers(2, 17)) if ri == 0 else int(rng.integers(4, 25))
+        c1, c2 = rand_ct(op, lv, 600 + 2 * k), rand_ct(op, lv, 700 + 2 * k)
+        t1, t2 = dev(g, c1), dev(g, c2)
+        out = torch.full((2, lv - 1, op.N), -1, dtype=torch.int64, device="cuda")
+        reqs.append((ri, lv, t1, t2, out, srv.submit(ri, lv, t1, t2, out)))
+    for ri, lv, t1, t2, out, tk in reqs:
+        srv.wait(tk, 120000)
+        assert srv.poll(tk)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["pending"] == 0
+    assert st["batches"] < len(reqs)  # requests were batched
+    assert 0 < st["p50_ms"] <= st["p99_ms"]
+    srv.close()
+    for ri, lv, t1, t2, out, tk in reqs:
+        ctx = ctxs[ri]
+        alone = torch.empty_like(out)
+        g.he_mul_rescale(ctx, t1, t2, evks[ri], lv, alone, g.workspace(ctx, lv))
+        torch.cuda.synchronize()
+        assert torch.equal(out, alone), (ri, lv)
+
+
+def test_server_admission_errors(g):
+    import torch
+    ctx = ctx_for(g, "n16")
+    op = oracle.preset("n16")
+    evk = dev(g, rand_evk(op, 150))
+    small = g.he_batch_workspace_bytes(ctx, [8])
+    srv = g.Server([ctx], [evk], hbm_budget=small, max_batch=4, streams=2)
+    a = torch.zeros((2, 24, op.N), dtype=torch.int64, device="cuda")
+    out = torch.zeros((2, 23, op.N), dtype=torch.int64, device="cuda")
+    with pytest.raises(g.HeError) as e:  # a level-24 request never fits this budget
+        srv.submit(0, 24, a, a, out)
+    assert e.value.code == g.HE_ENOMEM
+    with pytest.raises(g.HeError) as e:
+        srv.submit(0, 1, a, a, out)
+    assert e.value.code == g.HE_ELEVEL
+    b = torch.zeros((2, 8, op.N), dtype=torch.int64, device="cuda")
+    o2 = torch.zeros((2, 7, op.N), dtype=torch.int64, device="cuda")
+    tk = srv.submit(0, 8, b, b, o2)
+    rc = g.lib().he_server_wait(srv.ptr, tk, 0)
+    assert rc in (g.HE_OK, g.HE_ETIMEOUT)
+    srv.wait(tk, 60000)
+    srv.close()
+
+
 def test_device_argument_errors(g):
     import torch
     ctx = ctx_for(g, "n12")
