@@ -492,7 +492,8 @@ def run_ours(args):
 
     serving = None
     if preset == "n16" and not args.no_serve:
-        serving = run_serving(g, dev)
+        serving = {"poisson_2000": run_serving(g, dev),
+                   "saturating_20000": run_serving(g, dev, rate_hz=20000.0, duration_s=2.0)}
 
     # ---- CPU oracle baseline (rank 0, N=1 only) ----
     cpu = None

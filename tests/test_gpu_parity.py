@@ -307,15 +307,17 @@ def test_server_continuous_batching_matches_single(g):
     budget = 4 * g.he_batch_workspace_bytes(ctxs[1], [16])
     srv = g.Server(ctxs, evks, hbm_budget=budget, max_batch=8, streams=3)
     rng = np.random.default_rng(9)
-    reqs = []
+    staged = []
     for k in range(40):
         ri = int(rng.random() < 0.3)
         op = ops[ri]
         lv = int(rng.integers(2, 17)) if ri == 0 else int(rng.integers(4, 25))
         c1, c2 = rand_ct(op, lv, 600 + 2 * k), rand_ct(op, lv, 700 + 2 * k)
-        t1, t2 = dev(g, c1), dev(g, c2)
         out = torch.full((2, lv - 1, op.N), -1, dtype=torch.int64, device="cuda")
-        reqs.append((ri, lv, t1, t2, out, srv.submit(ri, lv, t1, t2, out)))
+        staged.append((ri, lv, dev(g, c1), dev(g, c2), out))
+    torch.cuda.synchronize()
+    # submit back to back: later requests arrive while earlier batches run
+    reqs = [(ri, lv, t1, t2, out, srv.submit(ri, lv, t1, t2, out)) for ri, lv, t1, t2, out in staged]
     for ri, lv, t1, t2, out, tk in reqs:
         srv.wait(tk, 120000)
         assert srv.poll(tk)
