@@ -48,6 +48,22 @@ WORKLOADS = {
 NPAIRS = 8
 
 
+def reduce_max(x: float, device=None) -> float:
+    """Max of a per-rank float over all ranks (no-op without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -392,13 +408,9 @@ def run_ours(args):
     clk = clocks.stop()
     if wsz > 1:
         torch.distributed.barrier()
-    elapsed_ms = t0.elapsed_time(t1)
+    elapsed_ms = reduce_max(t0.elapsed_time(t1), dev)
     lat = np.array([a.elapsed_time(b) for a, b in ev])
-    if wsz > 1:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = wsz * args.steps / (elapsed_ms * 1e-3)
+    value = job_rate(args.steps, wsz, elapsed_ms * 1e-3)
     launches_per_step = 13 if prm.logN > 12 else 9
 
     # ---- end to end: host buffers through he_mul_rescale_host ----
@@ -419,12 +431,8 @@ def run_ours(args):
     for k in range(e2e_steps):
         a, b = pin_np[k % 2]
         g.he_mul_rescale_host(ctx, a, b, evk_t, level, out_np, hws, stream)
-    e2e_s = time.perf_counter() - te
-    if wsz > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = wsz * e2e_steps / e2e_s
+    e2e_s = reduce_max(time.perf_counter() - te, dev)
+    e2e_val = job_rate(e2e_steps, wsz, e2e_s)
     h2d = 2 * 2 * level * N * 8
     d2h = 2 * (level - 1) * N * 8
 
