@@ -151,6 +151,29 @@ int he_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, void *
 int he_mul_rescale(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *evk_dev, int level,
                    uint64_t *out, void *ws, size_t ws_bytes, void *stream);
 
+/* he_mul_rescale with no workspace argument.  The paper has no counterpart:
+ * this is a library convenience for callers that cannot allocate device
+ * memory or keep a workspace between calls (for example a host application
+ * whose device memory is owned entirely by another allocator, or a binding
+ * with no device allocator of its own).  The workspace is a scratch array of
+ * HE_STATIC_SCRATCH_BYTES inside the library's own device memory, one per
+ * device; nothing is allocated by the call.
+ *  - Limit: levels whose he_workspace_bytes exceeds HE_STATIC_SCRATCH_BYTES
+ *    (64 MiB: every level of logN <= 15 parameter sets of this size, logN 16
+ *    up to level 8) return HE_ENOMEM; use he_mul_rescale for those.
+ *  - The first call with a device current looks up that device's scratch
+ *    address (cudaGetSymbolAddress), which may load the library's device
+ *    code; make that first call outside any stream capture.
+ *  - The current device must be the context's (HE_EINVAL otherwise).
+ *  - Nothing in the scratch needs to start at zero.
+ *  - All calls on one device share the scratch: calls whose executions
+ *    overlap (different streams, or threads without ordering between their
+ *    streams) race and give wrong results.  Calls on one stream are safe.
+ * Results are bit-identical to he_mul_rescale. */
+#define HE_STATIC_SCRATCH_BYTES (64u << 20)
+int he_mul_rescale_static(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *evk_dev,
+                          int level, uint64_t *out, void *stream);
+
 /* he_mul_rescale on HOST buffers: copies ct1, ct2 ([2][level][N], host) to the
  * device, runs the path and copies the result ([2][level-1][N]) back to `out`
  * (host), then waits for the stream.  ws is device memory of at least

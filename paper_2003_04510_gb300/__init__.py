@@ -100,6 +100,8 @@ _SIGS = {
                                        ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "he_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "he_host_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int]),
+    "he_mul_rescale_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "he_mul_rescale_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                            ctypes.c_void_p]),
@@ -312,6 +314,16 @@ def he_mul(ctx, ct1, ct2, evk, level, out, ws, stream=None):
 def he_mul_rescale(ctx, ct1, ct2, evk, level, out, ws, stream=None):
     _check(lib().he_mul_rescale(ctx.ptr, _dev_ptr(ct1), _dev_ptr(ct2), _dev_ptr(evk), level, _dev_ptr(out),
                                 _dev_ptr(ws), ws.numel() * 8, _stream_ptr(stream)), "he_mul_rescale")
+
+
+# he_mul_rescale_static's scratch size (HE_STATIC_SCRATCH_BYTES in he.h)
+HE_STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def he_mul_rescale_static(ctx, ct1, ct2, evk, level, out, stream=None):
+    """he_mul_rescale with the library's fixed device scratch as workspace (no allocation)."""
+    _check(lib().he_mul_rescale_static(ctx.ptr, _dev_ptr(ct1), _dev_ptr(ct2), _dev_ptr(evk), level, _dev_ptr(out),
+                                       _stream_ptr(stream)), "he_mul_rescale_static")
 
 
 def he_rescale(ctx, ct, level, out, ws, stream=None):
