@@ -147,6 +147,9 @@ cudaError_t launch_ntt(const he_ctx *ctx, u64 *base, const NttGroup *groups, int
 cudaError_t launch_ntt2(const he_ctx *ctx, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups,
                         bool inverse, cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr);
 cudaError_t configure_ntt(const he_ctx *ctx);
+// Number of final stages (the contiguous pass's last round) whose twiddle
+// runs the device table stores transposed; 0 for an unsupported logN.
+int ntt_direct_stages(int logN);
 cudaError_t run_tensor(const he_ctx *c, const JobRef &R, cudaStream_t st);
 cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st);
 cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st);

@@ -303,6 +303,9 @@ int build_context(he_ctx *c, const he_params *p, bool device)
     std::vector<unsigned char> img(off, 0);
     char *base = (char *)c->arena;
     std::vector<DevPrime> dp(E);
+    const int direct = ntt_direct_stages(logN);
+    if (direct <= 0) return HE_EINVAL;
+    const int sd = logN - direct;  // first stage with transposed runs
     for (int e = 0; e < E; e++) {
         u64 m = c->ext[e];
         int b = bitlen(m);
@@ -320,6 +323,19 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         for (int k = 0; k < N; k++) {
             W[k] = make_ulonglong2(c->w[e][k], c->wsh[e][k]);
             IW[k] = make_ulonglong2(c->iw[e][k], c->iwsh[e][k]);
+        }
+        // The last `direct` stages' runs are stored transposed (the NTT's
+        // contiguous pass reads them one entry per thread): stage m = 2^sigma,
+        // lp = sigma - sd, entry m + T 2^lp + j moves to m + j 2^sd + T.
+        for (int sigma = sd; sigma < logN; sigma++) {
+            const int lp = sigma - sd;
+            const size_t m = (size_t)1 << sigma;
+            for (size_t T = 0; T < ((size_t)1 << sd); T++)
+                for (size_t j = 0; j < ((size_t)1 << lp); j++) {
+                    const size_t from = m + (T << lp) + j, to = m + (j << sd) + T;
+                    W[to] = make_ulonglong2(c->w[e][from], c->wsh[e][from]);
+                    IW[to] = make_ulonglong2(c->iw[e][from], c->iwsh[e][from]);
+                }
         }
     }
     memcpy(img.data() + o_primes, dp.data(), sizeof(DevPrime) * E);

@@ -59,6 +59,28 @@ __device__ __forceinline__ u64 shoup_approx(u64 x, u64 w, u64 wp, u64 q)
     return x * w - qh * q;
 }
 
+// The same remainder with the subtraction folded into the multiply-adds:
+// x*w - qh*q = x*w + qh*nq (mod 2^64), nq = 2^64 - q.  The low word comes
+// from two chained 32x32 -> 64-bit multiply-adds, the high word from four
+// 32-bit multiply-adds on top of its carry-in; exact mod 2^64, which is
+// enough since the remainder is below 4q.
+__device__ __forceinline__ u64 shoup_approx_nq(u64 x, u64 w, u64 wp, u64 nq)
+{
+    const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
+    const uint32_t p0 = (uint32_t)wp, p1 = (uint32_t)(wp >> 32);
+    const u64 qh = mad_wide(x1, p1, (u64)mul_hi32(x1, p0) + mul_hi32(x0, p1));
+    const uint32_t h0 = (uint32_t)qh, h1 = (uint32_t)(qh >> 32);
+    const uint32_t w0 = (uint32_t)w, w1 = (uint32_t)(w >> 32);
+    const uint32_t n0 = (uint32_t)nq, n1 = (uint32_t)(nq >> 32);
+    const u64 lo = mad_wide(h0, n0, mad_wide(x0, w0, 0ull));
+    uint32_t hi = (uint32_t)(lo >> 32);
+    hi += x0 * w1;
+    hi += x1 * w0;
+    hi += h0 * n1;
+    hi += h1 * n0;
+    return (lo & 0xFFFFFFFFull) | ((u64)hi << 32);
+}
+
 __device__ __forceinline__ u64 shoup(u64 x, u64 w, u64 wp, u64 q) { return csub(shoup_lazy(x, w, wp, q), q); }
 
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) { return csub(a + b, q); }

@@ -53,10 +53,10 @@ struct NttArgs {
 // Forward (Cooley-Tukey) butterfly with no correction step: the modified
 // Shoup product t lies in [0, 4q), so each stage adds at most 4q to the
 // range.  From canonical inputs, values stay below (1 + 4 log N) q < 2^64 for
-// q < 2^57.9 and are reduced once, on the final store.
-__device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, ulonglong2 w, u64 q, u64 q4)
+// q < 2^57.9 and are reduced once, on the final store.  nq = 2^64 - q.
+__device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, ulonglong2 w, u64 nq, u64 q4)
 {
-    const u64 t = shoup_approx(y, w.x, w.y, q);
+    const u64 t = shoup_approx_nq(y, w.x, w.y, nq);
     y = x + q4 - t;
     x = x + t;
 }
@@ -64,24 +64,39 @@ __device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, ulonglong2 w, u64 q, u64
 // Inverse (Gentleman-Sande) butterfly on values in [0, 4q): the sum is
 // brought back below 4q with one conditional subtraction, the difference
 // goes through the modified Shoup product, which lands in [0, 4q).
-__device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, ulonglong2 w, u64 q, u64 q4)
+__device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, ulonglong2 w, u64 nq, u64 q4)
 {
     u64 s = x + y;
     s = s >= q4 ? s - q4 : s;
     const u64 d = x + q4 - y;
-    y = shoup_approx(d, w.x, w.y, q);
+    y = shoup_approx_nq(d, w.x, w.y, nq);
     x = s;
+}
+
+// 16-byte read-only load that does not allocate in L1 (twiddles read once).
+__device__ __forceinline__ ulonglong2 ld_tw(const ulonglong2 *p)
+{
+    ulonglong2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
+    return v;
 }
 
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
-template <int LOGM, int TE, bool STRIDED>
+// Pass geometry.  RL is the pass's last round in forward order (the round
+// whose sets are 2^RL consecutive elements).  In the contiguous pass each
+// twiddle of that round is used by exactly one thread, so its twiddles are
+// read straight into registers; only the earlier rounds' twiddles (stages
+// l < LOGM - RL) are staged in shared memory.  The strided pass stages all of
+// TB_W[1, M), which every tile shares.  Data tiles are double-buffered.
+template <int LOGM, int TE, bool STRIDED, int RL>
 struct Geometry {
     static constexpr int M = 1 << LOGM;
-    static constexpr int NG = TE / M;                           // groups (or columns) per tile
-    static constexpr int TWN = STRIDED ? M - 1 : NG * (M - 1);  // twiddle pairs staged per tile
-    static constexpr int DATA = TE + TE / 16;                   // padded words per data buffer
-    static constexpr int NBUF = STRIDED ? 2 : 1;                // data buffers (double-buffered if strided)
+    static constexpr int NG = TE / M;                                   // groups (or columns) per tile
+    static constexpr int LS = STRIDED ? LOGM : LOGM - RL;               // stages with shared-memory twiddles
+    static constexpr int TWN = STRIDED ? M - 1 : NG * ((1 << LS) - 1);  // twiddle pairs staged per tile
+    static constexpr int DATA = TE + TE / 16;                           // padded words per data buffer
+    static constexpr int NBUF = 2;
     static constexpr size_t SMEM = sizeof(ulonglong2) * TWN + sizeof(u64) * NBUF * DATA;
 };
 
@@ -90,23 +105,35 @@ template <int LOGM, int TE, bool STRIDED>
 __device__ __forceinline__ int tw_slot(int l, int grp, int x)
 {
     if (STRIDED) return (1 << l) - 1 + x;
-    return Geometry<LOGM, TE, STRIDED>::NG * ((1 << l) - 1) + (grp << l) + x;
+    return (TE >> LOGM) * ((1 << l) - 1) + (grp << l) + x;
 }
+
+// Register twiddles of the direct round: for each of the thread's SPT sets,
+// the 2^R - 1 twiddles of its stages, stage lp at offset 2^lp - 1.
+template <int R, int SPT>
+struct TwReg {
+    ulonglong2 t[SPT][(1 << R) - 1];
+};
 
 // One round of R stages [l0, l0 + R) on every register set of the tile.
 // The 2^R elements of a set sit at shared-memory word padi(e0) + c + (c >> 4)
 // with c = v * 2^lo_bits * (STRIDED ? NG : 1): for every configuration used
 // (R >= 3) the low four bits of e0 plus those of c never carry, so the
 // padding of e0 + c splits into padi(e0) plus a compile-time offset.
-template <int LOGM, int TE, int R, bool STRIDED, bool INV, int NT>
-__device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *tw, int l0, u64 q, u64 q4)
+// DIRECT: twiddles come from TR (the contiguous pass's last round).
+template <int LOGM, int TE, int R, bool STRIDED, bool INV, int NT, bool DIRECT, class TRT>
+__device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *tw, const TRT &TR, int l0, u64 nq, u64 q4)
 {
     constexpr int M = 1 << LOGM;
     constexpr int NG = TE / M;
     constexpr int SETS = TE >> R;
+    constexpr int SPT = SETS / NT;
     constexpr int CSTEP = STRIDED ? NG : 1;
+    static_assert(SETS % NT == 0, "sets must divide evenly over the threads");
     const int lo_bits = LOGM - l0 - R;
-    for (int s = threadIdx.x; s < SETS; s += NT) {
+#pragma unroll
+    for (int si = 0; si < SPT; si++) {
+        const int s = threadIdx.x + si * NT;
         int grp, khi, klo;
         if (STRIDED) {
             grp = s % NG;
@@ -137,7 +164,11 @@ __device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *tw, int l0,
 #pragma unroll
                 for (int v = 0; v < (1 << R); v++) {
                     if (v & h) continue;
-                    ct_bfly(a[v], a[v + h], t[v >> (R - lp)], q, q4);
+                    const int j = v >> (R - lp);
+                    ulonglong2 w;
+                    if constexpr (DIRECT) w = TR.t[si][(1 << lp) - 1 + j];
+                    else w = t[j];
+                    ct_bfly(a[v], a[v + h], w, nq, q4);
                 }
             }
         } else {
@@ -149,7 +180,11 @@ __device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *tw, int l0,
 #pragma unroll
                 for (int v = 0; v < (1 << R); v++) {
                     if (v & h) continue;
-                    gs_bfly(a[v], a[v + h], t[v >> (R - lp)], q, q4);
+                    const int j = v >> (R - lp);
+                    ulonglong2 w;
+                    if constexpr (DIRECT) w = TR.t[si][(1 << lp) - 1 + j];
+                    else w = t[j];
+                    gs_bfly(a[v], a[v + h], w, nq, q4);
                 }
             }
         }
@@ -178,7 +213,10 @@ __global__ void __launch_bounds__(TE >> cmax(RA, cmax(RB, RC)))
 k_ntt_pass(const NttArgs P)
 {
     constexpr int NT = TE >> cmax(RA, cmax(RB, RC));
-    using Gm = Geometry<LOGM, TE, STRIDED>;
+    constexpr int RL = RC ? RC : RB;  // last round in forward order
+    constexpr int L0 = LOGM - RL;     // its first stage
+    constexpr bool DIRECT = !STRIDED;
+    using Gm = Geometry<LOGM, TE, STRIDED, RL>;
     constexpr int NG = Gm::NG;
     static_assert(RA + RB + RC == LOGM, "rounds must cover the pass");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -191,63 +229,86 @@ k_ntt_pass(const NttArgs P)
     const NttGroup &G = P.groups[gidx];
     const int nl = (int)G.nl;
     const DevPrime pr = P.primes[G.prime];
+    const u64 nq = 0ull - pr.q;
     const int N = 1 << P.logN;
     const int stride = N >> LOGM;
     const int s0 = STRIDED ? 0 : P.logN - LOGM;
 
-    // twiddles of this tile -> shared memory (16-byte async copies)
-    const ulonglong2 *twg = INV ? pr.iw : pr.w;
-    for (int f = threadIdx.x; f < Gm::TWN; f += NT) {
-        int gsrc;
-        if (STRIDED) {
-            gsrc = 1 + f;
-        } else {
-            const int l = 31 - __clz(f / NG + 1);  // NG (2^l - 1) <= f < NG (2^(l+1) - 1)
-            const int x = f - NG * ((1 << l) - 1);
-            gsrc = (1 << (s0 + l)) + tile * NG * (1 << l) + x;
-        }
-        __pipeline_memcpy_async(&tw[f], &twg[gsrc], 16);
-    }
     // data tile of limb i of the group -> shared memory (8-byte async copies)
     auto load_tile = [&](int i, u64 *b) {
         const u64 *src = FIRST ? P.src + (size_t)G.src[i] * N : P.dst + (size_t)G.dst[i] * N;
         for (int e = threadIdx.x; e < TE; e += NT)
             __pipeline_memcpy_async(&b[padi(e)], src + tile_gi<LOGM, TE, STRIDED>(e, tile, stride), 8);
     };
+    // staged twiddles of this tile -> shared memory (16-byte async copies)
+    const ulonglong2 *twg = INV ? pr.iw : pr.w;
+    if (STRIDED) {
+        for (int f = threadIdx.x; f < Gm::TWN; f += NT) __pipeline_memcpy_async(&tw[f], &twg[1 + f], 16);
+    } else {
+#pragma unroll
+        for (int l = 0; l < Gm::LS; l++) {
+            const int n = NG << l;
+            const ulonglong2 *g = twg + (1 << (s0 + l)) + (size_t)tile * n;
+            for (int f = threadIdx.x; f < n; f += NT) __pipeline_memcpy_async(&tw[NG * ((1 << l) - 1) + f], &g[f], 16);
+        }
+    }
     load_tile(0, buf);
     __pipeline_commit();
 
+    // the direct round's twiddles -> registers (reloaded for every limb from
+    // L2 so that they are live only during that round).  The device table
+    // stores the runs of these stages transposed: entry m + T 2^lp + j of
+    // stage m = 2^(s0 + L0 + lp) sits at m + j 2^(s0 + L0) + T, so for each j
+    // a warp reads consecutive entries.
+    constexpr int SPT = (TE >> RL) / NT;
+    auto load_direct = [&](TwReg<RL, SPT> &T) {
+#pragma unroll
+        for (int si = 0; si < SPT; si++) {
+            const int s = threadIdx.x + si * NT;
+            const int khi = s & ((1 << L0) - 1);
+            const int gg = tile * NG + (s >> L0);
+            const int Tn = (gg << L0) + khi;
+#pragma unroll
+            for (int lp = 0; lp < RL; lp++) {
+                const ulonglong2 *g = twg + (1 << (s0 + L0 + lp)) + Tn;
+#pragma unroll
+                for (int j = 0; j < (1 << lp); j++)
+                    T.t[si][(1 << lp) - 1 + j] = ld_tw(g + ((size_t)j << (s0 + L0)));
+            }
+        }
+    };
+
     for (int i = 0; i < nl; i++) {
-        u64 *sm = buf + (Gm::NBUF == 2 ? (i & 1) * Gm::DATA : 0);
-        if (Gm::NBUF == 2 && i + 1 < nl) {
+        u64 *sm = buf + (i & 1) * Gm::DATA;
+        TwReg<RL, SPT> TR;
+        if (DIRECT && INV) load_direct(TR);  // the inverse starts with the direct round
+        if (i + 1 < nl) {
             load_tile(i + 1, buf + ((i + 1) & 1) * Gm::DATA);
             __pipeline_commit();
             __pipeline_wait_prior(1);
         } else {
-            if (Gm::NBUF == 1 && i > 0) {  // single buffer: load this limb now
-                load_tile(i, buf);
-                __pipeline_commit();
-            }
             __pipeline_wait_prior(0);
         }
         __syncthreads();
         if (!INV) {
-            ntt_round<LOGM, TE, RA, STRIDED, false, NT>(sm, tw, 0, pr.q, pr.q4);
+            ntt_round<LOGM, TE, RA, STRIDED, false, NT, false>(sm, tw, TR, 0, nq, pr.q4);
+            if (DIRECT && RC == 0) load_direct(TR);
             __syncthreads();
-            ntt_round<LOGM, TE, RB, STRIDED, false, NT>(sm, tw, RA, pr.q, pr.q4);
+            ntt_round<LOGM, TE, RB, STRIDED, false, NT, DIRECT && RC == 0>(sm, tw, TR, RA, nq, pr.q4);
+            if (DIRECT && RC != 0) load_direct(TR);
             __syncthreads();
             if (RC) {
-                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, false, NT>(sm, tw, RA + RB, pr.q, pr.q4);
+                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, false, NT, DIRECT>(sm, tw, TR, RA + RB, nq, pr.q4);
                 __syncthreads();
             }
         } else {
             if (RC) {
-                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, true, NT>(sm, tw, RA + RB, pr.q, pr.q4);
+                ntt_round<LOGM, TE, (RC ? RC : 1), STRIDED, true, NT, DIRECT>(sm, tw, TR, RA + RB, nq, pr.q4);
                 __syncthreads();
             }
-            ntt_round<LOGM, TE, RB, STRIDED, true, NT>(sm, tw, RA, pr.q, pr.q4);
+            ntt_round<LOGM, TE, RB, STRIDED, true, NT, DIRECT && RC == 0>(sm, tw, TR, RA, nq, pr.q4);
             __syncthreads();
-            ntt_round<LOGM, TE, RA, STRIDED, true, NT>(sm, tw, 0, pr.q, pr.q4);
+            ntt_round<LOGM, TE, RA, STRIDED, true, NT, false>(sm, tw, TR, 0, nq, pr.q4);
             __syncthreads();
         }
         // shared memory -> HBM, 16-byte stores, output reduction on the last pass
@@ -277,7 +338,7 @@ template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, 
 cudaError_t run_pass(const NttArgs &a, int ngroups, cudaStream_t st)
 {
     constexpr int NT = TE >> cmax(RA, cmax(RB, RC));
-    constexpr size_t smem = Geometry<LOGM, TE, STRIDED>::SMEM;
+    constexpr size_t smem = Geometry<LOGM, TE, STRIDED, (RC ? RC : RB)>::SMEM;
     auto kern = k_ntt_pass<LOGM, RA, RB, RC, STRIDED, INV, FIRST, LAST, TE>;
     static bool configured = false;  // once per instantiation
     if (!configured) {
@@ -289,6 +350,17 @@ cudaError_t run_pass(const NttArgs &a, int ngroups, cudaStream_t st)
     kern<<<ngroups * a.tiles, NT, smem, st>>>(a);
     return cudaGetLastError();
 }
+
+// Pass plans per ring size: the strided pass covers the first S1 stages
+// (rounds A1, B1, C1), the contiguous pass the last S2 (rounds A2, B2, C2).
+// N = 2^12 is one contiguous pass of rounds 4, 4, 4.
+template <int LOGN> struct Plan;
+template <> struct Plan<13> { static constexpr int S1 = 7, A1 = 4, B1 = 3, C1 = 0, S2 = 6, A2 = 3, B2 = 3, C2 = 0; };
+template <> struct Plan<14> { static constexpr int S1 = 7, A1 = 4, B1 = 3, C1 = 0, S2 = 7, A2 = 4, B2 = 3, C2 = 0; };
+template <> struct Plan<15> { static constexpr int S1 = 8, A1 = 4, B1 = 4, C1 = 0, S2 = 7, A2 = 4, B2 = 3, C2 = 0; };
+template <> struct Plan<16> { static constexpr int S1 = 8, A1 = 4, B1 = 4, C1 = 0, S2 = 8, A2 = 4, B2 = 4, C2 = 0; };
+template <> struct Plan<17> { static constexpr int S1 = 9, A1 = 3, B1 = 3, C1 = 3, S2 = 8, A2 = 4, B2 = 4, C2 = 0; };
+template <int LOGN> constexpr int plan_direct() { return Plan<LOGN>::C2 ? Plan<LOGN>::C2 : Plan<LOGN>::B2; }
 
 // Two-pass transform: the strided pass covers the first S1 stages (forward
 // order), the contiguous pass the last S2.
@@ -323,6 +395,13 @@ cudaError_t two_pass(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cuda
     return e;
 }
 
+template <int LOGN>
+cudaError_t two_pass_plan(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag)
+{
+    using P = Plan<LOGN>;
+    return two_pass<P::S1, P::A1, P::B1, P::C1, P::S2, P::A2, P::B2, P::C2>(c, a, ngroups, inverse, st, tag);
+}
+
 }  // namespace
 
 cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups, bool inverse,
@@ -348,12 +427,25 @@ cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGrou
         prof_mark(c, st, tag, inverse ? ".inv" : ".fwd");
         return e;
     }
-    case 13: return two_pass<7, 4, 3, 0, 6, 3, 3, 0>(c, a, ngroups, inverse, st, tag);
-    case 14: return two_pass<7, 4, 3, 0, 7, 4, 3, 0>(c, a, ngroups, inverse, st, tag);
-    case 15: return two_pass<8, 4, 4, 0, 7, 4, 3, 0>(c, a, ngroups, inverse, st, tag);
-    case 16: return two_pass<8, 4, 4, 0, 8, 4, 4, 0>(c, a, ngroups, inverse, st, tag);
-    case 17: return two_pass<9, 3, 3, 3, 8, 4, 4, 0>(c, a, ngroups, inverse, st, tag);
+    case 13: return two_pass_plan<13>(c, a, ngroups, inverse, st, tag);
+    case 14: return two_pass_plan<14>(c, a, ngroups, inverse, st, tag);
+    case 15: return two_pass_plan<15>(c, a, ngroups, inverse, st, tag);
+    case 16: return two_pass_plan<16>(c, a, ngroups, inverse, st, tag);
+    case 17: return two_pass_plan<17>(c, a, ngroups, inverse, st, tag);
     default: return cudaErrorInvalidValue;
+    }
+}
+
+int ntt_direct_stages(int logN)
+{
+    switch (logN) {
+    case 12: return 4;  // the single pass's third round
+    case 13: return plan_direct<13>();
+    case 14: return plan_direct<14>();
+    case 15: return plan_direct<15>();
+    case 16: return plan_direct<16>();
+    case 17: return plan_direct<17>();
+    default: return 0;
     }
 }
 
