@@ -113,6 +113,7 @@ struct he_ctx {
     std::vector<u64> ninv, ninv_sh;                  // [E]
     // level-independent ModDown constants
     std::vector<u64> PB;                 // [L][KP]: [Phat_k]_{q_i} split at bit 28, zero-padded
+    std::vector<u64> PBP;                // [L][KP]: [Phat_k P^-1]_{q_i}, same format (fused ModDown)
     std::vector<ulonglong2> pinv;        // [L]: P^-1 mod q_i
     std::vector<ulonglong2> phat_inv;    // [K]: Phat_k^-1 mod p_k
     std::vector<he::HostLevel> host_levels;  // index l (1..L)
@@ -122,6 +123,7 @@ struct he_ctx {
     size_t arena_bytes = 0;
     he::DevPrime *d_primes = nullptr;    // [E]
     const u64 *d_PB = nullptr;
+    const u64 *d_PBP = nullptr;
     const ulonglong2 *d_pinv = nullptr;
     std::vector<he::DevLevel> dev_levels;  // index l (host copy of the device structs)
     he::DevLevel *d_levels = nullptr;      // [L+1]

@@ -169,6 +169,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
 
     // ModDown constants
     c->PB.assign((size_t)L * c->KP, 0);
+    c->PBP.assign((size_t)L * c->KP, 0);
     c->pinv.resize(L);
     c->phat_inv.resize(K);
     for (int k = 0; k < K; k++) {
@@ -187,6 +188,12 @@ int build_context(he_ctx *c, const he_params *p, bool device)
             P = mul(P, c->ext[k] % qi, qi);
         }
         c->pinv[i] = pair(inv(P, qi), qi);
+        for (int k = 0; k < K; k++) {
+            u64 v = 1;
+            for (int k2 = 0; k2 < K; k2++)
+                if (k2 != k) v = mul(v, c->ext[k2] % qi, qi);
+            c->PBP[(size_t)i * c->KP + k] = split28(mul(v, c->pinv[i].x, qi));
+        }
     }
 
     // per level
@@ -280,6 +287,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         o_iw[e] = take(sizeof(ulonglong2) * N);
     }
     const size_t o_PB = take(sizeof(u64) * c->PB.size());
+    const size_t o_PBP = take(sizeof(u64) * c->PBP.size());
     const size_t o_pinv = take(sizeof(ulonglong2) * L);
     const size_t o_levels = take(sizeof(DevLevel) * (L + 1));
     struct LvlOff { size_t modupB, qinv, pq, j[9]; };
@@ -340,6 +348,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
     }
     memcpy(img.data() + o_primes, dp.data(), sizeof(DevPrime) * E);
     memcpy(img.data() + o_PB, c->PB.data(), sizeof(u64) * c->PB.size());
+    memcpy(img.data() + o_PBP, c->PBP.data(), sizeof(u64) * c->PBP.size());
     memcpy(img.data() + o_pinv, c->pinv.data(), sizeof(ulonglong2) * L);
     c->dev_levels.assign(L + 1, DevLevel());
     c->jobs.assign(L + 1, LevelJobs());
@@ -388,6 +397,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
     if (cudaMemcpy(c->arena, img.data(), off, cudaMemcpyHostToDevice) != cudaSuccess) return HE_ECUDA;
     c->d_primes = (DevPrime *)(base + o_primes);
     c->d_PB = (const u64 *)(base + o_PB);
+    c->d_PBP = (const u64 *)(base + o_PBP);
     c->d_pinv = (const ulonglong2 *)(base + o_pinv);
     c->d_levels = (DevLevel *)(base + o_levels);
     if (configure_ntt(c) != cudaSuccess) return HE_ECUDA;

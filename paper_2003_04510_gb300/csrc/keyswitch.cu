@@ -7,11 +7,13 @@
 //                  U_j[t] = sum_{i in I_j} y_i [Qhat_{j,i}]_t mod t, with the
 //                  y_i = x_i Qhat^-1 factor already applied by the iNTT.
 //                  Lazy accumulation (the paper's delayed-modulo idea for
-//                  CRT, Sec. 5.3): operands split at bit 28, four 32x32->64
-//                  multiply-adds per term, one Barrett reduction per output.
+//                  CRT, Sec. 5.3): operands split at bit 28, three 32x32->64
+//                  multiply-adds per term (Karatsuba), one Barrett reduction
+//                  per output.
 //  k_inner_product Region 2 of Fig. 2: KS_{b,a}[t] = sum_j U_j[t] evk_j.{b,a}[t].
 //  k_moddown_conv  mod down (Sec. 7): conv_i = sum_k y_k [Phat_k]_{q_i} mod q_i;
-//                  the fused variant also folds in the rescale residue.
+//                  the fused variant uses constants [Phat_k P^-1]_{q_i}, giving
+//                  conv_i P^-1 directly, and folds in the rescale residue.
 //  k_combine_*     the final additions (Fig. 2) and the rescale division.
 //
 // Every kernel handles two consecutive coefficients per thread with 16-byte
@@ -113,12 +115,12 @@ k_modup(const JobRef R, const DevLevel *__restrict__ lv_arr, const DevPrime *__r
 #pragma unroll
         for (int i = 0; i < A; i++) {
             const u64 c = sB[u][i];
-            mac28(ax, x0[i], x1[i], c);
-            mac28(ay, z0[i], z1[i], c);
+            mac28k(ax, x0[i], x1[i], x0[i] + x1[i], c);
+            mac28k(ay, z0[i], z1[i], z0[i] + z1[i], c);
         }
         const u64 q = sq[u], mu = smu[u];
         const unsigned sh = ss[u];
-        st2(Uj + (size_t)se[u] * N + n, barrett128(acc3_value(ax), q, mu, sh), barrett128(acc3_value(ay), q, mu, sh));
+        st2(Uj + (size_t)se[u] * N + n, barrett128(acc3k_value(ax), q, mu, sh), barrett128(acc3k_value(ay), q, mu, sh));
     }
 }
 
@@ -172,15 +174,15 @@ __device__ __forceinline__ void conv_one(const uint32_t *x0, const uint32_t *x1,
 #pragma unroll
     for (int k = 0; k < KM; k++) {
         const u64 c = b[k];
-        mac28(ax, x0[k], x1[k], c);
-        mac28(ay, z0[k], z1[k], c);
+        mac28k(ax, x0[k], x1[k], x0[k] + x1[k], c);
+        mac28k(ay, z0[k], z1[k], z0[k] + z1[k], c);
     }
-    cx = barrett128(acc3_value(ax), q, mu, sh);
-    cy = barrett128(acc3_value(ay), q, mu, sh);
+    cx = barrett128(acc3k_value(ax), q, mu, sh);
+    cy = barrett128(acc3k_value(ay), q, mu, sh);
 }
 
 template <int KM, bool FUSED>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, KM <= 8 ? 3 : 1)
 k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__restrict__ pinv,
                const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int N, int chunks)
 {
@@ -225,24 +227,25 @@ k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__r
     __syncthreads();
     u64 rx = 0, ry = 0;
     if (FUSED) {
+        // PB rows already carry the factor P^-1: the conversion yields
+        // conv_{l-1} P^-1, and r = r0 + r1 P^-1 - conv_{l-1} P^-1
         const int r = kModdownChunk;
         const u64 q = sq[r];
         u64 cx, cy;
         conv_one<KM>(x0, x1, z0, z1, sB[r], q, smu[r], ss[r], cx, cy);
         const ulonglong2 r0 = ld2(rr + (size_t)h * N + n), r1 = ld2(rr + (size_t)(2 + h) * N + n);
         const ulonglong2 pv = spv[r];
-        rx = add_mod(r0.x, shoup(sub_mod(r1.x, cx, q), pv.x, pv.y, q), q);
-        ry = add_mod(r0.y, shoup(sub_mod(r1.y, cy, q), pv.x, pv.y, q), q);
+        rx = add_mod(r0.x, sub_mod(shoup(r1.x, pv.x, pv.y, q), cx, q), q);
+        ry = add_mod(r0.y, sub_mod(shoup(r1.y, pv.x, pv.y, q), cy, q), q);
     }
     for (int r = 0; r < cnt; r++) {
         const u64 q = sq[r];
         u64 cx, cy;
         conv_one<KM>(x0, x1, z0, z1, sB[r], q, smu[r], ss[r], cx, cy);
         if (FUSED) {
-            // r < q_{l-1} < q_i: r is already a residue mod q_i
-            const ulonglong2 pv = spv[r];
-            cx = add_mod(shoup(cx, pv.x, pv.y, q), rx, q);
-            cy = add_mod(shoup(cy, pv.x, pv.y, q), ry, q);
+            // conv_i P^-1 + r; r < q_{l-1} < q_i is already a residue mod q_i
+            cx = add_mod(cx, rx, q);
+            cy = add_mod(cy, ry, q);
         }
         st2(z + ((size_t)h * nout + i0 + r) * N + n, cx, cy);
     }
@@ -364,7 +367,7 @@ cudaError_t run_moddown_conv(const he_ctx *c, const JobRef &R, bool fused, cudaS
 #define HE_MD(KK)                                                                                                   \
     do {                                                                                                            \
         if (fused)                                                                                                  \
-            k_moddown_conv<KK, true><<<g, kThreads, 0, st>>>(R, c->d_PB, c->d_pinv, c->d_levels, c->d_primes, K,   \
+            k_moddown_conv<KK, true><<<g, kThreads, 0, st>>>(R, c->d_PBP, c->d_pinv, c->d_levels, c->d_primes, K,  \
                                                              c->N, chunks);                                         \
         else                                                                                                        \
             k_moddown_conv<KK, false><<<g, kThreads, 0, st>>>(R, c->d_PB, c->d_pinv, c->d_levels, c->d_primes, K,  \

@@ -142,6 +142,21 @@ __device__ __forceinline__ void mac28(Acc3 &s, uint32_t x0, uint32_t x1, u64 bpa
     s.a2 = mad_wide(x1, b1, s.a2);
 }
 
+// Karatsuba form of mac28: three multiply-adds per term, x0*b0 (into a0),
+// x1*b1 (into a2) and (x0+x1)*(b0+b1) (into a1, which then holds the sum of
+// all three products' middle parts plus a0 and a2; acc3k_value takes them
+// out).  xs = x0 + x1 is formed once per input.  For x, b < 2^57 and at most
+// 16 terms: a0 < 2^60, a2 < 2^62 and a1 < 16 * 9 * 2^56 < 2^64, and the
+// recovered middle sum x0*b1 + x1*b0 stays below 2^62, so acc3k_value returns
+// exactly what acc3_value returns for the four-product form.
+__device__ __forceinline__ void mac28k(Acc3 &s, uint32_t x0, uint32_t x1, uint32_t xs, u64 bpacked)
+{
+    const uint32_t b0 = (uint32_t)bpacked, b1 = (uint32_t)(bpacked >> 32);
+    s.a0 = mad_wide(x0, b0, s.a0);
+    s.a2 = mad_wide(x1, b1, s.a2);
+    s.a1 = mad_wide(xs, b0 + b1, s.a1);
+}
+
 __device__ __forceinline__ U128 acc3_value(const Acc3 &s)
 {
     U128 v;
@@ -152,4 +167,13 @@ __device__ __forceinline__ U128 acc3_value(const Acc3 &s)
     c += v.lo < t2 ? 1ull : 0ull;
     v.hi = (s.a1 >> 36) + (s.a2 >> 8) + c;
     return v;
+}
+
+__device__ __forceinline__ U128 acc3k_value(const Acc3 &k)
+{
+    Acc3 t;
+    t.a0 = k.a0;
+    t.a1 = k.a1 - k.a0 - k.a2;
+    t.a2 = k.a2;
+    return acc3_value(t);
 }
