@@ -126,7 +126,9 @@ k_modup(const JobRef R, const DevLevel *__restrict__ lv_arr, const DevPrime *__r
 
 // grid: x over N/2/kThreads, y over ext limbs (up to K + lmax), z over jobs.
 // U: [beta][E][N] (own-digit rows read from d2), evk: [dnum][2][K+L][N],
-// KS: [2][E][N].
+// KS: [2][E][N].  The digit loop is unrolled to BM >= beta with guards, so
+// every operand load of a thread is issued before the first product.
+template <int BM>
 __global__ void __launch_bounds__(kThreads)
 k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__restrict__ lv_arr,
                 const DevPrime *__restrict__ primes, int K, int L, int N)
@@ -134,23 +136,32 @@ k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__r
     const BatchItem it = job_of(R, blockIdx.z);
     const DevLevel &lv = lv_arr[it.level];
     const int e = blockIdx.y;
-    const int E = lv.E, EL = K + L;
+    const int E = lv.E, EL = K + L, beta = lv.beta;
     if (e >= E) return;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[e];
     const u64 *U = it.ws + (size_t)lv.o_u * N, *d2 = it.ws + (size_t)lv.o_d2 * N;
+    ulonglong2 u[BM], kb[BM], ka[BM];
+#pragma unroll
+    for (int j = 0; j < BM; j++) {
+        if (j < beta) {
+            const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
+            const bool own = e >= K && e - K >= lo && e - K < lo + nj;
+            const u64 *up = own ? d2 + (size_t)(e - K) * N : U + ((size_t)j * E + e) * N;
+            u[j] = ld2(up + n);
+            kb[j] = ld2(evk + ((size_t)(2 * j) * EL + e) * N + n);
+            ka[j] = ld2(evk + ((size_t)(2 * j + 1) * EL + e) * N + n);
+        }
+    }
     U128 bx = {0, 0}, by = {0, 0}, ax = {0, 0}, ay = {0, 0};
-    for (int j = 0; j < lv.beta; j++) {
-        const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
-        const bool own = e >= K && e - K >= lo && e - K < lo + nj;
-        const u64 *up = own ? d2 + (size_t)(e - K) * N : U + ((size_t)j * E + e) * N;
-        const ulonglong2 u = ld2(up + n);
-        const ulonglong2 kb = ld2(evk + ((size_t)(2 * j) * EL + e) * N + n);
-        const ulonglong2 ka = ld2(evk + ((size_t)(2 * j + 1) * EL + e) * N + n);
-        mac(bx, u.x, kb.x);
-        mac(by, u.y, kb.y);
-        mac(ax, u.x, ka.x);
-        mac(ay, u.y, ka.y);
+#pragma unroll
+    for (int j = 0; j < BM; j++) {
+        if (j < beta) {
+            mac(bx, u[j].x, kb[j].x);
+            mac(by, u[j].y, kb[j].y);
+            mac(ax, u[j].x, ka[j].x);
+            mac(ay, u[j].y, ka[j].y);
+        }
     }
     u64 *KS = it.ws + (size_t)lv.o_ks * N;
     st2(KS + (size_t)e * N + n, barrett128(bx, pr.q, pr.mu, pr.s), barrett128(by, pr.q, pr.mu, pr.s));
@@ -353,7 +364,13 @@ cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, 
     dim3 g = grid_x(c->N);
     g.y = c->K + R.lmax;
     g.z = R.B;
-    k_inner_product<<<g, kThreads, 0, st>>>(R, evk, c->d_levels, c->d_primes, c->K, c->L, c->N);
+    const int bm = (c->L + c->alpha - 1) / c->alpha;  // the most digits any level has
+#define HE_IP(B) k_inner_product<B><<<g, kThreads, 0, st>>>(R, evk, c->d_levels, c->d_primes, c->K, c->L, c->N)
+    if (bm <= 2) HE_IP(2);
+    else if (bm <= 4) HE_IP(4);
+    else if (bm <= 8) HE_IP(8);
+    else HE_IP(16);
+#undef HE_IP
     return cudaGetLastError();
 }
 
