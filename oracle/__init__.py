@@ -81,6 +81,9 @@ def lib():
             "or_keyswitch": (None, [i32, i32, i32, i32, i32, P, P, P, P, P, P, P, P, P]),
             "or_he_mul": (None, [i32, i32, i32, i32, i32, P, P, P, P, P, P, P, P]),
             "or_rescale": (None, [i32, i32, P, P, P, P]),
+            "or_automorphism": (None, [P, i32, u64, u64, P]),
+            "or_keygen_rot": (None, [i32, i32, i32, i32, P, P, P, P, dbl, P, u64, u64, P]),
+            "or_rotate": (None, [i32, i32, i32, i32, i32, P, P, P, P, P, u64, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -278,6 +281,41 @@ def he_mul(prm: Params, ct1, ct2, evk, level: int) -> np.ndarray:
 def rescale(prm: Params, ct, level: int) -> np.ndarray:
     out = np.zeros((2, level - 1, prm.N), dtype=np.uint64)
     lib().or_rescale(prm.logN, level, _p(prm.q), _p(prm.psi_q), _p(_u64(ct)), _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Rotation (NEXT-1): Galois automorphisms and key switching with rotation keys.
+# --------------------------------------------------------------------------
+def galois_elt(prm: Params, steps: int) -> int:
+    """g = 5^steps mod 2N: kappa_g moves slot k+steps to slot k (steps may be negative)."""
+    return pow(5, steps % (prm.N // 2), 2 * prm.N)
+
+
+def conj_elt(prm: Params) -> int:
+    """g = 2N - 1: kappa_g conjugates every slot."""
+    return 2 * prm.N - 1
+
+
+def automorphism(a, q: int, g: int, logN: int) -> np.ndarray:
+    """a(X) -> a(X^g) mod (X^N + 1, q), coefficient form."""
+    a = _u64(a)
+    out = np.zeros_like(a)
+    lib().or_automorphism(_p(a), logN, q, g, _p(out))
+    return out
+
+
+def keygen_rot(prm: Params, sk: np.ndarray, g: int, seed: int) -> np.ndarray:
+    rk = np.zeros((prm.dnum, 2, prm.K + prm.L, prm.N), dtype=np.uint64)
+    lib().or_keygen_rot(prm.logN, prm.L, prm.K, prm.alpha, _p(prm.q), _p(prm.psi_q), _p(prm.p),
+                        _p(prm.psi_p), prm.sigma, _p(np.ascontiguousarray(sk, dtype=np.int64)), g, seed, _p(rk))
+    return rk
+
+
+def rotate(prm: Params, ct, g: int, rk, level: int) -> np.ndarray:
+    out = np.zeros((2, level, prm.N), dtype=np.uint64)
+    lib().or_rotate(prm.logN, level, prm.L, prm.K, prm.alpha, _p(prm.q), _p(prm.psi_q), _p(prm.p),
+                    _p(prm.psi_p), _p(_u64(ct)), g, _p(_u64(rk)), _p(out))
     return out
 
 

@@ -257,7 +257,7 @@ static int64_t rng_zo(rng_t *r)
 
 /* Stream identifiers (fixed; the product library uses the same numbers). */
 enum { ST_SK = 1, ST_PK_A = 2, ST_PK_E = 3, ST_ENC_U = 4, ST_ENC_E0 = 5, ST_ENC_E1 = 6,
-       ST_EVK_A = 16, ST_EVK_E = 48 };
+       ST_EVK_A = 16, ST_EVK_E = 48, ST_ROT_A = 80, ST_ROT_E = 112 };
 
 /* Exposed samplers for the distribution tests. */
 void or_sample_gauss(uint64_t seed, uint64_t stream, double sigma, int64_t n, int64_t *out)
@@ -681,4 +681,118 @@ void or_rescale(int logN, int l, const uint64_t *q, const uint64_t *psi_q, const
         }
     }
     free(r); free(ri);
+}
+
+/* ---------------------------------------------------------------------------
+ * Galois automorphism kappa_g : a(X) -> a(X^g) on Z_q[X]/(X^N + 1), g odd in
+ * [1, 2N).  Written from the definition: coefficient i goes to exponent
+ * i*g mod 2N, and an exponent e >= N is X^(e-N) * X^N = -X^(e-N).  (Rotation
+ * is not in the paper; it is the next operation built on the paper's key
+ * switching, Fig. 2.)  a, out: [N] coefficient form, out != a.
+ * ------------------------------------------------------------------------- */
+void or_automorphism(const uint64_t *a, int logN, uint64_t q, uint64_t g, uint64_t *out)
+{
+    uint64_t N = 1ull << logN, twoN = 2 * N;
+    for (uint64_t i = 0; i < N; i++) {
+        uint64_t e = (uint64_t)(((u128)i * (g % twoN)) % twoN);
+        if (e < N) out[e] = a[i] % q;
+        else out[e - N] = submod(0, a[i], q);
+    }
+}
+
+/* The same on a small signed polynomial (the secret key). */
+static void small_automorphism(const int64_t *a, int logN, uint64_t g, int64_t *out)
+{
+    uint64_t N = 1ull << logN, twoN = 2 * N;
+    for (uint64_t i = 0; i < N; i++) {
+        uint64_t e = (uint64_t)(((u128)i * (g % twoN)) % twoN);
+        if (e < N) out[e] = a[i];
+        else out[e - N] = -a[i];
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Key-switching key from kappa_g(s) to s (a "rotation key"): the evk of
+ * or_keygen_evk with kappa_g(s) in place of s^2,
+ *   b_j[t] = a_j[t] s + e_j + [t = q_i, i in I_j] (P mod q_i) kappa_g(s)  mod t,
+ * a_j uniform (stream ST_ROT_A + j), e_j Gaussian (stream ST_ROT_E + j).
+ * Layout as evk: [dnum][2][K+L][N], b first, ext order, NTT domain.
+ * ------------------------------------------------------------------------- */
+void or_keygen_rot(int logN, int L, int K, int alpha, const uint64_t *q, const uint64_t *psi_q,
+                   const uint64_t *p, const uint64_t *psi_p, double sigma, const int64_t *s, uint64_t g,
+                   uint64_t seed, uint64_t *rk)
+{
+    or_mod M = mk_mod(logN, L, K, alpha, q, psi_q, p, psi_p);
+    uint64_t N = 1ull << logN;
+    int E = K + L, dnum = n_digits(L, alpha);
+    int64_t *ks = (int64_t *)malloc(N * sizeof(int64_t));
+    small_automorphism(s, logN, g, ks);
+    uint64_t *S = (uint64_t *)malloc(N * sizeof(uint64_t));
+    uint64_t *KSn = (uint64_t *)malloc(N * sizeof(uint64_t));
+    uint64_t *Ej = (uint64_t *)malloc(N * sizeof(uint64_t));
+    int64_t *e = (int64_t *)malloc(N * sizeof(int64_t));
+    for (int j = 0; j < dnum; j++) {
+        rng_t ra = rng_open(seed, ST_ROT_A + j), re = rng_open(seed, ST_ROT_E + j);
+        for (uint64_t n = 0; n < N; n++) e[n] = rng_gauss(&re, sigma);
+        uint64_t *bj = rk + ((size_t)j * 2 + 0) * E * N;
+        uint64_t *aj = rk + ((size_t)j * 2 + 1) * E * N;
+        for (int x = 0; x < E; x++) {
+            uint64_t t = ext_mod(&M, x);
+            uint64_t *a = aj + (size_t)x * N, *b = bj + (size_t)x * N;
+            for (uint64_t n = 0; n < N; n++) a[n] = rng_below(&ra, t);
+            small_to_ntt(s, S, logN, t, ext_psi(&M, x));
+            small_to_ntt(ks, KSn, logN, t, ext_psi(&M, x));
+            small_to_ntt(e, Ej, logN, t, ext_psi(&M, x));
+            int in_digit = (x >= K) && (x - K) >= digit_lo(j, alpha) && (x - K) < digit_hi(j, alpha, L);
+            uint64_t Pmod = 1;
+            if (in_digit)
+                for (int k = 0; k < K; k++) Pmod = mulmod(Pmod, p[k] % t, t);
+            for (uint64_t n = 0; n < N; n++) {
+                uint64_t v = addmod(mulmod(a[n], S[n], t), Ej[n], t);
+                if (in_digit) v = addmod(v, mulmod(Pmod, KSn[n], t), t);
+                b[n] = v;
+            }
+        }
+    }
+    free(ks); free(S); free(KSn); free(Ej); free(e);
+}
+
+/* ---------------------------------------------------------------------------
+ * HE rotation by the automorphism kappa_g at level l.  (kappa(b), kappa(a))
+ * decrypts under kappa(s): kappa(b) - kappa(a) kappa(s) = kappa(m).  Key
+ * switching x = -kappa(a) with the key for kappa(s) (Fig. 2's region 2 flow:
+ * ModUp, NTT, inner product, ModDown) gives
+ *   out = (kappa(b) + ModDown(KS_b), ModDown(KS_a)),
+ * which decrypts to kappa(b) - kappa(a) kappa(s) + small.  kappa is applied
+ * in coefficient form (iNTT, definition, NTT).  ct, out: [2][l][N].
+ * ------------------------------------------------------------------------- */
+void or_rotate(int logN, int l, int L, int K, int alpha, const uint64_t *q, const uint64_t *psi_q,
+               const uint64_t *p, const uint64_t *psi_p, const uint64_t *ct, uint64_t g, const uint64_t *rk,
+               uint64_t *out)
+{
+    uint64_t N = 1ull << logN;
+    size_t LN = (size_t)l * N;
+    uint64_t *kc = (uint64_t *)malloc(2 * LN * sizeof(uint64_t));
+    uint64_t *tmp = (uint64_t *)malloc(N * sizeof(uint64_t));
+    uint64_t *ks = (uint64_t *)malloc(2 * LN * sizeof(uint64_t));
+    for (int h = 0; h < 2; h++)
+        for (int i = 0; i < l; i++) {
+            const uint64_t *src = ct + (size_t)h * LN + (size_t)i * N;
+            uint64_t *dst = kc + (size_t)h * LN + (size_t)i * N;
+            memcpy(tmp, src, N * sizeof(uint64_t));
+            or_intt(tmp, logN, q[i], psi_q[i]);
+            or_automorphism(tmp, logN, q[i], g, dst);
+            or_ntt(dst, logN, q[i], psi_q[i]);
+        }
+    uint64_t *x = kc + LN;  /* x = -kappa(a), in place */
+    for (int i = 0; i < l; i++)
+        for (uint64_t n = 0; n < N; n++) x[(size_t)i * N + n] = submod(0, x[(size_t)i * N + n], q[i]);
+    or_keyswitch(logN, l, L, K, alpha, q, psi_q, p, psi_p, x, rk, ks, NULL, NULL);
+    for (int i = 0; i < l; i++)
+        for (uint64_t n = 0; n < N; n++) {
+            size_t o = (size_t)i * N + n;
+            out[o] = addmod(kc[o], ks[o], q[i]);
+            out[LN + o] = ks[LN + o];
+        }
+    free(kc); free(tmp); free(ks);
 }
