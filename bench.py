@@ -456,6 +456,29 @@ def run_ours(args):
         per_kernel[k] = d
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_total"]) if per_kernel else None
 
+    # ---- HE rotation (Galois automorphism + key switch) on the same workload ----
+    rot = None
+    if not args.no_rotate:
+        gal = g.he_galois_elt(ctx, 1)
+        rk_t = g.to_device(g.he_keygen_rot(ctx, ks + 77, sk, gal), dev)
+        rot_out = torch.empty((2, level, N), dtype=torch.int64, device=dev)
+        for k in range(3):
+            g.he_rotate(ctx, ct_t[k % NPAIRS][0], rk_t, level, gal, rot_out, ws, stream)
+        torch.cuda.synchronize()
+        zr = g.he_decrypt(ctx, sk, g.to_host(rot_out), level, sc)
+        rot_err = float(np.abs(zr - np.roll(si.messages(N // 2, s1 + 17 * 2), -1)).max())
+        reps = max(20, min(args.steps, 1000))
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        for k in range(reps):
+            g.he_rotate(ctx, ct_t[k % NPAIRS][0], rk_t, level, gal, rot_out, ws, stream)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        rms = r0.elapsed_time(r1) / reps
+        rot = {"HE_Rotate_per_s": 1e3 / rms, "ms": rms, "level": level, "steps": 1, "reps": reps,
+               "decrypt_max_err": rot_err}
+        del rk_t
+
     # ALU ceiling: register-resident butterfly probe
     bfly_peak = g.he_probe_butterfly_rate(152 * 8, 4096, stream)
     probe = {"butterfly_per_s": bfly_peak}
@@ -530,6 +553,7 @@ def run_ours(args):
             "inner_product_hbm": ip,
             "probe": probe,
             "kernels": per_kernel,
+            "rotate": rot,
             "batched": batched,
             "serving": serving,
             "cpu_baseline": cpu,
@@ -551,6 +575,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-rotate", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

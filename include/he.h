@@ -291,6 +291,31 @@ int he_server_stats(he_server *s, he_server_report *stats);
  * that were never launched are dropped. */
 int he_server_destroy(he_server *s);
 
+/* ---- rotation ---------------------------------------------------------------
+ * HE rotation is not in the paper; it is the next operation built on the
+ * paper's key switching (Fig. 2, region 2), reusing every kernel of it.
+ * kappa_g : a(X) -> a(X^g) (g odd, 1 <= g < 2N) maps a ciphertext of m under
+ * s to one of kappa_g(m) under kappa_g(s); key switching back to s uses a
+ * rotation key, the evaluation key with kappa_g(s) in place of s^2. */
+
+/* g = 5^steps mod 2N: kappa_g moves slot k+steps to slot k (left rotation by
+ * `steps`, which may be negative).  2N - 1 conjugates every slot.  0 if ctx
+ * is NULL. */
+uint64_t he_galois_elt(const he_ctx *ctx, int steps);
+/* Rotation key for kappa_g: rk [dnum][2][K+L][N] host, same layout as evk;
+ * b_j = a_j s + e_j + [t in digit j] P kappa_g(s), a_j and e_j drawn from
+ * `seed` (streams distinct from the evaluation key's).  HE_EINVAL for an even
+ * or out-of-range g. */
+int he_keygen_rot(he_ctx *ctx, uint64_t seed, const int64_t *sk, uint64_t galois, uint64_t *rk);
+/* HE rotation at `level` (device): out = (kappa(b) + ModDown(KS_b),
+ * ModDown(KS_a)) with KS = sum_j ModUp_j(-kappa(a)) rk_j; out decrypts under
+ * s to kappa_g(m) at the same level and scale.  ct, out: [2][level][N] device,
+ * out may not alias ct; ws as for he_mul (he_workspace_bytes(level)).
+ * HE_EINVAL for an even or out-of-range g, HE_ELEVEL for level outside 1..L,
+ * HE_ENOMEM if ws_bytes is too small. */
+int he_rotate(he_ctx *ctx, const uint64_t *ct, const uint64_t *rk_dev, int level, uint64_t galois, uint64_t *out,
+              void *ws, size_t ws_bytes, void *stream);
+
 /* ---- profiling ------------------------------------------------------------ */
 
 /* Enable (1) or disable (0) per-kernel CUDA-event marks on this context's

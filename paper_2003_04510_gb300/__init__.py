@@ -119,6 +119,11 @@ _SIGS = {
     "he_batch_graph_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "he_batch_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "he_probe_butterfly_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "he_galois_elt": (ctypes.c_uint64, [ctypes.c_void_p, ctypes.c_int]),
+    "he_keygen_rot": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
+                                     ctypes.c_void_p]),
+    "he_rotate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "he_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "he_mul_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
@@ -324,6 +329,29 @@ def he_mul_rescale_static(ctx, ct1, ct2, evk, level, out, stream=None):
     """he_mul_rescale with the library's fixed device scratch as workspace (no allocation)."""
     _check(lib().he_mul_rescale_static(ctx.ptr, _dev_ptr(ct1), _dev_ptr(ct2), _dev_ptr(evk), level, _dev_ptr(out),
                                        _stream_ptr(stream)), "he_mul_rescale_static")
+
+
+def he_galois_elt(ctx, steps: int) -> int:
+    """5^steps mod 2N (left rotation by `steps` slots)."""
+    return int(lib().he_galois_elt(ctx.ptr, int(steps)))
+
+
+def he_conj_elt(ctx) -> int:
+    """2N - 1 (slot-wise complex conjugation)."""
+    return 2 * ctx.N - 1
+
+
+def he_keygen_rot(ctx, seed: int, sk: np.ndarray, galois: int) -> np.ndarray:
+    prm = ctx.prm
+    rk = np.zeros((ctx.dnum, 2, prm.K + prm.L, ctx.N), dtype=np.uint64)
+    _check(lib().he_keygen_rot(ctx.ptr, seed, _np_ptr(np.ascontiguousarray(sk, dtype=np.int64)), galois, _np_ptr(rk)),
+           "he_keygen_rot")
+    return rk
+
+
+def he_rotate(ctx, ct, rk, level, galois, out, ws, stream=None):
+    _check(lib().he_rotate(ctx.ptr, _dev_ptr(ct), _dev_ptr(rk), level, galois, _dev_ptr(out), _dev_ptr(ws),
+                           ws.numel() * 8, _stream_ptr(stream)), "he_rotate")
 
 
 def he_rescale(ctx, ct, level, out, ws, stream=None):

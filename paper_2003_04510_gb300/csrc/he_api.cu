@@ -69,6 +69,9 @@ struct Stages {
 // The HE Mul pipeline for one job or a batch (JobRef).  fused = ModDown and
 // rescale merged (out is [2][l-1][N]); otherwise out is the level-l product.
 // NTT group offsets are relative to ntt_base.
+int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, bool fused,
+                  cudaStream_t st);
+
 int run_pipeline(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, bool fused,
                  cudaStream_t st)
 {
@@ -76,6 +79,13 @@ int run_pipeline(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, con
     // Region 1: tensor product
     HE_TRY(run_tensor(c, R, st));
     prof_mark(c, st, "tensor");
+    return run_keyswitch(c, R, ntt_base, S, evk, fused, st);
+}
+
+// Region 2 and the final additions, on d0, d1, d2 already in the workspace.
+int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, bool fused,
+                  cudaStream_t st)
+{
     // key switching: iNTT(d2) (times N^-1 Qhat^-1), ModUp, NTT, inner product
     const int *cnt = S.counts;
     HE_TRY(launch_ntt(c, ntt_base, S.intt1, S.n_intt1, true, st, "intt_d2", cnt ? cnt + 0 : nullptr));
@@ -245,6 +255,23 @@ int he_mul_rescale(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, const ui
     if (!aligned(ct1) || !aligned(ct2) || !aligned(out) || !aligned(ws) || !aligned(evk)) return HE_EINVAL;
     if (ws_bytes < ws_bytes_for(c, level)) return HE_ENOMEM;
     return hemul_pipeline(c, ct1, ct2, evk, level, out, (u64 *)ws, true, S(stream));
+}
+
+int he_rotate(he_ctx *c, const uint64_t *ct, const uint64_t *rk, int level, uint64_t galois, uint64_t *out, void *ws,
+              size_t ws_bytes, void *stream)
+{
+    if (check_dev(c) || !ct || !rk || !out || !ws) return HE_EINVAL;
+    if (galois % 2 == 0 || galois >= 2 * (uint64_t)c->N) return HE_EINVAL;
+    if (level < 1 || level > c->L) return HE_ELEVEL;
+    if (!aligned(ct) || !aligned(out) || !aligned(ws) || !aligned(rk)) return HE_EINVAL;
+    if (ws_bytes < ws_bytes_for(c, level)) return HE_ENOMEM;
+    cudaStream_t st = S(stream);
+    u64 *w = (u64 *)ws;
+    prof_mark(c, st, "");
+    HE_TRY(run_automorph(c, ct, w, level, galois, st));
+    prof_mark(c, st, "automorph");
+    return run_keyswitch(c, single_job(nullptr, nullptr, out, w, level), w, level_stages(c, level, false), rk, false,
+                         st);
 }
 
 int he_rescale(he_ctx *c, const uint64_t *ct, int level, uint64_t *out, void *ws, size_t ws_bytes, void *stream)

@@ -67,7 +67,8 @@ struct Stream {
     }
 };
 
-enum { kSk = 1, kPkA = 2, kPkE = 3, kEncU = 4, kEncE0 = 5, kEncE1 = 6, kEvkA = 16, kEvkE = 48 };
+enum { kSk = 1, kPkA = 2, kPkE = 3, kEncU = 4, kEncE0 = 5, kEncE1 = 6, kEvkA = 16, kEvkE = 48,
+       kRotA = 80, kRotE = 112 };
 
 inline u64 lift(int64_t v, u64 m)
 {
@@ -159,32 +160,54 @@ void make_pk(const he_ctx *c, u64 seed, const int64_t *s, u64 *pk)
     }
 }
 
-void make_evk(const he_ctx *c, u64 seed, const int64_t *s, u64 *evk)
+// Key-switching key to s for the source key `from` (NTT domain per limb):
+// b_j = a_j s + e_j + [t in digit j] P from.  The evaluation key has
+// from = s^2 (streams kEvkA/kEvkE), a rotation key from = kappa_g(s)
+// (streams kRotA/kRotE).
+void make_switch_key(const he_ctx *c, u64 seed, const int64_t *s, const int64_t *from_small, bool square, int sa0,
+                     int se0, u64 *key)
 {
     const int N = c->N, L = c->L, K = c->K, E = c->E;
-    std::vector<u64> S(N), Er(N);
+    std::vector<u64> S(N), F(N), Er(N);
     std::vector<int64_t> err(N);
     for (int j = 0; j < c->dnum; j++) {
-        Stream sa(seed, kEvkA + j), se(seed, kEvkE + j);
+        Stream sa(seed, sa0 + j), se(seed, se0 + j);
         for (int k = 0; k < N; k++) err[k] = se.gauss(c->prm.sigma);
         const int lo = j * c->alpha, hi = std::min((j + 1) * c->alpha, L);
-        u64 *B = evk + (size_t)(2 * j) * E * N, *A = evk + (size_t)(2 * j + 1) * E * N;
+        u64 *B = key + (size_t)(2 * j) * E * N, *A = key + (size_t)(2 * j + 1) * E * N;
         for (int e = 0; e < E; e++) {
             const u64 t = c->ext[e];
             u64 *a = A + (size_t)e * N, *b = B + (size_t)e * N;
             for (int k = 0; k < N; k++) a[k] = sa.below(t);
             small_ntt(c, e, s, S.data());
             small_ntt(c, e, err.data(), Er.data());
+            if (!square) small_ntt(c, e, from_small, F.data());
             const bool gadget = e >= K && (e - K) >= lo && (e - K) < hi;
             u64 Pm = 1;
             for (int k = 0; k < K && gadget; k++) Pm = mul(Pm, c->ext[k] % t, t);
             for (int k = 0; k < N; k++) {
                 u64 v = add(mul(a[k], S[k], t), Er[k], t);
-                if (gadget) v = add(v, mul(Pm, mul(S[k], S[k], t), t), t);
+                if (gadget) v = add(v, mul(Pm, square ? mul(S[k], S[k], t) : F[k], t), t);
                 b[k] = v;
             }
         }
     }
+}
+
+// a(X) -> a(X^g) mod X^N + 1 on a small signed polynomial
+void small_automorphism(int N, const int64_t *a, u64 g, int64_t *out)
+{
+    const u64 twoN = 2 * (u64)N;
+    for (int i = 0; i < N; i++) {
+        const u64 e = (u64)i * (g % twoN) % twoN;
+        if (e < (u64)N) out[e] = a[i];
+        else out[e - N] = -a[i];
+    }
+}
+
+void make_evk(const he_ctx *c, u64 seed, const int64_t *s, u64 *evk)
+{
+    make_switch_key(c, seed, s, nullptr, true, kEvkA, kEvkE, evk);
 }
 
 // ---- canonical embedding ---------------------------------------------------
@@ -239,6 +262,26 @@ int he_keygen_from_sk(he_ctx *c, uint64_t seed, const int64_t *sk, uint64_t *pk,
     if (!c || !sk) return HE_EINVAL;
     if (pk) make_pk(c, seed, sk, pk);
     if (evk) make_evk(c, seed, sk, evk);
+    return HE_OK;
+}
+
+uint64_t he_galois_elt(const he_ctx *c, int steps)
+{
+    if (!c) return 0;
+    const u64 twoN = 2 * (u64)c->N, half = (u64)c->N / 2;
+    const u64 e = (u64)(((long long)steps % (long long)half + (long long)half) % (long long)half);
+    u64 g = 1;
+    for (u64 k = 0; k < e; k++) g = g * 5 % twoN;
+    return g;
+}
+
+int he_keygen_rot(he_ctx *c, uint64_t seed, const int64_t *sk, uint64_t galois, uint64_t *rk)
+{
+    if (!c || !sk || !rk) return HE_EINVAL;
+    if (galois % 2 == 0 || galois >= 2 * (u64)c->N) return HE_EINVAL;
+    std::vector<int64_t> ks(c->N);
+    small_automorphism(c->N, sk, galois, ks.data());
+    make_switch_key(c, seed, sk, ks.data(), false, kRotA, kRotE, rk);
     return HE_OK;
 }
 

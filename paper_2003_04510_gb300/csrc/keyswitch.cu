@@ -326,6 +326,35 @@ k_rescale_combine(const u64 *__restrict__ ct, const u64 *__restrict__ Z, u64 *__
         shoup(sub_mod(c.y, zz.y, pr.q), qv.x, qv.y, pr.q));
 }
 
+// Galois automorphism kappa_g in the NTT domain (bit-reversed evaluation
+// order): entry i holds a(psi^(2 br(i) + 1)), so kappa_g(a) at entry i is
+// a(psi^(g (2 br(i) + 1))), the entry j with 2 br(j) + 1 = g (2 br(i) + 1)
+// mod 2N -- a gather, the same for every limb.  Writes the rotation's key
+// switching inputs into the workspace: d0 = kappa(b), d1 = 0,
+// d2 = -kappa(a) mod q_i.  grid: x over N/2/kThreads, y over limbs.
+__global__ void __launch_bounds__(kThreads)
+k_automorph(const u64 *__restrict__ ct, u64 *__restrict__ ws, const DevLevel *__restrict__ lv_arr,
+            const DevPrime *__restrict__ primes, int K, int l, int N, int logN, unsigned long long g)
+{
+    const int i = blockIdx.y;
+    const DevLevel &lv = lv_arr[l];
+    const u64 q = primes[K + i].q;
+    const unsigned n = 2 * (blockIdx.x * kThreads + threadIdx.x);
+    const unsigned long long twoN = 2ull * (unsigned)N;
+    const u64 *b = ct + (size_t)i * N, *a = ct + ((size_t)l + i) * N;
+    unsigned src[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const unsigned br = __brev(n + k) >> (32 - logN);
+        const unsigned long long e = (g * (2ull * br + 1)) % twoN;
+        src[k] = __brev((unsigned)((e - 1) / 2)) >> (32 - logN);
+    }
+    const u64 a0 = a[src[0]], a1 = a[src[1]];
+    st2(ws + (size_t)lv.o_d0 * N + (size_t)i * N + n, b[src[0]], b[src[1]]);
+    st2(ws + (size_t)lv.o_d1 * N + (size_t)i * N + n, 0, 0);
+    st2(ws + (size_t)lv.o_d2 * N + (size_t)i * N + n, a0 ? q - a0 : 0, a1 ? q - a1 : 0);
+}
+
 inline dim3 grid_x(int N) { return dim3((unsigned)(N / 2 / kThreads)); }
 
 }  // namespace
@@ -336,6 +365,14 @@ cudaError_t run_tensor(const he_ctx *c, const JobRef &R, cudaStream_t st)
     g.y = R.lmax;
     g.z = R.B;
     k_tensor<<<g, kThreads, 0, st>>>(R, c->d_primes, c->d_levels, c->K, c->N);
+    return cudaGetLastError();
+}
+
+cudaError_t run_automorph(const he_ctx *c, const u64 *ct, u64 *ws, int l, u64 g, cudaStream_t st)
+{
+    dim3 grid = grid_x(c->N);
+    grid.y = l;
+    k_automorph<<<grid, kThreads, 0, st>>>(ct, ws, c->d_levels, c->d_primes, c->K, l, c->N, c->logN, g);
     return cudaGetLastError();
 }
 

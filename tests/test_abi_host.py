@@ -89,6 +89,24 @@ def test_host_keygen_matches_oracle_n15(g):
     assert np.array_equal(pk, oracle.keygen_pk(op, osk, ks))
 
 
+def test_host_rotation_keys_match_oracle_n12(g):
+    name = "n12"
+    ctx = g.Context(g.PRESETS[name][0], device=False)
+    op = oracle.preset(name)
+    sk = oracle.keygen_sk(op, si.SEEDS[name][0])
+    for steps in (1, -1, 7, op.N // 2 + 3):
+        gl = g.he_galois_elt(ctx, steps)
+        assert gl == oracle.galois_elt(op, steps)
+        assert np.array_equal(g.he_keygen_rot(ctx, 77, sk, gl), oracle.keygen_rot(op, sk, gl, 77))
+    gc = g.he_conj_elt(ctx)
+    assert gc == oracle.conj_elt(op)
+    assert np.array_equal(g.he_keygen_rot(ctx, 78, sk, gc), oracle.keygen_rot(op, sk, gc, 78))
+    for bad in (0, 2, 2 * op.N, 2 * op.N + 1):
+        with pytest.raises(g.HeError) as e:
+            g.he_keygen_rot(ctx, 1, sk, bad)
+        assert e.value.code == g.HE_EINVAL
+
+
 def test_argument_errors_are_status_codes(g):
     bad = g.Params(11, 3, 1, 1, 50, 51, 64)  # logN below range
     with pytest.raises(g.HeError) as e:

@@ -379,3 +379,67 @@ def test_device_argument_errors(g):
     rc = g.lib().he_mul(ctx.ptr, mis.data_ptr(), a.data_ptr(), a.data_ptr(), 3, out.data_ptr(), ws.data_ptr(),
                         ws.numel() * 8, None)
     assert rc == g.HE_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# rotation (Galois automorphism + key switching with a rotation key)
+# ---------------------------------------------------------------------------
+def gpu_rotate(g, ctx, ct, rk_t, level, gal):
+    import torch
+    out = torch.empty((2, level, ctx.N), dtype=torch.int64, device="cuda")
+    g.he_rotate(ctx, dev(g, ct), rk_t, level, gal, out, g.workspace(ctx, level))
+    torch.cuda.synchronize()
+    return host(g, out)
+
+
+def test_rotate_n12_every_level_and_conjugate(g):
+    op, sc, sk, pk, evk, m1, m2, ct1, ct2 = real_inputs("n12")
+    ctx = ctx_for(g, "n12")
+    for steps in (1, -1, 5):
+        gal = oracle.galois_elt(op, steps)
+        rk = oracle.keygen_rot(op, sk, gal, 900 + steps % 50)
+        rk_t = dev(g, rk)
+        for level in (3, 2, 1):
+            c = np.ascontiguousarray(np.stack([ct1[0, :level], ct1[1, :level]]))
+            assert np.array_equal(gpu_rotate(g, ctx, c, rk_t, level, gal), oracle.rotate(op, c, gal, rk, level)), \
+                (steps, level)
+        z = oracle.decrypt(op, sk, gpu_rotate(g, ctx, ct1, rk_t, op.L, gal), op.L, sc)
+        assert np.abs(z - np.roll(m1, -steps)).max() < 2.0 ** -16
+    gal = oracle.conj_elt(op)
+    rk = oracle.keygen_rot(op, sk, gal, 950)
+    got = gpu_rotate(g, ctx, ct2, dev(g, rk), op.L, gal)
+    assert np.array_equal(got, oracle.rotate(op, ct2, gal, rk, op.L))
+    assert np.abs(oracle.decrypt(op, sk, got, op.L, sc) - np.conj(m2)).max() < 2.0 ** -16
+
+
+@pytest.mark.parametrize("level", [24, 13])
+def test_rotate_n16_real_keys(g, level):
+    op, sc, sk, pk, evk, m1, m2, ct1, ct2 = real_inputs("n16")
+    ctx = ctx_for(g, "n16")
+    gal = oracle.galois_elt(op, 3)
+    rk = oracle.keygen_rot(op, sk, gal, 1611)
+    c = np.ascontiguousarray(np.stack([ct1[0, :level], ct1[1, :level]]))
+    got = gpu_rotate(g, ctx, c, dev(g, rk), level, gal)
+    assert np.array_equal(got, oracle.rotate(op, c, gal, rk, level))
+    z = oracle.decrypt(op, sk, got, level, sc)
+    assert np.abs(z - np.roll(m1, -3)).max() < 2.0 ** -24
+
+
+def test_rotate_argument_errors(g):
+    import torch
+    ctx = ctx_for(g, "n12")
+    N = ctx.N
+    a = torch.zeros((2, 3, N), dtype=torch.int64, device="cuda")
+    out = torch.zeros((2, 3, N), dtype=torch.int64, device="cuda")
+    rk = torch.zeros((ctx.dnum, 2, ctx.prm.K + ctx.prm.L, N), dtype=torch.int64, device="cuda")
+    ws = g.workspace(ctx, 3)
+    for bad_g, code in ((2, g.HE_EINVAL), (2 * N + 1, g.HE_EINVAL)):
+        with pytest.raises(g.HeError) as e:
+            g.he_rotate(ctx, a, rk, 3, bad_g, out, ws)
+        assert e.value.code == code
+    with pytest.raises(g.HeError) as e:
+        g.he_rotate(ctx, a, rk, 4, 5, out, ws)
+    assert e.value.code == g.HE_ELEVEL
+    with pytest.raises(g.HeError) as e:
+        g.he_rotate(ctx, a, rk, 3, 5, out, ws[: ws.numel() // 2])
+    assert e.value.code == g.HE_ENOMEM
