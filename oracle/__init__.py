@@ -84,6 +84,11 @@ def lib():
             "or_automorphism": (None, [P, i32, u64, u64, P]),
             "or_keygen_rot": (None, [i32, i32, i32, i32, P, P, P, P, dbl, P, u64, u64, P]),
             "or_rotate": (None, [i32, i32, i32, i32, i32, P, P, P, P, P, u64, P, P]),
+            "or_add": (None, [i32, i32, P, P, P, P]),
+            "or_sub": (None, [i32, i32, P, P, P, P]),
+            "or_plain_ntt": (None, [i32, i32, P, P, P, P]),
+            "or_mul_plain": (None, [i32, i32, P, P, P, P]),
+            "or_add_plain": (None, [i32, i32, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -316,6 +321,40 @@ def rotate(prm: Params, ct, g: int, rk, level: int) -> np.ndarray:
     out = np.zeros((2, level, prm.N), dtype=np.uint64)
     lib().or_rotate(prm.logN, level, prm.L, prm.K, prm.alpha, _p(prm.q), _p(prm.psi_q), _p(prm.p),
                     _p(prm.psi_p), _p(_u64(ct)), g, _p(_u64(rk)), _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# HE Add / Sub (Sec. 3.2) and plaintext operations (NEXT-4).
+# --------------------------------------------------------------------------
+def add(prm: Params, ct1, ct2, level: int) -> np.ndarray:
+    out = np.zeros((2, level, prm.N), dtype=np.uint64)
+    lib().or_add(prm.logN, level, _p(prm.q), _p(_u64(ct1)), _p(_u64(ct2)), _p(out))
+    return out
+
+
+def sub(prm: Params, ct1, ct2, level: int) -> np.ndarray:
+    out = np.zeros((2, level, prm.N), dtype=np.uint64)
+    lib().or_sub(prm.logN, level, _p(prm.q), _p(_u64(ct1)), _p(_u64(ct2)), _p(out))
+    return out
+
+
+def plain_ntt(prm: Params, coeffs, level: int) -> np.ndarray:
+    pt = np.zeros((level, prm.N), dtype=np.uint64)
+    lib().or_plain_ntt(prm.logN, level, _p(prm.q), _p(prm.psi_q), _p(np.ascontiguousarray(coeffs, dtype=np.int64)),
+                       _p(pt))
+    return pt
+
+
+def mul_plain(prm: Params, ct, pt, level: int) -> np.ndarray:
+    out = np.zeros((2, level, prm.N), dtype=np.uint64)
+    lib().or_mul_plain(prm.logN, level, _p(prm.q), _p(_u64(ct)), _p(_u64(pt)), _p(out))
+    return out
+
+
+def add_plain(prm: Params, ct, pt, level: int) -> np.ndarray:
+    out = np.zeros((2, level, prm.N), dtype=np.uint64)
+    lib().or_add_plain(prm.logN, level, _p(prm.q), _p(_u64(ct)), _p(_u64(pt)), _p(out))
     return out
 
 

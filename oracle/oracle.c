@@ -796,3 +796,72 @@ void or_rotate(int logN, int l, int L, int K, int alpha, const uint64_t *q, cons
         }
     free(kc); free(tmp); free(ks);
 }
+
+/* ---------------------------------------------------------------------------
+ * HE Add (Sec. 3.2, "HEAAN computation"): c3.ax = mod(c1.ax + c2.ax, q),
+ * c3.bx = mod(c1.bx + c2.bx, q), element-wise per limb.  The difference is
+ * the same with a subtraction.  ct1, ct2, out: [2][l][N].
+ * ------------------------------------------------------------------------- */
+void or_add(int logN, int l, const uint64_t *q, const uint64_t *ct1, const uint64_t *ct2, uint64_t *out)
+{
+    uint64_t N = 1ull << logN;
+    for (int h = 0; h < 2; h++)
+        for (int i = 0; i < l; i++)
+            for (uint64_t n = 0; n < N; n++) {
+                size_t o = ((size_t)h * l + i) * N + n;
+                out[o] = addmod(ct1[o], ct2[o], q[i]);
+            }
+}
+
+void or_sub(int logN, int l, const uint64_t *q, const uint64_t *ct1, const uint64_t *ct2, uint64_t *out)
+{
+    uint64_t N = 1ull << logN;
+    for (int h = 0; h < 2; h++)
+        for (int i = 0; i < l; i++)
+            for (uint64_t n = 0; n < N; n++) {
+                size_t o = ((size_t)h * l + i) * N + n;
+                out[o] = submod(ct1[o], ct2[o], q[i]);
+            }
+}
+
+/* ---------------------------------------------------------------------------
+ * Plaintext operations.  A plaintext at level l is the integer polynomial of
+ * the encoder (Sec. 3.1) reduced mod each q_i and transformed by Algo 3:
+ * pt [l][N] NTT domain.  Multiplying a ciphertext by it multiplies both
+ * halves (b - a s becomes (b - a s) pt, so the message is multiplied and the
+ * scale is the product of the scales); adding it adds to the b half only.
+ * ------------------------------------------------------------------------- */
+void or_plain_ntt(int logN, int l, const uint64_t *q, const uint64_t *psi_q, const int64_t *coeffs, uint64_t *pt)
+{
+    uint64_t N = 1ull << logN;
+    for (int i = 0; i < l; i++) {
+        uint64_t *o = pt + (size_t)i * N;
+        for (uint64_t n = 0; n < N; n++) {
+            int64_t c = coeffs[n];
+            o[n] = c >= 0 ? (uint64_t)c % q[i] : submod(0, (uint64_t)(-(c + 1)) + 1, q[i]);
+        }
+        or_ntt(o, logN, q[i], psi_q[i]);
+    }
+}
+
+void or_mul_plain(int logN, int l, const uint64_t *q, const uint64_t *ct, const uint64_t *pt, uint64_t *out)
+{
+    uint64_t N = 1ull << logN;
+    for (int h = 0; h < 2; h++)
+        for (int i = 0; i < l; i++)
+            for (uint64_t n = 0; n < N; n++) {
+                size_t o = ((size_t)h * l + i) * N + n;
+                out[o] = mulmod(ct[o], pt[(size_t)i * N + n], q[i]);
+            }
+}
+
+void or_add_plain(int logN, int l, const uint64_t *q, const uint64_t *ct, const uint64_t *pt, uint64_t *out)
+{
+    uint64_t N = 1ull << logN;
+    for (int i = 0; i < l; i++)
+        for (uint64_t n = 0; n < N; n++) {
+            size_t o = (size_t)i * N + n;
+            out[o] = addmod(ct[o], pt[o], q[i]);
+            out[(size_t)l * N + o] = ct[(size_t)l * N + o];
+        }
+}
