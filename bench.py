@@ -479,6 +479,31 @@ def run_ours(args):
                "decrypt_max_err": rot_err}
         del rk_t
 
+    # ---- a multiplication chain down the levels (HE Mul + rescale at every level) ----
+    chain = None
+    if not args.no_rotate and level > 2:
+        outs_c = [torch.empty((2, l - 1, N), dtype=torch.int64, device=dev) for l in range(level, 1, -1)]
+
+        def run_chain():
+            cur = ct_t[0][0]
+            for k, l in enumerate(range(level, 1, -1)):
+                g.he_mul_rescale(ctx, cur, cur, evk_t, l, outs_c[k], ws, stream)
+                cur = outs_c[k]
+
+        for _ in range(3):
+            run_chain()
+        torch.cuda.synchronize()
+        creps = 20
+        c0, c1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(creps):
+            run_chain()
+        c1e.record(stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1e) / creps
+        chain = {"levels": f"{level}->1", "he_muls": level - 1, "ms_per_chain": cms,
+                 "HE_Mul_per_s": (level - 1) / (cms * 1e-3), "reps": creps}
+
     # ALU ceiling: register-resident butterfly probe
     bfly_peak = g.he_probe_butterfly_rate(152 * 8, 4096, stream)
     probe = {"butterfly_per_s": bfly_peak}
@@ -554,6 +579,7 @@ def run_ours(args):
             "probe": probe,
             "kernels": per_kernel,
             "rotate": rot,
+            "chain": chain,
             "batched": batched,
             "serving": serving,
             "cpu_baseline": cpu,

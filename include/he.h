@@ -291,6 +291,25 @@ int he_server_stats(he_server *s, he_server_report *stats);
  * that were never launched are dropped. */
 int he_server_destroy(he_server *s);
 
+/* ---- HE Add and plaintext operations --------------------------------------- */
+
+/* HE Add (Sec. 3.2): out.b = c1.b + c2.b, out.a = c1.a + c2.a mod q_i, element
+ * by element with one conditional subtraction.  he_sub: the difference (no
+ * paper counterpart; same shape).  ct1, ct2, out: [2][level][N] device, same
+ * level and scale; out may alias an input.  HE_ELEVEL for level outside 1..L. */
+int he_add(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, int level, uint64_t *out, void *stream);
+int he_sub(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, int level, uint64_t *out, void *stream);
+/* A plaintext at `level` in the NTT domain (host): the integer polynomial
+ * `coeffs` (int64[N], e.g. from he_encode) reduced mod q_0..q_{level-1} and
+ * transformed by Algo 3; pt: [level][N]. */
+int he_plain_ntt(he_ctx *ctx, const int64_t *coeffs, int level, uint64_t *pt);
+/* Plaintext product (both halves times pt, element-wise in the NTT domain;
+ * the message is multiplied, scales multiply: rescale afterwards) and
+ * plaintext sum (pt added to the b half).  ct, out: [2][level][N], pt:
+ * [level][N], device; out may alias ct. */
+int he_mul_plain(he_ctx *ctx, const uint64_t *ct, const uint64_t *pt, int level, uint64_t *out, void *stream);
+int he_add_plain(he_ctx *ctx, const uint64_t *ct, const uint64_t *pt, int level, uint64_t *out, void *stream);
+
 /* ---- rotation ---------------------------------------------------------------
  * HE rotation is not in the paper; it is the next operation built on the
  * paper's key switching (Fig. 2, region 2), reusing every kernel of it.

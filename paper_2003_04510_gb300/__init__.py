@@ -120,6 +120,15 @@ _SIGS = {
     "he_batch_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "he_probe_butterfly_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "he_galois_elt": (ctypes.c_uint64, [ctypes.c_void_p, ctypes.c_int]),
+    "he_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                              ctypes.c_void_p]),
+    "he_sub": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                              ctypes.c_void_p]),
+    "he_plain_ntt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "he_mul_plain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
+    "he_add_plain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
     "he_keygen_rot": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
                                      ctypes.c_void_p]),
     "he_rotate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
@@ -329,6 +338,31 @@ def he_mul_rescale_static(ctx, ct1, ct2, evk, level, out, stream=None):
     """he_mul_rescale with the library's fixed device scratch as workspace (no allocation)."""
     _check(lib().he_mul_rescale_static(ctx.ptr, _dev_ptr(ct1), _dev_ptr(ct2), _dev_ptr(evk), level, _dev_ptr(out),
                                        _stream_ptr(stream)), "he_mul_rescale_static")
+
+
+def he_add(ctx, ct1, ct2, level, out, stream=None):
+    _check(lib().he_add(ctx.ptr, _dev_ptr(ct1), _dev_ptr(ct2), level, _dev_ptr(out), _stream_ptr(stream)), "he_add")
+
+
+def he_sub(ctx, ct1, ct2, level, out, stream=None):
+    _check(lib().he_sub(ctx.ptr, _dev_ptr(ct1), _dev_ptr(ct2), level, _dev_ptr(out), _stream_ptr(stream)), "he_sub")
+
+
+def he_plain_ntt(ctx, coeffs: np.ndarray, level: int) -> np.ndarray:
+    pt = np.zeros((level, ctx.N), dtype=np.uint64)
+    _check(lib().he_plain_ntt(ctx.ptr, _np_ptr(np.ascontiguousarray(coeffs, dtype=np.int64)), level, _np_ptr(pt)),
+           "he_plain_ntt")
+    return pt
+
+
+def he_mul_plain(ctx, ct, pt, level, out, stream=None):
+    _check(lib().he_mul_plain(ctx.ptr, _dev_ptr(ct), _dev_ptr(pt), level, _dev_ptr(out), _stream_ptr(stream)),
+           "he_mul_plain")
+
+
+def he_add_plain(ctx, ct, pt, level, out, stream=None):
+    _check(lib().he_add_plain(ctx.ptr, _dev_ptr(ct), _dev_ptr(pt), level, _dev_ptr(out), _stream_ptr(stream)),
+           "he_add_plain")
 
 
 def he_galois_elt(ctx, steps: int) -> int:

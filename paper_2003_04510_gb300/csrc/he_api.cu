@@ -257,6 +257,37 @@ int he_mul_rescale(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, const ui
     return hemul_pipeline(c, ct1, ct2, evk, level, out, (u64 *)ws, true, S(stream));
 }
 
+namespace {
+int elementwise(he_ctx *c, int op, const uint64_t *x, const uint64_t *y, int level, uint64_t *out, void *stream)
+{
+    if (check_dev(c) || !x || !y || !out) return HE_EINVAL;
+    if (level < 1 || level > c->L) return HE_ELEVEL;
+    if (!aligned(x) || !aligned(y) || !aligned(out)) return HE_EINVAL;
+    HE_TRY(run_elementwise(c, op, x, y, out, level, S(stream)));
+    return HE_OK;
+}
+}  // namespace
+
+int he_add(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, int level, uint64_t *out, void *stream)
+{
+    return elementwise(c, 0, ct1, ct2, level, out, stream);
+}
+
+int he_sub(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, int level, uint64_t *out, void *stream)
+{
+    return elementwise(c, 1, ct1, ct2, level, out, stream);
+}
+
+int he_mul_plain(he_ctx *c, const uint64_t *ct, const uint64_t *pt, int level, uint64_t *out, void *stream)
+{
+    return elementwise(c, 2, ct, pt, level, out, stream);
+}
+
+int he_add_plain(he_ctx *c, const uint64_t *ct, const uint64_t *pt, int level, uint64_t *out, void *stream)
+{
+    return elementwise(c, 3, ct, pt, level, out, stream);
+}
+
 int he_rotate(he_ctx *c, const uint64_t *ct, const uint64_t *rk, int level, uint64_t galois, uint64_t *out, void *ws,
               size_t ws_bytes, void *stream)
 {

@@ -154,6 +154,8 @@ cudaError_t configure_ntt(const he_ctx *ctx);
 int ntt_direct_stages(int logN);
 cudaError_t run_tensor(const he_ctx *c, const JobRef &R, cudaStream_t st);
 cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st);
+// Element-wise ops: 0 add, 1 sub, 2 times plaintext, 3 plus plaintext (b half).
+cudaError_t run_elementwise(const he_ctx *c, int op, const u64 *x, const u64 *y, u64 *out, int l, cudaStream_t st);
 // Rotation's first step: d0 = kappa_g(b), d1 = 0, d2 = -kappa_g(a) into ws (level l).
 cudaError_t run_automorph(const he_ctx *c, const u64 *ct, u64 *ws, int l, u64 g, cudaStream_t st);
 cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st);

@@ -73,7 +73,7 @@ enum { kSk = 1, kPkA = 2, kPkE = 3, kEncU = 4, kEncE0 = 5, kEncE1 = 6, kEvkA = 1
 inline u64 lift(int64_t v, u64 m)
 {
     if (v >= 0) return (u64)v % m;
-    u64 r = (u64)(-v) % m;
+    u64 r = (0ull - (u64)v) % m;  // |v|, also for INT64_MIN
     return r ? m - r : 0;
 }
 
@@ -262,6 +262,19 @@ int he_keygen_from_sk(he_ctx *c, uint64_t seed, const int64_t *sk, uint64_t *pk,
     if (!c || !sk) return HE_EINVAL;
     if (pk) make_pk(c, seed, sk, pk);
     if (evk) make_evk(c, seed, sk, evk);
+    return HE_OK;
+}
+
+int he_plain_ntt(he_ctx *c, const int64_t *coeffs, int level, uint64_t *pt)
+{
+    if (!c || !coeffs || !pt) return HE_EINVAL;
+    if (level < 1 || level > c->L) return HE_ELEVEL;
+    for (int i = 0; i < level; i++) {
+        u64 *o = pt + (size_t)i * c->N;
+        const u64 q = c->ext[c->K + i];
+        for (int k = 0; k < c->N; k++) o[k] = lift(coeffs[k], q);
+        host_ntt(c, c->K + i, o);
+    }
     return HE_OK;
 }
 

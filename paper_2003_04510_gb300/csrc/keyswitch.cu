@@ -355,6 +355,42 @@ k_automorph(const u64 *__restrict__ ct, u64 *__restrict__ ws, const DevLevel *__
     st2(ws + (size_t)lv.o_d2 * N + (size_t)i * N + n, a0 ? q - a0 : 0, a1 ? q - a1 : 0);
 }
 
+// Element-wise ciphertext operations (HE Add of Sec. 3.2 and its relatives).
+// OP 0: out = x + y (both halves); 1: out = x - y; 2: out = x * pt (both
+// halves, pt [l][N]); 3: out.b = x.b + pt, out.a = x.a.  x, y, out:
+// [2][l][N]; out may alias an input (each word is read, then written, by
+// one thread).  grid: x over N/2/kThreads, y over limbs, z over the halves.
+template <int OP>
+__global__ void __launch_bounds__(kThreads)
+k_elementwise(const u64 *x, const u64 *y, u64 *out, const DevPrime *__restrict__ primes, int K, int l, int N)
+{
+    const int i = blockIdx.y, h = blockIdx.z;
+    const DevPrime pr = primes[K + i];
+    const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
+    const size_t o = ((size_t)h * l + i) * N + n;
+    const ulonglong2 a = ld2(x + o);
+    u64 r0, r1;
+    if (OP == 0 || OP == 1) {
+        const ulonglong2 b = ld2(y + o);
+        r0 = OP == 0 ? add_mod(a.x, b.x, pr.q) : sub_mod(a.x, b.x, pr.q);
+        r1 = OP == 0 ? add_mod(a.y, b.y, pr.q) : sub_mod(a.y, b.y, pr.q);
+    } else if (OP == 2) {
+        const ulonglong2 b = ld2(y + (size_t)i * N + n);
+        r0 = mul_mod(a.x, b.x, pr.q, pr.mu, pr.s);
+        r1 = mul_mod(a.y, b.y, pr.q, pr.mu, pr.s);
+    } else {
+        if (h == 0) {
+            const ulonglong2 b = ld2(y + (size_t)i * N + n);
+            r0 = add_mod(a.x, b.x, pr.q);
+            r1 = add_mod(a.y, b.y, pr.q);
+        } else {
+            r0 = a.x;
+            r1 = a.y;
+        }
+    }
+    st2(out + o, r0, r1);
+}
+
 inline dim3 grid_x(int N) { return dim3((unsigned)(N / 2 / kThreads)); }
 
 }  // namespace
@@ -365,6 +401,20 @@ cudaError_t run_tensor(const he_ctx *c, const JobRef &R, cudaStream_t st)
     g.y = R.lmax;
     g.z = R.B;
     k_tensor<<<g, kThreads, 0, st>>>(R, c->d_primes, c->d_levels, c->K, c->N);
+    return cudaGetLastError();
+}
+
+cudaError_t run_elementwise(const he_ctx *c, int op, const u64 *x, const u64 *y, u64 *out, int l, cudaStream_t st)
+{
+    dim3 grid = grid_x(c->N);
+    grid.y = l;
+    grid.z = 2;
+    switch (op) {
+    case 0: k_elementwise<0><<<grid, kThreads, 0, st>>>(x, y, out, c->d_primes, c->K, l, c->N); break;
+    case 1: k_elementwise<1><<<grid, kThreads, 0, st>>>(x, y, out, c->d_primes, c->K, l, c->N); break;
+    case 2: k_elementwise<2><<<grid, kThreads, 0, st>>>(x, y, out, c->d_primes, c->K, l, c->N); break;
+    default: k_elementwise<3><<<grid, kThreads, 0, st>>>(x, y, out, c->d_primes, c->K, l, c->N); break;
+    }
     return cudaGetLastError();
 }
 

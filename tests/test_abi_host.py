@@ -107,6 +107,18 @@ def test_host_rotation_keys_match_oracle_n12(g):
         assert e.value.code == g.HE_EINVAL
 
 
+def test_host_plaintext_ntt_matches_oracle(g):
+    for name in ("n12", "n16"):
+        ctx = g.Context(g.PRESETS[name][0], device=False)
+        op = oracle.preset(name)
+        rng = np.random.default_rng(5)
+        t = rng.integers(-(1 << 62), 1 << 62, size=op.N, dtype=np.int64)
+        t[0] = np.iinfo(np.int64).min
+        t[1] = np.iinfo(np.int64).max
+        for level in (op.L, 1):
+            assert np.array_equal(g.he_plain_ntt(ctx, t, level), oracle.plain_ntt(op, t, level))
+
+
 def test_argument_errors_are_status_codes(g):
     bad = g.Params(11, 3, 1, 1, 50, 51, 64)  # logN below range
     with pytest.raises(g.HeError) as e:

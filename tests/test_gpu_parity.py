@@ -443,3 +443,89 @@ def test_rotate_argument_errors(g):
     with pytest.raises(g.HeError) as e:
         g.he_rotate(ctx, a, rk, 3, 5, out, ws[: ws.numel() // 2])
     assert e.value.code == g.HE_ENOMEM
+
+
+# ---------------------------------------------------------------------------
+# HE Add / Sub, plaintext ops, and a multiplication chain down the levels
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,level", [("n12", 3), ("n16", 24), ("n16", 7)])
+def test_add_sub_plain_ops(g, name, level):
+    import torch
+    ctx = ctx_for(g, name)
+    op = oracle.preset(name)
+    c1, c2 = rand_ct(op, level, 301), rand_ct(op, level, 303)
+    c1[:, :, :3] = np.array([int(q) - 1 for q in op.q[:level]], dtype=np.uint64)[None, :, None]
+    c2[:, :, :3] = np.array([int(q) - 1 for q in op.q[:level]], dtype=np.uint64)[None, :, None]
+    rng = np.random.default_rng(level)
+    t = rng.integers(-(1 << 60), 1 << 60, size=op.N, dtype=np.int64)
+    pt = oracle.plain_ntt(op, t, level)
+    a, b, p = dev(g, c1), dev(g, c2), dev(g, pt)
+    out = torch.empty_like(a)
+    cases = [(g.he_add, b, oracle.add(op, c1, c2, level)), (g.he_sub, b, oracle.sub(op, c1, c2, level)),
+             (g.he_mul_plain, p, oracle.mul_plain(op, c1, pt, level)),
+             (g.he_add_plain, p, oracle.add_plain(op, c1, pt, level))]
+    for fn, y, want in cases:
+        fn(ctx, a, y, level, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(g, out), want), fn.__name__
+    # in place (out aliases the first operand)
+    a2 = a.clone()
+    g.he_add(ctx, a2, b, level, a2)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(g, a2), oracle.add(op, c1, c2, level))
+
+
+def test_squaring_chain_n12_decrypts(g):
+    """Scale q_{L-1}; HE Mul + rescale at every level down to level 1, bit-exact
+    to the oracle at each level and decrypting to m^(2^k)."""
+    import torch
+    op, sc, sk, pk, evk, m1, m2, ct1, ct2 = real_inputs("n12")
+    ctx = ctx_for(g, "n12")
+    evk_t = dev(g, evk)
+    m = 0.5 * m1
+    L = op.L
+    scale = float(int(op.q[L - 1]))
+    ct = oracle.encrypt_poly(op, pk, encode(m, op.logN, scale), L, 1211)
+    cur = dev(g, ct)
+    want_ct, want = ct, m
+    for l in range(L, 1, -1):
+        nxt = torch.empty((2, l - 1, op.N), dtype=torch.int64, device="cuda")
+        g.he_mul_rescale(ctx, cur, cur, evk_t, l, nxt, g.workspace(ctx, l))
+        torch.cuda.synchronize()
+        want_ct = oracle.rescale(op, oracle.he_mul(op, want_ct, want_ct, evk, l), l)
+        got = host(g, nxt)
+        assert np.array_equal(got, want_ct), l
+        scale = scale * scale / int(op.q[l - 1])
+        want = want * want
+        assert np.abs(oracle.decrypt(op, sk, got, l - 1, scale) - want).max() < 2.0 ** -12
+        cur = nxt
+
+
+@pytest.mark.slow
+def test_squaring_chain_n15_all_levels(g):
+    """N=2^15, 16 levels: 15 HE Mul + rescale steps, bit-exact at every level."""
+    import torch
+    name = "n15"
+    ctx = ctx_for(g, name)
+    op = oracle.preset(name)
+    ks = si.SEEDS[name][0]
+    sk = oracle.keygen_sk(op, ks)
+    pk = oracle.keygen_pk(op, sk, ks)
+    evk = oracle.keygen_evk(op, sk, ks)
+    m = 0.5 * si.messages(op.N // 2, 1512)
+    L = op.L
+    scale = float(int(op.q[L - 1]))
+    want_ct = oracle.encrypt_poly(op, pk, encode(m, op.logN, scale), L, 1513)
+    cur, evk_t = dev(g, want_ct), dev(g, evk)
+    want = m
+    for l in range(L, 1, -1):
+        nxt = torch.empty((2, l - 1, op.N), dtype=torch.int64, device="cuda")
+        g.he_mul_rescale(ctx, cur, cur, evk_t, l, nxt, g.workspace(ctx, l))
+        torch.cuda.synchronize()
+        want_ct = oracle.rescale(op, oracle.he_mul(op, want_ct, want_ct, evk, l), l)
+        assert np.array_equal(host(g, nxt), want_ct), l
+        scale = scale * scale / int(op.q[l - 1])
+        want = want * want
+        cur = nxt
+    z = oracle.decrypt(op, sk, host(g, cur), 1, scale)
+    assert np.abs(z - want).max() < 2.0 ** -20
