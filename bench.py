@@ -283,6 +283,9 @@ def run_batched(g, ctx, evk_t, dev, stream, wsz, count=64, reps=20):
         jobs.append((g.to_device(a, dev), g.to_device(b, dev), out, lv))
     wsb = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device=dev)
     ws1 = g.workspace(ctx, max(levels), device=dev)
+    # launch shapes picked by the library's autotuner on this very batch
+    shape_before = g.he_get_shape(ctx)
+    best, tried = g.he_autotune(ctx, jobs, evk_t, wsb, reps=3, stream=stream)
 
     def batch():
         g.he_mul_batch(ctx, jobs, evk_t, wsb, stream)
@@ -316,6 +319,9 @@ def run_batched(g, ctx, evk_t, dev, stream, wsz, count=64, reps=20):
                      "batch_latency_ms_p50": float(np.percentile(lat, 50)),
                      "batch_latency_ms_p99": float(np.percentile(lat, 99))}
     graph.close()
+    g.he_set_shape(ctx, *shape_before)
+    res["autotune"] = {"group_cap": best[0], "modup_chunk": best[1], "ms_per_batch": best[2],
+                       "tried": [{"group_cap": t[0], "modup_chunk": t[1], "ms": t[2]} for t in tried]}
     res["config"] = {"jobs": count, "N": N, "levels": "uniform 4..24 (seed 1604)", "mean_level": float(np.mean(levels)),
                      "operands": "uniform residues"}
     return res
@@ -407,6 +413,9 @@ def run_ours(args):
         a, b = ct_t[k % NPAIRS]
         g.he_mul_rescale(ctx, a, b, evk_t, level, outs[k % NPAIRS], ws, stream)
 
+    # launch shapes picked by the library's autotuner for this single HE Mul
+    tune_best, tune_tried = g.he_autotune(ctx, [(ct_t[0][0], ct_t[0][1], outs[0], level)], evk_t, ws, reps=20,
+                                          stream=stream)
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
@@ -608,6 +617,8 @@ def run_ours(args):
             "inner_product_hbm": ip,
             "probe": probe,
             "kernels": per_kernel,
+            "autotune": {"group_cap": tune_best[0], "modup_chunk": tune_best[1], "ms": tune_best[2],
+                         "tried": [{"group_cap": t[0], "modup_chunk": t[1], "ms": t[2]} for t in tune_tried]},
             "rotate": rot,
             "chain": chain,
             "batched": batched,

@@ -335,6 +335,30 @@ int he_keygen_rot(he_ctx *ctx, uint64_t seed, const int64_t *sk, uint64_t galois
 int he_rotate(he_ctx *ctx, const uint64_t *ct, const uint64_t *rk_dev, int level, uint64_t galois, uint64_t *out,
               void *ws, size_t ws_bytes, void *stream);
 
+/* ---- launch shapes and autotuning (no paper counterpart) ------------------ */
+
+/* Launch shape of the path: NTT limbs that share a CTA (they share the
+ * staged twiddles; 1..4) and ModUp targets per CTA (4, 8 or 16).  Speed only:
+ * every shape gives bit-identical results.  Default {4, 8}.  A batch graph
+ * keeps the ModUp shape it was captured with. */
+typedef struct {
+    int group_cap;
+    int modup_chunk;
+    double ms; /* he_autotune: measured milliseconds per call; else 0 */
+} he_shape;
+
+/* HE_EINVAL for a NULL context or an unsupported value. */
+int he_set_shape(he_ctx *ctx, const he_shape *shape);
+int he_get_shape(const he_ctx *ctx, he_shape *shape);
+/* Time every shape on the caller's own work and keep the fastest in ctx:
+ * count == 1 times he_mul_rescale on jobs[0] (ws of he_workspace_bytes),
+ * count > 1 times he_mul_batch on the jobs (ws of he_batch_workspace_bytes),
+ * `reps` calls per shape after one warm-up call, CUDA events on `stream`.
+ * The jobs' outputs are overwritten.  best: the shape kept; tried (optional,
+ * max_tried entries): every shape with its time, *n_tried set. */
+int he_autotune(he_ctx *ctx, const he_job *jobs, int count, const uint64_t *evk_dev, void *ws, size_t ws_bytes,
+                int reps, void *stream, he_shape *best, he_shape *tried, int max_tried, int *n_tried);
+
 /* ---- profiling ------------------------------------------------------------ */
 
 /* Enable (1) or disable (0) per-kernel CUDA-event marks on this context's

@@ -120,6 +120,11 @@ _SIGS = {
     "he_batch_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "he_probe_butterfly_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "he_galois_elt": (ctypes.c_uint64, [ctypes.c_void_p, ctypes.c_int]),
+    "he_set_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "he_get_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "he_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_int, ctypes.c_void_p]),
     "he_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                               ctypes.c_void_p]),
     "he_sub": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
@@ -363,6 +368,36 @@ def he_mul_plain(ctx, ct, pt, level, out, stream=None):
 def he_add_plain(ctx, ct, pt, level, out, stream=None):
     _check(lib().he_add_plain(ctx.ptr, _dev_ptr(ct), _dev_ptr(pt), level, _dev_ptr(out), _stream_ptr(stream)),
            "he_add_plain")
+
+
+class he_shape(ctypes.Structure):
+    _fields_ = [("group_cap", ctypes.c_int), ("modup_chunk", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
+def he_set_shape(ctx, group_cap: int, modup_chunk: int):
+    sh = he_shape(group_cap, modup_chunk, 0.0)
+    _check(lib().he_set_shape(ctx.ptr, ctypes.byref(sh)), "he_set_shape")
+
+
+def he_get_shape(ctx) -> tuple[int, int]:
+    sh = he_shape()
+    _check(lib().he_get_shape(ctx.ptr, ctypes.byref(sh)), "he_get_shape")
+    return sh.group_cap, sh.modup_chunk
+
+
+def he_autotune(ctx, jobs, evk, ws, reps: int = 3, stream=None):
+    """jobs: list of (ct1, ct2, out, level) device tensors (one job: the single
+    path).  Returns (best (cap, chunk, ms), [(cap, chunk, ms) tried])."""
+    arr = (he_job * len(jobs))()
+    for i, (a, b, o, lv) in enumerate(jobs):
+        arr[i] = he_job(_dev_ptr(a), _dev_ptr(b), _dev_ptr(o), int(lv))
+    best = he_shape()
+    tried = (he_shape * 16)()
+    n = ctypes.c_int()
+    _check(lib().he_autotune(ctx.ptr, ctypes.cast(arr, ctypes.c_void_p), len(jobs), _dev_ptr(evk), _dev_ptr(ws),
+                             ws.numel() * 8, reps, _stream_ptr(stream), ctypes.byref(best),
+                             ctypes.cast(tried, ctypes.c_void_p), 16, ctypes.byref(n)), "he_autotune")
+    return (best.group_cap, best.modup_chunk, best.ms), [(t.group_cap, t.modup_chunk, t.ms) for t in tried[: n.value]]
 
 
 def he_galois_elt(ctx, steps: int) -> int:

@@ -470,7 +470,9 @@ int he_mul_batch(he_ctx *c, int count, const he_job *jobs, const uint64_t *evk, 
     }
     if (off * N >= ((size_t)1 << 32) * N) return HE_EINVAL;  // offsets are 32-bit limb counts
     // regroup by prime across jobs: limbs of different jobs share a twiddle tile
-    std::vector<NttGroup> g1 = group_jobs(l1), g2 = group_jobs(l2), g3 = group_jobs(l3), g4 = group_jobs(l4);
+    const int cap = c->group_cap;
+    std::vector<NttGroup> g1 = group_jobs(l1, cap), g2 = group_jobs(l2, cap), g3 = group_jobs(l3, cap),
+                          g4 = group_jobs(l4, cap);
     std::vector<unsigned char> head(hdr, 0);
     const size_t items_bytes = round_up(sizeof(BatchItem) * count);
     memcpy(head.data(), items.data(), sizeof(BatchItem) * count);
@@ -513,6 +515,80 @@ int he_profile(he_ctx *c, int enable)
     }
     c->prof = enable != 0;
     c->prof_used = 0;
+    return HE_OK;
+}
+
+int he_set_shape(he_ctx *c, const he_shape *sh)
+{
+    if (!c || !sh) return HE_EINVAL;
+    if (sh->group_cap < 1 || sh->group_cap > kGroupMax) return HE_EINVAL;
+    if (sh->modup_chunk != 4 && sh->modup_chunk != 8 && sh->modup_chunk != 16) return HE_EINVAL;
+    c->group_cap = sh->group_cap;
+    c->modup_chunk = sh->modup_chunk;
+    if (c->device) c->jobs = c->jobs_cap[c->group_cap - 1];
+    return HE_OK;
+}
+
+int he_get_shape(const he_ctx *c, he_shape *sh)
+{
+    if (!c || !sh) return HE_EINVAL;
+    sh->group_cap = c->group_cap;
+    sh->modup_chunk = c->modup_chunk;
+    sh->ms = 0;
+    return HE_OK;
+}
+
+int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, void *ws, size_t ws_bytes, int reps,
+                void *stream, he_shape *best, he_shape *tried, int max_tried, int *n_tried)
+{
+    if (check_dev(c) || !jobs || count < 1 || !evk || !ws || !best || reps < 1) return HE_EINVAL;
+    he_shape keep;
+    he_get_shape(c, &keep);
+    auto call = [&]() -> int {
+        if (count == 1)
+            return he_mul_rescale(c, jobs[0].ct1, jobs[0].ct2, evk, jobs[0].level, jobs[0].out, ws, ws_bytes, stream);
+        return he_mul_batch(c, count, jobs, evk, ws, ws_bytes, stream);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return HE_ECUDA;
+    }
+    const bool prof = c->prof;
+    c->prof = false;
+    int rc = HE_OK, n = 0;
+    he_shape top = keep;
+    top.ms = -1;
+    const int caps[] = {1, 2, 3, 4}, chunks[] = {4, 8, 16};
+    for (int cap : caps)
+        for (int ch : chunks) {
+            he_shape sh = {cap, ch, 0};
+            he_set_shape(c, &sh);
+            if ((rc = call()) != HE_OK) break;  // warm-up (and argument check)
+            cudaEventRecord(e0, S(stream));
+            for (int r = 0; r < reps && rc == HE_OK; r++) rc = call();
+            cudaEventRecord(e1, S(stream));
+            if (rc != HE_OK) break;
+            float ms = 0;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = HE_ECUDA;
+                break;
+            }
+            sh.ms = ms / reps;
+            if (tried && n < max_tried) tried[n] = sh;
+            n++;
+            if (top.ms < 0 || sh.ms < top.ms) top = sh;
+        }
+    c->prof = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_tried) *n_tried = std::min(n, max_tried);
+    if (rc != HE_OK) {
+        he_set_shape(c, &keep);
+        return rc;
+    }
+    he_set_shape(c, &top);
+    *best = top;
     return HE_OK;
 }
 
@@ -745,7 +821,7 @@ int he_batch_graph_launch(he_batch_graph *g, int count, const he_job *jobs, void
     }
     int *counts = (int *)(g->pinned + g->counts_off);
     for (int t = 0; t < 4; t++) {
-        std::vector<NttGroup> grp = group_jobs(lists[t]);
+        std::vector<NttGroup> grp = group_jobs(lists[t], c->group_cap);
         if ((int)grp.size() > g->list_max[t]) return HE_EINVAL;
         memcpy(g->pinned + g->lists_off[t], grp.data(), sizeof(NttGroup) * grp.size());
         counts[t] = (int)grp.size();

@@ -45,8 +45,9 @@ struct NttGroup {
     u64 scale[kGroupMax], scale_sh[kGroupMax];
 };
 
-// Group single-limb jobs by prime (order within a prime is kept).
-std::vector<NttGroup> group_jobs(const std::vector<NttJob> &jobs);
+// Group single-limb jobs by prime, at most `cap` limbs per group (order
+// within a prime is kept).
+std::vector<NttGroup> group_jobs(const std::vector<NttJob> &jobs, int cap = kGroupMax);
 
 // Per-level constants on the device.
 struct DevLevel {
@@ -79,7 +80,8 @@ struct WsLayout {
     size_t d0, d1, d2, y, u, ks, ys, r, z, total;
 };
 
-// Job lists of one level, stored in the context's device arena.
+// Job lists of one level, stored in the context's device arena (one set
+// per group cap 1..kGroupMax; jobs[l] is the set of the context's cap).
 struct LevelJobs {
     const NttGroup *intt1;    int n_intt1;     // d2 -> y          (+2 fused: d0,d1 last limb -> r[0..1])
     const NttGroup *intt1f;   int n_intt1f;    // fused variant
@@ -106,6 +108,10 @@ struct he_ctx {
     int N, logN, L, K, alpha, dnum, E;  // E = K + L
     int AP, KP;                          // alpha and K padded to a kernel width (1,2,4,8,12,16)
     bool device;
+    // launch shapes (speed only; he_autotune / he_set_shape): NTT limbs per
+    // group (1..kGroupMax) and ModUp targets per CTA (4, 8 or 16)
+    int group_cap = he::kGroupMax;
+    int modup_chunk = 8;
     std::vector<u64> ext;                // moduli, ext order
     std::vector<u64> psi;                // smallest primitive 2N-th roots, ext order
     // host tables (for the host NTT used by keygen / encrypt / decrypt)
@@ -127,7 +133,8 @@ struct he_ctx {
     const ulonglong2 *d_pinv = nullptr;
     std::vector<he::DevLevel> dev_levels;  // index l (host copy of the device structs)
     he::DevLevel *d_levels = nullptr;      // [L+1]
-    std::vector<he::LevelJobs> jobs;       // index l
+    std::vector<he::LevelJobs> jobs;       // index l: the lists of group_cap
+    std::vector<he::LevelJobs> jobs_cap[he::kGroupMax];  // [cap-1][l]: every cap's lists
     // optional per-kernel event marks (he_profile); consecutive marks on one
     // stream bracket one kernel each
     mutable bool prof = false;

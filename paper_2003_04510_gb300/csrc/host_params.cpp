@@ -60,14 +60,15 @@ static ulonglong2 pair(u64 v, u64 m) { return make_ulonglong2(v, shoup(v, m)); }
 // base-conversion constant stored split at bit 28 for the kernels' lazy MACs
 static u64 split28(u64 b) { return (b & 0xFFFFFFFull) | ((b >> 28) << 32); }
 
-std::vector<NttGroup> group_jobs(const std::vector<NttJob> &jobs)
+std::vector<NttGroup> group_jobs(const std::vector<NttJob> &jobs, int cap)
 {
+    cap = std::max(1, std::min(cap, kGroupMax));
     std::vector<NttGroup> out;
     std::vector<int> open_for_prime;  // index into out of the group being filled, per prime
     for (const NttJob &j : jobs) {
         if (j.prime >= open_for_prime.size()) open_for_prime.resize(j.prime + 1, -1);
         int g = open_for_prime[j.prime];
-        if (g < 0 || out[g].nl == (unsigned)kGroupMax) {
+        if (g < 0 || out[g].nl == (unsigned)cap) {
             NttGroup ng;
             memset(&ng, 0, sizeof(ng));
             ng.prime = j.prime;
@@ -290,9 +291,11 @@ int build_context(he_ctx *c, const he_params *p, bool device)
     const size_t o_PBP = take(sizeof(u64) * c->PBP.size());
     const size_t o_pinv = take(sizeof(ulonglong2) * L);
     const size_t o_levels = take(sizeof(DevLevel) * (L + 1));
-    struct LvlOff { size_t modupB, qinv, pq, j[9]; };
+    // per level and group cap: the nine NTT group lists
+    struct LvlOff { size_t modupB, qinv, pq, j[kGroupMax][9]; };
     std::vector<LvlOff> lo(L + 1);
-    std::vector<std::vector<std::vector<NttGroup>>> gl(L + 1, std::vector<std::vector<NttGroup>>(9));
+    std::vector<std::vector<std::vector<std::vector<NttGroup>>>> gl(
+        L + 1, std::vector<std::vector<std::vector<NttGroup>>>(kGroupMax, std::vector<std::vector<NttGroup>>(9)));
     for (int l = 1; l <= L; l++) {
         HostLevel &H = c->host_levels[l];
         lo[l].modupB = take(sizeof(u64) * H.modupB.size());
@@ -300,10 +303,11 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         lo[l].pq = take(sizeof(ulonglong2) * H.pinv_qinv.size());
         const std::vector<NttJob> *lists[9] = {&H.intt1, &H.intt1f, &H.ntt_up, &H.intt2, &H.intt2f,
                                                &H.ntt_conv, &H.ntt_z, &H.rs_intt, &H.rs_ntt};
-        for (int t = 0; t < 9; t++) {
-            gl[l][t] = group_jobs(*lists[t]);
-            lo[l].j[t] = take(sizeof(NttGroup) * std::max<size_t>(1, gl[l][t].size()));
-        }
+        for (int cap = 1; cap <= kGroupMax; cap++)
+            for (int t = 0; t < 9; t++) {
+                gl[l][cap - 1][t] = group_jobs(*lists[t], cap);
+                lo[l].j[cap - 1][t] = take(sizeof(NttGroup) * std::max<size_t>(1, gl[l][cap - 1][t].size()));
+            }
     }
     c->arena_bytes = off;
     if (cudaGetDevice(&c->device_id) != cudaSuccess) return HE_ECUDA;
@@ -352,6 +356,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
     memcpy(img.data() + o_pinv, c->pinv.data(), sizeof(ulonglong2) * L);
     c->dev_levels.assign(L + 1, DevLevel());
     c->jobs.assign(L + 1, LevelJobs());
+    for (int cap = 0; cap < kGroupMax; cap++) c->jobs_cap[cap].assign(L + 1, LevelJobs());
     for (int l = 1; l <= L; l++) {
         HostLevel &H = c->host_levels[l];
         DevLevel &D = c->dev_levels[l];
@@ -374,25 +379,28 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         D.modupB = (const u64 *)(base + lo[l].modupB);
         D.qinv_last = (const ulonglong2 *)(base + lo[l].qinv);
         D.pinv_qinv = (const ulonglong2 *)(base + lo[l].pq);
-        const NttGroup *dptr[9];
-        int cnt[9];
-        for (int t = 0; t < 9; t++) {
-            const std::vector<NttGroup> &G = gl[l][t];
-            if (!G.empty()) memcpy(img.data() + lo[l].j[t], G.data(), sizeof(NttGroup) * G.size());
-            dptr[t] = (const NttGroup *)(base + lo[l].j[t]);
-            cnt[t] = (int)G.size();
+        for (int cap = 1; cap <= kGroupMax; cap++) {
+            const NttGroup *dptr[9];
+            int cnt[9];
+            for (int t = 0; t < 9; t++) {
+                const std::vector<NttGroup> &G = gl[l][cap - 1][t];
+                if (!G.empty()) memcpy(img.data() + lo[l].j[cap - 1][t], G.data(), sizeof(NttGroup) * G.size());
+                dptr[t] = (const NttGroup *)(base + lo[l].j[cap - 1][t]);
+                cnt[t] = (int)G.size();
+            }
+            LevelJobs &J = c->jobs_cap[cap - 1][l];
+            J.intt1 = dptr[0];    J.n_intt1 = cnt[0];
+            J.intt1f = dptr[1];   J.n_intt1f = cnt[1];
+            J.ntt_up = dptr[2];   J.n_ntt_up = cnt[2];
+            J.intt2 = dptr[3];    J.n_intt2 = cnt[3];
+            J.intt2f = dptr[4];   J.n_intt2f = cnt[4];
+            J.ntt_conv = dptr[5]; J.n_ntt_conv = cnt[5];
+            J.ntt_z = dptr[6];    J.n_ntt_z = cnt[6];
+            J.rs_intt = dptr[7];  J.n_rs_intt = cnt[7];
+            J.rs_ntt = dptr[8];   J.n_rs_ntt = cnt[8];
         }
-        LevelJobs &J = c->jobs[l];
-        J.intt1 = dptr[0];    J.n_intt1 = cnt[0];
-        J.intt1f = dptr[1];   J.n_intt1f = cnt[1];
-        J.ntt_up = dptr[2];   J.n_ntt_up = cnt[2];
-        J.intt2 = dptr[3];    J.n_intt2 = cnt[3];
-        J.intt2f = dptr[4];   J.n_intt2f = cnt[4];
-        J.ntt_conv = dptr[5]; J.n_ntt_conv = cnt[5];
-        J.ntt_z = dptr[6];    J.n_ntt_z = cnt[6];
-        J.rs_intt = dptr[7];  J.n_rs_intt = cnt[7];
-        J.rs_ntt = dptr[8];   J.n_rs_ntt = cnt[8];
     }
+    c->jobs = c->jobs_cap[c->group_cap - 1];
     memcpy(img.data() + o_levels, c->dev_levels.data(), sizeof(DevLevel) * (L + 1));
     if (cudaMemcpy(c->arena, img.data(), off, cudaMemcpyHostToDevice) != cudaSuccess) return HE_ECUDA;
     c->d_primes = (DevPrime *)(base + o_primes);

@@ -58,16 +58,14 @@ k_tensor(const JobRef R, const DevPrime *__restrict__ primes, const DevLevel *__
     st2(d2 + (size_t)i * N + n, mul_mod(a1.x, a2.x, pr.q, pr.mu, pr.s), mul_mod(a1.y, a2.y, pr.q, pr.mu, pr.s));
 }
 
-// grid: x over N/2/kThreads, y over (digit, chunk of kModupChunk targets),
+// grid: x over N/2/kThreads, y over (digit, chunk of CH targets),
 // z over jobs.  Input: the scaled iNTT of d2 (y region), output U: [beta][E][N].
 // Target u of digit j (u < E - n_j) is ext limb u below the digit's own limbs,
 // u + n_j above.  Digits are padded to A limbs with zero constants (the padding
 // loads reread a real limb, whose value is multiplied by zero), so the MAC loop
 // has no predicates; the chunk's constants and prime parameters sit in shared
 // memory.
-constexpr int kModupChunk = 8;
-
-template <int A>
+template <int A, int CH>
 __global__ void __launch_bounds__(kThreads)
 k_modup(const JobRef R, const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int N,
         int chunks)
@@ -78,13 +76,13 @@ k_modup(const JobRef R, const DevLevel *__restrict__ lv_arr, const DevPrime *__r
     if (j >= lv.beta) return;
     const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
     const int E = lv.E;
-    const int u0 = (blockIdx.y - j * chunks) * kModupChunk;
-    const int cnt = min(kModupChunk, E - nj - u0);
+    const int u0 = (blockIdx.y - j * chunks) * CH;
+    const int cnt = min(CH, E - nj - u0);
     if (cnt <= 0) return;
-    __shared__ u64 sB[kModupChunk][A];
-    __shared__ u64 sq[kModupChunk], smu[kModupChunk];
-    __shared__ unsigned ss[kModupChunk];
-    __shared__ int se[kModupChunk];
+    __shared__ u64 sB[CH][A];
+    __shared__ u64 sq[CH], smu[CH];
+    __shared__ unsigned ss[CH];
+    __shared__ int se[CH];
     const u64 *B = lv.modupB + (size_t)j * E * A;
     for (int t = threadIdx.x; t < cnt * A; t += kThreads) {
         const int u = u0 + t / A;
@@ -426,16 +424,17 @@ cudaError_t run_automorph(const he_ctx *c, const u64 *ct, u64 *ws, int l, u64 g,
     return cudaGetLastError();
 }
 
-cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st)
+template <int CH>
+cudaError_t launch_modup(const he_ctx *c, const JobRef &R, cudaStream_t st)
 {
     // the most targets any digit of any level up to lmax has: K + (beta - 1) alpha
     const int beta = (R.lmax + c->alpha - 1) / c->alpha;
-    const int chunks = (c->K + (beta - 1) * c->alpha + kModupChunk - 1) / kModupChunk;
+    const int chunks = (c->K + (beta - 1) * c->alpha + CH - 1) / CH;
     dim3 g = grid_x(c->N);
     g.y = beta * chunks;
     g.z = R.B;
     const int a = c->AP;
-#define HE_MODUP(AA) k_modup<AA><<<g, kThreads, 0, st>>>(R, c->d_levels, c->d_primes, c->K, c->N, chunks)
+#define HE_MODUP(AA) k_modup<AA, CH><<<g, kThreads, 0, st>>>(R, c->d_levels, c->d_primes, c->K, c->N, chunks)
     if (a == 1) HE_MODUP(1);
     else if (a == 2) HE_MODUP(2);
     else if (a == 4) HE_MODUP(4);
@@ -444,6 +443,13 @@ cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st)
     else HE_MODUP(16);
 #undef HE_MODUP
     return cudaGetLastError();
+}
+
+cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st)
+{
+    if (c->modup_chunk == 4) return launch_modup<4>(c, R, st);
+    if (c->modup_chunk == 16) return launch_modup<16>(c, R, st);
+    return launch_modup<8>(c, R, st);
 }
 
 cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st)

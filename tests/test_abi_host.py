@@ -119,6 +119,18 @@ def test_host_plaintext_ntt_matches_oracle(g):
             assert np.array_equal(g.he_plain_ntt(ctx, t, level), oracle.plain_ntt(op, t, level))
 
 
+def test_shape_setters(g):
+    ctx = g.Context(g.PRESETS["n12"][0], device=False)
+    assert g.he_get_shape(ctx) == (4, 8)
+    g.he_set_shape(ctx, 2, 16)
+    assert g.he_get_shape(ctx) == (2, 16)
+    for cap, chunk in ((0, 8), (5, 8), (4, 6), (4, 32)):
+        with pytest.raises(g.HeError) as e:
+            g.he_set_shape(ctx, cap, chunk)
+        assert e.value.code == g.HE_EINVAL
+    assert g.he_get_shape(ctx) == (2, 16)
+
+
 def test_argument_errors_are_status_codes(g):
     bad = g.Params(11, 3, 1, 1, 50, 51, 64)  # logN below range
     with pytest.raises(g.HeError) as e:

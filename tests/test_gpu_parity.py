@@ -529,3 +529,50 @@ def test_squaring_chain_n15_all_levels(g):
         cur = nxt
     z = oracle.decrypt(op, sk, host(g, cur), 1, scale)
     assert np.abs(z - want).max() < 2.0 ** -20
+
+
+
+# ---------------------------------------------------------------------------
+# launch shapes and the autotuner: speed only, bits unchanged
+# ---------------------------------------------------------------------------
+def test_every_shape_is_bit_identical_n16(g):
+    op, sc, sk, pk, evk, m1, m2, ct1, ct2 = real_inputs("n16")
+    ctx = ctx_for(g, "n16")
+    evk_t = dev(g, evk)
+    level = 17
+    c1 = np.ascontiguousarray(np.stack([ct1[0, :level], ct1[1, :level]]))
+    c2 = np.ascontiguousarray(np.stack([ct2[0, :level], ct2[1, :level]]))
+    want = oracle.rescale(op, oracle.he_mul(op, c1, c2, evk, level), level)
+    try:
+        for cap, chunk in ((1, 4), (2, 16), (3, 8), (4, 16)):
+            g.he_set_shape(ctx, cap, chunk)
+            assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want), (cap, chunk)
+    finally:
+        g.he_set_shape(ctx, 4, 8)
+
+
+def test_autotune_batch_keeps_results(g):
+    import torch
+    ctx = ctx_for(g, "n15")
+    op = oracle.preset("n15")
+    evk = rand_evk(op, 700)
+    evk_t = dev(g, evk)
+    levels = [16, 9, 3, 12]
+    jobs, want = [], []
+    for k, lv in enumerate(levels):
+        a, b = rand_ct(op, lv, 710 + 4 * k), rand_ct(op, lv, 712 + 4 * k)
+        jobs.append((dev(g, a), dev(g, b), torch.empty((2, lv - 1, op.N), dtype=torch.int64, device="cuda"), lv))
+        want.append(oracle.rescale(op, oracle.he_mul(op, a, b, evk, lv), lv))
+    ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
+    try:
+        best, tried = g.he_autotune(ctx, jobs, evk_t, ws, reps=2)
+        assert len(tried) == 12 and all(t[2] > 0 for t in tried)
+        assert best[:2] == g.he_get_shape(ctx) and best[2] == min(t[2] for t in tried)
+        for j in jobs:
+            j[2].zero_()
+        g.he_mul_batch(ctx, jobs, evk_t, ws)
+        torch.cuda.synchronize()
+        for j, w in zip(jobs, want):
+            assert np.array_equal(host(g, j[2]), w)
+    finally:
+        g.he_set_shape(ctx, 4, 8)
