@@ -196,6 +196,30 @@ __device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *tw, const T
     }
 }
 
+// L2 prefetch of the lines load_direct_tw will read (one thread per eight,
+// which share a 128-byte line of the transposed runs); issued when a CTA
+// starts, so the last round's loads hit L2 instead of DRAM.
+template <int LOGM, int TE, int RL, int NT>
+__device__ __forceinline__ void prefetch_direct_tw(const ulonglong2 *twg, int tile, int s0)
+{
+    constexpr int L0 = LOGM - RL;
+    constexpr int NG = TE >> LOGM;
+    constexpr int SPT = (TE >> RL) / NT;
+    if (threadIdx.x & 7) return;
+#pragma unroll
+    for (int si = 0; si < SPT; si++) {
+        const int s = threadIdx.x + si * NT;
+        const int Tn = ((tile * NG + (s >> L0)) << L0) + (s & ((1 << L0) - 1));
+#pragma unroll
+        for (int lp = 0; lp < RL; lp++) {
+            const ulonglong2 *g = twg + (1 << (s0 + L0 + lp)) + Tn;
+#pragma unroll
+            for (int j = 0; j < (1 << lp); j++)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(g + ((size_t)j << (s0 + L0))));
+        }
+    }
+}
+
 // global index of tile element e
 template <int LOGM, int TE, bool STRIDED>
 __device__ __forceinline__ size_t tile_gi(int e, int tile, int stride)
@@ -254,6 +278,7 @@ k_ntt_pass(const NttArgs P)
     }
     load_tile(0, buf);
     __pipeline_commit();
+    if (DIRECT) prefetch_direct_tw<LOGM, TE, RL, NT>(twg, tile, s0);
 
     // the direct round's twiddles -> registers (reloaded for every limb from
     // L2 so that they are live only during that round).  The device table
