@@ -320,8 +320,8 @@ def run_batched(g, ctx, evk_t, dev, stream, wsz, count=64, reps=20):
                      "batch_latency_ms_p99": float(np.percentile(lat, 99))}
     graph.close()
     g.he_set_shape(ctx, *shape_before)
-    res["autotune"] = {"group_cap": best[0], "modup_chunk": best[1], "ms_per_batch": best[2],
-                       "tried": [{"group_cap": t[0], "modup_chunk": t[1], "ms": t[2]} for t in tried]}
+    res["autotune"] = {"group_cap": best[0], "modup_chunk": best[1], "pdl": best[2], "ms_per_batch": best[3],
+                       "tried": [{"group_cap": t[0], "modup_chunk": t[1], "pdl": t[2], "ms": t[3]} for t in tried]}
     res["config"] = {"jobs": count, "N": N, "levels": "uniform 4..24 (seed 1604)", "mean_level": float(np.mean(levels)),
                      "operands": "uniform residues"}
     return res
@@ -617,8 +617,10 @@ def run_ours(args):
             "inner_product_hbm": ip,
             "probe": probe,
             "kernels": per_kernel,
-            "autotune": {"group_cap": tune_best[0], "modup_chunk": tune_best[1], "ms": tune_best[2],
-                         "tried": [{"group_cap": t[0], "modup_chunk": t[1], "ms": t[2]} for t in tune_tried]},
+            "autotune": {"group_cap": tune_best[0], "modup_chunk": tune_best[1], "pdl": tune_best[2],
+                         "ms": tune_best[3],
+                         "tried": [{"group_cap": t[0], "modup_chunk": t[1], "pdl": t[2], "ms": t[3]}
+                                   for t in tune_tried]},
             "rotate": rot,
             "chain": chain,
             "batched": batched,

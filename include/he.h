@@ -338,12 +338,16 @@ int he_rotate(he_ctx *ctx, const uint64_t *ct, const uint64_t *rk_dev, int level
 /* ---- launch shapes and autotuning (no paper counterpart) ------------------ */
 
 /* Launch shape of the path: NTT limbs that share a CTA (they share the
- * staged twiddles; 1..4) and ModUp targets per CTA (4, 8 or 16).  Speed only:
- * every shape gives bit-identical results.  Default {4, 8}.  A batch graph
- * keeps the ModUp shape it was captured with. */
+ * staged twiddles; 1..4), ModUp targets per CTA (4, 8 or 16), and whether the
+ * path's kernels use programmatic dependent launch (1: a kernel's CTAs may be
+ * scheduled while its predecessor drains; each waits for it in hardware
+ * before touching its data).  Speed only: every shape gives bit-identical
+ * results.  Default {4, 8, 1}.  A batch graph keeps the shape it was
+ * captured with, except the limb-group cap. */
 typedef struct {
     int group_cap;
     int modup_chunk;
+    int pdl;
     double ms; /* he_autotune: measured milliseconds per call; else 0 */
 } he_shape;
 

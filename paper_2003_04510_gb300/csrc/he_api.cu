@@ -523,8 +523,10 @@ int he_set_shape(he_ctx *c, const he_shape *sh)
     if (!c || !sh) return HE_EINVAL;
     if (sh->group_cap < 1 || sh->group_cap > kGroupMax) return HE_EINVAL;
     if (sh->modup_chunk != 4 && sh->modup_chunk != 8 && sh->modup_chunk != 16) return HE_EINVAL;
+    if (sh->pdl != 0 && sh->pdl != 1) return HE_EINVAL;
     c->group_cap = sh->group_cap;
     c->modup_chunk = sh->modup_chunk;
+    c->pdl = sh->pdl != 0;
     if (c->device) c->jobs = c->jobs_cap[c->group_cap - 1];
     return HE_OK;
 }
@@ -534,6 +536,7 @@ int he_get_shape(const he_ctx *c, he_shape *sh)
     if (!c || !sh) return HE_EINVAL;
     sh->group_cap = c->group_cap;
     sh->modup_chunk = c->modup_chunk;
+    sh->pdl = c->pdl ? 1 : 0;
     sh->ms = 0;
     return HE_OK;
 }
@@ -559,10 +562,11 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
     int rc = HE_OK, n = 0;
     he_shape top = keep;
     top.ms = -1;
-    const int caps[] = {1, 2, 3, 4}, chunks[] = {4, 8, 16};
+    const int caps[] = {1, 2, 3, 4}, chunks[] = {4, 8, 16}, pdls[] = {1, 0};
+    for (int pdl : pdls)
     for (int cap : caps)
         for (int ch : chunks) {
-            he_shape sh = {cap, ch, 0};
+            he_shape sh = {cap, ch, pdl, 0};
             he_set_shape(c, &sh);
             if ((rc = call()) != HE_OK) break;  // warm-up (and argument check)
             cudaEventRecord(e0, S(stream));

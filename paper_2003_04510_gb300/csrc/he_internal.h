@@ -112,6 +112,7 @@ struct he_ctx {
     // group (1..kGroupMax) and ModUp targets per CTA (4, 8 or 16)
     int group_cap = he::kGroupMax;
     int modup_chunk = 8;
+    bool pdl = true;                     // programmatic dependent launch between the path's kernels
     std::vector<u64> ext;                // moduli, ext order
     std::vector<u64> psi;                // smallest primitive 2N-th roots, ext order
     // host tables (for the host NTT used by keygen / encrypt / decrypt)
@@ -151,6 +152,34 @@ int build_context(he_ctx *ctx, const he_params *p, bool device);
 // unless profiling is enabled on the context).
 void prof_mark(const he_ctx *ctx, cudaStream_t st, const char *tag, const char *suffix = nullptr);
 // ngroups > 0 launches; dev_count (optional) bounds the groups on the device.
+// Kernel launch with programmatic dependent launch allowed when `dep` is
+// set: the kernel's CTAs may be scheduled while the previous kernel on the
+// stream drains, so every such kernel executes griddep_wait() before it
+// touches memory that earlier work on the stream produces or reads (static
+// tables may be read before).  Errors are left for cudaGetLastError().
+template <typename... KArgs, typename... Args>
+inline void launch_k(bool dep, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args... args)
+{
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = dep ? at : nullptr;
+    cfg.numAttrs = dep ? 1 : 0;
+    (void)cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
+#ifdef __CUDACC__
+// Wait for the previous kernel on the stream (a no-op without a programmatic
+// dependency).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
 cudaError_t launch_ntt(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, bool inverse,
                        cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr);
 cudaError_t launch_ntt2(const he_ctx *ctx, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups,

@@ -48,6 +48,7 @@ k_tensor(const JobRef R, const DevPrime *__restrict__ primes, const DevLevel *__
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[K + i];
     const size_t ob = (size_t)i * N + n, oa = ((size_t)l + i) * N + n;
+    griddep_wait();
     const ulonglong2 b1 = ld2(it.ct1 + ob), a1 = ld2(it.ct1 + oa), b2 = ld2(it.ct2 + ob), a2 = ld2(it.ct2 + oa);
     u64 *d0 = it.ws + (size_t)lv.o_d0 * N, *d1 = it.ws + (size_t)lv.o_d1 * N, *d2 = it.ws + (size_t)lv.o_d2 * N;
     st2(d0 + (size_t)i * N + n, mul_mod(b1.x, b2.x, pr.q, pr.mu, pr.s), mul_mod(b1.y, b2.y, pr.q, pr.mu, pr.s));
@@ -99,6 +100,7 @@ k_modup(const JobRef R, const DevLevel *__restrict__ lv_arr, const DevPrime *__r
     }
     const u64 *y = it.ws + (size_t)lv.o_y * N;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
+    griddep_wait();
     uint32_t x0[A], x1[A], z0[A], z1[A];
 #pragma unroll
     for (int i = 0; i < A; i++) {
@@ -139,6 +141,7 @@ k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__r
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[e];
     const u64 *U = it.ws + (size_t)lv.o_u * N, *d2 = it.ws + (size_t)lv.o_d2 * N;
+    griddep_wait();
     ulonglong2 u[BM], kb[BM], ka[BM];
 #pragma unroll
     for (int j = 0; j < BM; j++) {
@@ -226,6 +229,7 @@ k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__r
     const u64 *ys = it.ws + (size_t)lv.o_ys * N, *rr = it.ws + (size_t)lv.o_r * N;
     u64 *z = it.ws + (size_t)lv.o_z * N;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
+    griddep_wait();
     uint32_t x0[KM], x1[KM], z0[KM], z1[KM];
 #pragma unroll
     for (int k = 0; k < KM; k++) {
@@ -276,6 +280,7 @@ k_combine_plain(const JobRef R, const ulonglong2 *__restrict__ pinv, const DevLe
     const ulonglong2 pv = pinv[i];
     const u64 *d = it.ws + (size_t)(h ? lv.o_d1 : lv.o_d0) * N;
     const u64 *KS = it.ws + (size_t)lv.o_ks * N, *C = it.ws + (size_t)lv.o_z * N;
+    griddep_wait();
     const ulonglong2 dv = ld2(d + (size_t)i * N + n);
     const ulonglong2 ks = ld2(KS + ((size_t)h * E + K + i) * N + n);
     const ulonglong2 c = ld2(C + ((size_t)h * l + i) * N + n);
@@ -301,6 +306,7 @@ k_combine_rescale(const JobRef R, const ulonglong2 *__restrict__ pinv, const Dev
     const ulonglong2 qv = lv.qinv_last[i];
     const u64 *d = it.ws + (size_t)(h ? lv.o_d1 : lv.o_d0) * N;
     const u64 *KS = it.ws + (size_t)lv.o_ks * N, *Z = it.ws + (size_t)lv.o_z * N;
+    griddep_wait();
     const ulonglong2 dv = ld2(d + (size_t)i * N + n);
     const ulonglong2 ks = ld2(KS + ((size_t)h * E + K + i) * N + n);
     const ulonglong2 zz = ld2(Z + ((size_t)h * (l - 1) + i) * N + n);
@@ -318,6 +324,7 @@ k_rescale_combine(const u64 *__restrict__ ct, const u64 *__restrict__ Z, u64 *__
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[K + i];
     const ulonglong2 qv = lv_arr[l].qinv_last[i];
+    griddep_wait();
     const ulonglong2 c = ld2(ct + ((size_t)h * l + i) * N + n);
     const ulonglong2 zz = ld2(Z + ((size_t)h * (l - 1) + i) * N + n);
     st2(out + ((size_t)h * (l - 1) + i) * N + n, shoup(sub_mod(c.x, zz.x, pr.q), qv.x, qv.y, pr.q),
@@ -347,6 +354,7 @@ k_automorph(const u64 *__restrict__ ct, u64 *__restrict__ ws, const DevLevel *__
         const unsigned long long e = (g * (2ull * br + 1)) % twoN;
         src[k] = __brev((unsigned)((e - 1) / 2)) >> (32 - logN);
     }
+    griddep_wait();
     const u64 a0 = a[src[0]], a1 = a[src[1]];
     st2(ws + (size_t)lv.o_d0 * N + (size_t)i * N + n, b[src[0]], b[src[1]]);
     st2(ws + (size_t)lv.o_d1 * N + (size_t)i * N + n, 0, 0);
@@ -366,6 +374,7 @@ k_elementwise(const u64 *x, const u64 *y, u64 *out, const DevPrime *__restrict__
     const DevPrime pr = primes[K + i];
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const size_t o = ((size_t)h * l + i) * N + n;
+    griddep_wait();
     const ulonglong2 a = ld2(x + o);
     u64 r0, r1;
     if (OP == 0 || OP == 1) {
@@ -398,7 +407,7 @@ cudaError_t run_tensor(const he_ctx *c, const JobRef &R, cudaStream_t st)
     dim3 g = grid_x(c->N);
     g.y = R.lmax;
     g.z = R.B;
-    k_tensor<<<g, kThreads, 0, st>>>(R, c->d_primes, c->d_levels, c->K, c->N);
+    launch_k(c->pdl, k_tensor, g, dim3(kThreads), 0, st, R, c->d_primes, c->d_levels, c->K, c->N);
     return cudaGetLastError();
 }
 
@@ -408,10 +417,10 @@ cudaError_t run_elementwise(const he_ctx *c, int op, const u64 *x, const u64 *y,
     grid.y = l;
     grid.z = 2;
     switch (op) {
-    case 0: k_elementwise<0><<<grid, kThreads, 0, st>>>(x, y, out, c->d_primes, c->K, l, c->N); break;
-    case 1: k_elementwise<1><<<grid, kThreads, 0, st>>>(x, y, out, c->d_primes, c->K, l, c->N); break;
-    case 2: k_elementwise<2><<<grid, kThreads, 0, st>>>(x, y, out, c->d_primes, c->K, l, c->N); break;
-    default: k_elementwise<3><<<grid, kThreads, 0, st>>>(x, y, out, c->d_primes, c->K, l, c->N); break;
+    case 0: launch_k(c->pdl, k_elementwise<0>, grid, dim3(kThreads), 0, st, x, y, out, c->d_primes, c->K, l, c->N); break;
+    case 1: launch_k(c->pdl, k_elementwise<1>, grid, dim3(kThreads), 0, st, x, y, out, c->d_primes, c->K, l, c->N); break;
+    case 2: launch_k(c->pdl, k_elementwise<2>, grid, dim3(kThreads), 0, st, x, y, out, c->d_primes, c->K, l, c->N); break;
+    default: launch_k(c->pdl, k_elementwise<3>, grid, dim3(kThreads), 0, st, x, y, out, c->d_primes, c->K, l, c->N); break;
     }
     return cudaGetLastError();
 }
@@ -420,7 +429,8 @@ cudaError_t run_automorph(const he_ctx *c, const u64 *ct, u64 *ws, int l, u64 g,
 {
     dim3 grid = grid_x(c->N);
     grid.y = l;
-    k_automorph<<<grid, kThreads, 0, st>>>(ct, ws, c->d_levels, c->d_primes, c->K, l, c->N, c->logN, g);
+    launch_k(c->pdl, k_automorph, grid, dim3(kThreads), 0, st, ct, ws, c->d_levels, c->d_primes, c->K, l, c->N, c->logN,
+             (unsigned long long)g);
     return cudaGetLastError();
 }
 
@@ -434,7 +444,7 @@ cudaError_t launch_modup(const he_ctx *c, const JobRef &R, cudaStream_t st)
     g.y = beta * chunks;
     g.z = R.B;
     const int a = c->AP;
-#define HE_MODUP(AA) k_modup<AA, CH><<<g, kThreads, 0, st>>>(R, c->d_levels, c->d_primes, c->K, c->N, chunks)
+#define HE_MODUP(AA) launch_k(c->pdl, k_modup<AA, CH>, g, dim3(kThreads), 0, st, R, c->d_levels, c->d_primes, c->K, c->N, chunks)
     if (a == 1) HE_MODUP(1);
     else if (a == 2) HE_MODUP(2);
     else if (a == 4) HE_MODUP(4);
@@ -458,7 +468,7 @@ cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, 
     g.y = c->K + R.lmax;
     g.z = R.B;
     const int bm = (c->L + c->alpha - 1) / c->alpha;  // the most digits any level has
-#define HE_IP(B) k_inner_product<B><<<g, kThreads, 0, st>>>(R, evk, c->d_levels, c->d_primes, c->K, c->L, c->N)
+#define HE_IP(B) launch_k(c->pdl, k_inner_product<B>, g, dim3(kThreads), 0, st, R, evk, c->d_levels, c->d_primes, c->K, c->L, c->N)
     if (bm <= 2) HE_IP(2);
     else if (bm <= 4) HE_IP(4);
     else if (bm <= 8) HE_IP(8);
@@ -477,10 +487,10 @@ cudaError_t run_moddown_conv(const he_ctx *c, const JobRef &R, bool fused, cudaS
 #define HE_MD(KK)                                                                                                   \
     do {                                                                                                            \
         if (fused)                                                                                                  \
-            k_moddown_conv<KK, true><<<g, kThreads, 0, st>>>(R, c->d_PBP, c->d_pinv, c->d_levels, c->d_primes, K,  \
+            launch_k(c->pdl, k_moddown_conv<KK, true>, g, dim3(kThreads), 0, st, R, c->d_PBP, c->d_pinv, c->d_levels, c->d_primes, K,  \
                                                              c->N, chunks);                                         \
         else                                                                                                        \
-            k_moddown_conv<KK, false><<<g, kThreads, 0, st>>>(R, c->d_PB, c->d_pinv, c->d_levels, c->d_primes, K,  \
+            launch_k(c->pdl, k_moddown_conv<KK, false>, g, dim3(kThreads), 0, st, R, c->d_PB, c->d_pinv, c->d_levels, c->d_primes, K,  \
                                                               c->N, chunks);                                        \
     } while (0)
     const int kp = c->KP;
@@ -499,7 +509,7 @@ cudaError_t run_combine_plain(const he_ctx *c, const JobRef &R, cudaStream_t st)
     dim3 g = grid_x(c->N);
     g.y = R.lmax;
     g.z = 2 * R.B;
-    k_combine_plain<<<g, kThreads, 0, st>>>(R, c->d_pinv, c->d_levels, c->d_primes, c->K, c->N);
+    launch_k(c->pdl, k_combine_plain, g, dim3(kThreads), 0, st, R, c->d_pinv, c->d_levels, c->d_primes, c->K, c->N);
     return cudaGetLastError();
 }
 
@@ -508,7 +518,7 @@ cudaError_t run_combine_rescale(const he_ctx *c, const JobRef &R, cudaStream_t s
     dim3 g = grid_x(c->N);
     g.y = R.lmax - 1;
     g.z = 2 * R.B;
-    k_combine_rescale<<<g, kThreads, 0, st>>>(R, c->d_pinv, c->d_levels, c->d_primes, c->K, c->N);
+    launch_k(c->pdl, k_combine_rescale, g, dim3(kThreads), 0, st, R, c->d_pinv, c->d_levels, c->d_primes, c->K, c->N);
     return cudaGetLastError();
 }
 
@@ -517,7 +527,7 @@ cudaError_t run_rescale_combine(const he_ctx *c, const u64 *ct, const u64 *Z, u6
     dim3 g = grid_x(c->N);
     g.y = l - 1;
     g.z = 2;
-    k_rescale_combine<<<g, kThreads, 0, st>>>(ct, Z, out, c->d_levels, c->d_primes, c->K, l, c->N);
+    launch_k(c->pdl, k_rescale_combine, g, dim3(kThreads), 0, st, ct, Z, out, c->d_levels, c->d_primes, c->K, l, c->N);
     return cudaGetLastError();
 }
 

@@ -48,6 +48,7 @@ struct NttArgs {
     int logN;
     int tiles;       // tiles per limb
     const int *count;  // optional device-side group count (grids sized for a maximum)
+    bool pdl;          // launched with programmatic dependent launch
 };
 
 // Forward (Cooley-Tukey) butterfly with no correction step: the modified
@@ -276,9 +277,10 @@ k_ntt_pass(const NttArgs P)
             for (int f = threadIdx.x; f < n; f += NT) __pipeline_memcpy_async(&tw[NG * ((1 << l) - 1) + f], &g[f], 16);
         }
     }
+    if (DIRECT) prefetch_direct_tw<LOGM, TE, RL, NT>(twg, tile, s0);
+    griddep_wait();  // the limbs come from the previous kernels
     load_tile(0, buf);
     __pipeline_commit();
-    if (DIRECT) prefetch_direct_tw<LOGM, TE, RL, NT>(twg, tile, s0);
 
     // the direct round's twiddles -> registers (reloaded for every limb from
     // L2 so that they are live only during that round).  The device table
@@ -372,7 +374,7 @@ cudaError_t run_pass(const NttArgs &a, int ngroups, cudaStream_t st)
         configured = true;
     }
     if (ngroups == 0) return cudaSuccess;
-    kern<<<ngroups * a.tiles, NT, smem, st>>>(a);
+    launch_k(a.pdl, kern, dim3(ngroups * a.tiles), dim3(NT), smem, st, a);
     return cudaGetLastError();
 }
 
@@ -441,6 +443,7 @@ cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGrou
     a.logN = c->logN;
     a.tiles = 1;
     a.count = dev_count;
+    a.pdl = c->pdl;
     switch (c->logN) {
     case 12: {
         if (ngroups == 0) {

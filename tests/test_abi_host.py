@@ -121,14 +121,14 @@ def test_host_plaintext_ntt_matches_oracle(g):
 
 def test_shape_setters(g):
     ctx = g.Context(g.PRESETS["n12"][0], device=False)
-    assert g.he_get_shape(ctx) == (4, 8)
-    g.he_set_shape(ctx, 2, 16)
-    assert g.he_get_shape(ctx) == (2, 16)
-    for cap, chunk in ((0, 8), (5, 8), (4, 6), (4, 32)):
+    assert g.he_get_shape(ctx) == (4, 8, 1)
+    g.he_set_shape(ctx, 2, 16, 0)
+    assert g.he_get_shape(ctx) == (2, 16, 0)
+    for cap, chunk, pdl in ((0, 8, 1), (5, 8, 1), (4, 6, 1), (4, 32, 1), (4, 8, 2)):
         with pytest.raises(g.HeError) as e:
-            g.he_set_shape(ctx, cap, chunk)
+            g.he_set_shape(ctx, cap, chunk, pdl)
         assert e.value.code == g.HE_EINVAL
-    assert g.he_get_shape(ctx) == (2, 16)
+    assert g.he_get_shape(ctx) == (2, 16, 0)
 
 
 def test_argument_errors_are_status_codes(g):

@@ -544,11 +544,11 @@ def test_every_shape_is_bit_identical_n16(g):
     c2 = np.ascontiguousarray(np.stack([ct2[0, :level], ct2[1, :level]]))
     want = oracle.rescale(op, oracle.he_mul(op, c1, c2, evk, level), level)
     try:
-        for cap, chunk in ((1, 4), (2, 16), (3, 8), (4, 16)):
-            g.he_set_shape(ctx, cap, chunk)
-            assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want), (cap, chunk)
+        for cap, chunk, pdl in ((1, 4, 1), (2, 16, 0), (3, 8, 1), (4, 16, 0), (4, 8, 1)):
+            g.he_set_shape(ctx, cap, chunk, pdl)
+            assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want), (cap, chunk, pdl)
     finally:
-        g.he_set_shape(ctx, 4, 8)
+        g.he_set_shape(ctx, 4, 8, 1)
 
 
 def test_autotune_batch_keeps_results(g):
@@ -566,8 +566,8 @@ def test_autotune_batch_keeps_results(g):
     ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
     try:
         best, tried = g.he_autotune(ctx, jobs, evk_t, ws, reps=2)
-        assert len(tried) == 12 and all(t[2] > 0 for t in tried)
-        assert best[:2] == g.he_get_shape(ctx) and best[2] == min(t[2] for t in tried)
+        assert len(tried) == 24 and all(t[3] > 0 for t in tried)
+        assert best[:3] == g.he_get_shape(ctx) and best[3] == min(t[3] for t in tried)
         for j in jobs:
             j[2].zero_()
         g.he_mul_batch(ctx, jobs, evk_t, ws)
@@ -575,4 +575,4 @@ def test_autotune_batch_keeps_results(g):
         for j, w in zip(jobs, want):
             assert np.array_equal(host(g, j[2]), w)
     finally:
-        g.he_set_shape(ctx, 4, 8)
+        g.he_set_shape(ctx, 4, 8, 1)
