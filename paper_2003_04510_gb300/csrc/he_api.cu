@@ -98,11 +98,11 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
     HE_TRY(launch_ntt(c, ntt_base, S.intt2, S.n_intt2, true, st, "intt_special", cnt ? cnt + 2 : nullptr));
     HE_TRY(run_moddown_conv(c, R, fused, st));
     prof_mark(c, st, "moddown_conv");
-    HE_TRY(launch_ntt(c, ntt_base, S.ntt_last, S.n_ntt_last, false, st, "ntt_moddown", cnt ? cnt + 3 : nullptr));
     if (fused) {
-        HE_TRY(run_combine_rescale(c, R, st));
-        prof_mark(c, st, "combine_rescale");
+        // the final combine runs in the last NTT pass (writes each job's output)
+        HE_TRY(launch_ntt_combine(c, ntt_base, S.ntt_last, S.n_ntt_last, R, st, "ntt_moddown", cnt ? cnt + 3 : nullptr));
     } else {
+        HE_TRY(launch_ntt(c, ntt_base, S.ntt_last, S.n_ntt_last, false, st, "ntt_moddown", cnt ? cnt + 3 : nullptr));
         HE_TRY(run_combine_plain(c, R, st));
         prof_mark(c, st, "combine");
     }
@@ -459,6 +459,9 @@ int he_mul_batch(he_ctx *c, int count, const he_job *jobs, const uint64_t *evk, 
             for (NttJob j : src) {
                 j.src += (unsigned)off;
                 j.dst += (unsigned)off;
+                j.cd += (unsigned)off;
+                j.cks += (unsigned)off;
+                j.job = (unsigned)i;
                 dst.push_back(j);
             }
         };
@@ -820,6 +823,9 @@ int he_batch_graph_launch(he_batch_graph *g, int count, const he_job *jobs, void
             for (NttJob j : *src[t]) {
                 j.src += (unsigned)off;
                 j.dst += (unsigned)off;
+                j.cd += (unsigned)off;
+                j.cks += (unsigned)off;
+                j.job = (unsigned)i;
                 lists[t].push_back(j);
             }
     }

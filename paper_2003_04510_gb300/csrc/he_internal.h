@@ -34,6 +34,9 @@ struct DevPrime {
 struct NttJob {
     unsigned src, dst, prime, pad;
     u64 scale, scale_sh;
+    // fused final combine (forward NTT of the ModDown + rescale limbs): job
+    // index in the launch, h << 31 | i, and the limbs d_h[i] and KS_h[K+i]
+    unsigned job, ci, cd, cks;
 };
 
 // What the NTT kernels consume: up to kGroupMax limb transforms that share a
@@ -43,6 +46,7 @@ struct NttGroup {
     unsigned prime, nl, pad0, pad1;
     unsigned src[kGroupMax], dst[kGroupMax];
     u64 scale[kGroupMax], scale_sh[kGroupMax];
+    unsigned job[kGroupMax], ci[kGroupMax], cd[kGroupMax], cks[kGroupMax];  // NttJob's combine fields
 };
 
 // Group single-limb jobs by prime, at most `cap` limbs per group (order
@@ -74,6 +78,9 @@ struct JobRef {
     int B;                   // number of jobs
     int lmax;                // largest level among them
 };
+#ifdef __CUDACC__
+__device__ __forceinline__ BatchItem job_item(const JobRef &R, int z) { return R.items ? R.items[z] : R.one; }
+#endif
 
 // Workspace layout of one HE Mul at level l (offsets in limbs).
 struct WsLayout {
@@ -185,6 +192,11 @@ cudaError_t launch_ntt(const he_ctx *ctx, u64 *base, const NttGroup *groups, int
 cudaError_t launch_ntt2(const he_ctx *ctx, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups,
                         bool inverse, cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr);
 cudaError_t configure_ntt(const he_ctx *ctx);
+// Forward NTT of the fused ModDown + rescale limbs with the final combine in
+// its last pass: out[h][i] = (d_h[i] + KS_h[K+i] P^-1 - NTT(z)) q_{l-1}^-1,
+// written to each job's output (groups carry the combine fields).
+cudaError_t launch_ntt_combine(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
+                               cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr);
 // Number of final stages (the contiguous pass's last round) whose twiddle
 // runs the device table stores transposed; 0 for an unsupported logN.
 int ntt_direct_stages(int logN);
@@ -197,6 +209,5 @@ cudaError_t run_automorph(const he_ctx *c, const u64 *ct, u64 *ws, int l, u64 g,
 cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st);
 cudaError_t run_moddown_conv(const he_ctx *c, const JobRef &R, bool fused, cudaStream_t st);
 cudaError_t run_combine_plain(const he_ctx *c, const JobRef &R, cudaStream_t st);
-cudaError_t run_combine_rescale(const he_ctx *c, const JobRef &R, cudaStream_t st);
 cudaError_t run_rescale_combine(const he_ctx *c, const u64 *ct, const u64 *Z, u64 *out, int l, cudaStream_t st);
 }  // namespace he

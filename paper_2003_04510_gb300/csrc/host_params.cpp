@@ -81,6 +81,10 @@ std::vector<NttGroup> group_jobs(const std::vector<NttJob> &jobs, int cap)
         G.dst[G.nl] = j.dst;
         G.scale[G.nl] = j.scale;
         G.scale_sh[G.nl] = j.scale_sh;
+        G.job[G.nl] = j.job;
+        G.ci[G.nl] = j.ci;
+        G.cd[G.nl] = j.cd;
+        G.cks[G.nl] = j.cks;
         G.nl++;
     }
     return out;
@@ -254,7 +258,9 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         for (int h = 0; h < 2; h++)
             for (int i = 0; i + 1 < l; i++)
                 H.ntt_z.push_back(NttJob{(unsigned)(W.z + (size_t)h * (l - 1) + i),
-                                         (unsigned)(W.z + (size_t)h * (l - 1) + i), (unsigned)(K + i), 0, 0, 0});
+                                         (unsigned)(W.z + (size_t)h * (l - 1) + i), (unsigned)(K + i), 0, 0, 0, 0,
+                                         ((unsigned)h << 31) | (unsigned)i, (unsigned)((h ? W.d1 : W.d0) + i),
+                                         (unsigned)(W.ks + (size_t)h * El + K + i)});
         // rescale on its own: src offsets are relative to the input ciphertext
         for (int h = 0; h < 2; h++)
             H.rs_intt.push_back(NttJob{(unsigned)((size_t)h * l + l - 1), (unsigned)(W.r + h), (unsigned)(K + l - 1), 0,

@@ -14,7 +14,9 @@
 //  k_moddown_conv  mod down (Sec. 7): conv_i = sum_k y_k [Phat_k]_{q_i} mod q_i;
 //                  the fused variant uses constants [Phat_k P^-1]_{q_i}, giving
 //                  conv_i P^-1 directly, and folds in the rescale residue.
-//  k_combine_*     the final additions (Fig. 2) and the rescale division.
+//  k_combine_plain the final additions (Fig. 2) after a plain ModDown; with
+//                  rescale, the same combine runs in the last NTT pass of the
+//                  ModDown limbs (ntt.cu).
 //
 // Every kernel handles two consecutive coefficients per thread with 16-byte
 // loads and stores; the limb-major layouts keep all accesses coalesced.  A
@@ -289,32 +291,6 @@ k_combine_plain(const JobRef R, const ulonglong2 *__restrict__ pinv, const DevLe
     st2(it.out + ((size_t)h * l + i) * N + n, x, y);
 }
 
-// Fused ModDown + rescale: out[h][i] = (d_h[i] + KS_h[K+i] P^-1 - Z[h][i]) q_{l-1}^-1, i < l-1
-// grid: x over N/2/kThreads, y over limbs, z over 2 * jobs (h = z & 1).
-__global__ void __launch_bounds__(kThreads)
-k_combine_rescale(const JobRef R, const ulonglong2 *__restrict__ pinv, const DevLevel *__restrict__ lv_arr,
-                  const DevPrime *__restrict__ primes, int K, int N)
-{
-    const BatchItem it = job_of(R, blockIdx.z >> 1);
-    const int h = blockIdx.z & 1, l = it.level, i = blockIdx.y;
-    if (i >= l - 1) return;
-    const DevLevel &lv = lv_arr[l];
-    const int E = K + l;
-    const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
-    const DevPrime pr = primes[K + i];
-    const ulonglong2 pv = pinv[i];
-    const ulonglong2 qv = lv.qinv_last[i];
-    const u64 *d = it.ws + (size_t)(h ? lv.o_d1 : lv.o_d0) * N;
-    const u64 *KS = it.ws + (size_t)lv.o_ks * N, *Z = it.ws + (size_t)lv.o_z * N;
-    griddep_wait();
-    const ulonglong2 dv = ld2(d + (size_t)i * N + n);
-    const ulonglong2 ks = ld2(KS + ((size_t)h * E + K + i) * N + n);
-    const ulonglong2 zz = ld2(Z + ((size_t)h * (l - 1) + i) * N + n);
-    const u64 x = sub_mod(add_mod(dv.x, shoup(ks.x, pv.x, pv.y, pr.q), pr.q), zz.x, pr.q);
-    const u64 y = sub_mod(add_mod(dv.y, shoup(ks.y, pv.x, pv.y, pr.q), pr.q), zz.y, pr.q);
-    st2(it.out + ((size_t)h * (l - 1) + i) * N + n, shoup(x, qv.x, qv.y, pr.q), shoup(y, qv.x, qv.y, pr.q));
-}
-
 // Rescale on its own: out[h][i] = (c_h[i] - Z[h][i]) q_{l-1}^-1, i < l-1
 __global__ void __launch_bounds__(kThreads)
 k_rescale_combine(const u64 *__restrict__ ct, const u64 *__restrict__ Z, u64 *__restrict__ out,
@@ -510,15 +486,6 @@ cudaError_t run_combine_plain(const he_ctx *c, const JobRef &R, cudaStream_t st)
     g.y = R.lmax;
     g.z = 2 * R.B;
     launch_k(c->pdl, k_combine_plain, g, dim3(kThreads), 0, st, R, c->d_pinv, c->d_levels, c->d_primes, c->K, c->N);
-    return cudaGetLastError();
-}
-
-cudaError_t run_combine_rescale(const he_ctx *c, const JobRef &R, cudaStream_t st)
-{
-    dim3 g = grid_x(c->N);
-    g.y = R.lmax - 1;
-    g.z = 2 * R.B;
-    launch_k(c->pdl, k_combine_rescale, g, dim3(kThreads), 0, st, R, c->d_pinv, c->d_levels, c->d_primes, c->K, c->N);
     return cudaGetLastError();
 }
 

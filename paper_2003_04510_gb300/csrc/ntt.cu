@@ -29,6 +29,8 @@
 // In the strided (first forward / last inverse) pass s0 = 0 and G = 0, so
 // every tile uses twiddles [1, 2^M); in the contiguous pass the tile's groups
 // [g0, g0 + NG) use, per stage l, the run [2^(s0+l) + g0 2^l, + NG 2^l).
+#include <cstring>
+
 #include <cuda_pipeline_primitives.h>
 
 #include "he_internal.h"
@@ -49,6 +51,10 @@ struct NttArgs {
     int tiles;       // tiles per limb
     const int *count;  // optional device-side group count (grids sized for a maximum)
     bool pdl;          // launched with programmatic dependent launch
+    // fused final combine (COMBINE passes only)
+    JobRef R;
+    const DevLevel *levels;
+    const ulonglong2 *pinv;
 };
 
 // Forward (Cooley-Tukey) butterfly with no correction step: the modified
@@ -233,10 +239,11 @@ __device__ __forceinline__ size_t tile_gi(int e, int tile, int stride)
 // One pass of LOGM stages over a group of limbs.  Rounds RA, RB, RC (RC may
 // be 0) in forward order; the inverse runs them in reverse.  FIRST: read
 // group.src (else group.dst); LAST: apply the output reduction / scaling.
-template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE>
+template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE, bool COMBINE = false>
 __global__ void __launch_bounds__(TE >> cmax(RA, cmax(RB, RC)))
 k_ntt_pass(const NttArgs P)
 {
+    static_assert(!COMBINE || (LAST && !INV && !STRIDED), "the combine follows a forward contiguous last pass");
     constexpr int NT = TE >> cmax(RA, cmax(RB, RC));
     constexpr int RL = RC ? RC : RB;  // last round in forward order
     constexpr int L0 = LOGM - RL;     // its first stage
@@ -338,6 +345,27 @@ k_ntt_pass(const NttArgs P)
             ntt_round<LOGM, TE, RA, STRIDED, true, NT, false>(sm, tw, TR, 0, nq, pr.q4);
             __syncthreads();
         }
+        if (COMBINE) {
+            // out[h][ci] = (d_h[ci] + KS_h[K+ci] P^-1 - z) q_{l-1}^-1 for the job's output
+            const BatchItem it = job_item(P.R, (int)G.job[i]);
+            const int ci = (int)(G.ci[i] & 0x7fffffffu), hh = (int)(G.ci[i] >> 31);
+            const ulonglong2 pv = P.pinv[ci], qv = P.levels[it.level].qinv_last[ci];
+            u64 *o = it.out + ((size_t)hh * (it.level - 1) + ci) * N;
+            const u64 *dd = P.dst + (size_t)G.cd[i] * N, *kk = P.dst + (size_t)G.cks[i] * N;
+            for (int h = threadIdx.x; h < TE / 2; h += NT) {
+                const int e = 2 * h;
+                const size_t gi = tile_gi<LOGM, TE, STRIDED>(e, tile, stride);
+                const u64 zx = shoup(sm[padi(e)], 1, pr.r64, pr.q), zy = shoup(sm[padi(e + 1)], 1, pr.r64, pr.q);
+                const ulonglong2 dv = *reinterpret_cast<const ulonglong2 *>(dd + gi);
+                const ulonglong2 kv = *reinterpret_cast<const ulonglong2 *>(kk + gi);
+                const u64 x = sub_mod(add_mod(dv.x, shoup(kv.x, pv.x, pv.y, pr.q), pr.q), zx, pr.q);
+                const u64 y = sub_mod(add_mod(dv.y, shoup(kv.y, pv.x, pv.y, pr.q), pr.q), zy, pr.q);
+                *reinterpret_cast<ulonglong2 *>(o + gi) =
+                    make_ulonglong2(shoup(x, qv.x, qv.y, pr.q), shoup(y, qv.x, qv.y, pr.q));
+            }
+            __syncthreads();  // the next prefetch reuses this buffer
+            continue;
+        }
         // shared memory -> HBM, 16-byte stores, output reduction on the last pass
         u64 *dst = P.dst + (size_t)G.dst[i] * N;
         const u64 sc = G.scale[i], scs = G.scale_sh[i];
@@ -361,12 +389,12 @@ k_ntt_pass(const NttArgs P)
 }
 
 // ngroups == 0 only sets the kernel's shared-memory limit (no launch).
-template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE>
+template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE, bool COMBINE = false>
 cudaError_t run_pass(const NttArgs &a, int ngroups, cudaStream_t st)
 {
     constexpr int NT = TE >> cmax(RA, cmax(RB, RC));
     constexpr size_t smem = Geometry<LOGM, TE, STRIDED, (RC ? RC : RB)>::SMEM;
-    auto kern = k_ntt_pass<LOGM, RA, RB, RC, STRIDED, INV, FIRST, LAST, TE>;
+    auto kern = k_ntt_pass<LOGM, RA, RB, RC, STRIDED, INV, FIRST, LAST, TE, COMBINE>;
     static bool configured = false;  // once per instantiation
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -429,7 +457,54 @@ cudaError_t two_pass_plan(const he_ctx *c, NttArgs a, int ngroups, bool inverse,
     return two_pass<P::S1, P::A1, P::B1, P::C1, P::S2, P::A2, P::B2, P::C2>(c, a, ngroups, inverse, st, tag);
 }
 
+// Forward transform whose last pass also applies the final combine.
+template <int LOGN>
+cudaError_t combine_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag)
+{
+    using P = Plan<LOGN>;
+    constexpr int TE = 2048;
+    a.tiles = (1 << LOGN) / TE;
+    if (ngroups == 0) return run_pass<P::S2, P::A2, P::B2, P::C2, false, false, false, true, TE, true>(a, 0, st);
+    cudaError_t e = run_pass<P::S1, P::A1, P::B1, P::C1, true, false, true, false, TE>(a, ngroups, st);
+    if (e != cudaSuccess) return e;
+    prof_mark(c, st, tag, ".fwd_pass1");
+    e = run_pass<P::S2, P::A2, P::B2, P::C2, false, false, false, true, TE, true>(a, ngroups, st);
+    prof_mark(c, st, tag, ".fwd_pass2_combine");
+    return e;
+}
+
 }  // namespace
+
+cudaError_t launch_ntt_combine(const he_ctx *c, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
+                               cudaStream_t st, const char *tag, const int *dev_count)
+{
+    if (ngroups < 0) return cudaSuccess;  // ngroups == 0: configure the kernels only
+    NttArgs a;
+    a.src = base;
+    a.dst = base;
+    a.groups = groups;
+    a.primes = c->d_primes;
+    a.logN = c->logN;
+    a.tiles = 1;
+    a.count = dev_count;
+    a.pdl = c->pdl;
+    a.R = R;
+    a.levels = c->d_levels;
+    a.pinv = c->d_pinv;
+    switch (c->logN) {
+    case 12: {
+        cudaError_t e = run_pass<12, 4, 4, 4, false, false, true, true, 4096, true>(a, ngroups, st);
+        if (ngroups) prof_mark(c, st, tag, ".fwd_combine");
+        return e;
+    }
+    case 13: return combine_plan<13>(c, a, ngroups, st, tag);
+    case 14: return combine_plan<14>(c, a, ngroups, st, tag);
+    case 15: return combine_plan<15>(c, a, ngroups, st, tag);
+    case 16: return combine_plan<16>(c, a, ngroups, st, tag);
+    case 17: return combine_plan<17>(c, a, ngroups, st, tag);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups, bool inverse,
                         cudaStream_t st, const char *tag, const int *dev_count)
@@ -485,6 +560,13 @@ cudaError_t launch_ntt(const he_ctx *c, u64 *base, const NttGroup *groups, int n
 
 // Set the dynamic shared-memory limit of every NTT pass this ring size uses
 // (done once per context, before any launch or stream capture).
-cudaError_t configure_ntt(const he_ctx *c) { return launch_ntt2(c, nullptr, nullptr, nullptr, 0, false, nullptr); }
+cudaError_t configure_ntt(const he_ctx *c)
+{
+    cudaError_t e = launch_ntt2(c, nullptr, nullptr, nullptr, 0, false, nullptr);
+    if (e != cudaSuccess) return e;
+    JobRef R;
+    memset(&R, 0, sizeof(R));
+    return launch_ntt_combine(c, nullptr, nullptr, 0, R, nullptr);
+}
 
 }  // namespace he
