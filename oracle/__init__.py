@@ -89,6 +89,8 @@ def lib():
             "or_plain_ntt": (None, [i32, i32, P, P, P, P]),
             "or_mul_plain": (None, [i32, i32, P, P, P, P]),
             "or_add_plain": (None, [i32, i32, P, P, P, P]),
+            "or_seeded_a": (u64, [u64, i32, u64, u64]),
+            "or_keygen_evk_seeded": (None, [i32, i32, i32, i32, P, P, P, P, dbl, P, u64, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -219,6 +221,19 @@ def keygen_evk(prm: Params, sk: np.ndarray, seed: int) -> np.ndarray:
     lib().or_keygen_evk(prm.logN, prm.L, prm.K, prm.alpha, _p(prm.q), _p(prm.psi_q), _p(prm.p),
                         _p(prm.psi_p), prm.sigma, _p(sk), seed, _p(evk))
     return evk
+
+
+def keygen_evk_seeded(prm: Params, sk: np.ndarray, seed: int) -> np.ndarray:
+    """Evaluation key whose a halves come from the per-element counter sampler
+    (seeded_a); the full [dnum][2][K+L][N] key, b halves first."""
+    evk = np.zeros((prm.dnum, 2, prm.K + prm.L, prm.N), dtype=np.uint64)
+    lib().or_keygen_evk_seeded(prm.logN, prm.L, prm.K, prm.alpha, _p(prm.q), _p(prm.psi_q), _p(prm.p),
+                               _p(prm.psi_p), prm.sigma, _p(sk), seed, _p(evk))
+    return evk
+
+
+def seeded_a(seed: int, j: int, idx: int, t: int) -> int:
+    return int(lib().or_seeded_a(seed, j, idx, t))
 
 
 def encrypt_poly(prm: Params, pk: np.ndarray, pt: np.ndarray, level: int, seed: int) -> np.ndarray:

@@ -865,3 +865,59 @@ void or_add_plain(int logN, int l, const uint64_t *q, const uint64_t *ct, const 
             out[(size_t)l * N + o] = ct[(size_t)l * N + o];
         }
 }
+
+/* ---------------------------------------------------------------------------
+ * Seeded evaluation key (NEXT-3: halve the key's bytes).  The a halves come
+ * from a counter-based sampler that can be evaluated for any single element:
+ *   S_j            = mix64(seed + (ST_SEED_A + j + 1) gamma)   (stream state)
+ *   w1, w2         = words 2*idx and 2*idx + 1 of that stream, idx = e*N + n
+ *   a_j[e][n]      = floor((w1 * 2^64 + w2) * t / 2^128),  t = the e-th modulus
+ * (uniform up to a bias below t / 2^128; no rejection loop).  The b halves
+ * are those of or_keygen_evk with these a's:
+ *   b_j = a_j s + e_j + [t in digit j] P s^2, e_j from stream ST_EVK_E + j.
+ * Layout as evk: [dnum][2][K+L][N]; a device stores only the b halves.
+ * ------------------------------------------------------------------------- */
+enum { ST_SEED_A = 144 };
+
+uint64_t or_seeded_a(uint64_t seed, int j, uint64_t idx, uint64_t t)
+{
+    uint64_t S = mix64(seed + ((uint64_t)(ST_SEED_A + j) + 1) * SM_GAMMA);
+    uint64_t w1 = mix64(S + (2 * idx + 1) * SM_GAMMA), w2 = mix64(S + (2 * idx + 2) * SM_GAMMA);
+    u128 hi = (u128)w1 * t, lo = (u128)w2 * t;
+    return (uint64_t)((hi + (lo >> 64)) >> 64);
+}
+
+void or_keygen_evk_seeded(int logN, int L, int K, int alpha, const uint64_t *q, const uint64_t *psi_q,
+                          const uint64_t *p, const uint64_t *psi_p, double sigma, const int64_t *s,
+                          uint64_t seed, uint64_t *evk)
+{
+    or_mod M = mk_mod(logN, L, K, alpha, q, psi_q, p, psi_p);
+    uint64_t N = 1ull << logN;
+    int E = K + L, dnum = n_digits(L, alpha);
+    uint64_t *S = (uint64_t *)malloc(N * sizeof(uint64_t));
+    uint64_t *Ej = (uint64_t *)malloc(N * sizeof(uint64_t));
+    int64_t *e = (int64_t *)malloc(N * sizeof(int64_t));
+    for (int j = 0; j < dnum; j++) {
+        rng_t re = rng_open(seed, ST_EVK_E + j);
+        for (uint64_t n = 0; n < N; n++) e[n] = rng_gauss(&re, sigma);
+        uint64_t *bj = evk + ((size_t)j * 2 + 0) * E * N;
+        uint64_t *aj = evk + ((size_t)j * 2 + 1) * E * N;
+        for (int x = 0; x < E; x++) {
+            uint64_t t = ext_mod(&M, x);
+            uint64_t *a = aj + (size_t)x * N, *b = bj + (size_t)x * N;
+            for (uint64_t n = 0; n < N; n++) a[n] = or_seeded_a(seed, j, (uint64_t)x * N + n, t);
+            small_to_ntt(s, S, logN, t, ext_psi(&M, x));
+            small_to_ntt(e, Ej, logN, t, ext_psi(&M, x));
+            int in_digit = (x >= K) && (x - K) >= digit_lo(j, alpha) && (x - K) < digit_hi(j, alpha, L);
+            uint64_t Pmod = 1;
+            if (in_digit)
+                for (int k = 0; k < K; k++) Pmod = mulmod(Pmod, p[k] % t, t);
+            for (uint64_t n = 0; n < N; n++) {
+                uint64_t v = addmod(mulmod(a[n], S[n], t), Ej[n], t);
+                if (in_digit) v = addmod(v, mulmod(Pmod, mulmod(S[n], S[n], t), t), t);
+                b[n] = v;
+            }
+        }
+    }
+    free(S); free(Ej); free(e);
+}
