@@ -291,6 +291,26 @@ int he_server_stats(he_server *s, he_server_report *stats);
  * that were never launched are dropped. */
 int he_server_destroy(he_server *s);
 
+/* ---- seeded evaluation keys (no paper counterpart: halve the key's bytes) -- */
+
+/* Evaluation key whose a halves are a function of a seed: a_j[e][n] =
+ * floor((w1 2^64 + w2) t_e / 2^128), w1 and w2 the SplitMix64 words 2(eN+n)
+ * and 2(eN+n)+1 of stream 144+j of `seed` (t_e the e-th modulus, ext order);
+ * b_j = a_j s + e_j + [t_e in digit j] P s^2 as for he_keygen.  Writes only
+ * the b halves, evk_b [dnum][K+L][N] (host).  A seeded key is a different key
+ * from he_keygen's (other a halves), equally valid. */
+int he_keygen_seeded(he_ctx *ctx, uint64_t seed, const int64_t *sk, uint64_t *evk_b);
+/* Declare that the device buffer evk_b_dev holds the b halves of the seeded
+ * key of `seed` ([dnum][K+L][N]): every call of this context that receives
+ * this pointer as its evaluation key regenerates the a halves inside the
+ * inner product instead of reading them (half the key's HBM traffic and
+ * footprint).  At most 64 registered keys; registering a pointer again
+ * replaces its seed.  he_evk_unregister forgets a pointer (HE_OK if it was
+ * not registered).  Batch graphs keep the choice made when they were
+ * captured. */
+int he_evk_register_seeded(he_ctx *ctx, const uint64_t *evk_b_dev, uint64_t seed);
+int he_evk_unregister(he_ctx *ctx, const uint64_t *evk_dev);
+
 /* ---- HE Add and plaintext operations --------------------------------------- */
 
 /* HE Add (Sec. 3.2): out.b = c1.b + c2.b, out.a = c1.a + c2.a mod q_i, element

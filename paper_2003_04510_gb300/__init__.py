@@ -120,6 +120,9 @@ _SIGS = {
     "he_batch_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "he_probe_butterfly_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "he_galois_elt": (ctypes.c_uint64, [ctypes.c_void_p, ctypes.c_int]),
+    "he_keygen_seeded": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
+    "he_evk_register_seeded": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
+    "he_evk_unregister": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "he_set_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "he_get_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "he_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
@@ -400,6 +403,23 @@ def he_autotune(ctx, jobs, evk, ws, reps: int = 3, stream=None):
                              ctypes.cast(tried, ctypes.c_void_p), 64, ctypes.byref(n)), "he_autotune")
     return ((best.group_cap, best.modup_chunk, best.pdl, best.ms),
             [(t.group_cap, t.modup_chunk, t.pdl, t.ms) for t in tried[: n.value]])
+
+
+def he_keygen_seeded(ctx, seed: int, sk: np.ndarray) -> np.ndarray:
+    """b halves [dnum][K+L][N] of the seeded evaluation key of `seed`."""
+    prm = ctx.prm
+    evk_b = np.zeros((ctx.dnum, prm.K + prm.L, ctx.N), dtype=np.uint64)
+    _check(lib().he_keygen_seeded(ctx.ptr, seed, _np_ptr(np.ascontiguousarray(sk, dtype=np.int64)),
+                                  _np_ptr(evk_b)), "he_keygen_seeded")
+    return evk_b
+
+
+def he_evk_register_seeded(ctx, evk_b_dev, seed: int):
+    _check(lib().he_evk_register_seeded(ctx.ptr, _dev_ptr(evk_b_dev), seed), "he_evk_register_seeded")
+
+
+def he_evk_unregister(ctx, evk_dev):
+    _check(lib().he_evk_unregister(ctx.ptr, _dev_ptr(evk_dev)), "he_evk_unregister")
 
 
 def he_galois_elt(ctx, steps: int) -> int:

@@ -521,6 +521,35 @@ int he_profile(he_ctx *c, int enable)
     return HE_OK;
 }
 
+int he_evk_register_seeded(he_ctx *c, const uint64_t *evk_b, uint64_t seed)
+{
+    if (check_dev(c) || !evk_b || !aligned(evk_b)) return HE_EINVAL;
+    he_evk_unregister(c, evk_b);
+    if (c->seeded.size() >= 64) return HE_ENOMEM;
+    he_ctx::SeededKey k;
+    k.ptr = evk_b;
+    // stream state of digit j: word (144 + j) of the seed's SplitMix64 generator
+    for (int j = 0; j < kMaxDigits; j++) {
+        u64 z = seed + (u64)(144 + j + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        k.state[j] = z ^ (z >> 31);
+    }
+    c->seeded.push_back(k);
+    return HE_OK;
+}
+
+int he_evk_unregister(he_ctx *c, const uint64_t *evk)
+{
+    if (!c || !evk) return HE_EINVAL;
+    for (size_t i = 0; i < c->seeded.size(); i++)
+        if (c->seeded[i].ptr == evk) {
+            c->seeded.erase(c->seeded.begin() + (long)i);
+            return HE_OK;
+        }
+    return HE_OK;
+}
+
 int he_set_shape(he_ctx *c, const he_shape *sh)
 {
     if (!c || !sh) return HE_EINVAL;

@@ -141,6 +141,13 @@ struct he_ctx {
     const ulonglong2 *d_pinv = nullptr;
     std::vector<he::DevLevel> dev_levels;  // index l (host copy of the device structs)
     he::DevLevel *d_levels = nullptr;      // [L+1]
+    // evaluation keys stored as b halves only (he_evk_register_seeded): the
+    // device pointer and the SplitMix64 stream state of each digit's a halves
+    struct SeededKey {
+        const u64 *ptr;
+        u64 state[he::kMaxDigits];
+    };
+    std::vector<SeededKey> seeded;
     std::vector<he::LevelJobs> jobs;       // index l: the lists of group_cap
     std::vector<he::LevelJobs> jobs_cap[he::kGroupMax];  // [cap-1][l]: every cap's lists
     // optional per-kernel event marks (he_profile); consecutive marks on one

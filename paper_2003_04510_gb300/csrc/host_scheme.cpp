@@ -68,7 +68,7 @@ struct Stream {
 };
 
 enum { kSk = 1, kPkA = 2, kPkE = 3, kEncU = 4, kEncE0 = 5, kEncE1 = 6, kEvkA = 16, kEvkE = 48,
-       kRotA = 80, kRotE = 112 };
+       kRotA = 80, kRotE = 112, kSeedA = 144 };
 
 inline u64 lift(int64_t v, u64 m)
 {
@@ -194,6 +194,38 @@ void make_switch_key(const he_ctx *c, u64 seed, const int64_t *s, const int64_t 
     }
 }
 
+// Seeded evaluation key: b halves only, with a_j[e][n] = floor((w1 2^64 + w2)
+// t / 2^128), w1 and w2 words 2(eN+n) and 2(eN+n)+1 of stream kSeedA + j.
+void make_seeded_evk(const he_ctx *c, u64 seed, const int64_t *s, u64 *evk_b)
+{
+    const int N = c->N, L = c->L, K = c->K, E = c->E;
+    std::vector<u64> S(N), Er(N);
+    std::vector<int64_t> err(N);
+    for (int j = 0; j < c->dnum; j++) {
+        Stream se(seed, kEvkE + j), sa(seed, kSeedA + j);
+        for (int k = 0; k < N; k++) err[k] = se.gauss(c->prm.sigma);
+        const int lo = j * c->alpha, hi = std::min((j + 1) * c->alpha, L);
+        for (int e = 0; e < E; e++) {
+            const u64 t = c->ext[e];
+            u64 *b = evk_b + ((size_t)j * E + e) * N;
+            small_ntt(c, e, s, S.data());
+            small_ntt(c, e, err.data(), Er.data());
+            const bool gadget = e >= K && (e - K) >= lo && (e - K) < hi;
+            u64 Pm = 1;
+            for (int k = 0; k < K && gadget; k++) Pm = mul(Pm, c->ext[k] % t, t);
+            for (int k = 0; k < N; k++) {
+                const u64 idx = (u64)e * N + k;
+                const u64 w1 = mix(sa.s + (2 * idx + 1) * kGamma), w2 = mix(sa.s + (2 * idx + 2) * kGamma);
+                const u128 hiw = (u128)w1 * t, low = (u128)w2 * t;
+                const u64 a = (u64)((hiw + (low >> 64)) >> 64);
+                u64 v = add(mul(a, S[k], t), Er[k], t);
+                if (gadget) v = add(v, mul(Pm, mul(S[k], S[k], t), t), t);
+                b[k] = v;
+            }
+        }
+    }
+}
+
 // a(X) -> a(X^g) mod X^N + 1 on a small signed polynomial
 void small_automorphism(int N, const int64_t *a, u64 g, int64_t *out)
 {
@@ -286,6 +318,13 @@ uint64_t he_galois_elt(const he_ctx *c, int steps)
     u64 g = 1;
     for (u64 k = 0; k < e; k++) g = g * 5 % twoN;
     return g;
+}
+
+int he_keygen_seeded(he_ctx *c, uint64_t seed, const int64_t *sk, uint64_t *evk_b)
+{
+    if (!c || !sk || !evk_b) return HE_EINVAL;
+    make_seeded_evk(c, seed, sk, evk_b);
+    return HE_OK;
 }
 
 int he_keygen_rot(he_ctx *c, uint64_t seed, const int64_t *sk, uint64_t galois, uint64_t *rk)

@@ -24,6 +24,7 @@
 // bringing its own operands, workspace and level (JobRef); blocks beyond a
 // job's level exit at once.
 #include <algorithm>
+#include <cstring>
 
 #include "he_internal.h"
 #include "modarith.cuh"
@@ -127,13 +128,36 @@ k_modup(const JobRef R, const DevLevel *__restrict__ lv_arr, const DevPrime *__r
 }
 
 // grid: x over N/2/kThreads, y over ext limbs (up to K + lmax), z over jobs.
-// U: [beta][E][N] (own-digit rows read from d2), evk: [dnum][2][K+L][N],
-// KS: [2][E][N].  The digit loop is unrolled to BM >= beta with guards, so
-// every operand load of a thread is issued before the first product.
-template <int BM>
+// Seeded evaluation key: a_j[e][n] = floor((w1 2^64 + w2) t / 2^128) with
+// w1, w2 the SplitMix64 words 2(eN+n) and 2(eN+n)+1 of digit j's stream
+// (state S_j): any element is computed on its own.
+struct SeedStates {
+    u64 s[kMaxDigits];
+};
+
+__device__ __forceinline__ u64 splitmix_word(u64 state, u64 i)
+{
+    u64 z = state + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ u64 seeded_a(u64 state, u64 idx, u64 t)
+{
+    const u64 w1 = splitmix_word(state, 2 * idx), w2 = splitmix_word(state, 2 * idx + 1);
+    const u64 lo = w1 * t, hi = __umul64hi(w1, t), sum = lo + __umul64hi(w2, t);
+    return hi + (sum < lo ? 1ull : 0ull);
+}
+
+// U: [beta][E][N] (own-digit rows read from d2), evk: [dnum][2][K+L][N]
+// (SEEDED: [dnum][K+L][N], b halves only, a halves regenerated), KS: [2][E][N].
+// The digit loop is unrolled to BM >= beta with guards, so every operand
+// load of a thread is issued before the first product.
+template <int BM, bool SEEDED>
 __global__ void __launch_bounds__(kThreads)
 k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__restrict__ lv_arr,
-                const DevPrime *__restrict__ primes, int K, int L, int N)
+                const DevPrime *__restrict__ primes, int K, int L, int N, const SeedStates seeds)
 {
     const BatchItem it = job_of(R, blockIdx.z);
     const DevLevel &lv = lv_arr[it.level];
@@ -152,8 +176,14 @@ k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__r
             const bool own = e >= K && e - K >= lo && e - K < lo + nj;
             const u64 *up = own ? d2 + (size_t)(e - K) * N : U + ((size_t)j * E + e) * N;
             u[j] = ld2(up + n);
-            kb[j] = ld2(evk + ((size_t)(2 * j) * EL + e) * N + n);
-            ka[j] = ld2(evk + ((size_t)(2 * j + 1) * EL + e) * N + n);
+            if (SEEDED) {
+                kb[j] = ld2(evk + ((size_t)j * EL + e) * N + n);
+                const u64 idx = (u64)e * (u64)N + n;
+                ka[j] = make_ulonglong2(seeded_a(seeds.s[j], idx, pr.q), seeded_a(seeds.s[j], idx + 1, pr.q));
+            } else {
+                kb[j] = ld2(evk + ((size_t)(2 * j) * EL + e) * N + n);
+                ka[j] = ld2(evk + ((size_t)(2 * j + 1) * EL + e) * N + n);
+            }
         }
     }
     U128 bx = {0, 0}, by = {0, 0}, ax = {0, 0}, ay = {0, 0};
@@ -444,7 +474,23 @@ cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, 
     g.y = c->K + R.lmax;
     g.z = R.B;
     const int bm = (c->L + c->alpha - 1) / c->alpha;  // the most digits any level has
-#define HE_IP(B) launch_k(c->pdl, k_inner_product<B>, g, dim3(kThreads), 0, st, R, evk, c->d_levels, c->d_primes, c->K, c->L, c->N)
+    SeedStates ss;
+    memset(&ss, 0, sizeof(ss));
+    bool seeded = false;
+    for (const auto &k : c->seeded)
+        if (k.ptr == evk) {
+            seeded = true;
+            memcpy(ss.s, k.state, sizeof(ss.s));
+        }
+#define HE_IP(B)                                                                                                     \
+    do {                                                                                                             \
+        if (seeded)                                                                                                  \
+            launch_k(c->pdl, k_inner_product<B, true>, g, dim3(kThreads), 0, st, R, evk, c->d_levels, c->d_primes,   \
+                     c->K, c->L, c->N, ss);                                                                          \
+        else                                                                                                         \
+            launch_k(c->pdl, k_inner_product<B, false>, g, dim3(kThreads), 0, st, R, evk, c->d_levels, c->d_primes,  \
+                     c->K, c->L, c->N, ss);                                                                          \
+    } while (0)
     if (bm <= 2) HE_IP(2);
     else if (bm <= 4) HE_IP(4);
     else if (bm <= 8) HE_IP(8);

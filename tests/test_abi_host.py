@@ -119,6 +119,15 @@ def test_host_plaintext_ntt_matches_oracle(g):
             assert np.array_equal(g.he_plain_ntt(ctx, t, level), oracle.plain_ntt(op, t, level))
 
 
+def test_host_seeded_key_matches_oracle_n12(g):
+    name = "n12"
+    ctx = g.Context(g.PRESETS[name][0], device=False)
+    op = oracle.preset(name)
+    sk = oracle.keygen_sk(op, si.SEEDS[name][0])
+    full = oracle.keygen_evk_seeded(op, sk, 4242)
+    assert np.array_equal(g.he_keygen_seeded(ctx, 4242, sk), full[:, 0])
+
+
 def test_shape_setters(g):
     ctx = g.Context(g.PRESETS["n12"][0], device=False)
     assert g.he_get_shape(ctx) == (4, 8, 1)

@@ -576,3 +576,43 @@ def test_autotune_batch_keeps_results(g):
             assert np.array_equal(host(g, j[2]), w)
     finally:
         g.he_set_shape(ctx, 4, 8, 1)
+
+
+
+# ---------------------------------------------------------------------------
+# seeded evaluation key: b halves on the device, a halves regenerated
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,levels", [("n12", (3, 2)), ("n16", (24, 9))])
+def test_seeded_key_he_mul_bit_exact(g, name, levels):
+    import torch
+    op, sc, sk, pk, evk, m1, m2, ct1, ct2 = real_inputs(name)
+    ctx = ctx_for(g, name)
+    seed = 5150
+    full = oracle.keygen_evk_seeded(op, sk, seed)
+    evk_b = dev(g, np.ascontiguousarray(full[:, 0]))
+    g.he_evk_register_seeded(ctx, evk_b, seed)
+    try:
+        for level in levels:
+            c1 = np.ascontiguousarray(np.stack([ct1[0, :level], ct1[1, :level]]))
+            c2 = np.ascontiguousarray(np.stack([ct2[0, :level], ct2[1, :level]]))
+            want = oracle.he_mul(op, c1, c2, full, level)
+            assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_b, level, fused=False), want), level
+            got = gpu_mul(g, ctx, c1, c2, evk_b, level, fused=True)
+            assert np.array_equal(got, oracle.rescale(op, want, level)), level
+        z = oracle.decrypt(op, sk, got, levels[-1] - 1, sc * sc / int(op.q[levels[-1] - 1]))
+        assert np.abs(z - m1 * m2).max() < (2.0 ** -14 if name == "n12" else 2.0 ** -24)
+        # the same jobs batched
+        jobs, want = [], []
+        for level in levels:
+            c1 = np.ascontiguousarray(np.stack([ct1[0, :level], ct1[1, :level]]))
+            c2 = np.ascontiguousarray(np.stack([ct2[0, :level], ct2[1, :level]]))
+            jobs.append((dev(g, c1), dev(g, c2), torch.empty((2, level - 1, op.N), dtype=torch.int64, device="cuda"),
+                         level))
+            want.append(oracle.rescale(op, oracle.he_mul(op, c1, c2, full, level), level))
+        ws = torch.empty(g.he_batch_workspace_bytes(ctx, list(levels)) // 8, dtype=torch.int64, device="cuda")
+        g.he_mul_batch(ctx, jobs, evk_b, ws)
+        torch.cuda.synchronize()
+        for j, w in zip(jobs, want):
+            assert np.array_equal(host(g, j[2]), w)
+    finally:
+        g.he_evk_unregister(ctx, evk_b)
