@@ -352,16 +352,27 @@ k_ntt_pass(const NttArgs P)
             const ulonglong2 pv = P.pinv[ci], qv = P.levels[it.level].qinv_last[ci];
             u64 *o = it.out + ((size_t)hh * (it.level - 1) + ci) * N;
             const u64 *dd = P.dst + (size_t)G.cd[i] * N, *kk = P.dst + (size_t)G.cks[i] * N;
-            for (int h = threadIdx.x; h < TE / 2; h += NT) {
-                const int e = 2 * h;
-                const size_t gi = tile_gi<LOGM, TE, STRIDED>(e, tile, stride);
-                const u64 zx = shoup(sm[padi(e)], 1, pr.r64, pr.q), zy = shoup(sm[padi(e + 1)], 1, pr.r64, pr.q);
-                const ulonglong2 dv = *reinterpret_cast<const ulonglong2 *>(dd + gi);
-                const ulonglong2 kv = *reinterpret_cast<const ulonglong2 *>(kk + gi);
-                const u64 x = sub_mod(add_mod(dv.x, shoup(kv.x, pv.x, pv.y, pr.q), pr.q), zx, pr.q);
-                const u64 y = sub_mod(add_mod(dv.y, shoup(kv.y, pv.x, pv.y, pr.q), pr.q), zy, pr.q);
-                *reinterpret_cast<ulonglong2 *>(o + gi) =
-                    make_ulonglong2(shoup(x, qv.x, qv.y, pr.q), shoup(y, qv.x, qv.y, pr.q));
+            // four pairs per step: their d and KS loads are all in flight before the first product
+            constexpr int PAIRS = TE / 2 / NT, B4 = PAIRS >= 4 ? 4 : PAIRS;
+            static_assert(PAIRS % B4 == 0, "pairs per thread");
+            for (int b0 = 0; b0 < PAIRS; b0 += B4) {
+                ulonglong2 dv[B4], kv[B4];
+#pragma unroll
+                for (int k = 0; k < B4; k++) {
+                    const size_t gi = tile_gi<LOGM, TE, STRIDED>(2 * (threadIdx.x + (b0 + k) * NT), tile, stride);
+                    dv[k] = __ldg(reinterpret_cast<const ulonglong2 *>(dd + gi));
+                    kv[k] = __ldg(reinterpret_cast<const ulonglong2 *>(kk + gi));
+                }
+#pragma unroll
+                for (int k = 0; k < B4; k++) {
+                    const int e = 2 * (threadIdx.x + (b0 + k) * NT);
+                    const size_t gi = tile_gi<LOGM, TE, STRIDED>(e, tile, stride);
+                    const u64 zx = shoup(sm[padi(e)], 1, pr.r64, pr.q), zy = shoup(sm[padi(e + 1)], 1, pr.r64, pr.q);
+                    const u64 x = sub_mod(add_mod(dv[k].x, shoup(kv[k].x, pv.x, pv.y, pr.q), pr.q), zx, pr.q);
+                    const u64 y = sub_mod(add_mod(dv[k].y, shoup(kv[k].y, pv.x, pv.y, pr.q), pr.q), zy, pr.q);
+                    *reinterpret_cast<ulonglong2 *>(o + gi) =
+                        make_ulonglong2(shoup(x, qv.x, qv.y, pr.q), shoup(y, qv.x, qv.y, pr.q));
+                }
             }
             __syncthreads();  // the next prefetch reuses this buffer
             continue;
