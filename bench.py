@@ -249,22 +249,27 @@ def kernel_work(name: str, prm, level: int):
 
 
 def committed_traffic(kernel: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None
-    when the kernel source changed after the capture (its sha256 prefix differs)."""
+    """Per-launch DRAM bytes of `kernel` (a name of the bench's event profile)
+    from a committed ncu summary under profiles/ that names it ("bench kernel:
+    <name>") with "traffic_bytes_per_launch | <bytes>", or None when no summary
+    covers it or the source file it names changed after the capture (sha256
+    prefix)."""
+    import glob
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", "ntt_fwd_contig_n16.md")
-    src = os.path.join(ROOT, "paper_2003_04510_gb300", "csrc", "ntt.cu")
-    if kernel != "ntt_modup.fwd_pass2" or not os.path.exists(path):
-        return None
-    txt = open(path).read()
-    m = re.search(r"sha256 prefix ([0-9a-f]{16})", txt)
-    t = re.search(r"traffic_bytes_per_launch \| (\d+)", txt)
-    if not m or not t:
-        return None
-    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != m.group(1):
-        return None
-    return int(t.group(1))
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        txt = open(path).read()
+        for m in re.finditer(r"bench kernel: ([\w.]+) \| source (\S+) sha256 prefix ([0-9a-f]{16}) \| "
+                             r"traffic_bytes_per_launch (\d+)", txt):
+            if m.group(1) != kernel:
+                continue
+            src = os.path.join(ROOT, m.group(2))
+            if not os.path.exists(src):
+                return None
+            if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != m.group(3):
+                return None
+            return int(m.group(4))
+    return None
 
 
 def run_batched(g, ctx, evk_t, dev, stream, wsz, count=64, reps=20):
@@ -414,8 +419,14 @@ def run_ours(args):
         g.he_mul_rescale(ctx, a, b, evk_t, level, outs[k % NPAIRS], ws, stream)
 
     # launch shapes picked by the library's autotuner for this single HE Mul
-    tune_best, tune_tried = g.he_autotune(ctx, [(ct_t[0][0], ct_t[0][1], outs[0], level)], evk_t, ws, reps=20,
-                                          stream=stream)
+    # (or fixed by --shape, e.g. for a profiler run)
+    if args.shape:
+        cap, chunk, pdl = (int(v) for v in args.shape.split(","))
+        g.he_set_shape(ctx, cap, chunk, pdl)
+        tune_best, tune_tried = (cap, chunk, pdl, 0.0), []
+    else:
+        tune_best, tune_tried = g.he_autotune(ctx, [(ct_t[0][0], ct_t[0][1], outs[0], level)], evk_t, ws, reps=20,
+                                              stream=stream)
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
@@ -595,16 +606,18 @@ def run_ours(args):
                     "peak_source": "measured: the NTT's own butterfly on register-resident data "
                                    "(he_probe_butterfly_rate), same clocks, same run"}
         elif kind == "mac":
-            # one base-conversion MAC is four 32x32->64 multiply-adds; the
-            # butterfly probe's Shoup product is ten multiplies
+            # one Karatsuba base-conversion MAC is three 32x32->64 multiply-adds;
+            # the probe's butterfly costs seven in wide-multiply units (five
+            # wide products plus four 32-bit ones at half the cost)
             ach = work / avg_s / 1e9
-            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": 2.5 * bfly_peak / 1e9,
-                    "unit": "GMAC/s", "frac": ach / (2.5 * bfly_peak / 1e9), "traffic": None,
-                    "peak_source": "derived: 2.5 x measured butterfly probe rate (multiply count ratio 10:4)"}
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": 7.0 / 3.0 * bfly_peak / 1e9,
+                    "unit": "GMAC/s", "frac": ach / (7.0 / 3.0 * bfly_peak / 1e9), "traffic": committed_traffic(dom),
+                    "peak_source": "derived: 7/3 x measured butterfly probe rate (wide-multiply count ratio)"}
         elif kind == "hbm":
             ach = work / avg_s / 1e9
             roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": ach / hbm_peak, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+                    "frac": ach / hbm_peak, "traffic": committed_traffic(dom),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
     # HBM view of the key-switch inner product (the evk stream)
     ip = None
     if "inner_product" in per_kernel:
@@ -680,6 +693,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-rotate", action="store_true")
+    ap.add_argument("--shape", default="", help="fixed launch shape CAP,CHUNK,PDL instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
