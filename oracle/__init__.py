@@ -91,6 +91,12 @@ def lib():
             "or_add_plain": (None, [i32, i32, P, P, P, P]),
             "or_seeded_a": (u64, [u64, i32, u64, u64]),
             "or_keygen_evk_seeded": (None, [i32, i32, i32, i32, P, P, P, P, dbl, P, u64, P]),
+            "or_nr_polymul": (None, [i32, i32, P, P, P, i32, P, i32, P, i32, P]),
+            "or_nr_he_mul": (None, [i32, i32, i32, i32, i32, P, P, P, P, P, P]),
+            "or_nr_rescale": (None, [i32, i32, i32, P, P]),
+            "or_nr_keygen": (None, [i32, i32, i32, P, P, dbl, P, u64, P, P]),
+            "or_nr_encrypt": (None, [i32, i32, i32, i32, P, P, dbl, P, P, u64, P]),
+            "or_nr_decrypt": (None, [i32, i32, i32, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -406,3 +412,124 @@ def decrypt(prm: Params, sk, ct, level: int, scale: float) -> np.ndarray:
     m = decrypt_residues(prm, sk, ct, level)
     coeffs = crt_centered(m, prm.q[:level])
     return decode(np.array([float(c) for c in coeffs]) / scale, prm.logN)
+
+
+# --------------------------------------------------------------------------
+# NEXT-2: the paper's non-RNS HEAAN HE Mul (BigInt coefficients modulo powers
+# of two; CRT / NTT / iCRT polynomial products).  Word-major BigInt arrays:
+# a[w][n] = word w of coefficient n, little-endian, ceil(k/64) words.
+# --------------------------------------------------------------------------
+@dataclass
+class NrParams:
+    logN: int
+    logQ: int         # top modulus Q = 2^logQ (fresh ciphertexts at logq = logQ)
+    logp: int         # rescaling factor p = 2^logp (= the scaling factor Delta)
+    np1: int          # primes of a ciphertext x ciphertext product (region 1)
+    np2: int          # primes of a ciphertext x evaluation-key product (region 2)
+    h: int = 64
+    sigma: float = 3.2
+    primes: np.ndarray = field(default=None, repr=False)
+    psis: np.ndarray = field(default=None, repr=False)
+
+    @property
+    def N(self) -> int:
+        return 1 << self.logN
+
+
+def nwords(k: int) -> int:
+    return (k + 63) // 64
+
+
+def nr_params(logN: int, logQ: int, logp: int, prime_bits: int = 57, h: int = 64) -> NrParams:
+    """np from the product bounds: P > 4 N 2^(2 logQ) (region 1 and key
+    generation) and P > 4 N 2^(3 logQ) (region 2); primes are the largest
+    prime_bits-bit primes = 1 mod 2N, descending, with their smallest roots."""
+    import math
+    cand = np.zeros(96, dtype=np.uint64)
+    rc = lib().or_gen_primes(logN, prime_bits, len(cand), None, 0, _p(cand))
+    assert rc == 0
+
+    def count(bits):  # fewest leading primes whose product exceeds 2^bits
+        tot = 0.0
+        for i, q in enumerate(cand):
+            tot += math.log2(int(q))
+            if tot > bits:
+                return i + 1
+        raise ValueError("not enough primes")
+
+    np1 = count(2 * logQ + logN + 2)
+    np2 = count(3 * logQ + logN + 2)
+    primes = np.ascontiguousarray(cand[:np2])
+    psis = np.array([lib().or_min_psi(int(q), logN) for q in primes], dtype=np.uint64)
+    return NrParams(logN, logQ, logp, np1, np2, h, 3.2, primes, psis)
+
+
+def nr_polymul(prm: NrParams, A, wa: int, B, wb: int, kout: int, small=None, np_: int = None) -> np.ndarray:
+    out = np.zeros((nwords(kout), prm.N), dtype=np.uint64)
+    npr = np_ or prm.np2
+    lib().or_nr_polymul(prm.logN, npr, _p(prm.primes), _p(prm.psis), _p(_u64(A)), wa,
+                        _p(_u64(B)) if B is not None else None, wb,
+                        _p(np.ascontiguousarray(small, dtype=np.int64)) if small is not None else None, kout, _p(out))
+    return out
+
+
+def nr_keygen(prm: NrParams, sk, seed: int):
+    pk = np.zeros((2, nwords(prm.logQ), prm.N), dtype=np.uint64)
+    evk = np.zeros((2, nwords(2 * prm.logQ), prm.N), dtype=np.uint64)
+    lib().or_nr_keygen(prm.logN, prm.logQ, prm.np1, _p(prm.primes), _p(prm.psis), prm.sigma,
+                       _p(np.ascontiguousarray(sk, dtype=np.int64)), seed, _p(pk), _p(evk))
+    return pk, evk
+
+
+def nr_encrypt(prm: NrParams, pk, pt, logq: int, seed: int) -> np.ndarray:
+    ct = np.zeros((2, nwords(logq), prm.N), dtype=np.uint64)
+    lib().or_nr_encrypt(prm.logN, logq, prm.logQ, prm.np1, _p(prm.primes), _p(prm.psis), prm.sigma, _p(_u64(pk)),
+                        _p(np.ascontiguousarray(pt, dtype=np.int64)), seed, _p(ct))
+    return ct
+
+
+def nr_decrypt_coeffs(prm: NrParams, sk, ct, logq: int) -> np.ndarray:
+    m = np.zeros(prm.N, dtype=np.float64)
+    lib().or_nr_decrypt(prm.logN, logq, prm.np1, _p(prm.primes), _p(prm.psis),
+                        _p(np.ascontiguousarray(sk, dtype=np.int64)), _p(_u64(ct)), _p(m))
+    return m
+
+
+def nr_decrypt(prm: NrParams, sk, ct, logq: int, scale: float) -> np.ndarray:
+    from .encoding import decode
+    return decode(nr_decrypt_coeffs(prm, sk, ct, logq) / scale, prm.logN)
+
+
+def nr_he_mul(prm: NrParams, ct1, ct2, evk, logq: int) -> np.ndarray:
+    out = np.zeros((2, nwords(logq), prm.N), dtype=np.uint64)
+    lib().or_nr_he_mul(prm.logN, logq, prm.logQ, prm.np1, prm.np2, _p(prm.primes), _p(prm.psis), _p(_u64(ct1)),
+                       _p(_u64(ct2)), _p(_u64(evk)), _p(out))
+    return out
+
+
+def nr_rescale(prm: NrParams, ct, logq: int) -> np.ndarray:
+    out = np.zeros((2, nwords(logq - prm.logp), prm.N), dtype=np.uint64)
+    lib().or_nr_rescale(prm.logN, logq, prm.logp, _p(_u64(ct)), _p(out))
+    return out
+
+
+def words_to_ints(a: np.ndarray, k: int) -> list[int]:
+    """Word-major [W][N] -> Python ints (unsigned, < 2^k)."""
+    W, N = a.shape
+    out = []
+    for n in range(N):
+        v = 0
+        for w in range(W - 1, -1, -1):
+            v = (v << 64) | int(a[w, n])
+        out.append(v % (1 << k))
+    return out
+
+
+def ints_to_words(vals, k: int) -> np.ndarray:
+    W = nwords(k)
+    a = np.zeros((W, len(vals)), dtype=np.uint64)
+    for n, v in enumerate(vals):
+        v %= 1 << k
+        for w in range(W):
+            a[w, n] = (v >> (64 * w)) & ((1 << 64) - 1)
+    return a

@@ -921,3 +921,367 @@ void or_keygen_evk_seeded(int logN, int L, int K, int alpha, const uint64_t *q, 
     }
     free(S); free(Ej); free(e);
 }
+
+/* ===========================================================================
+ * NEXT-2: the paper's own (non-RNS) HEAAN HE Mul.
+ *
+ * Ciphertext and key coefficients are BigInts modulo powers of two (Sec. 3,
+ * Table 3: q = 2^logq, Q = 2^logQ, p = 2^logp), stored word-major: word w of
+ * coefficient n at a[w * N + n], W = ceil(k / 64) words for a k-bit modulus,
+ * little-endian, the top word holding k - 64 (W - 1) bits.  A polynomial
+ * product goes through the paper's five steps (Fig. 2, Sec. 4): CRT (BigInt
+ * -> residues mod np primes p_i, P = prod p_i), NTT, element-wise products,
+ * iNTT, iCRT (residues -> BigInt).  The iCRT here is exact: X = sum_i
+ * [x_i Phat_i^-1]_{p_i} Phat_i as a multiword integer, reduced mod P by
+ * subtraction, taken as the centred representative (P exceeds four times the
+ * product's magnitude) and truncated to the output modulus.
+ * ======================================================================== */
+#define MW_MAX 96 /* words of a multiword integer in the iCRT */
+
+static int nwords(int k) { return (k + 63) / 64; }
+
+/* X mod p for the word-major coefficient n of a (w words) */
+static uint64_t mw_mod(const uint64_t *a, int w, uint64_t N, uint64_t n, uint64_t p)
+{
+    u128 r = 0;
+    for (int i = w - 1; i >= 0; i--) r = ((r << 64) | a[(size_t)i * N + n]) % p;
+    return (uint64_t)r;
+}
+
+/* acc (len words) += v * b (nb words) */
+static void mw_mac(uint64_t *acc, int len, uint64_t v, const uint64_t *b, int nb)
+{
+    u128 carry = 0;
+    for (int i = 0; i < len; i++) {
+        u128 t = (u128)acc[i] + carry + (i < nb ? (u128)v * b[i] : 0);
+        acc[i] = (uint64_t)t;
+        carry = t >> 64;
+    }
+}
+static int mw_cmp(const uint64_t *a, const uint64_t *b, int len)
+{
+    for (int i = len - 1; i >= 0; i--)
+        if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
+    return 0;
+}
+static void mw_sub(uint64_t *a, const uint64_t *b, int len) /* a -= b (mod 2^(64 len)) */
+{
+    uint64_t borrow = 0;
+    for (int i = 0; i < len; i++) {
+        u128 t = (u128)a[i] - b[i] - borrow;
+        a[i] = (uint64_t)t;
+        borrow = (uint64_t)(t >> 64) ? 1 : 0;
+    }
+}
+static void mw_shr1(uint64_t *a, int len)
+{
+    for (int i = 0; i < len; i++) a[i] = (a[i] >> 1) | (i + 1 < len ? a[i + 1] << 63 : 0);
+}
+
+/* The CRT tables of np primes: Phat_i (multiword), [Phat_i^-1]_{p_i}, P, P/2. */
+typedef struct {
+    int np, len;
+    uint64_t p[MW_MAX], psi[MW_MAX], phinv[MW_MAX];
+    uint64_t Phat[MW_MAX][MW_MAX], P[MW_MAX], Phalf[MW_MAX];
+} crt_t;
+
+static void crt_init(crt_t *T, int np, const uint64_t *p, const uint64_t *psi)
+{
+    memset(T, 0, sizeof(*T));
+    T->np = np;
+    T->len = np + 2;
+    for (int i = 0; i < np; i++) {
+        T->p[i] = p[i];
+        T->psi[i] = psi[i];
+    }
+    T->P[0] = 1;
+    for (int i = 0; i < np; i++) {
+        uint64_t t[MW_MAX] = {0};
+        mw_mac(t, T->len, p[i], T->P, T->len);
+        memcpy(T->P, t, sizeof(t));
+    }
+    for (int i = 0; i < np; i++) {
+        T->Phat[i][0] = 1;
+        for (int j = 0; j < np; j++)
+            if (j != i) {
+                uint64_t t[MW_MAX] = {0};
+                mw_mac(t, T->len, p[j], T->Phat[i], T->len);
+                memcpy(T->Phat[i], t, sizeof(t));
+            }
+        uint64_t r = 0; /* Phat_i mod p_i */
+        for (int w = T->len - 1; w >= 0; w--) r = (uint64_t)((((u128)r << 64) | T->Phat[i][w]) % p[i]);
+        T->phinv[i] = invmod(r, p[i]);
+    }
+    memcpy(T->Phalf, T->P, sizeof(T->P));
+    mw_shr1(T->Phalf, T->len);
+}
+
+/* C = A * B mod (X^N + 1, 2^kout).  A: wa words per coefficient (unsigned);
+ * B: wb words (unsigned), or, when bs != NULL, the small signed polynomial bs.
+ * The primes must satisfy P > 4 N max|A| max|B|. */
+static void nr_polymul(int logN, const crt_t *T, const uint64_t *A, int wa, const uint64_t *B, int wb,
+                       const int64_t *bs, int kout, uint64_t *C)
+{
+    uint64_t N = 1ull << logN;
+    int np = T->np, wo = nwords(kout);
+    uint64_t *ra = (uint64_t *)malloc(N * sizeof(uint64_t)), *rb = (uint64_t *)malloc(N * sizeof(uint64_t));
+    uint64_t *Y = (uint64_t *)malloc((size_t)np * N * sizeof(uint64_t));
+    for (int i = 0; i < np; i++) {
+        uint64_t p = T->p[i];
+        for (uint64_t n = 0; n < N; n++) {
+            ra[n] = mw_mod(A, wa, N, n, p);
+            rb[n] = bs ? (bs[n] >= 0 ? (uint64_t)bs[n] % p : submod(0, (uint64_t)(-bs[n]), p)) : mw_mod(B, wb, N, n, p);
+        }
+        or_ntt(ra, logN, p, T->psi[i]);
+        or_ntt(rb, logN, p, T->psi[i]);
+        for (uint64_t n = 0; n < N; n++) ra[n] = mulmod(ra[n], rb[n], p);
+        or_intt(ra, logN, p, T->psi[i]);
+        for (uint64_t n = 0; n < N; n++) Y[(size_t)i * N + n] = mulmod(ra[n], T->phinv[i], p);
+    }
+    for (uint64_t n = 0; n < N; n++) {
+        uint64_t X[MW_MAX] = {0};
+        for (int i = 0; i < np; i++) mw_mac(X, T->len, Y[(size_t)i * N + n], T->Phat[i], T->len);
+        while (mw_cmp(X, T->P, T->len) >= 0) mw_sub(X, T->P, T->len);
+        if (mw_cmp(X, T->Phalf, T->len) > 0) mw_sub(X, T->P, T->len); /* negative: two's complement */
+        for (int w = 0; w < wo; w++) {
+            uint64_t v = w < T->len ? X[w] : (X[T->len - 1] >> 63 ? ~0ull : 0);
+            if (w == wo - 1 && (kout & 63)) v &= (1ull << (kout & 63)) - 1;
+            C[(size_t)w * N + n] = v;
+        }
+    }
+    free(ra); free(rb); free(Y);
+}
+
+/* out = (a + b) mod 2^k and out = (a - b) mod 2^k, word-major, w = nwords(k) */
+static void nr_addsub(uint64_t N, int k, const uint64_t *a, const uint64_t *b, int sub, uint64_t *out)
+{
+    int w = nwords(k);
+    for (uint64_t n = 0; n < N; n++) {
+        uint64_t c = 0;
+        for (int i = 0; i < w; i++) {
+            size_t o = (size_t)i * N + n;
+            u128 t = sub ? (u128)a[o] - b[o] - c : (u128)a[o] + b[o] + c;
+            out[o] = (uint64_t)t;
+            c = sub ? ((uint64_t)(t >> 64) ? 1 : 0) : (uint64_t)(t >> 64);
+        }
+        if (k & 63) out[(size_t)(w - 1) * N + n] &= (1ull << (k & 63)) - 1;
+    }
+}
+
+/* out = floor((a + 2^(s-1)) / 2^s) mod 2^kout: the division by a power of
+ * two with rounding (rescale by p = 2^logp, and the key switch's division by
+ * Q = 2^logQ).  a: nwords(kin) words. */
+static void nr_shift_round(uint64_t N, const uint64_t *a, int kin, int s, int kout, uint64_t *out)
+{
+    int wi = nwords(kin), wo = nwords(kout);
+    uint64_t t[MW_MAX + 1];
+    for (uint64_t n = 0; n < N; n++) {
+        memset(t, 0, sizeof(t));
+        for (int i = 0; i < wi; i++) t[i] = a[(size_t)i * N + n];
+        uint64_t half[MW_MAX + 1] = {0};
+        half[(s - 1) / 64] = 1ull << ((s - 1) & 63);
+        uint64_t c = 0;
+        for (int i = 0; i <= wi; i++) {
+            u128 v = (u128)t[i] + half[i] + c;
+            t[i] = (uint64_t)v;
+            c = (uint64_t)(v >> 64);
+        }
+        for (int w = 0; w < wo; w++) {
+            int bit = s + 64 * w, q = bit / 64, r = bit & 63;
+            uint64_t v = (q <= wi ? t[q] >> r : 0);
+            if (r && q + 1 <= wi) v |= t[q + 1] << (64 - r);
+            if (w == wo - 1 && (kout & 63)) v &= (1ull << (kout & 63)) - 1;
+            out[(size_t)w * N + n] = v;
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Non-RNS HE Mul at logq (Fig. 2): region 1 multiplies the ciphertexts mod q,
+ * d0 = b1 b2, d1 = a1 b2 + a2 b1, d2 = a1 a2; region 2 multiplies d2 by the
+ * evaluation key (coefficients mod Q^2, encrypting Q s^2) mod qQ and divides
+ * by Q with rounding; c3 = (d0 + ks_b, d1 + ks_a) mod q.  Decryption relation
+ * of Sec. 3.1: b - a s = m + e.  ct: [2][W_q][N] word-major, b half first;
+ * evk: [2][W_{2 logQ}][N].  np1 primes for region 1, np2 for region 2.
+ * ------------------------------------------------------------------------- */
+void or_nr_he_mul(int logN, int logq, int logQ, int np1, int np2, const uint64_t *primes, const uint64_t *psis,
+                  const uint64_t *ct1, const uint64_t *ct2, const uint64_t *evk, uint64_t *out)
+{
+    uint64_t N = 1ull << logN;
+    int wq = nwords(logq), wqQ = nwords(logq + logQ), wQQ = nwords(2 * logQ);
+    size_t PQ = (size_t)wq * N, PQQ = (size_t)wqQ * N;
+    crt_t *T1 = (crt_t *)malloc(sizeof(crt_t)), *T2 = (crt_t *)malloc(sizeof(crt_t));
+    crt_init(T1, np1, primes, psis);
+    crt_init(T2, np2, primes, psis);
+    const uint64_t *b1 = ct1, *a1 = ct1 + PQ, *b2 = ct2, *a2 = ct2 + PQ;
+    uint64_t *d0 = (uint64_t *)malloc(PQ * 8), *d1 = (uint64_t *)malloc(PQ * 8), *d2 = (uint64_t *)malloc(PQ * 8);
+    uint64_t *t = (uint64_t *)malloc(PQ * 8);
+    nr_polymul(logN, T1, b1, wq, b2, wq, NULL, logq, d0);
+    nr_polymul(logN, T1, a1, wq, b2, wq, NULL, logq, d1);
+    nr_polymul(logN, T1, a2, wq, b1, wq, NULL, logq, t);
+    nr_addsub(N, logq, d1, t, 0, d1);
+    nr_polymul(logN, T1, a1, wq, a2, wq, NULL, logq, d2);
+    uint64_t *k = (uint64_t *)malloc(PQQ * 8), *ks = (uint64_t *)malloc(PQ * 8);
+    for (int h = 0; h < 2; h++) {
+        nr_polymul(logN, T2, d2, wq, evk + (size_t)h * wQQ * N, wQQ, NULL, logq + logQ, k);
+        nr_shift_round(N, k, logq + logQ, logQ, logq, ks);
+        nr_addsub(N, logq, h ? d1 : d0, ks, 0, out + (size_t)h * PQ);
+    }
+    free(T1); free(T2); free(d0); free(d1); free(d2); free(t); free(k); free(ks);
+}
+
+/* Rescale by p = 2^logp (Sec. 3.1): c' = round(c / p) mod q/p. */
+void or_nr_rescale(int logN, int logq, int logp, const uint64_t *ct, uint64_t *out)
+{
+    uint64_t N = 1ull << logN;
+    int wq = nwords(logq), wo = nwords(logq - logp);
+    for (int h = 0; h < 2; h++)
+        nr_shift_round(N, ct + (size_t)h * wq * N, logq, logp, logq - logp, out + (size_t)h * wo * N);
+}
+
+/* A product mod (X^N + 1, 2^kout), exposed for the schoolbook pins. */
+void or_nr_polymul(int logN, int np, const uint64_t *primes, const uint64_t *psis, const uint64_t *A, int wa,
+                   const uint64_t *B, int wb, const int64_t *bs, int kout, uint64_t *C)
+{
+    crt_t *T = (crt_t *)malloc(sizeof(crt_t));
+    crt_init(T, np, primes, psis);
+    nr_polymul(logN, T, A, wa, B, wb, bs, kout, C);
+    free(T);
+}
+
+/* Uniform BigInt coefficients mod 2^k from a stream (word by word). */
+static void nr_uniform(rng_t *r, uint64_t N, int k, uint64_t *a)
+{
+    int w = nwords(k);
+    for (uint64_t n = 0; n < N; n++)
+        for (int i = 0; i < w; i++) {
+            uint64_t v = rng_next(r);
+            if (i == w - 1 && (k & 63)) v &= (1ull << (k & 63)) - 1;
+            a[(size_t)i * N + n] = v;
+        }
+}
+static void nr_add_small(uint64_t N, int k, uint64_t *a, const int64_t *s) /* a += s mod 2^k */
+{
+    int w = nwords(k);
+    for (uint64_t n = 0; n < N; n++) {
+        uint64_t add = (uint64_t)s[n], ext = s[n] < 0 ? ~0ull : 0, c = 0;
+        for (int i = 0; i < w; i++) {
+            u128 t = (u128)a[(size_t)i * N + n] + (i == 0 ? add : ext) + c;
+            a[(size_t)i * N + n] = (uint64_t)t;
+            c = (uint64_t)(t >> 64);
+        }
+        if (k & 63) a[(size_t)(w - 1) * N + n] &= (1ull << (k & 63)) - 1;
+    }
+}
+
+enum { ST_NR_PK_A = 200, ST_NR_PK_E = 201, ST_NR_EVK_A = 202, ST_NR_EVK_E = 203, ST_NR_U = 204,
+       ST_NR_E0 = 205, ST_NR_E1 = 206 };
+
+/* Keys (Sec. 3.1 with the non-RNS moduli): pk mod Q: a uniform, b = a s + e;
+ * evk mod Q^2: a uniform, b = a s + e + Q s^2.  sk from or_keygen_sk. */
+void or_nr_keygen(int logN, int logQ, int np, const uint64_t *primes, const uint64_t *psis, double sigma,
+                  const int64_t *s, uint64_t seed, uint64_t *pk, uint64_t *evk)
+{
+    uint64_t N = 1ull << logN;
+    int wQ = nwords(logQ), wQQ = nwords(2 * logQ);
+    crt_t *T = (crt_t *)malloc(sizeof(crt_t));
+    crt_init(T, np, primes, psis);
+    int64_t *e = (int64_t *)malloc(N * sizeof(int64_t));
+    /* pk */
+    rng_t ra = rng_open(seed, ST_NR_PK_A), re = rng_open(seed, ST_NR_PK_E);
+    nr_uniform(&ra, N, logQ, pk + (size_t)wQ * N);
+    nr_polymul(logN, T, pk + (size_t)wQ * N, wQ, NULL, 0, s, logQ, pk);
+    for (uint64_t n = 0; n < N; n++) e[n] = rng_gauss(&re, sigma);
+    nr_add_small(N, logQ, pk, e);
+    /* evk: b = a s + e + Q s^2 mod Q^2 */
+    rng_t rea = rng_open(seed, ST_NR_EVK_A), ree = rng_open(seed, ST_NR_EVK_E);
+    nr_uniform(&rea, N, 2 * logQ, evk + (size_t)wQQ * N);
+    nr_polymul(logN, T, evk + (size_t)wQQ * N, wQQ, NULL, 0, s, 2 * logQ, evk);
+    for (uint64_t n = 0; n < N; n++) e[n] = rng_gauss(&ree, sigma);
+    nr_add_small(N, 2 * logQ, evk, e);
+    int64_t *s2 = (int64_t *)calloc(N, sizeof(int64_t)); /* s^2 in Z[X]/(X^N+1), small */
+    for (uint64_t i = 0; i < N; i++)
+        if (s[i])
+            for (uint64_t j = 0; j < N; j++)
+                if (s[j]) {
+                    uint64_t d = i + j;
+                    if (d < N) s2[d] += s[i] * s[j];
+                    else s2[d - N] -= s[i] * s[j];
+                }
+    /* + Q s^2: add s2 shifted left by logQ bits */
+    for (uint64_t n = 0; n < N; n++) {
+        uint64_t tmp[MW_MAX] = {0}, add[MW_MAX] = {0};
+        for (int i = 0; i < wQQ; i++) tmp[i] = evk[(size_t)i * N + n];
+        int64_t v = s2[n];
+        uint64_t mag = v < 0 ? (uint64_t)(-v) : (uint64_t)v;
+        add[logQ / 64] = mag << (logQ & 63);
+        if ((logQ & 63) && logQ / 64 + 1 < MW_MAX) add[logQ / 64 + 1] = mag >> (64 - (logQ & 63));
+        if (v < 0) mw_sub(tmp, add, wQQ + 1);
+        else {
+            uint64_t c = 0;
+            for (int i = 0; i <= wQQ; i++) {
+                u128 t2 = (u128)tmp[i] + add[i] + c;
+                tmp[i] = (uint64_t)t2;
+                c = (uint64_t)(t2 >> 64);
+            }
+        }
+        for (int i = 0; i < wQQ; i++) {
+            uint64_t x = tmp[i];
+            if (i == wQQ - 1 && ((2 * logQ) & 63)) x &= (1ull << ((2 * logQ) & 63)) - 1;
+            evk[(size_t)i * N + n] = x;
+        }
+    }
+    free(T); free(e); free(s2);
+}
+
+/* Encryption at logq of the integer plaintext pt (Sec. 3.1):
+ * a = v pk.a + e1, b = v pk.b + e0 + pt (mod q), v ZO(1/2). */
+void or_nr_encrypt(int logN, int logq, int logQ, int np, const uint64_t *primes, const uint64_t *psis,
+                   double sigma, const uint64_t *pk, const int64_t *pt, uint64_t seed, uint64_t *ct)
+{
+    uint64_t N = 1ull << logN;
+    int wQ = nwords(logQ), wq = nwords(logq);
+    crt_t *T = (crt_t *)malloc(sizeof(crt_t));
+    crt_init(T, np, primes, psis);
+    int64_t *v = (int64_t *)malloc(N * sizeof(int64_t)), *e = (int64_t *)malloc(N * sizeof(int64_t));
+    rng_t ru = rng_open(seed, ST_NR_U), r0 = rng_open(seed, ST_NR_E0), r1 = rng_open(seed, ST_NR_E1);
+    for (uint64_t n = 0; n < N; n++) v[n] = rng_zo(&ru);
+    nr_polymul(logN, T, pk, wQ, NULL, 0, v, logq, ct);
+    nr_polymul(logN, T, pk + (size_t)wQ * N, wQ, NULL, 0, v, logq, ct + (size_t)wq * N);
+    for (uint64_t n = 0; n < N; n++) e[n] = rng_gauss(&r0, sigma) + pt[n];
+    nr_add_small(N, logq, ct, e);
+    for (uint64_t n = 0; n < N; n++) e[n] = rng_gauss(&r1, sigma);
+    nr_add_small(N, logq, ct + (size_t)wq * N, e);
+    free(T); free(v); free(e);
+}
+
+/* m = b - a s mod q, centred, returned as doubles (|m| < 2^1023). */
+void or_nr_decrypt(int logN, int logq, int np, const uint64_t *primes, const uint64_t *psis, const int64_t *s,
+                   const uint64_t *ct, double *m)
+{
+    uint64_t N = 1ull << logN;
+    int wq = nwords(logq);
+    crt_t *T = (crt_t *)malloc(sizeof(crt_t));
+    crt_init(T, np, primes, psis);
+    uint64_t *as = (uint64_t *)malloc((size_t)wq * N * 8), *r = (uint64_t *)malloc((size_t)wq * N * 8);
+    nr_polymul(logN, T, ct + (size_t)wq * N, wq, NULL, 0, s, logq, as);
+    nr_addsub(N, logq, ct, as, 1, r);
+    for (uint64_t n = 0; n < N; n++) {
+        int neg = (r[(size_t)(wq - 1) * N + n] >> (((logq - 1) & 63))) & 1; /* top bit of the logq-bit value */
+        double acc = 0, scale = 1;
+        uint64_t c = 1;
+        for (int i = 0; i < wq; i++) {
+            uint64_t x = r[(size_t)i * N + n];
+            if (neg) { /* value - q: negate the logq-bit two's complement */
+                u128 t = (u128)(~x) + c;
+                x = (uint64_t)t;
+                c = (uint64_t)(t >> 64);
+                if (i == wq - 1 && (logq & 63)) x &= (1ull << (logq & 63)) - 1;
+            }
+            acc += (double)x * scale;
+            scale *= 18446744073709551616.0;
+        }
+        m[n] = neg ? -acc : acc;
+    }
+    free(T); free(as); free(r);
+}
