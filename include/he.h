@@ -355,6 +355,40 @@ int he_keygen_rot(he_ctx *ctx, uint64_t seed, const int64_t *sk, uint64_t galois
 int he_rotate(he_ctx *ctx, const uint64_t *ct, const uint64_t *rk_dev, int level, uint64_t galois, uint64_t *out,
               void *ws, size_t ws_bytes, void *stream);
 
+/* ---- the paper's own non-RNS HE Mul (Sec. 3-4, Fig. 2) ---------------------
+ * HEAAN as the paper measures it: ciphertext coefficients are BigInts modulo
+ * q = 2^logq (fresh: q = Q = 2^logQ), the evaluation key's modulo Q^2 and
+ * encrypting Q s^2; rescale divides by p = 2^logp with rounding.  BigInt
+ * polynomials are word-major: word w of coefficient n at a[w * N + n],
+ * little-endian, ceil(k / 64) words for modulus 2^k; ciphertexts [2][Wq][N]
+ * (b half first), keys [2][W_{2 logQ}][N].  Each polynomial product is the
+ * paper's CRT -> NTT -> element-wise product -> iNTT -> iCRT over the context's
+ * ciphertext primes: create the context with q_bits = 57 and L >= the plan's
+ * np2 (64 at logQ = 1200, N = 2^16); region 1 uses np1 of them (43 there).
+ * Decryption relation as above: b - a s = m + e (mod q).  Supported: logQ <=
+ * 1216, 1 <= logp < logQ. */
+typedef struct he_nr_plan he_nr_plan;
+/* Tables (CRT constants, iCRT multiword constants) and NTT job lists for
+ * (logQ, logp) on the context's device; HE_EINVAL if the context has too few
+ * primes for P > 4 N 2^(3 logQ) or unsupported sizes. */
+int he_nr_plan_create(he_ctx *ctx, int logQ, int logp, he_nr_plan **out);
+int he_nr_plan_destroy(he_nr_plan *plan);
+int he_nr_plan_info(const he_nr_plan *plan, int *np1, int *np2);
+size_t he_nr_workspace_bytes(const he_nr_plan *plan);
+/* The evaluation key in the NTT-RNS form region 2 uses: CRT and NTT of its
+ * two halves over np2 primes, once per key.  evk: [2][W_{2 logQ}][N] device;
+ * prep: he_nr_evk_bytes(plan) bytes of device memory. */
+size_t he_nr_evk_bytes(const he_nr_plan *plan);
+int he_nr_evk_prepare(he_nr_plan *plan, const uint64_t *evk, uint64_t *prep, void *stream);
+/* out = HE Mul of ct1, ct2 at logq (Fig. 2): region 1 d0 = b1 b2, d1 = a1 b2 +
+ * a2 b1, d2 = a1 a2 mod q; region 2 KS = d2 * evk mod qQ, divided by Q with
+ * rounding; out = (d0 + KS_b, d1 + KS_a) mod q.  HE_ELEVEL for logq outside
+ * (logp, logQ]; HE_ENOMEM for a short workspace. */
+int he_nr_mul(he_nr_plan *plan, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *evk_prep, int logq,
+              uint64_t *out, void *ws, size_t ws_bytes, void *stream);
+/* Rescale (Sec. 3.1): out = round(ct / 2^logp) mod 2^(logq - logp), [2][W][N]. */
+int he_nr_rescale(he_nr_plan *plan, const uint64_t *ct, int logq, uint64_t *out, void *stream);
+
 /* ---- launch shapes and autotuning (no paper counterpart) ------------------ */
 
 /* Launch shape of the path: NTT limbs that share a CTA (they share the

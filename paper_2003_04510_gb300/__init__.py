@@ -120,6 +120,16 @@ _SIGS = {
     "he_batch_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "he_probe_butterfly_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "he_galois_elt": (ctypes.c_uint64, [ctypes.c_void_p, ctypes.c_int]),
+    "he_nr_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "he_nr_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "he_nr_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "he_nr_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "he_nr_evk_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "he_nr_evk_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "he_nr_mul": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "he_nr_rescale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
     "he_keygen_seeded": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "he_evk_register_seeded": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
     "he_evk_unregister": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -420,6 +430,49 @@ def he_evk_register_seeded(ctx, evk_b_dev, seed: int):
 
 def he_evk_unregister(ctx, evk_dev):
     _check(lib().he_evk_unregister(ctx.ptr, _dev_ptr(evk_dev)), "he_evk_unregister")
+
+
+class NrPlan:
+    """The paper's non-RNS HE Mul (BigInt coefficients modulo powers of two) on a
+    context created with q_bits = 57 and enough primes (he_nr_plan_*)."""
+
+    def __init__(self, ctx: Context, logQ: int, logp: int):
+        self.ctx, self.logQ, self.logp = ctx, logQ, logp
+        self.ptr = ctypes.c_void_p()
+        _check(lib().he_nr_plan_create(ctx.ptr, logQ, logp, ctypes.byref(self.ptr)), "he_nr_plan_create")
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().he_nr_plan_info(self.ptr, ctypes.byref(a), ctypes.byref(b)), "he_nr_plan_info")
+        self.np1, self.np2 = a.value, b.value
+
+    def workspace(self, device="cuda"):
+        import torch
+        return torch.empty(lib().he_nr_workspace_bytes(self.ptr) // 8, dtype=torch.int64, device=device)
+
+    def prepare_evk(self, evk_dev, stream=None):
+        import torch
+        prep = torch.empty(lib().he_nr_evk_bytes(self.ptr) // 8, dtype=torch.int64, device=evk_dev.device)
+        _check(lib().he_nr_evk_prepare(self.ptr, _dev_ptr(evk_dev), _dev_ptr(prep), _stream_ptr(stream)),
+               "he_nr_evk_prepare")
+        return prep
+
+    def mul(self, ct1, ct2, prep, logq, out, ws, stream=None):
+        _check(lib().he_nr_mul(self.ptr, _dev_ptr(ct1), _dev_ptr(ct2), _dev_ptr(prep), logq, _dev_ptr(out),
+                               _dev_ptr(ws), ws.numel() * 8, _stream_ptr(stream)), "he_nr_mul")
+
+    def rescale(self, ct, logq, out, stream=None):
+        _check(lib().he_nr_rescale(self.ptr, _dev_ptr(ct), logq, _dev_ptr(out), _stream_ptr(stream)),
+               "he_nr_rescale")
+
+    def close(self):
+        if self.ptr:
+            lib().he_nr_plan_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def he_galois_elt(ctx, steps: int) -> int:
