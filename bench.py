@@ -586,6 +586,51 @@ def run_ours(args):
         chain = {"levels": f"{level}->1", "he_muls": level - 1, "ms_per_chain": cms,
                  "HE_Mul_per_s": (level - 1) / (cms * 1e-3), "reps": creps}
 
+    # ---- the paper's own non-RNS HE Mul at its parameters (N=2^16, log Q=1200, log p=30) ----
+    nonrns = None
+    if not args.no_rotate and preset == "n16":
+        nr_ctx = g.Context(g.Params(16, 64, 1, 16, 57, 57, 192), device=True)
+        plan = g.NrPlan(nr_ctx, 1200, 30)
+        NW = (1200 + 63) // 64
+
+        def words(k, seed):  # a seeded BigInt polynomial mod 2^k, word-major
+            a = si.uniform_residues([1 << 62] * ((k + 63) // 64), (N,), seed)
+            a = (a << np.uint64(2)) | (a & np.uint64(3))
+            if k % 64:
+                a[-1] &= np.uint64((1 << (k % 64)) - 1)
+            return a
+
+        nct = [(g.to_device(np.stack([words(1200, 11000 + 4 * k), words(1200, 11001 + 4 * k)]), dev),
+                g.to_device(np.stack([words(1200, 11002 + 4 * k), words(1200, 11003 + 4 * k)]), dev)) for k in range(2)]
+        nevk = g.to_device(np.stack([words(2400, 11100), words(2400, 11101)]), dev)
+        prep = plan.prepare_evk(nevk, stream)
+        nws = plan.workspace(device=dev)
+        nout = torch.empty((2, NW, N), dtype=torch.int64, device=dev)
+        for k in range(3):
+            plan.mul(nct[k % 2][0], nct[k % 2][1], prep, 1200, nout, nws, stream)
+        torch.cuda.synchronize()
+        nreps = 30
+        n0, n1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0.record(stream)
+        for k in range(nreps):
+            plan.mul(nct[k % 2][0], nct[k % 2][1], prep, 1200, nout, nws, stream)
+        n1.record(stream)
+        torch.cuda.synchronize()
+        nms = n0.elapsed_time(n1) / nreps
+        g.he_profile(nr_ctx, True)
+        for k in range(10):
+            plan.mul(nct[k % 2][0], nct[k % 2][1], prep, 1200, nout, nws, stream)
+        nprof = g.he_profile_read(nr_ctx)
+        g.he_profile(nr_ctx, False)
+        nonrns = {"workload": "the paper's non-RNS HEAAN HE Mul (Fig. 2): N=2^16, log Q=1200 (19-word BigInts), "
+                              f"CRT to {plan.np1}/{plan.np2} 57-bit primes, evk mod Q^2",
+                  "ms_per_he_mul": nms, "HE_Mul_per_s": 1e3 / nms, "reps": nreps,
+                  "paper_gpu_ms": 38.1, "paper_gpu": "Titan RTX, GPU-CLH, 32-bit words (context, other hardware)",
+                  "kernels_us": {k: v[0] / v[1] * 1e3 for k, v in nprof.items()},
+                  "data": "seeded uniform words (same work as encryptions)"}
+        plan.close()
+        del nws, prep, nevk, nct, nout
+
     # ALU ceiling: register-resident butterfly probe
     bfly_peak = g.he_probe_butterfly_rate(152 * 8, 4096, stream)
     probe = {"butterfly_per_s": bfly_peak}
@@ -669,6 +714,7 @@ def run_ours(args):
                          "tried": [{"group_cap": t[0], "modup_chunk": t[1], "pdl": t[2], "ms": t[3]}
                                    for t in tune_tried]},
             "seeded_evk": seeded,
+            "nonrns_paper": nonrns,
             "rotate": rot,
             "chain": chain,
             "batched": batched,
