@@ -45,7 +45,7 @@ namespace he {
 namespace {
 
 constexpr int kT = 256;     // one coefficient per thread (CRT, products, rescale)
-constexpr int kIT = 128;    // iCRT threads per CTA (their y values sit in shared memory)
+constexpr int kIT = 128;    // iCRT threads per CTA
 constexpr int kCP = 8;      // primes per CTA in the CRT
 constexpr int kMaxNp = 64;  // primes of a plan (the context's ciphertext primes)
 constexpr int kChunkBlock = 40;  // 28-bit chunks accumulated before a reduction
@@ -146,11 +146,15 @@ k_nr_ks_mult(u64 *__restrict__ r, const u64 *__restrict__ ek, int np, const DevP
 // iCRT of polys y[poly][np][N] (y_i = [x_i Phat_i^-1]_{p_i}) into BigInts.
 // T = sum_i y_i M_i + NEG_u (mod 2^(64 W)), M_i = Phat_i mod 2^(64 W),
 // NEG_u = (2^(64 W) - u P + rnd) mod 2^(64 W), u = round(sum_i y_i / p_i).
+// Each thread keeps one accumulator per column in registers (column w
+// collects the low words of y_i M_i[w] and the high words of y_i M_i[w-1]),
+// in passes over at most 19 columns, reading the y_i once per pass; the
+// carries run after each pass's sums.
 // KS = false: out[poly] = T mod 2^kout (wo words; polys ostride * N words apart).
 // KS = true: out[poly] = d[poly] + floor((T + 2^(s-1)) / 2^s) mod 2^kout, the
 // rounding term being part of NEG_u (s = logQ).
-// grid: x over N / kIT, y over polys; dynamic shared memory holds y
-// ([np][kIT]), M ([np][W]) and NEG ([np + 1][W]).
+// grid: x over N / kIT, y over polys; dynamic shared memory holds M
+// ([np][W]) and NEG ([np + 1][W]).
 template <int W, bool KS>
 __global__ void __launch_bounds__(kIT)
 k_nr_icrt(const u64 *__restrict__ y, int np, const u64 *__restrict__ M, const u64 *__restrict__ NEG,
@@ -158,67 +162,90 @@ k_nr_icrt(const u64 *__restrict__ y, int np, const u64 *__restrict__ M, const u6
           const u64 *__restrict__ d, int s, int N)
 {
     extern __shared__ __align__(16) u64 sh[];
-    u64 *sy = sh;                         // [np][kIT]
-    u64 *sM = sy + (size_t)np * kIT;      // [np][W]
+    u64 *sM = sh;                         // [np][W]
     u64 *sN = sM + (size_t)np * W;        // [np + 1][W]
     for (int t = threadIdx.x; t < np * W; t += kIT) sM[t] = M[t];
     for (int t = threadIdx.x; t < (np + 1) * W; t += kIT) sN[t] = NEG[t];
     const int n = blockIdx.x * kIT + threadIdx.x;
     const u64 *yp = y + (size_t)blockIdx.y * np * N + n;
-    griddep_wait();
-    double f = 0;
-    for (int i = 0; i < np; i++) {
-        const u64 v = yp[(size_t)i * N];
-        sy[i * kIT + threadIdx.x] = v;
-        f = fma((double)v, inv[i], f);
-    }
-    const int u = (int)llrint(f);
     __syncthreads();
-    const u64 *neg = sN + (size_t)u * W;
+    griddep_wait();
+    // columns in passes of CW (one pass for W <= 24): fewer live accumulators;
+    // the high words of a pass's last column seed the next pass's first one
+    constexpr int CW = W > 24 ? (W + 1) / 2 : W;
+    constexpr int NPASS = (W + CW - 1) / CW;
     u64 *o = out + (size_t)blockIdx.y * ostride * N + n;
     const u64 *dp = KS ? d + (size_t)blockIdx.y * ostride * N + n : nullptr;
     const int q0 = s >> 6, r = s & 63;
-    U128 nxt = {0, 0};
-    u64 carry = 0, prev = 0, dc = 0;
-    for (int w = 0; w < W; w++) {
-        U128 acc = nxt;
-        acc.lo += carry;
-        acc.hi += acc.lo < carry ? 1ull : 0ull;
-        nxt.lo = 0;
-        nxt.hi = 0;
-        for (int i = 0; i < np; i++) {
-            const u64 a = sy[i * kIT + threadIdx.x], m = sM[i * W + w];
-            const u64 lo = a * m, hi = __umul64hi(a, m);
-            acc.lo += lo;
-            acc.hi += acc.lo < lo ? 1ull : 0ull;
-            nxt.lo += hi;
-            nxt.hi += nxt.lo < hi ? 1ull : 0ull;
+    u64 carry = 0, prev = 0, dc = 0, ov_lo = 0;
+    uint32_t ov_hi = 0;
+    int u = 0;
+#pragma unroll
+    for (int ps = 0; ps < NPASS; ps++) {
+        const int w0 = ps * CW;
+        u64 lo[CW + 1];
+        uint32_t hi[CW + 1];  // carries out of the low words: at most 2 np per column
+#pragma unroll
+        for (int w = 0; w <= CW; w++) {
+            lo[w] = 0;
+            hi[w] = 0;
         }
-        const u64 ng = neg[w];
-        acc.lo += ng;
-        acc.hi += acc.lo < ng ? 1ull : 0ull;
-        const u64 col = acc.lo;
-        carry = acc.hi;
-        if (!KS) {
-            if (w < wo) {
-                u64 v = col;
-                if (w == wo - 1 && (kout & 63)) v &= (1ull << (kout & 63)) - 1;
-                o[(size_t)w * N] = v;
+        lo[0] = ov_lo;
+        hi[0] = ov_hi;
+        double f = 0;
+        u64 ynext = yp[0];
+        for (int i = 0; i < np; i++) {
+            const u64 a = ynext;
+            if (i + 1 < np) ynext = yp[(size_t)(i + 1) * N];
+            if (ps == 0) f = fma((double)a, inv[i], f);
+            const u64 *m = sM + (size_t)i * W + w0;
+#pragma unroll
+            for (int w = 0; w < CW; w++) {
+                if (w0 + w < W) {
+                    const u64 mw = m[w];
+                    const u64 pl = a * mw, ph = __umul64hi(a, mw);
+                    lo[w] += pl;
+                    hi[w] += lo[w] < pl ? 1u : 0u;
+                    lo[w + 1] += ph;
+                    hi[w + 1] += lo[w + 1] < ph ? 1u : 0u;
+                }
             }
-        } else {
-            // output word j = bits [s + 64 j, s + 64 j + 64) of T: columns q0 + j and q0 + j + 1
-            const int j = w - q0 - 1;
-            if (j >= 0 && j < wo) {
-                u64 v = r ? (prev >> r) | (col << (64 - r)) : prev;
-                const u64 dv = dp[(size_t)j * N];
-                u64 sum = v + dv;
-                const u64 c1 = sum < v ? 1ull : 0ull;
-                sum += dc;
-                dc = c1 + (sum < dc ? 1ull : 0ull);
-                if (j == wo - 1 && (kout & 63)) sum &= (1ull << (kout & 63)) - 1;
-                o[(size_t)j * N] = sum;
+        }
+        if (ps == 0) u = (int)llrint(f);
+        ov_lo = lo[CW];
+        ov_hi = hi[CW];
+        const u64 *neg = sN + (size_t)u * W;
+#pragma unroll
+        for (int k = 0; k < CW; k++) {
+            const int w = w0 + k;
+            if (w >= W) break;
+            u64 col = lo[k] + carry;
+            u64 c = (u64)hi[k] + (col < carry ? 1ull : 0ull);
+            const u64 ng = neg[w];
+            col += ng;
+            c += col < ng ? 1ull : 0ull;
+            carry = c;
+            if (!KS) {
+                if (w < wo) {
+                    u64 v = col;
+                    if (w == wo - 1 && (kout & 63)) v &= (1ull << (kout & 63)) - 1;
+                    o[(size_t)w * N] = v;
+                }
+            } else {
+                // output word j = bits [s + 64 j, s + 64 j + 64) of T: columns q0 + j and q0 + j + 1
+                const int j = w - q0 - 1;
+                if (j >= 0 && j < wo) {
+                    const u64 v = r ? (prev >> r) | (col << (64 - r)) : prev;
+                    const u64 dv = dp[(size_t)j * N];
+                    u64 sum = v + dv;
+                    const u64 c1 = sum < v ? 1ull : 0ull;
+                    sum += dc;
+                    dc = c1 + (sum < dc ? 1ull : 0ull);
+                    if (j == wo - 1 && (kout & 63)) sum &= (1ull << (kout & 63)) - 1;
+                    o[(size_t)j * N] = sum;
+                }
+                prev = col;
             }
-            prev = col;
         }
     }
 }
@@ -363,11 +390,11 @@ cudaError_t launch_icrt(const he_nr_plan *pl, const u64 *y, int np, const u64 *M
                         u64 *out, int ostride, int wo, int kout, const u64 *d, int s, int polys, cudaStream_t st)
 {
     const he_ctx *c = pl->c;
-    const size_t smem = sizeof(u64) * ((size_t)np * kIT + (size_t)np * W + (size_t)(np + 1) * W);
+    const size_t smem = sizeof(u64) * ((size_t)np * W + (size_t)(np + 1) * W);
     auto kern = k_nr_icrt<W, KS>;
     static bool configured = false;
     if (!configured) {
-        const size_t most = sizeof(u64) * ((size_t)kMaxNp * kIT + (size_t)kMaxNp * W + (size_t)(kMaxNp + 1) * W);
+        const size_t most = sizeof(u64) * ((size_t)kMaxNp * W + (size_t)(kMaxNp + 1) * W);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
         if (e != cudaSuccess) return e;
         configured = true;
