@@ -379,6 +379,69 @@ def run_serving(g, dev, rate_hz=2000.0, duration_s=10.0, streams=4, max_batch=64
             "hbm_budget_bytes": budget}
 
 
+def run_single(g, preset, level, dev, stream, rank, reps=300, npairs=2):
+    """Single HE Mul + rescale at another ring size (N = 2^17 beside the
+    default 2^16): autotuned shape, per-step latency, per-kernel profile and
+    the inner product's HBM fraction."""
+    import torch
+    prm, scale_bits = g.PRESETS[preset]
+    sc = 2.0 ** scale_bits
+    ctx = g.Context(prm, device=True)
+    N = ctx.N
+    ks, s1, s2 = si.SEEDS[preset]
+    sk, pk, evk = g.he_keygen(ctx, ks + 1000 * rank)
+    evk_t = g.to_device(evk, dev)
+    del evk
+    ct_t = [(g.to_device(g.he_encrypt(ctx, pk, si.messages(N // 2, s1 + 17 * k), sc, level, s1 + 17 * k), dev),
+             g.to_device(g.he_encrypt(ctx, pk, si.messages(N // 2, s2 + 17 * k), sc, level, s2 + 17 * k), dev))
+            for k in range(npairs)]
+    outs = [torch.empty((2, level - 1, N), dtype=torch.int64, device=dev) for _ in range(npairs)]
+    ws = g.workspace(ctx, level, device=dev)
+    best, _ = g.he_autotune(ctx, [(ct_t[0][0], ct_t[0][1], outs[0], level)], evk_t, ws, reps=10, stream=stream)
+
+    def step(k):
+        a, b = ct_t[k % npairs]
+        g.he_mul_rescale(ctx, a, b, evk_t, level, outs[k % npairs], ws, stream)
+
+    for k in range(5):
+        step(k)
+    torch.cuda.synchronize()
+    z = g.he_decrypt(ctx, sk, g.to_host(outs[0]), level - 1, sc * sc / float(ctx.q[level - 1]))
+    err = float(np.abs(z - si.messages(N // 2, s1) * si.messages(N // 2, s2)).max())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(reps):
+        ev[k][0].record(stream)
+        step(k)
+        ev[k][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    lat = np.array([a.elapsed_time(b) for a, b in ev])
+    g.he_profile(ctx, True)
+    for k in range(10):
+        step(k)
+    prof = g.he_profile_read(ctx)
+    g.he_profile(ctx, False)
+    kernels_us = {k: v[0] / v[1] * 1e3 for k, v in prof.items()}
+    ip = None
+    if "inner_product" in prof:
+        _, b = kernel_work("inner_product", ctx.prm, level)
+        ip = b / (kernels_us["inner_product"] * 1e-6) / 1e9
+    res = {"workload": WORKLOADS[preset][2], "HE_Mul_per_s": 1e3 / ms, "ms": ms, "reps": reps,
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+           "autotune": {"group_cap": best[0], "modup_chunk": best[1], "pdl": best[2]},
+           "kernels_us": kernels_us, "inner_product_gbs": ip,
+           "evk_bytes": int(evk_t.numel() * 8), "decrypt_max_err": err,
+           "l2": f"{npairs} ciphertext pairs + evk rotated "
+                 f"({(npairs * 4 * level + 2 * ctx.dnum * (prm.K + prm.L)) * N * 8 / 1e6:.0f} MB > 129 MB L2)"}
+    del ws, outs, ct_t, evk_t
+    ctx.close()
+    return res
+
+
 def run_ours(args):
     import torch
     import paper_2003_04510_gb300 as g
@@ -670,6 +733,11 @@ def run_ours(args):
         ach = b / (per_kernel["inner_product"]["ms_avg"] * 1e-3) / 1e9
         ip = {"achieved_gbs": ach, "peak_gbs": hbm_peak, "frac": ach / hbm_peak}
 
+    # ---- the same single HE Mul at N = 2^17 (level 44 -> 43, dnum 4) ----
+    n17 = None
+    if preset == "n16" and not args.no_n17:
+        n17 = run_single(g, "n17", WORKLOADS["n17"][1], dev, stream, rank)
+
     # ---- batched configuration: 64 HE Muls at uneven levels, one launch sequence ----
     batched = None
     if preset == "n16" and not args.no_batch:
@@ -713,6 +781,7 @@ def run_ours(args):
                          "ms": tune_best[3],
                          "tried": [{"group_cap": t[0], "modup_chunk": t[1], "pdl": t[2], "ms": t[3]}
                                    for t in tune_tried]},
+            "n17_single": n17,
             "seeded_evk": seeded,
             "nonrns_paper": nonrns,
             "rotate": rot,
@@ -739,6 +808,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-rotate", action="store_true")
+    ap.add_argument("--no-n17", action="store_true", help="skip the N=2^17 single HE Mul section")
     ap.add_argument("--shape", default="", help="fixed launch shape CAP,CHUNK,PDL instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -192,6 +192,31 @@ inline void launch_k(bool dep, void (*k)(KArgs...), dim3 grid, dim3 block, size_
 // Wait for the previous kernel on the stream (a no-op without a programmatic
 // dependency).
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// L2 eviction policies.  Streams read once per HE Mul (the evaluation key,
+// the input ciphertexts, ModUp outputs) are marked evict-first, so they pass
+// through L2 without displacing the NTT twiddle tables, which every HE Mul
+// rereads and which are marked evict-last.
+__device__ __forceinline__ u64 l2_policy_stream()
+{
+    u64 p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ u64 l2_policy_keep()
+{
+    u64 p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// 16-byte read-only load with an L2 policy, no L1 allocation.
+__device__ __forceinline__ ulonglong2 ld2_hint(const void *p, u64 pol)
+{
+    ulonglong2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+                 : "=l"(v.x), "=l"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
 #endif
 
 cudaError_t launch_ntt(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, bool inverse,

@@ -52,7 +52,9 @@ k_tensor(const JobRef R, const DevPrime *__restrict__ primes, const DevLevel *__
     const DevPrime pr = primes[K + i];
     const size_t ob = (size_t)i * N + n, oa = ((size_t)l + i) * N + n;
     griddep_wait();
-    const ulonglong2 b1 = ld2(it.ct1 + ob), a1 = ld2(it.ct1 + oa), b2 = ld2(it.ct2 + ob), a2 = ld2(it.ct2 + oa);
+    const u64 pol = l2_policy_stream();  // the inputs are read once
+    const ulonglong2 b1 = ld2_hint(it.ct1 + ob, pol), a1 = ld2_hint(it.ct1 + oa, pol),
+                     b2 = ld2_hint(it.ct2 + ob, pol), a2 = ld2_hint(it.ct2 + oa, pol);
     u64 *d0 = it.ws + (size_t)lv.o_d0 * N, *d1 = it.ws + (size_t)lv.o_d1 * N, *d2 = it.ws + (size_t)lv.o_d2 * N;
     st2(d0 + (size_t)i * N + n, mul_mod(b1.x, b2.x, pr.q, pr.mu, pr.s), mul_mod(b1.y, b2.y, pr.q, pr.mu, pr.s));
     U128 x = mul_wide(a1.x, b2.x), y = mul_wide(a1.y, b2.y);
@@ -168,6 +170,9 @@ k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__r
     const DevPrime pr = primes[e];
     const u64 *U = it.ws + (size_t)lv.o_u * N, *d2 = it.ws + (size_t)lv.o_d2 * N;
     griddep_wait();
+    // the key and the ModUp outputs are read once: evict-first keeps them from
+    // displacing the twiddle tables in L2
+    const u64 pol = l2_policy_stream();
     ulonglong2 u[BM], kb[BM], ka[BM];
 #pragma unroll
     for (int j = 0; j < BM; j++) {
@@ -175,14 +180,14 @@ k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__r
             const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
             const bool own = e >= K && e - K >= lo && e - K < lo + nj;
             const u64 *up = own ? d2 + (size_t)(e - K) * N : U + ((size_t)j * E + e) * N;
-            u[j] = ld2(up + n);
+            u[j] = own ? ld2(up + n) : ld2_hint(up + n, pol);
             if (SEEDED) {
-                kb[j] = ld2(evk + ((size_t)j * EL + e) * N + n);
+                kb[j] = ld2_hint(evk + ((size_t)j * EL + e) * N + n, pol);
                 const u64 idx = (u64)e * (u64)N + n;
                 ka[j] = make_ulonglong2(seeded_a(seeds.s[j], idx, pr.q), seeded_a(seeds.s[j], idx + 1, pr.q));
             } else {
-                kb[j] = ld2(evk + ((size_t)(2 * j) * EL + e) * N + n);
-                ka[j] = ld2(evk + ((size_t)(2 * j + 1) * EL + e) * N + n);
+                kb[j] = ld2_hint(evk + ((size_t)(2 * j) * EL + e) * N + n, pol);
+                ka[j] = ld2_hint(evk + ((size_t)(2 * j + 1) * EL + e) * N + n, pol);
             }
         }
     }

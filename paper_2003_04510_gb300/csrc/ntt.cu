@@ -81,12 +81,8 @@ __device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, ulonglong2 w, u64 nq, u6
 }
 
 // 16-byte read-only load that does not allocate in L1 (twiddles read once).
-__device__ __forceinline__ ulonglong2 ld_tw(const ulonglong2 *p)
-{
-    ulonglong2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
-    return v;
-}
+// The table's lines are kept in L2 (evict-last): every HE Mul rereads them.
+__device__ __forceinline__ ulonglong2 ld_tw(const ulonglong2 *p) { return ld2_hint(p, l2_policy_keep()); }
 
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
@@ -222,7 +218,7 @@ __device__ __forceinline__ void prefetch_direct_tw(const ulonglong2 *twg, int ti
             const ulonglong2 *g = twg + (1 << (s0 + L0 + lp)) + Tn;
 #pragma unroll
             for (int j = 0; j < (1 << lp); j++)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(g + ((size_t)j << (s0 + L0))));
+                asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(g + ((size_t)j << (s0 + L0))));
         }
     }
 }
