@@ -325,8 +325,10 @@ def run_batched(g, ctx, evk_t, dev, stream, wsz, count=64, reps=20):
                      "batch_latency_ms_p99": float(np.percentile(lat, 99))}
     graph.close()
     g.he_set_shape(ctx, *shape_before)
-    res["autotune"] = {"group_cap": best[0], "modup_chunk": best[1], "pdl": best[2], "ms_per_batch": best[3],
-                       "tried": [{"group_cap": t[0], "modup_chunk": t[1], "pdl": t[2], "ms": t[3]} for t in tried]}
+    res["autotune"] = {"group_cap": best[0], "modup_chunk": best[1], "pdl": best[2], "ntt_r8": best[3],
+                       "ms_per_batch": best[4],
+                       "tried": [{"group_cap": t[0], "modup_chunk": t[1], "pdl": t[2], "ntt_r8": t[3], "ms": t[4]}
+                                 for t in tried]}
     res["config"] = {"jobs": count, "N": N, "levels": "uniform 4..24 (seed 1604)", "mean_level": float(np.mean(levels)),
                      "operands": "uniform residues"}
     return res
@@ -432,7 +434,7 @@ def run_single(g, preset, level, dev, stream, rank, reps=300, npairs=2):
         ip = b / (kernels_us["inner_product"] * 1e-6) / 1e9
     res = {"workload": WORKLOADS[preset][2], "HE_Mul_per_s": 1e3 / ms, "ms": ms, "reps": reps,
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-           "autotune": {"group_cap": best[0], "modup_chunk": best[1], "pdl": best[2]},
+           "autotune": {"group_cap": best[0], "modup_chunk": best[1], "pdl": best[2], "ntt_r8": best[3]},
            "kernels_us": kernels_us, "inner_product_gbs": ip,
            "evk_bytes": int(evk_t.numel() * 8), "decrypt_max_err": err,
            "l2": f"{npairs} ciphertext pairs + evk rotated "
@@ -484,9 +486,9 @@ def run_ours(args):
     # launch shapes picked by the library's autotuner for this single HE Mul
     # (or fixed by --shape, e.g. for a profiler run)
     if args.shape:
-        cap, chunk, pdl = (int(v) for v in args.shape.split(","))
-        g.he_set_shape(ctx, cap, chunk, pdl)
-        tune_best, tune_tried = (cap, chunk, pdl, 0.0), []
+        cap, chunk, pdl, r8 = ([int(v) for v in args.shape.split(",")] + [0])[:4]
+        g.he_set_shape(ctx, cap, chunk, pdl, r8)
+        tune_best, tune_tried = (cap, chunk, pdl, r8, 0.0), []
     else:
         tune_best, tune_tried = g.he_autotune(ctx, [(ct_t[0][0], ct_t[0][1], outs[0], level)], evk_t, ws, reps=20,
                                               stream=stream)
@@ -778,8 +780,8 @@ def run_ours(args):
             "probe": probe,
             "kernels": per_kernel,
             "autotune": {"group_cap": tune_best[0], "modup_chunk": tune_best[1], "pdl": tune_best[2],
-                         "ms": tune_best[3],
-                         "tried": [{"group_cap": t[0], "modup_chunk": t[1], "pdl": t[2], "ms": t[3]}
+                         "ntt_r8": tune_best[3], "ms": tune_best[4],
+                         "tried": [{"group_cap": t[0], "modup_chunk": t[1], "pdl": t[2], "ntt_r8": t[3], "ms": t[4]}
                                    for t in tune_tried]},
             "n17_single": n17,
             "seeded_evk": seeded,
@@ -809,7 +811,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-rotate", action="store_true")
     ap.add_argument("--no-n17", action="store_true", help="skip the N=2^17 single HE Mul section")
-    ap.add_argument("--shape", default="", help="fixed launch shape CAP,CHUNK,PDL instead of autotuning")
+    ap.add_argument("--shape", default="", help="fixed launch shape CAP,CHUNK,PDL[,R8] instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -392,23 +392,30 @@ int he_nr_rescale(he_nr_plan *plan, const uint64_t *ct, int logq, uint64_t *out,
 /* ---- launch shapes and autotuning (no paper counterpart) ------------------ */
 
 /* Launch shape of the path: NTT limbs that share a CTA (they share the
- * staged twiddles; 1..4), ModUp targets per CTA (4, 8 or 16), and whether the
+ * staged twiddles; 1..4), ModUp targets per CTA (4, 8 or 16), whether the
  * path's kernels use programmatic dependent launch (1: a kernel's CTAs may be
  * scheduled while its predecessor drains; each waits for it in hardware
- * before touching its data).  Speed only: every shape gives bit-identical
- * results.  Default {4, 8, 1}.  A batch graph keeps the shape it was
- * captured with, except the limb-group cap. */
+ * before touching its data), and which of the four NTT sites of the key
+ * switch (bit 0 the iNTT of d2, 1 the NTT of the ModUp outputs, 2 the iNTT of
+ * the special limbs, 3 the NTT of the ModDown limbs) use the radix-8 plan
+ * (rounds of at most three stages, 256 threads per tile) instead of the
+ * radix-16 one (128 threads per tile).  Speed only: every shape gives
+ * bit-identical results.  Default {4, 8, 1, 0}.  A batch graph keeps the
+ * shape it was captured with, except the limb-group cap. */
 typedef struct {
     int group_cap;
     int modup_chunk;
     int pdl;
-    double ms; /* he_autotune: measured milliseconds per call; else 0 */
+    int ntt_r8; /* 0..15 */
+    double ms;  /* he_autotune: measured milliseconds per call; else 0 */
 } he_shape;
 
 /* HE_EINVAL for a NULL context or an unsupported value. */
 int he_set_shape(he_ctx *ctx, const he_shape *shape);
 int he_get_shape(const he_ctx *ctx, he_shape *shape);
-/* Time every shape on the caller's own work and keep the fastest in ctx:
+/* Time shapes on the caller's own work and keep the fastest in ctx: every
+ * (group_cap, modup_chunk, pdl) with the radix-16 NTT plan, then every
+ * nonzero ntt_r8 mask on the best of those (39 shapes);
  * count == 1 times he_mul_rescale on jobs[0] (ws of he_workspace_bytes),
  * count > 1 times he_mul_batch on the jobs (ws of he_batch_workspace_bytes),
  * `reps` calls per shape after one warm-up call, CUDA events on `stream`.

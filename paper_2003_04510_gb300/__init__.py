@@ -385,23 +385,25 @@ def he_add_plain(ctx, ct, pt, level, out, stream=None):
 
 class he_shape(ctypes.Structure):
     _fields_ = [("group_cap", ctypes.c_int), ("modup_chunk", ctypes.c_int), ("pdl", ctypes.c_int),
-                ("ms", ctypes.c_double)]
+                ("ntt_r8", ctypes.c_int), ("ms", ctypes.c_double)]
 
 
-def he_set_shape(ctx, group_cap: int, modup_chunk: int, pdl: int = 1):
-    sh = he_shape(group_cap, modup_chunk, pdl, 0.0)
+def he_set_shape(ctx, group_cap: int, modup_chunk: int, pdl: int = 1, ntt_r8: int = 0):
+    sh = he_shape(group_cap, modup_chunk, pdl, ntt_r8, 0.0)
     _check(lib().he_set_shape(ctx.ptr, ctypes.byref(sh)), "he_set_shape")
 
 
-def he_get_shape(ctx) -> tuple[int, int, int]:
+def he_get_shape(ctx) -> tuple[int, int, int, int]:
+    """(group_cap, modup_chunk, pdl, ntt_r8)"""
     sh = he_shape()
     _check(lib().he_get_shape(ctx.ptr, ctypes.byref(sh)), "he_get_shape")
-    return sh.group_cap, sh.modup_chunk, sh.pdl
+    return sh.group_cap, sh.modup_chunk, sh.pdl, sh.ntt_r8
 
 
 def he_autotune(ctx, jobs, evk, ws, reps: int = 3, stream=None):
     """jobs: list of (ct1, ct2, out, level) device tensors (one job: the single
-    path).  Returns (best (cap, chunk, pdl, ms), [(cap, chunk, pdl, ms) tried])."""
+    path).  Returns (best (cap, chunk, pdl, ntt_r8, ms), [the same for every
+    shape tried])."""
     arr = (he_job * len(jobs))()
     for i, (a, b, o, lv) in enumerate(jobs):
         arr[i] = he_job(_dev_ptr(a), _dev_ptr(b), _dev_ptr(o), int(lv))
@@ -411,8 +413,8 @@ def he_autotune(ctx, jobs, evk, ws, reps: int = 3, stream=None):
     _check(lib().he_autotune(ctx.ptr, ctypes.cast(arr, ctypes.c_void_p), len(jobs), _dev_ptr(evk), _dev_ptr(ws),
                              ws.numel() * 8, reps, _stream_ptr(stream), ctypes.byref(best),
                              ctypes.cast(tried, ctypes.c_void_p), 64, ctypes.byref(n)), "he_autotune")
-    return ((best.group_cap, best.modup_chunk, best.pdl, best.ms),
-            [(t.group_cap, t.modup_chunk, t.pdl, t.ms) for t in tried[: n.value]])
+    return ((best.group_cap, best.modup_chunk, best.pdl, best.ntt_r8, best.ms),
+            [(t.group_cap, t.modup_chunk, t.pdl, t.ntt_r8, t.ms) for t in tried[: n.value]])
 
 
 def he_keygen_seeded(ctx, seed: int, sk: np.ndarray) -> np.ndarray:

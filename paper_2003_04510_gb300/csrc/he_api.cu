@@ -88,21 +88,24 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
 {
     // key switching: iNTT(d2) (times N^-1 Qhat^-1), ModUp, NTT, inner product
     const int *cnt = S.counts;
-    HE_TRY(launch_ntt(c, ntt_base, S.intt1, S.n_intt1, true, st, "intt_d2", cnt ? cnt + 0 : nullptr));
+    auto r8 = [c](int site) { return ((c->ntt_r8 >> site) & 1) != 0; };
+    HE_TRY(launch_ntt(c, ntt_base, S.intt1, S.n_intt1, true, st, "intt_d2", cnt ? cnt + 0 : nullptr, r8(0)));
     HE_TRY(run_modup(c, R, st));
     prof_mark(c, st, "modup");
-    HE_TRY(launch_ntt(c, ntt_base, S.ntt_up, S.n_ntt_up, false, st, "ntt_modup", cnt ? cnt + 1 : nullptr));
+    HE_TRY(launch_ntt(c, ntt_base, S.ntt_up, S.n_ntt_up, false, st, "ntt_modup", cnt ? cnt + 1 : nullptr, r8(1)));
     HE_TRY(run_inner_product(c, R, evk, st));
     prof_mark(c, st, "inner_product");
     // ModDown: iNTT of the special limbs (times N^-1 Phat^-1), conversion, NTT
-    HE_TRY(launch_ntt(c, ntt_base, S.intt2, S.n_intt2, true, st, "intt_special", cnt ? cnt + 2 : nullptr));
+    HE_TRY(launch_ntt(c, ntt_base, S.intt2, S.n_intt2, true, st, "intt_special", cnt ? cnt + 2 : nullptr, r8(2)));
     HE_TRY(run_moddown_conv(c, R, fused, st));
     prof_mark(c, st, "moddown_conv");
     if (fused) {
         // the final combine runs in the last NTT pass (writes each job's output)
-        HE_TRY(launch_ntt_combine(c, ntt_base, S.ntt_last, S.n_ntt_last, R, st, "ntt_moddown", cnt ? cnt + 3 : nullptr));
+        HE_TRY(launch_ntt_combine(c, ntt_base, S.ntt_last, S.n_ntt_last, R, st, "ntt_moddown", cnt ? cnt + 3 : nullptr,
+                                  r8(3)));
     } else {
-        HE_TRY(launch_ntt(c, ntt_base, S.ntt_last, S.n_ntt_last, false, st, "ntt_moddown", cnt ? cnt + 3 : nullptr));
+        HE_TRY(launch_ntt(c, ntt_base, S.ntt_last, S.n_ntt_last, false, st, "ntt_moddown", cnt ? cnt + 3 : nullptr,
+                          r8(3)));
         HE_TRY(run_combine_plain(c, R, st));
         prof_mark(c, st, "combine");
     }
@@ -556,9 +559,11 @@ int he_set_shape(he_ctx *c, const he_shape *sh)
     if (sh->group_cap < 1 || sh->group_cap > kGroupMax) return HE_EINVAL;
     if (sh->modup_chunk != 4 && sh->modup_chunk != 8 && sh->modup_chunk != 16) return HE_EINVAL;
     if (sh->pdl != 0 && sh->pdl != 1) return HE_EINVAL;
+    if (sh->ntt_r8 < 0 || sh->ntt_r8 > 15) return HE_EINVAL;
     c->group_cap = sh->group_cap;
     c->modup_chunk = sh->modup_chunk;
     c->pdl = sh->pdl != 0;
+    c->ntt_r8 = sh->ntt_r8;
     if (c->device) c->jobs = c->jobs_cap[c->group_cap - 1];
     return HE_OK;
 }
@@ -569,6 +574,7 @@ int he_get_shape(const he_ctx *c, he_shape *sh)
     sh->group_cap = c->group_cap;
     sh->modup_chunk = c->modup_chunk;
     sh->pdl = c->pdl ? 1 : 0;
+    sh->ntt_r8 = c->ntt_r8;
     sh->ms = 0;
     return HE_OK;
 }
@@ -594,27 +600,36 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
     int rc = HE_OK, n = 0;
     he_shape top = keep;
     top.ms = -1;
+    auto time_shape = [&](he_shape sh) -> int {
+        he_set_shape(c, &sh);
+        int r = call();  // warm-up (and argument check)
+        if (r != HE_OK) return r;
+        cudaEventRecord(e0, S(stream));
+        for (int k = 0; k < reps && r == HE_OK; k++) r = call();
+        cudaEventRecord(e1, S(stream));
+        if (r != HE_OK) return r;
+        float ms = 0;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            return HE_ECUDA;
+        sh.ms = ms / reps;
+        if (tried && n < max_tried) tried[n] = sh;
+        n++;
+        if (top.ms < 0 || sh.ms < top.ms) top = sh;
+        return HE_OK;
+    };
+    // first the limb-group cap, ModUp chunk and PDL with the radix-16 NTT
+    // plan, then the NTT plan of each of the four pipeline sites on that shape
     const int caps[] = {1, 2, 3, 4}, chunks[] = {4, 8, 16}, pdls[] = {1, 0};
     for (int pdl : pdls)
-    for (int cap : caps)
-        for (int ch : chunks) {
-            he_shape sh = {cap, ch, pdl, 0};
-            he_set_shape(c, &sh);
-            if ((rc = call()) != HE_OK) break;  // warm-up (and argument check)
-            cudaEventRecord(e0, S(stream));
-            for (int r = 0; r < reps && rc == HE_OK; r++) rc = call();
-            cudaEventRecord(e1, S(stream));
-            if (rc != HE_OK) break;
-            float ms = 0;
-            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                rc = HE_ECUDA;
-                break;
-            }
-            sh.ms = ms / reps;
-            if (tried && n < max_tried) tried[n] = sh;
-            n++;
-            if (top.ms < 0 || sh.ms < top.ms) top = sh;
-        }
+        for (int cap : caps)
+            for (int ch : chunks)
+                if (rc == HE_OK) rc = time_shape({cap, ch, pdl, 0, 0});
+    const he_shape base = top;
+    for (int mask = 1; mask < 16 && rc == HE_OK; mask++) {
+        he_shape sh = base;
+        sh.ntt_r8 = mask;
+        rc = time_shape(sh);
+    }
     c->prof = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

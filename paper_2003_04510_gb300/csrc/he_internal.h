@@ -120,6 +120,7 @@ struct he_ctx {
     int group_cap = he::kGroupMax;
     int modup_chunk = 8;
     bool pdl = true;                     // programmatic dependent launch between the path's kernels
+    int ntt_r8 = 0;                      // bit s: the radix-8 NTT plan at pipeline NTT site s (0..3)
     std::vector<u64> ext;                // moduli, ext order
     std::vector<u64> psi;                // smallest primitive 2N-th roots, ext order
     // host tables (for the host NTT used by keygen / encrypt / decrypt)
@@ -219,16 +220,20 @@ __device__ __forceinline__ ulonglong2 ld2_hint(const void *p, u64 pol)
 }
 #endif
 
+// r8: the radix-8 plan (256 threads per tile) instead of the radix-16 one;
+// both give the same words.
 cudaError_t launch_ntt(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, bool inverse,
-                       cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr);
+                       cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr, bool r8 = false);
 cudaError_t launch_ntt2(const he_ctx *ctx, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups,
-                        bool inverse, cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr);
+                        bool inverse, cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr,
+                        bool r8 = false);
 cudaError_t configure_ntt(const he_ctx *ctx);
 // Forward NTT of the fused ModDown + rescale limbs with the final combine in
 // its last pass: out[h][i] = (d_h[i] + KS_h[K+i] P^-1 - NTT(z)) q_{l-1}^-1,
 // written to each job's output (groups carry the combine fields).
 cudaError_t launch_ntt_combine(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
-                               cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr);
+                               cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr,
+                               bool r8 = false);
 // Number of final stages (the contiguous pass's last round) whose twiddle
 // runs the device table stores transposed; 0 for an unsupported logN.
 int ntt_direct_stages(int logN);

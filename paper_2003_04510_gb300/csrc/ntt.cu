@@ -48,6 +48,7 @@ struct NttArgs {
     const NttGroup *groups;
     const DevPrime *primes;
     int logN;
+    int ts;          // first stage whose twiddle runs the table stores transposed
     int tiles;       // tiles per limb
     const int *count;  // optional device-side group count (grids sized for a maximum)
     bool pdl;          // launched with programmatic dependent launch
@@ -199,26 +200,48 @@ __device__ __forceinline__ void ntt_round(u64 *sm, const ulonglong2 *tw, const T
     }
 }
 
-// L2 prefetch of the lines load_direct_tw will read (one thread per eight,
-// which share a 128-byte line of the transposed runs); issued when a CTA
-// starts, so the last round's loads hit L2 instead of DRAM.
+// Table position of twiddle m + t of stage m = 2^sigma.  The table stores
+// the runs of every stage sigma >= ts transposed: with d = sigma - ts, entry
+// m + t sits at m + (t mod 2^d) 2^ts + floor(t / 2^d).
+__host__ __device__ __forceinline__ size_t tw_pos(int sigma, int ts, size_t t)
+{
+    const int d = sigma - ts;
+    if (d <= 0) return ((size_t)1 << sigma) + t;
+    return ((size_t)1 << sigma) + ((t & (((size_t)1 << d) - 1)) << ts) + (t >> d);
+}
+
+// The direct round's twiddles of set Tn (its stages s0 + L0 + lp, lp < RL,
+// all at or after ts): twiddle j of stage lp is entry Tn 2^lp + j of that
+// stage, at base_lp + j 2^ts with base_lp = m + ((Tn mod 2^e) 2^lp) 2^ts +
+// floor(Tn / 2^e), e = s0 + L0 - ts.  For consecutive sets a warp reads
+// 2^e runs of consecutive entries per j.
+__device__ __forceinline__ const ulonglong2 *direct_base(const ulonglong2 *twg, int sigma, int ts, int e, int lp, int Tn)
+{
+    return twg + ((size_t)1 << sigma) + ((size_t)((Tn & ((1 << e) - 1)) << lp) << ts) + (Tn >> e);
+}
+
+// L2 prefetch of the lines the direct round will read (one thread per
+// 128-byte line of the transposed runs: the sets whose floor(Tn / 2^e) is a
+// multiple of eight); issued when a CTA starts, so the round's loads hit L2
+// instead of DRAM.
 template <int LOGM, int TE, int RL, int NT>
-__device__ __forceinline__ void prefetch_direct_tw(const ulonglong2 *twg, int tile, int s0)
+__device__ __forceinline__ void prefetch_direct_tw(const ulonglong2 *twg, int tile, int s0, int ts)
 {
     constexpr int L0 = LOGM - RL;
     constexpr int NG = TE >> LOGM;
     constexpr int SPT = (TE >> RL) / NT;
-    if (threadIdx.x & 7) return;
+    const int e = s0 + L0 - ts;
 #pragma unroll
     for (int si = 0; si < SPT; si++) {
         const int s = threadIdx.x + si * NT;
         const int Tn = ((tile * NG + (s >> L0)) << L0) + (s & ((1 << L0) - 1));
+        if ((Tn >> e) & 7) continue;
 #pragma unroll
         for (int lp = 0; lp < RL; lp++) {
-            const ulonglong2 *g = twg + (1 << (s0 + L0 + lp)) + Tn;
+            const ulonglong2 *g = direct_base(twg, s0 + L0 + lp, ts, e, lp, Tn);
 #pragma unroll
             for (int j = 0; j < (1 << lp); j++)
-                asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(g + ((size_t)j << (s0 + L0))));
+                asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(g + ((size_t)j << ts)));
         }
     }
 }
@@ -235,8 +258,19 @@ __device__ __forceinline__ size_t tile_gi(int e, int tile, int stride)
 // One pass of LOGM stages over a group of limbs.  Rounds RA, RB, RC (RC may
 // be 0) in forward order; the inverse runs them in reverse.  FIRST: read
 // group.src (else group.dst); LAST: apply the output reduction / scaling.
+// Resident CTAs per SM the register allocation is bounded for (0: no bound):
+// 256-thread tiles (radix-8 rounds) five (51 registers), forward 128-thread
+// tiles six (85 registers, what their shared memory allows; measured faster
+// than the compiler's own choice), inverse 128-thread tiles unbounded (their
+// first pass holds the direct round's fifteen twiddles from the start and
+// spills under a bound).
+__host__ __device__ constexpr int ntt_min_blocks(int nt, int logm, bool inv)
+{
+    return logm >= 12 ? 0 : nt >= 256 ? 5 : inv ? 0 : 6;
+}
+
 template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE, bool COMBINE = false>
-__global__ void __launch_bounds__(TE >> cmax(RA, cmax(RB, RC)))
+__global__ void __launch_bounds__(TE >> cmax(RA, cmax(RB, RC)), ntt_min_blocks(TE >> cmax(RA, cmax(RB, RC)), LOGM, INV))
 k_ntt_pass(const NttArgs P)
 {
     static_assert(!COMBINE || (LAST && !INV && !STRIDED), "the combine follows a forward contiguous last pass");
@@ -276,21 +310,27 @@ k_ntt_pass(const NttArgs P)
 #pragma unroll
         for (int l = 0; l < Gm::LS; l++) {
             const int n = NG << l;
-            const ulonglong2 *g = twg + (1 << (s0 + l)) + (size_t)tile * n;
-            for (int f = threadIdx.x; f < n; f += NT) __pipeline_memcpy_async(&tw[NG * ((1 << l) - 1) + f], &g[f], 16);
+            if (s0 + l < P.ts) {
+                const ulonglong2 *g = twg + (1 << (s0 + l)) + (size_t)tile * n;
+                for (int f = threadIdx.x; f < n; f += NT)
+                    __pipeline_memcpy_async(&tw[NG * ((1 << l) - 1) + f], &g[f], 16);
+            } else {  // a stage of the transposed region (radix-8 plans)
+                for (int f = threadIdx.x; f < n; f += NT)
+                    __pipeline_memcpy_async(&tw[NG * ((1 << l) - 1) + f],
+                                            &twg[tw_pos(s0 + l, P.ts, (size_t)tile * n + f)], 16);
+            }
         }
     }
-    if (DIRECT) prefetch_direct_tw<LOGM, TE, RL, NT>(twg, tile, s0);
+    if (DIRECT) prefetch_direct_tw<LOGM, TE, RL, NT>(twg, tile, s0, P.ts);
     griddep_wait();  // the limbs come from the previous kernels
     load_tile(0, buf);
     __pipeline_commit();
 
     // the direct round's twiddles -> registers (reloaded for every limb from
-    // L2 so that they are live only during that round).  The device table
-    // stores the runs of these stages transposed: entry m + T 2^lp + j of
-    // stage m = 2^(s0 + L0 + lp) sits at m + j 2^(s0 + L0) + T, so for each j
-    // a warp reads consecutive entries.
+    // L2 so that they are live only during that round), from the table's
+    // transposed runs (direct_base).
     constexpr int SPT = (TE >> RL) / NT;
+    const int te = s0 + L0 - P.ts;
     auto load_direct = [&](TwReg<RL, SPT> &T) {
 #pragma unroll
         for (int si = 0; si < SPT; si++) {
@@ -300,10 +340,9 @@ k_ntt_pass(const NttArgs P)
             const int Tn = (gg << L0) + khi;
 #pragma unroll
             for (int lp = 0; lp < RL; lp++) {
-                const ulonglong2 *g = twg + (1 << (s0 + L0 + lp)) + Tn;
+                const ulonglong2 *g = direct_base(twg, s0 + L0 + lp, P.ts, te, lp, Tn);
 #pragma unroll
-                for (int j = 0; j < (1 << lp); j++)
-                    T.t[si][(1 << lp) - 1 + j] = ld_tw(g + ((size_t)j << (s0 + L0)));
+                for (int j = 0; j < (1 << lp); j++) T.t[si][(1 << lp) - 1 + j] = ld_tw(g + ((size_t)j << P.ts));
             }
         }
     };
@@ -424,6 +463,27 @@ template <> struct Plan<16> { static constexpr int S1 = 8, A1 = 4, B1 = 4, C1 = 
 template <> struct Plan<17> { static constexpr int S1 = 9, A1 = 3, B1 = 3, C1 = 3, S2 = 8, A2 = 4, B2 = 4, C2 = 0; };
 template <int LOGN> constexpr int plan_direct() { return Plan<LOGN>::C2 ? Plan<LOGN>::C2 : Plan<LOGN>::B2; }
 
+// Radix-8 plans: every round of at most three stages, so a tile has 256
+// threads (twice the radix-16 plans' threads per limb: launches over few
+// limbs fill more of the GPU).  The direct round (the contiguous pass's last
+// two or three stages) lies inside the transposed region of the table the
+// radix-16 plan lays out (plan_direct stages), so both plans share one table.
+template <int LOGN> struct Plan8;
+// The round orders are the ones whose shared-memory accesses are free of
+// bank conflicts with the one-word-per-16 padding (a warp's 32 8-byte words
+// in two wavefronts), checked exhaustively on the CPU.
+template <> struct Plan8<13> { static constexpr int S1 = 7, A1 = 3, B1 = 2, C1 = 2, S2 = 6, A2 = 3, B2 = 3, C2 = 0; };
+template <> struct Plan8<14> { static constexpr int S1 = 7, A1 = 3, B1 = 2, C1 = 2, S2 = 7, A2 = 2, B2 = 3, C2 = 2; };
+template <> struct Plan8<15> { static constexpr int S1 = 8, A1 = 2, B1 = 3, C1 = 3, S2 = 7, A2 = 2, B2 = 3, C2 = 2; };
+template <> struct Plan8<16> { static constexpr int S1 = 8, A1 = 2, B1 = 3, C1 = 3, S2 = 8, A2 = 2, B2 = 3, C2 = 3; };
+template <> struct Plan8<17> { static constexpr int S1 = 9, A1 = 3, B1 = 3, C1 = 3, S2 = 8, A2 = 2, B2 = 3, C2 = 3; };
+template <int LOGN> constexpr bool plan8_fits()
+{
+    return (Plan8<LOGN>::C2 ? Plan8<LOGN>::C2 : Plan8<LOGN>::B2) <= plan_direct<LOGN>();
+}
+static_assert(plan8_fits<13>() && plan8_fits<14>() && plan8_fits<15>() && plan8_fits<16>() && plan8_fits<17>(),
+              "the radix-8 direct round must lie in the transposed region");
+
 // Two-pass transform: the strided pass covers the first S1 stages (forward
 // order), the contiguous pass the last S2.
 template <int S1, int A1, int B1, int C1, int S2, int A2, int B2, int C2>
@@ -457,18 +517,23 @@ cudaError_t two_pass(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cuda
     return e;
 }
 
-template <int LOGN>
+template <int LOGN, class P = Plan<LOGN>>
 cudaError_t two_pass_plan(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag)
 {
-    using P = Plan<LOGN>;
     return two_pass<P::S1, P::A1, P::B1, P::C1, P::S2, P::A2, P::B2, P::C2>(c, a, ngroups, inverse, st, tag);
 }
 
-// Forward transform whose last pass also applies the final combine.
 template <int LOGN>
+cudaError_t two_pass_any(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag, bool r8)
+{
+    return r8 ? two_pass_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, inverse, st, tag)
+              : two_pass_plan<LOGN, Plan<LOGN>>(c, a, ngroups, inverse, st, tag);
+}
+
+// Forward transform whose last pass also applies the final combine.
+template <int LOGN, class P>
 cudaError_t combine_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag)
 {
-    using P = Plan<LOGN>;
     constexpr int TE = 2048;
     a.tiles = (1 << LOGN) / TE;
     if (ngroups == 0) return run_pass<P::S2, P::A2, P::B2, P::C2, false, false, false, true, TE, true>(a, 0, st);
@@ -480,10 +545,17 @@ cudaError_t combine_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t s
     return e;
 }
 
+template <int LOGN>
+cudaError_t combine_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, bool r8)
+{
+    return r8 ? combine_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, st, tag)
+              : combine_plan<LOGN, Plan<LOGN>>(c, a, ngroups, st, tag);
+}
+
 }  // namespace
 
 cudaError_t launch_ntt_combine(const he_ctx *c, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
-                               cudaStream_t st, const char *tag, const int *dev_count)
+                               cudaStream_t st, const char *tag, const int *dev_count, bool r8)
 {
     if (ngroups < 0) return cudaSuccess;  // ngroups == 0: configure the kernels only
     NttArgs a;
@@ -492,6 +564,7 @@ cudaError_t launch_ntt_combine(const he_ctx *c, u64 *base, const NttGroup *group
     a.groups = groups;
     a.primes = c->d_primes;
     a.logN = c->logN;
+    a.ts = c->logN - ntt_direct_stages(c->logN);
     a.tiles = 1;
     a.count = dev_count;
     a.pdl = c->pdl;
@@ -504,17 +577,17 @@ cudaError_t launch_ntt_combine(const he_ctx *c, u64 *base, const NttGroup *group
         if (ngroups) prof_mark(c, st, tag, ".fwd_combine");
         return e;
     }
-    case 13: return combine_plan<13>(c, a, ngroups, st, tag);
-    case 14: return combine_plan<14>(c, a, ngroups, st, tag);
-    case 15: return combine_plan<15>(c, a, ngroups, st, tag);
-    case 16: return combine_plan<16>(c, a, ngroups, st, tag);
-    case 17: return combine_plan<17>(c, a, ngroups, st, tag);
+    case 13: return combine_any<13>(c, a, ngroups, st, tag, r8);
+    case 14: return combine_any<14>(c, a, ngroups, st, tag, r8);
+    case 15: return combine_any<15>(c, a, ngroups, st, tag, r8);
+    case 16: return combine_any<16>(c, a, ngroups, st, tag, r8);
+    case 17: return combine_any<17>(c, a, ngroups, st, tag, r8);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups, bool inverse,
-                        cudaStream_t st, const char *tag, const int *dev_count)
+                        cudaStream_t st, const char *tag, const int *dev_count, bool r8)
 {
     if (ngroups < 0) return cudaSuccess;  // ngroups == 0: configure the kernels only
     NttArgs a;
@@ -523,6 +596,7 @@ cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGrou
     a.groups = groups;
     a.primes = c->d_primes;
     a.logN = c->logN;
+    a.ts = c->logN - ntt_direct_stages(c->logN);
     a.tiles = 1;
     a.count = dev_count;
     a.pdl = c->pdl;
@@ -537,11 +611,11 @@ cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGrou
         prof_mark(c, st, tag, inverse ? ".inv" : ".fwd");
         return e;
     }
-    case 13: return two_pass_plan<13>(c, a, ngroups, inverse, st, tag);
-    case 14: return two_pass_plan<14>(c, a, ngroups, inverse, st, tag);
-    case 15: return two_pass_plan<15>(c, a, ngroups, inverse, st, tag);
-    case 16: return two_pass_plan<16>(c, a, ngroups, inverse, st, tag);
-    case 17: return two_pass_plan<17>(c, a, ngroups, inverse, st, tag);
+    case 13: return two_pass_any<13>(c, a, ngroups, inverse, st, tag, r8);
+    case 14: return two_pass_any<14>(c, a, ngroups, inverse, st, tag, r8);
+    case 15: return two_pass_any<15>(c, a, ngroups, inverse, st, tag, r8);
+    case 16: return two_pass_any<16>(c, a, ngroups, inverse, st, tag, r8);
+    case 17: return two_pass_any<17>(c, a, ngroups, inverse, st, tag, r8);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -560,20 +634,24 @@ int ntt_direct_stages(int logN)
 }
 
 cudaError_t launch_ntt(const he_ctx *c, u64 *base, const NttGroup *groups, int ngroups, bool inverse, cudaStream_t st,
-                       const char *tag, const int *dev_count)
+                       const char *tag, const int *dev_count, bool r8)
 {
-    return launch_ntt2(c, base, base, groups, ngroups, inverse, st, tag, dev_count);
+    return launch_ntt2(c, base, base, groups, ngroups, inverse, st, tag, dev_count, r8);
 }
 
-// Set the dynamic shared-memory limit of every NTT pass this ring size uses
-// (done once per context, before any launch or stream capture).
+// Set the dynamic shared-memory limit of every NTT pass this ring size uses,
+// in both plans (done once per context, before any launch or stream capture).
 cudaError_t configure_ntt(const he_ctx *c)
 {
-    cudaError_t e = launch_ntt2(c, nullptr, nullptr, nullptr, 0, false, nullptr);
-    if (e != cudaSuccess) return e;
     JobRef R;
     memset(&R, 0, sizeof(R));
-    return launch_ntt_combine(c, nullptr, nullptr, 0, R, nullptr);
+    for (int r8 = 0; r8 < 2; r8++) {
+        cudaError_t e = launch_ntt2(c, nullptr, nullptr, nullptr, 0, false, nullptr, nullptr, nullptr, r8 != 0);
+        if (e != cudaSuccess) return e;
+        e = launch_ntt_combine(c, nullptr, nullptr, 0, R, nullptr, nullptr, nullptr, r8 != 0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace he

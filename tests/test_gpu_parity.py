@@ -544,9 +544,28 @@ def test_every_shape_is_bit_identical_n16(g):
     c2 = np.ascontiguousarray(np.stack([ct2[0, :level], ct2[1, :level]]))
     want = oracle.rescale(op, oracle.he_mul(op, c1, c2, evk, level), level)
     try:
-        for cap, chunk, pdl in ((1, 4, 1), (2, 16, 0), (3, 8, 1), (4, 16, 0), (4, 8, 1)):
-            g.he_set_shape(ctx, cap, chunk, pdl)
-            assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want), (cap, chunk, pdl)
+        for shape in ((1, 4, 1, 15), (2, 16, 0, 5), (3, 8, 1, 10), (4, 16, 0, 0), (4, 8, 1, 0), (1, 8, 1, 3)):
+            g.he_set_shape(ctx, *shape)
+            assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want), shape
+        g.he_set_shape(ctx, 2, 8, 1, 15)  # the plain ModDown path with the radix-8 plans
+        want_plain = oracle.he_mul(op, c1, c2, evk, level)
+        assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=False), want_plain)
+    finally:
+        g.he_set_shape(ctx, 4, 8, 1)
+
+
+@pytest.mark.parametrize("name,level", [("n15", 16), ("n15", 5), ("n17", 13)])
+def test_radix8_plans_bit_identical(g, name, level):
+    """Every NTT site on its radix-8 plan (the plans differ per ring size)."""
+    op = oracle.preset(name)
+    ctx = ctx_for(g, name)
+    evk = rand_evk(op, 900 + level)
+    evk_t = dev(g, evk)
+    c1, c2 = rand_ct(op, level, 910 + level), rand_ct(op, level, 920 + level)
+    try:
+        g.he_set_shape(ctx, 1, 8, 1, 15)
+        want = oracle.rescale(op, oracle.he_mul(op, c1, c2, evk, level), level)
+        assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want)
     finally:
         g.he_set_shape(ctx, 4, 8, 1)
 
@@ -566,8 +585,16 @@ def test_autotune_batch_keeps_results(g):
     ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
     try:
         best, tried = g.he_autotune(ctx, jobs, evk_t, ws, reps=2)
-        assert len(tried) == 24 and all(t[3] > 0 for t in tried)
-        assert best[:3] == g.he_get_shape(ctx) and best[3] == min(t[3] for t in tried)
+        assert len(tried) == 39 and all(t[4] > 0 for t in tried)
+        assert best[:4] == g.he_get_shape(ctx) and best[4] == min(t[4] for t in tried)
+        assert sorted(t[3] for t in tried[24:]) == list(range(1, 16))
+        for j in jobs:
+            j[2].zero_()
+        g.he_mul_batch(ctx, jobs, evk_t, ws)
+        torch.cuda.synchronize()
+        for j, w in zip(jobs, want):
+            assert np.array_equal(host(g, j[2]), w)
+        g.he_set_shape(ctx, 2, 8, 1, 15)  # the batch on the radix-8 plans
         for j in jobs:
             j[2].zero_()
         g.he_mul_batch(ctx, jobs, evk_t, ws)
