@@ -34,6 +34,9 @@ namespace he {
 namespace {
 
 constexpr int kThreads = 256;
+// Base conversions: two targets per loop trip, so one target's reduction
+// overlaps the next target's multiply-adds.
+constexpr int kConvUnroll = 2;
 
 __device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *reinterpret_cast<const ulonglong2 *>(p); }
 __device__ __forceinline__ void st2(u64 *p, u64 x, u64 y) { *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(x, y); }
@@ -115,6 +118,7 @@ k_modup(const JobRef R, const DevLevel *__restrict__ lv_arr, const DevPrime *__r
     }
     __syncthreads();
     u64 *Uj = it.ws + ((size_t)lv.o_u + (size_t)j * E) * N;
+#pragma unroll kConvUnroll
     for (int u = 0; u < cnt; u++) {
         Acc3 ax = {0, 0, 0}, ay = {0, 0, 0};
 #pragma unroll
@@ -231,7 +235,7 @@ __device__ __forceinline__ void conv_one(const uint32_t *x0, const uint32_t *x1,
 }
 
 template <int KM, bool FUSED>
-__global__ void __launch_bounds__(kThreads, KM <= 8 ? 3 : 1)
+__global__ void __launch_bounds__(kThreads, KM <= 8 ? 3 : 2)  // 85 / 128 registers
 k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__restrict__ pinv,
                const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int N, int chunks)
 {
@@ -288,6 +292,7 @@ k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__r
         rx = add_mod(r0.x, sub_mod(shoup(r1.x, pv.x, pv.y, q), cx, q), q);
         ry = add_mod(r0.y, sub_mod(shoup(r1.y, pv.x, pv.y, q), cy, q), q);
     }
+#pragma unroll kConvUnroll
     for (int r = 0; r < cnt; r++) {
         const u64 q = sq[r];
         u64 cx, cy;

@@ -106,7 +106,12 @@ __device__ __forceinline__ void mac(U128 &acc, u64 a, u64 b)
 // V mod q for V = acc < 2^(b+61); s = b - 2 (1 <= s <= 60), mu = floor(2^(64+s) / q).
 __device__ __forceinline__ u64 barrett128(U128 v, u64 q, u64 mu, unsigned s)
 {
-    u64 u = (v.lo >> s) | (v.hi << (64 - s));
+    // bits [s, s + 64) of v from two 32-bit funnel shifts (the word triple
+    // starts one word higher when s >= 32; the shift amount is s mod 32)
+    const uint32_t l0 = (uint32_t)v.lo, l1 = (uint32_t)(v.lo >> 32), h0 = (uint32_t)v.hi, h1 = (uint32_t)(v.hi >> 32);
+    const bool up = s >= 32;
+    const uint32_t w0 = up ? l1 : l0, w1 = up ? h0 : l1, w2 = up ? h1 : h0;
+    const u64 u = ((u64)__funnelshift_r(w1, w2, s) << 32) | __funnelshift_r(w0, w1, s);
     u64 qh = __umul64hi(u, mu);
     u64 r = v.lo - qh * q;  // in [0, 2q)
     return csub(r, q);
