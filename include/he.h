@@ -183,6 +183,22 @@ size_t he_host_workspace_bytes(const he_ctx *ctx, int level);
 int he_mul_rescale_host(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *evk_dev, int level,
                         uint64_t *out, void *ws, size_t ws_bytes, void *stream);
 
+/* A stream of HE Mul + rescale jobs from host buffers: job k's operands
+ * ct1[k], ct2[k] (host, [2][levels[k]][N]) are copied to the device, run
+ * through the path (he_mul_rescale) and the result copied to out[k] (host,
+ * [2][levels[k]-1][N]).  Uploads and downloads run on two copy streams the
+ * context owns, the path on `stream`, and `slots` (2..4) device staging slots
+ * let job k+1's upload and job k-1's download overlap job k's kernels (the
+ * host buffers should be pinned for that).  ws: device memory of at least
+ * he_host_stream_workspace_bytes(max level, slots) (one path workspace plus
+ * the slots).  Returns once every result is in host memory.  HE_ELEVEL for a
+ * level outside 2..L, HE_ENOMEM for a short workspace, HE_EINVAL otherwise.
+ * Calls on one context must not overlap (the copy streams are shared). */
+size_t he_host_stream_workspace_bytes(const he_ctx *ctx, int max_level, int slots);
+int he_mul_rescale_host_stream(he_ctx *ctx, int count, const uint64_t *const *ct1, const uint64_t *const *ct2,
+                               const int *levels, uint64_t *const *out, const uint64_t *evk_dev, void *ws,
+                               size_t ws_bytes, int slots, void *stream);
+
 /* ---- individual steps of the path (per-kernel parity) -------------------- */
 
 /* Forward / inverse NTT (Algo 3 / its inverse) of `count` limbs in place:

@@ -105,6 +105,10 @@ _SIGS = {
     "he_mul_rescale_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                            ctypes.c_void_p]),
+    "he_host_stream_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "he_mul_rescale_host_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]),
     "he_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "he_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
@@ -553,6 +557,30 @@ def he_mul_rescale_host(ctx, ct1: np.ndarray, ct2: np.ndarray, evk, level, out: 
     """ct1, ct2, out: host numpy uint64 arrays (pinned memory gives async copies)."""
     _check(lib().he_mul_rescale_host(ctx.ptr, _np_ptr(ct1), _np_ptr(ct2), _dev_ptr(evk), level, _np_ptr(out),
                                      _dev_ptr(ws), ws.numel() * 8, _stream_ptr(stream)), "he_mul_rescale_host")
+
+
+def he_host_stream_workspace_bytes(ctx, max_level: int, slots: int = 2) -> int:
+    return int(lib().he_host_stream_workspace_bytes(ctx.ptr, max_level, slots))
+
+
+def he_mul_rescale_host_stream(ctx, ct1s, ct2s, levels, outs, evk, ws, slots: int = 2, stream=None):
+    """Jobs from host buffers, pipelined: ct1s[k], ct2s[k] ([2][levels[k]][N])
+    and outs[k] ([2][levels[k]-1][N]) are host numpy uint64 arrays (pinned
+    memory lets the copies overlap the kernels)."""
+    n = len(levels)
+    if not (len(ct1s) == len(ct2s) == len(outs) == n):
+        raise ValueError("ct1s, ct2s, levels and outs differ in length")
+    for a in list(ct1s) + list(ct2s) + list(outs):
+        if a.dtype != np.uint64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffers must be C-contiguous uint64 arrays")
+    p1 = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data for a in ct1s])
+    p2 = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data for a in ct2s])
+    po = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data for a in outs])
+    lv = (ctypes.c_int * max(n, 1))(*[int(v) for v in levels])
+    _check(lib().he_mul_rescale_host_stream(ctx.ptr, n, ctypes.cast(p1, ctypes.c_void_p), ctypes.cast(p2, ctypes.c_void_p),
+                                            ctypes.cast(lv, ctypes.c_void_p), ctypes.cast(po, ctypes.c_void_p),
+                                            _dev_ptr(evk), _dev_ptr(ws), ws.numel() * 8, slots, _stream_ptr(stream)),
+           "he_mul_rescale_host_stream")
 
 
 def he_profile(ctx, enable: bool):

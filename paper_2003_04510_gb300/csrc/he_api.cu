@@ -212,6 +212,11 @@ int he_ctx_destroy(he_ctx *c)
 {
     if (!c) return HE_EINVAL;
     for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+    for (auto &slot : c->io_ev)
+        for (cudaEvent_t e : slot)
+            if (e) cudaEventDestroy(e);
+    if (c->io_h2d) cudaStreamDestroy(c->io_h2d);
+    if (c->io_d2h) cudaStreamDestroy(c->io_d2h);
     if (c->arena) cudaFree(c->arena);
     delete c;
     return HE_OK;
@@ -699,6 +704,69 @@ int he_mul_rescale_host(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, con
     int rc = hemul_pipeline(c, d1, d2, evk, level, dout, w, true, st);
     if (rc) return rc;
     HE_TRY(cudaMemcpyAsync(out, dout, 2 * (size_t)(level - 1) * limb, cudaMemcpyDeviceToHost, st));
+    HE_TRY(cudaStreamSynchronize(st));
+    return HE_OK;
+}
+
+size_t he_host_stream_workspace_bytes(const he_ctx *c, int max_level, int slots)
+{
+    if (!c || max_level < 2 || max_level > c->L || slots < 2 || slots > 4) return 0;
+    size_t path = 0;
+    for (int l = 2; l <= max_level; l++) path = std::max(path, ws_bytes_for(c, l));
+    const size_t limb = (size_t)c->N * sizeof(u64);
+    return path + (size_t)slots * (6 * (size_t)max_level - 2) * limb;
+}
+
+int he_mul_rescale_host_stream(he_ctx *c, int count, const uint64_t *const *ct1, const uint64_t *const *ct2,
+                               const int *levels, uint64_t *const *out, const uint64_t *evk, void *ws,
+                               size_t ws_bytes, int slots, void *stream)
+{
+    if (check_dev(c) || count < 0 || !evk || !ws || slots < 2 || slots > 4) return HE_EINVAL;
+    if (count == 0) return HE_OK;
+    if (!ct1 || !ct2 || !levels || !out) return HE_EINVAL;
+    if (!aligned(ws) || !aligned(evk)) return HE_EINVAL;
+    int ml = 0;
+    for (int k = 0; k < count; k++) {
+        if (!ct1[k] || !ct2[k] || !out[k]) return HE_EINVAL;
+        if (levels[k] < 2 || levels[k] > c->L) return HE_ELEVEL;
+        ml = std::max(ml, levels[k]);
+    }
+    if (ws_bytes < he_host_stream_workspace_bytes(c, ml, slots)) return HE_ENOMEM;
+    {
+        std::lock_guard<std::mutex> lk(c->io_mu);
+        if (!c->io_h2d && cudaStreamCreateWithFlags(&c->io_h2d, cudaStreamNonBlocking) != cudaSuccess) return HE_ECUDA;
+        if (!c->io_d2h && cudaStreamCreateWithFlags(&c->io_d2h, cudaStreamNonBlocking) != cudaSuccess) return HE_ECUDA;
+        for (auto &slot : c->io_ev)
+            for (cudaEvent_t &e : slot)
+                if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return HE_ECUDA;
+    }
+    size_t path = 0;
+    for (int l = 2; l <= ml; l++) path = std::max(path, ws_bytes_for(c, l));
+    const size_t limb = (size_t)c->N * sizeof(u64);
+    const size_t slot_bytes = (6 * (size_t)ml - 2) * limb;
+    u64 *w = (u64 *)ws;
+    cudaStream_t st = S(stream), up = c->io_h2d, down = c->io_d2h;
+    for (int k = 0; k < count; k++) {
+        const int s = k % slots, l = levels[k];
+        cudaEvent_t *ev = c->io_ev[s];  // 0: inputs copied, 1: path done, 2: result copied
+        char *sb = (char *)ws + path + (size_t)s * slot_bytes;
+        u64 *a = (u64 *)sb, *b = (u64 *)(sb + 2 * (size_t)ml * limb), *o = (u64 *)(sb + 4 * (size_t)ml * limb);
+        // the slot's inputs are free once the path of job k - slots has run
+        if (k >= slots) HE_TRY(cudaStreamWaitEvent(up, ev[1], 0));
+        HE_TRY(cudaMemcpyAsync(a, ct1[k], 2 * (size_t)l * limb, cudaMemcpyHostToDevice, up));
+        HE_TRY(cudaMemcpyAsync(b, ct2[k], 2 * (size_t)l * limb, cudaMemcpyHostToDevice, up));
+        HE_TRY(cudaEventRecord(ev[0], up));
+        // the path waits for its inputs and for the slot's previous result to be read back
+        HE_TRY(cudaStreamWaitEvent(st, ev[0], 0));
+        if (k >= slots) HE_TRY(cudaStreamWaitEvent(st, ev[2], 0));
+        int rc = hemul_pipeline(c, a, b, evk, l, o, w, true, st);
+        if (rc) return rc;
+        HE_TRY(cudaEventRecord(ev[1], st));
+        HE_TRY(cudaStreamWaitEvent(down, ev[1], 0));
+        HE_TRY(cudaMemcpyAsync(out[k], o, 2 * (size_t)(l - 1) * limb, cudaMemcpyDeviceToHost, down));
+        HE_TRY(cudaEventRecord(ev[2], down));
+    }
+    HE_TRY(cudaStreamSynchronize(down));
     HE_TRY(cudaStreamSynchronize(st));
     return HE_OK;
 }
