@@ -81,6 +81,7 @@ def lib():
             "or_keyswitch": (None, [i32, i32, i32, i32, i32, P, P, P, P, P, P, P, P, P]),
             "or_he_mul": (None, [i32, i32, i32, i32, i32, P, P, P, P, P, P, P, P]),
             "or_rescale": (None, [i32, i32, P, P, P, P]),
+            "or_he_mul_rescale_pq": (None, [i32, i32, i32, i32, i32, P, P, P, P, P, P, P, P]),
             "or_automorphism": (None, [P, i32, u64, u64, P]),
             "or_keygen_rot": (None, [i32, i32, i32, i32, P, P, P, P, dbl, P, u64, u64, P]),
             "or_rotate": (None, [i32, i32, i32, i32, i32, P, P, P, P, P, u64, P, P]),
@@ -301,6 +302,15 @@ def he_mul(prm: Params, ct1, ct2, evk, level: int) -> np.ndarray:
     out = np.zeros((2, level, prm.N), dtype=np.uint64)
     lib().or_he_mul(prm.logN, level, prm.L, prm.K, prm.alpha, _p(prm.q), _p(prm.psi_q), _p(prm.p),
                     _p(prm.psi_p), _p(_u64(ct1)), _p(_u64(ct2)), _p(_u64(evk)), _p(out))
+    return out
+
+
+def he_mul_rescale_pq(prm: Params, ct1, ct2, evk, level: int) -> np.ndarray:
+    """HE Mul with ModDown and rescale as one division by P q_{l-1} (one floor
+    instead of two); [2][level-1][N] NTT domain."""
+    out = np.zeros((2, level - 1, prm.N), dtype=np.uint64)
+    lib().or_he_mul_rescale_pq(prm.logN, level, prm.L, prm.K, prm.alpha, _p(prm.q), _p(prm.psi_q), _p(prm.p),
+                               _p(prm.psi_p), _p(_u64(ct1)), _p(_u64(ct2)), _p(_u64(evk)), _p(out))
     return out
 
 

@@ -684,6 +684,92 @@ void or_rescale(int logN, int l, const uint64_t *q, const uint64_t *psi_q, const
 }
 
 /* ---------------------------------------------------------------------------
+ * HE Mul followed by one division by M = P * q_{l-1}: ModDown and rescale
+ * folded into a single fast base conversion (the single-division variant of
+ * the key-switch tail; not in the paper, built on Fig. 2's flow and the
+ * full-RNS "mod down ... with an additional division" of Sec. 7).
+ * For each half h (b, a), over the basis Q_l and P, in the NTT domain:
+ *   Y_h[p_k] = KS_h[p_k],   Y_h[q_i] = P d_h[i] + KS_h[q_i]  (mod q_i)
+ * (the tensor products d0, d1 lifted by P, plus the inner product).  The
+ * basis B = (p_0, ..., p_{K-1}, q_{l-1}) with product M is dropped by:
+ *   x_j    = iNTT(Y_h[b_j]) in [0, b_j)
+ *   y_j    = x_j [Mhat_j^-1]_{b_j},   Mhat_j = M / b_j
+ *   conv_i = sum_j y_j [Mhat_j]_{q_i} mod q_i   (i < l-1), NTT(conv_i)
+ *   out_i  = (Y_h[q_i] - NTT(conv_i)) [M^-1]_{q_i}
+ * In coefficient form out = floor(Y / M) - floor(sum_j y_j / b_j) mod Q_{l-1},
+ * Y the CRT value of Y_h over P Q_l (one floor, where HE Mul followed by a
+ * rescale takes two).  ct1, ct2: [2][l][N]; out: [2][l-1][N]; 2 <= l.
+ * ------------------------------------------------------------------------- */
+void or_he_mul_rescale_pq(int logN, int l, int L, int K, int alpha, const uint64_t *q, const uint64_t *psi_q,
+                          const uint64_t *p, const uint64_t *psi_p, const uint64_t *ct1, const uint64_t *ct2,
+                          const uint64_t *evk, uint64_t *out)
+{
+    uint64_t N = 1ull << logN;
+    size_t LN = (size_t)l * N;
+    int E = K + l, nb = K + 1;
+    uint64_t *d = (uint64_t *)malloc(3 * LN * sizeof(uint64_t));
+    uint64_t *ks = (uint64_t *)malloc(2 * LN * sizeof(uint64_t));
+    uint64_t *KS = (uint64_t *)malloc((size_t)2 * E * N * sizeof(uint64_t));
+    uint64_t *Y = (uint64_t *)malloc((size_t)E * N * sizeof(uint64_t));
+    uint64_t *y = (uint64_t *)malloc((size_t)nb * N * sizeof(uint64_t));
+    uint64_t *conv = (uint64_t *)malloc(N * sizeof(uint64_t));
+    uint64_t *b = (uint64_t *)malloc((size_t)nb * sizeof(uint64_t));
+    uint64_t *bpsi = (uint64_t *)malloc((size_t)nb * sizeof(uint64_t));
+    or_tensor(logN, l, q, ct1, ct2, d, d + LN, d + 2 * LN);
+    or_keyswitch(logN, l, L, K, alpha, q, psi_q, p, psi_p, d + 2 * LN, evk, ks, NULL, KS);
+    for (int k = 0; k < K; k++) { b[k] = p[k]; bpsi[k] = psi_p[k]; }
+    b[K] = q[l - 1];
+    bpsi[K] = psi_q[l - 1];
+    for (int h = 0; h < 2; h++) {
+        const uint64_t *dh = d + (size_t)h * LN, *KSh = KS + (size_t)h * E * N;
+        /* Y_h = P d_h + KS_h */
+        for (int k = 0; k < K; k++) memcpy(Y + (size_t)k * N, KSh + (size_t)k * N, N * sizeof(uint64_t));
+        for (int i = 0; i < l; i++) {
+            uint64_t Pm = 1;
+            for (int k = 0; k < K; k++) Pm = mulmod(Pm, p[k] % q[i], q[i]);
+            for (uint64_t n = 0; n < N; n++)
+                Y[((size_t)K + i) * N + n] =
+                    addmod(mulmod(Pm, dh[(size_t)i * N + n], q[i]), KSh[((size_t)K + i) * N + n], q[i]);
+        }
+        /* x_j, y_j over the dropped basis B */
+        for (int j = 0; j < nb; j++) {
+            uint64_t *yj = y + (size_t)j * N;
+            size_t row = j < K ? (size_t)j : (size_t)K + l - 1;
+            memcpy(yj, Y + row * N, N * sizeof(uint64_t));
+            or_intt(yj, logN, b[j], bpsi[j]);
+            uint64_t mhat = 1;
+            for (int j2 = 0; j2 < nb; j2++)
+                if (j2 != j) mhat = mulmod(mhat, b[j2] % b[j], b[j]);
+            uint64_t mhat_inv = invmod(mhat, b[j]);
+            for (uint64_t n = 0; n < N; n++) yj[n] = mulmod(yj[n], mhat_inv, b[j]);
+        }
+        for (int i = 0; i < l - 1; i++) {
+            uint64_t qi = q[i], Mm = 1;
+            uint64_t *mh = (uint64_t *)malloc((size_t)nb * sizeof(uint64_t));
+            for (int j = 0; j < nb; j++) {
+                uint64_t v = 1;
+                for (int j2 = 0; j2 < nb; j2++)
+                    if (j2 != j) v = mulmod(v, b[j2] % qi, qi);
+                mh[j] = v;
+                Mm = mulmod(Mm, b[j] % qi, qi);
+            }
+            uint64_t Minv = invmod(Mm, qi);
+            for (uint64_t n = 0; n < N; n++) {
+                uint64_t acc = 0;
+                for (int j = 0; j < nb; j++) acc = addmod(acc, mulmod(y[(size_t)j * N + n] % qi, mh[j], qi), qi);
+                conv[n] = acc;
+            }
+            or_ntt(conv, logN, qi, psi_q[i]);
+            uint64_t *o = out + ((size_t)h * (l - 1) + i) * N;
+            for (uint64_t n = 0; n < N; n++)
+                o[n] = mulmod(submod(Y[((size_t)K + i) * N + n], conv[n], qi), Minv, qi);
+            free(mh);
+        }
+    }
+    free(d); free(ks); free(KS); free(Y); free(y); free(conv); free(b); free(bpsi);
+}
+
+/* ---------------------------------------------------------------------------
  * Galois automorphism kappa_g : a(X) -> a(X^g) on Z_q[X]/(X^N + 1), g odd in
  * [1, 2N).  Written from the definition: coefficient i goes to exponent
  * i*g mod 2N, and an exponent e >= N is X^(e-N) * X^N = -X^(e-N).  (Rotation
