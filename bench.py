@@ -629,6 +629,35 @@ def run_ours(args):
         g.he_evk_unregister(ctx, evk_b_t)
         del evk_b_t
 
+    # ---- ModDown and rescale as one division by P q_{l-1} (different words) ----
+    pq = None
+    if not args.no_rotate:
+        for k in range(3):
+            a, b = ct_t[k % NPAIRS]
+            g.he_mul_rescale_pq(ctx, a, b, evk_t, level, outs[k % NPAIRS], ws, stream)
+        torch.cuda.synchronize()
+        zq = g.he_decrypt(ctx, sk, g.to_host(outs[2]), level - 1, sc * sc / float(ctx.q[level - 1]))
+        m_q = si.messages(N // 2, s1 + 34) * si.messages(N // 2, s2 + 34)
+        reps = max(20, min(args.steps, 1000))
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for k in range(reps):
+            a, b = ct_t[k % NPAIRS]
+            g.he_mul_rescale_pq(ctx, a, b, evk_t, level, outs[k % NPAIRS], ws, stream)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        qms = q0.elapsed_time(q1) / reps
+        g.he_profile(ctx, True)
+        for k in range(20):
+            a, b = ct_t[k % NPAIRS]
+            g.he_mul_rescale_pq(ctx, a, b, evk_t, level, outs[k % NPAIRS], ws, stream)
+        qprof = g.he_profile_read(ctx)
+        g.he_profile(ctx, False)
+        md = qprof.get("moddown_conv")
+        pq = {"HE_Mul_per_s": 1e3 / qms, "ms": qms, "reps": reps,
+              "moddown_conv_us": (md[0] / md[1] * 1e3) if md else None,
+              "decrypt_max_err": float(np.abs(zq - m_q).max())}
+
     # ---- HE rotation (Galois automorphism + key switch) on the same workload ----
     rot = None
     if not args.no_rotate:
@@ -814,6 +843,7 @@ def run_ours(args):
                          "tried": [{"group_cap": t[0], "modup_chunk": t[1], "pdl": t[2], "ntt_r8": t[3], "ms": t[4]}
                                    for t in tune_tried]},
             "n17_single": n17,
+            "rescale_pq": pq,
             "seeded_evk": seeded,
             "nonrns_paper": nonrns,
             "rotate": rot,

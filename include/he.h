@@ -151,6 +151,18 @@ int he_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, void *
 int he_mul_rescale(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *evk_dev, int level,
                    uint64_t *out, void *ws, size_t ws_bytes, void *stream);
 
+/* HE Mul with ModDown and rescale as one division by M = P * q_{level-1}
+ * (Sec. 7's mod down "with an additional division", applied once for both
+ * divisions): with Y = P*(d0, d1) + KS over Q_level and P, the basis
+ * (p_0, ..., p_{K-1}, q_{level-1}) is dropped by one fast base conversion, so
+ * out = floor(Y / M) - floor(sum_j y_j / b_j) in coefficient form: one floor
+ * where he_mul_rescale takes two, hence different words (decrypting to the
+ * same product within the same error bound) and one fewer conversion row.
+ * out: [2][level-1][N], scale1*scale2/q_{level-1}.  level >= 2; errors as
+ * he_mul_rescale. */
+int he_mul_rescale_pq(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *evk_dev, int level,
+                      uint64_t *out, void *ws, size_t ws_bytes, void *stream);
+
 /* he_mul_rescale with no workspace argument.  The paper has no counterpart:
  * this is a library convenience for callers that cannot allocate device
  * memory or keep a workspace between calls (for example a host application

@@ -85,6 +85,9 @@ _SIGS = {
     "he_mul_rescale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.c_void_p]),
+    "he_mul_rescale_pq": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.c_void_p]),
     "he_rescale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_size_t, ctypes.c_void_p]),
     "he_step_ntt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -350,6 +353,12 @@ def he_mul(ctx, ct1, ct2, evk, level, out, ws, stream=None):
 def he_mul_rescale(ctx, ct1, ct2, evk, level, out, ws, stream=None):
     _check(lib().he_mul_rescale(ctx.ptr, _dev_ptr(ct1), _dev_ptr(ct2), _dev_ptr(evk), level, _dev_ptr(out),
                                 _dev_ptr(ws), ws.numel() * 8, _stream_ptr(stream)), "he_mul_rescale")
+
+
+def he_mul_rescale_pq(ctx, ct1, ct2, evk, level, out, ws, stream=None):
+    """HE Mul with ModDown and rescale as one division by P q_{level-1}."""
+    _check(lib().he_mul_rescale_pq(ctx.ptr, _dev_ptr(ct1), _dev_ptr(ct2), _dev_ptr(evk), level, _dev_ptr(out),
+                                   _dev_ptr(ws), ws.numel() * 8, _stream_ptr(stream)), "he_mul_rescale_pq")
 
 
 # he_mul_rescale_static's scratch size (HE_STATIC_SCRATCH_BYTES in he.h)

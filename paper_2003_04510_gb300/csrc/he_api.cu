@@ -66,24 +66,26 @@ struct Stages {
     const int *counts = nullptr;               // optional device-side counts of the four lists
 };
 
-// The HE Mul pipeline for one job or a batch (JobRef).  fused = ModDown and
-// rescale merged (out is [2][l-1][N]); otherwise out is the level-l product.
+// The HE Mul pipeline for one job or a batch (JobRef).  mode (TailMode):
+// kTailPlain, out is the level-l product; kTailRescale, ModDown and rescale
+// merged with two floors (out is [2][l-1][N], bit-identical to he_mul then
+// he_rescale); kTailRescalePQ, one division by P q_{l-1} (out [2][l-1][N]).
 // NTT group offsets are relative to ntt_base.
-int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, bool fused,
+int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, int mode,
                   cudaStream_t st);
 
-int run_pipeline(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, bool fused,
+int run_pipeline(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, int mode,
                  cudaStream_t st)
 {
     prof_mark(c, st, "");
     // Region 1: tensor product
     HE_TRY(run_tensor(c, R, st));
     prof_mark(c, st, "tensor");
-    return run_keyswitch(c, R, ntt_base, S, evk, fused, st);
+    return run_keyswitch(c, R, ntt_base, S, evk, mode, st);
 }
 
 // Region 2 and the final additions, on d0, d1, d2 already in the workspace.
-int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, bool fused,
+int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, int mode,
                   cudaStream_t st)
 {
     // key switching: iNTT(d2) (times N^-1 Qhat^-1), ModUp, NTT, inner product
@@ -97,9 +99,9 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
     prof_mark(c, st, "inner_product");
     // ModDown: iNTT of the special limbs (times N^-1 Phat^-1), conversion, NTT
     HE_TRY(launch_ntt(c, ntt_base, S.intt2, S.n_intt2, true, st, "intt_special", cnt ? cnt + 2 : nullptr, r8(2)));
-    HE_TRY(run_moddown_conv(c, R, fused, st));
+    HE_TRY(run_moddown_conv(c, R, mode, st));
     prof_mark(c, st, "moddown_conv");
-    if (fused) {
+    if (mode != kTailPlain) {
         // the final combine runs in the last NTT pass (writes each job's output)
         HE_TRY(launch_ntt_combine(c, ntt_base, S.ntt_last, S.n_ntt_last, R, st, "ntt_moddown", cnt ? cnt + 3 : nullptr,
                                   r8(3)));
@@ -127,25 +129,26 @@ JobRef single_job(const u64 *ct1, const u64 *ct2, u64 *out, u64 *ws, int l)
     return R;
 }
 
-Stages level_stages(const he_ctx *c, int l, bool fused)
+Stages level_stages(const he_ctx *c, int l, int mode)
 {
     const LevelJobs &J = c->jobs[l];
+    const bool fused = mode != kTailPlain;
     Stages S;
     S.intt1 = fused ? J.intt1f : J.intt1;
     S.n_intt1 = fused ? J.n_intt1f : J.n_intt1;
     S.ntt_up = J.ntt_up;
     S.n_ntt_up = J.n_ntt_up;
-    S.intt2 = fused ? J.intt2f : J.intt2;
-    S.n_intt2 = fused ? J.n_intt2f : J.n_intt2;
+    S.intt2 = mode == kTailRescalePQ ? J.intt2pq : fused ? J.intt2f : J.intt2;
+    S.n_intt2 = mode == kTailRescalePQ ? J.n_intt2pq : fused ? J.n_intt2f : J.n_intt2;
     S.ntt_last = fused ? J.ntt_z : J.ntt_conv;
     S.n_ntt_last = fused ? J.n_ntt_z : J.n_ntt_conv;
     return S;
 }
 
 int hemul_pipeline(he_ctx *c, const u64 *ct1, const u64 *ct2, const u64 *evk, int l, u64 *out, u64 *ws,
-                   bool fused, cudaStream_t st)
+                   int mode, cudaStream_t st)
 {
-    return run_pipeline(c, single_job(ct1, ct2, out, ws, l), ws, level_stages(c, l, fused), evk, fused, st);
+    return run_pipeline(c, single_job(ct1, ct2, out, ws, l), ws, level_stages(c, l, mode), evk, mode, st);
 }
 
 // ---- batches -------------------------------------------------------------
@@ -252,7 +255,7 @@ int he_mul(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *
     if (level < 1 || level > c->L) return HE_ELEVEL;
     if (!aligned(ct1) || !aligned(ct2) || !aligned(out) || !aligned(ws) || !aligned(evk)) return HE_EINVAL;
     if (ws_bytes < ws_bytes_for(c, level)) return HE_ENOMEM;
-    return hemul_pipeline(c, ct1, ct2, evk, level, out, (u64 *)ws, false, S(stream));
+    return hemul_pipeline(c, ct1, ct2, evk, level, out, (u64 *)ws, kTailPlain, S(stream));
 }
 
 int he_mul_rescale(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *evk, int level,
@@ -262,7 +265,17 @@ int he_mul_rescale(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, const ui
     if (level < 2 || level > c->L) return HE_ELEVEL;
     if (!aligned(ct1) || !aligned(ct2) || !aligned(out) || !aligned(ws) || !aligned(evk)) return HE_EINVAL;
     if (ws_bytes < ws_bytes_for(c, level)) return HE_ENOMEM;
-    return hemul_pipeline(c, ct1, ct2, evk, level, out, (u64 *)ws, true, S(stream));
+    return hemul_pipeline(c, ct1, ct2, evk, level, out, (u64 *)ws, kTailRescale, S(stream));
+}
+
+int he_mul_rescale_pq(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, const uint64_t *evk, int level,
+                      uint64_t *out, void *ws, size_t ws_bytes, void *stream)
+{
+    if (check_dev(c) || !ct1 || !ct2 || !evk || !out || !ws) return HE_EINVAL;
+    if (level < 2 || level > c->L) return HE_ELEVEL;
+    if (!aligned(ct1) || !aligned(ct2) || !aligned(out) || !aligned(ws) || !aligned(evk)) return HE_EINVAL;
+    if (ws_bytes < ws_bytes_for(c, level)) return HE_ENOMEM;
+    return hemul_pipeline(c, ct1, ct2, evk, level, out, (u64 *)ws, kTailRescalePQ, S(stream));
 }
 
 namespace {
@@ -309,7 +322,7 @@ int he_rotate(he_ctx *c, const uint64_t *ct, const uint64_t *rk, int level, uint
     prof_mark(c, st, "");
     HE_TRY(run_automorph(c, ct, w, level, galois, st));
     prof_mark(c, st, "automorph");
-    return run_keyswitch(c, single_job(nullptr, nullptr, out, w, level), w, level_stages(c, level, false), rk, false,
+    return run_keyswitch(c, single_job(nullptr, nullptr, out, w, level), w, level_stages(c, level, kTailPlain), rk, kTailPlain,
                          st);
 }
 
@@ -508,7 +521,7 @@ int he_mul_batch(he_ctx *c, int count, const he_job *jobs, const uint64_t *evk, 
     memset(&R.one, 0, sizeof(R.one));
     R.B = count;
     R.lmax = lmax;
-    return run_pipeline(c, R, data, Sg, evk, true, st);
+    return run_pipeline(c, R, data, Sg, evk, kTailRescale, st);
 }
 
 }  // extern "C"
@@ -701,7 +714,7 @@ int he_mul_rescale_host(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, con
     cudaStream_t st = S(stream);
     HE_TRY(cudaMemcpyAsync(d1, ct1, 2 * (size_t)level * limb, cudaMemcpyHostToDevice, st));
     HE_TRY(cudaMemcpyAsync(d2, ct2, 2 * (size_t)level * limb, cudaMemcpyHostToDevice, st));
-    int rc = hemul_pipeline(c, d1, d2, evk, level, dout, w, true, st);
+    int rc = hemul_pipeline(c, d1, d2, evk, level, dout, w, kTailRescale, st);
     if (rc) return rc;
     HE_TRY(cudaMemcpyAsync(out, dout, 2 * (size_t)(level - 1) * limb, cudaMemcpyDeviceToHost, st));
     HE_TRY(cudaStreamSynchronize(st));
@@ -759,7 +772,7 @@ int he_mul_rescale_host_stream(he_ctx *c, int count, const uint64_t *const *ct1,
         // the path waits for its inputs and for the slot's previous result to be read back
         HE_TRY(cudaStreamWaitEvent(st, ev[0], 0));
         if (k >= slots) HE_TRY(cudaStreamWaitEvent(st, ev[2], 0));
-        int rc = hemul_pipeline(c, a, b, evk, l, o, w, true, st);
+        int rc = hemul_pipeline(c, a, b, evk, l, o, w, kTailRescale, st);
         if (rc) return rc;
         HE_TRY(cudaEventRecord(ev[1], st));
         HE_TRY(cudaStreamWaitEvent(down, ev[1], 0));
@@ -891,7 +904,7 @@ int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws
         g_last_cuda_error = cudaGetErrorName(ce);
         rc = HE_ECUDA;
     }
-    if (rc == HE_OK) rc = run_pipeline(c, R, data, Sg, evk, true, st);
+    if (rc == HE_OK) rc = run_pipeline(c, R, data, Sg, evk, kTailRescale, st);
     ce = cudaStreamEndCapture(st, &g->graph);
     c->prof = prof;
     if (ce != cudaSuccess) g_last_cuda_error = cudaGetErrorName(ce);

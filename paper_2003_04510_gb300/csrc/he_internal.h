@@ -63,6 +63,7 @@ struct DevLevel {
     const u64 *modupB;             // [beta][E][A]: [Qhat_{j,i}]_t split at bit 28, zero-padded
     const ulonglong2 *qinv_last;   // [l-1]: q_{l-1}^-1 mod q_i (value, Shoup)
     const ulonglong2 *pinv_qinv;   // [l-1]: P^-1 * q_{l-1}^-1 mod q_i
+    const u64 *pbpq;               // [l-1][KP]: [Phat_k P^-1 q_{l-1}]_{q_i} (one division by P q_{l-1})
 };
 
 // One HE Mul of a launch: its operands, output, workspace base and level.
@@ -96,6 +97,7 @@ struct LevelJobs {
     const NttGroup *ntt_up;   int n_ntt_up;    // ModUp outputs, in place
     const NttGroup *intt2;    int n_intt2;     // KS specials -> ys (scaled by N^-1 Phat^-1)
     const NttGroup *intt2f;   int n_intt2f;    // + KS last limb -> r[2..3]
+    const NttGroup *intt2pq;  int n_intt2pq;   // intt2f with Phat^-1 q_{l-1}^-1 scales (one division by P q_{l-1})
     const NttGroup *ntt_conv; int n_ntt_conv;  // 2l conv limbs (plain ModDown)
     const NttGroup *ntt_z;    int n_ntt_z;     // 2(l-1) z limbs (fused ModDown + rescale)
     const NttGroup *rs_intt;  int n_rs_intt;   // rescale: last limb of b, a -> r
@@ -104,8 +106,9 @@ struct LevelJobs {
 
 struct HostLevel {
     WsLayout ws;
-    std::vector<NttJob> intt1, intt1f, ntt_up, intt2, intt2f, ntt_conv, ntt_z, rs_intt, rs_ntt;
+    std::vector<NttJob> intt1, intt1f, ntt_up, intt2, intt2f, ntt_conv, ntt_z, rs_intt, rs_ntt, intt2pq;
     std::vector<u64> modupB;
+    std::vector<u64> pbpq;  // [l-1][KP]: [Phat_k P^-1 q_{l-1}]_{q_i}, split at bit 28 (one division by P q_{l-1})
     std::vector<ulonglong2> qinv_last, pinv_qinv;
 };
 
@@ -251,7 +254,10 @@ cudaError_t run_elementwise(const he_ctx *c, int op, const u64 *x, const u64 *y,
 // Rotation's first step: d0 = kappa_g(b), d1 = 0, d2 = -kappa_g(a) into ws (level l).
 cudaError_t run_automorph(const he_ctx *c, const u64 *ct, u64 *ws, int l, u64 g, cudaStream_t st);
 cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st);
-cudaError_t run_moddown_conv(const he_ctx *c, const JobRef &R, bool fused, cudaStream_t st);
+// The key switch's tail: ModDown alone, ModDown then rescale (two floors,
+// bit-identical to he_mul then he_rescale), or one division by P q_{l-1}.
+enum TailMode { kTailPlain = 0, kTailRescale = 1, kTailRescalePQ = 2 };
+cudaError_t run_moddown_conv(const he_ctx *c, const JobRef &R, int mode, cudaStream_t st);
 cudaError_t run_combine_plain(const he_ctx *c, const JobRef &R, cudaStream_t st);
 cudaError_t run_rescale_combine(const he_ctx *c, const u64 *ct, const u64 *Z, u64 *out, int l, cudaStream_t st);
 }  // namespace he

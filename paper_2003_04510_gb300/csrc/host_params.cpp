@@ -251,6 +251,26 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         for (int h = 0; h < 2; h++)
             H.intt2f.push_back(NttJob{(unsigned)(W.ks + (size_t)h * El + K + l - 1), (unsigned)(W.r + 2 + h),
                                       (unsigned)(K + l - 1), 0, c->ninv[K + l - 1], c->ninv_sh[K + l - 1]});
+        // one division by M = P q_{l-1}: y_k = x_k [Mhat_k^-1]_{p_k}, Mhat_k = Phat_k q_{l-1};
+        // the conversion constants [Mhat_k P^-1]_{q_i} = [Phat_k P^-1 q_{l-1}]_{q_i}
+        for (int h = 0; h < 2; h++)
+            for (int k = 0; k < K; k++) {
+                u64 pk = c->ext[k];
+                u64 sc = mul(mul(c->ninv[k], c->phat_inv[k].x, pk), inv(ql % pk, pk), pk);
+                H.intt2pq.push_back(NttJob{(unsigned)(W.ks + (size_t)h * El + k),
+                                           (unsigned)(W.ys + (size_t)h * K + k), (unsigned)k, 0, sc, shoup(sc, pk)});
+            }
+        for (int h = 0; h < 2; h++) H.intt2pq.push_back(H.intt2f[(size_t)2 * K + h]);
+        H.pbpq.assign((size_t)std::max(l - 1, 1) * c->KP, 0);
+        for (int i = 0; i + 1 < l; i++) {
+            u64 qi = c->ext[K + i];
+            for (int k = 0; k < K; k++) {
+                u64 v = 1;
+                for (int k2 = 0; k2 < K; k2++)
+                    if (k2 != k) v = mul(v, c->ext[k2] % qi, qi);
+                H.pbpq[(size_t)i * c->KP + k] = split28(mul(mul(v, c->pinv[i].x, qi), ql % qi, qi));
+            }
+        }
         for (int h = 0; h < 2; h++)
             for (int i = 0; i < l; i++)
                 H.ntt_conv.push_back(NttJob{(unsigned)(W.z + (size_t)h * l + i), (unsigned)(W.z + (size_t)h * l + i),
@@ -298,19 +318,21 @@ int build_context(he_ctx *c, const he_params *p, bool device)
     const size_t o_pinv = take(sizeof(ulonglong2) * L);
     const size_t o_levels = take(sizeof(DevLevel) * (L + 1));
     // per level and group cap: the nine NTT group lists
-    struct LvlOff { size_t modupB, qinv, pq, j[kGroupMax][9]; };
+    constexpr int NL = 10;  // job lists per level
+    struct LvlOff { size_t modupB, qinv, pq, pbpq, j[kGroupMax][NL]; };
     std::vector<LvlOff> lo(L + 1);
     std::vector<std::vector<std::vector<std::vector<NttGroup>>>> gl(
-        L + 1, std::vector<std::vector<std::vector<NttGroup>>>(kGroupMax, std::vector<std::vector<NttGroup>>(9)));
+        L + 1, std::vector<std::vector<std::vector<NttGroup>>>(kGroupMax, std::vector<std::vector<NttGroup>>(NL)));
     for (int l = 1; l <= L; l++) {
         HostLevel &H = c->host_levels[l];
         lo[l].modupB = take(sizeof(u64) * H.modupB.size());
         lo[l].qinv = take(sizeof(ulonglong2) * H.qinv_last.size());
         lo[l].pq = take(sizeof(ulonglong2) * H.pinv_qinv.size());
-        const std::vector<NttJob> *lists[9] = {&H.intt1, &H.intt1f, &H.ntt_up, &H.intt2, &H.intt2f,
-                                               &H.ntt_conv, &H.ntt_z, &H.rs_intt, &H.rs_ntt};
+        lo[l].pbpq = take(sizeof(u64) * H.pbpq.size());
+        const std::vector<NttJob> *lists[NL] = {&H.intt1, &H.intt1f, &H.ntt_up, &H.intt2, &H.intt2f,
+                                                &H.ntt_conv, &H.ntt_z, &H.rs_intt, &H.rs_ntt, &H.intt2pq};
         for (int cap = 1; cap <= kGroupMax; cap++)
-            for (int t = 0; t < 9; t++) {
+            for (int t = 0; t < NL; t++) {
                 gl[l][cap - 1][t] = group_jobs(*lists[t], cap);
                 lo[l].j[cap - 1][t] = take(sizeof(NttGroup) * std::max<size_t>(1, gl[l][cap - 1][t].size()));
             }
@@ -382,13 +404,15 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         memcpy(img.data() + lo[l].modupB, H.modupB.data(), sizeof(u64) * H.modupB.size());
         memcpy(img.data() + lo[l].qinv, H.qinv_last.data(), sizeof(ulonglong2) * H.qinv_last.size());
         memcpy(img.data() + lo[l].pq, H.pinv_qinv.data(), sizeof(ulonglong2) * H.pinv_qinv.size());
+        memcpy(img.data() + lo[l].pbpq, H.pbpq.data(), sizeof(u64) * H.pbpq.size());
         D.modupB = (const u64 *)(base + lo[l].modupB);
         D.qinv_last = (const ulonglong2 *)(base + lo[l].qinv);
         D.pinv_qinv = (const ulonglong2 *)(base + lo[l].pq);
+        D.pbpq = (const u64 *)(base + lo[l].pbpq);
         for (int cap = 1; cap <= kGroupMax; cap++) {
-            const NttGroup *dptr[9];
-            int cnt[9];
-            for (int t = 0; t < 9; t++) {
+            const NttGroup *dptr[NL];
+            int cnt[NL];
+            for (int t = 0; t < NL; t++) {
                 const std::vector<NttGroup> &G = gl[l][cap - 1][t];
                 if (!G.empty()) memcpy(img.data() + lo[l].j[cap - 1][t], G.data(), sizeof(NttGroup) * G.size());
                 dptr[t] = (const NttGroup *)(base + lo[l].j[cap - 1][t]);
@@ -404,6 +428,7 @@ int build_context(he_ctx *c, const he_params *p, bool device)
             J.ntt_z = dptr[6];    J.n_ntt_z = cnt[6];
             J.rs_intt = dptr[7];  J.n_rs_intt = cnt[7];
             J.rs_ntt = dptr[8];   J.n_rs_ntt = cnt[8];
+            J.intt2pq = dptr[9];  J.n_intt2pq = cnt[9];
         }
     }
     c->jobs = c->jobs_cap[c->group_cap - 1];

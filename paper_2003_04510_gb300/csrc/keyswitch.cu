@@ -234,19 +234,30 @@ __device__ __forceinline__ void conv_one(const uint32_t *x0, const uint32_t *x1,
     cy = barrett128(acc3k_value(ay), q, mu, sh);
 }
 
-template <int KM, bool FUSED>
+// MODE (TailMode): kTailPlain: z[h][i] = conv_i for i < l.  kTailRescale:
+// z[h][i] = conv_i P^-1 + r (the fused ModDown + rescale above).
+// kTailRescalePQ: one division by M = P q_{l-1} over the basis (p_0..p_{K-1},
+// q_{l-1}): ys carry [Mhat_k^-1]_{p_k} (the special iNTT's scale), the last
+// limb's term is y_last = x_last [P^-1]_{q_{l-1}} = r0 + r1 P^-1 mod q_{l-1}
+// (x_last = P r0 + r1, the iNTT of P d_{l-1} + KS_{l-1}), and
+// z[h][i] = sum_k y_k [Mhat_k P^-1]_{q_i} + y_last = conv_i P^-1 mod q_i with
+// the per-level constants lv.pbpq: the combine pass then forms
+// (P d + KS - NTT(conv)) / M exactly as for two floors.
+template <int KM, int MODE>
 __global__ void __launch_bounds__(kThreads, KM <= 8 ? 3 : 2)  // 85 / 128 registers
 k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__restrict__ pinv,
                const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int N, int chunks)
 {
+    constexpr bool FUSED = MODE == kTailRescale, PQ = MODE == kTailRescalePQ;
     const BatchItem it = job_of(R, blockIdx.z);
     const int l = it.level;
     const DevLevel &lv = lv_arr[l];
     const int h = blockIdx.y / chunks;
-    const int nout = FUSED ? l - 1 : l;
+    const int nout = MODE != kTailPlain ? l - 1 : l;
     const int i0 = (blockIdx.y - h * chunks) * kModdownChunk;
     const int cnt = min(kModdownChunk, nout - i0);
     if (cnt <= 0) return;
+    const u64 *PBt = PQ ? lv.pbpq : PB;
     // rows 0..cnt-1: this chunk's outputs; row kModdownChunk: q_{l-1} (fused)
     __shared__ u64 sB[kModdownChunk + 1][KM];
     __shared__ u64 sq[kModdownChunk + 1], smu[kModdownChunk + 1];
@@ -255,12 +266,12 @@ k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__r
     for (int t = threadIdx.x; t < (kModdownChunk + 1) * KM; t += kThreads) {
         const int r = t / KM, k = t % KM;
         const int i = r < kModdownChunk ? i0 + r : l - 1;
-        if (r < cnt || (FUSED && r == kModdownChunk)) sB[r][k] = PB[(size_t)i * KM + k];
+        if (r < cnt || (FUSED && r == kModdownChunk)) sB[r][k] = PBt[(size_t)i * KM + k];
     }
     if (threadIdx.x <= kModdownChunk) {
         const int r = threadIdx.x;
         const int i = r < kModdownChunk ? i0 + r : l - 1;
-        if (r < cnt || (FUSED && r == kModdownChunk)) {
+        if (r < cnt || ((FUSED || PQ) && r == kModdownChunk)) {
             sq[r] = primes[K + i].q;
             smu[r] = primes[K + i].mu;
             ss[r] = primes[K + i].s;
@@ -292,13 +303,23 @@ k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__r
         rx = add_mod(r0.x, sub_mod(shoup(r1.x, pv.x, pv.y, q), cx, q), q);
         ry = add_mod(r0.y, sub_mod(shoup(r1.y, pv.x, pv.y, q), cy, q), q);
     }
+    if (PQ) {
+        // y_last = r0 + r1 P^-1 mod q_{l-1}; no conversion row to q_{l-1}
+        const int r = kModdownChunk;
+        const u64 q = sq[r];
+        const ulonglong2 r0 = ld2(rr + (size_t)h * N + n), r1 = ld2(rr + (size_t)(2 + h) * N + n);
+        const ulonglong2 pv = spv[r];
+        rx = add_mod(r0.x, shoup(r1.x, pv.x, pv.y, q), q);
+        ry = add_mod(r0.y, shoup(r1.y, pv.x, pv.y, q), q);
+    }
 #pragma unroll kConvUnroll
     for (int r = 0; r < cnt; r++) {
         const u64 q = sq[r];
         u64 cx, cy;
         conv_one<KM>(x0, x1, z0, z1, sB[r], q, smu[r], ss[r], cx, cy);
-        if (FUSED) {
-            // conv_i P^-1 + r; r < q_{l-1} < q_i is already a residue mod q_i
+        if (FUSED || PQ) {
+            // conv_i P^-1 + r (two floors) or + y_last (one division); both are
+            // below q_{l-1} < q_i, so already residues mod q_i
             cx = add_mod(cx, rx, q);
             cy = add_mod(cy, ry, q);
         }
@@ -509,7 +530,7 @@ cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, 
     return cudaGetLastError();
 }
 
-cudaError_t run_moddown_conv(const he_ctx *c, const JobRef &R, bool fused, cudaStream_t st)
+cudaError_t run_moddown_conv(const he_ctx *c, const JobRef &R, int mode, cudaStream_t st)
 {
     const int chunks = (R.lmax + kModdownChunk - 1) / kModdownChunk;
     dim3 g = grid_x(c->N);
@@ -518,12 +539,15 @@ cudaError_t run_moddown_conv(const he_ctx *c, const JobRef &R, bool fused, cudaS
     const int K = c->K;
 #define HE_MD(KK)                                                                                                   \
     do {                                                                                                            \
-        if (fused)                                                                                                  \
-            launch_k(c->pdl, k_moddown_conv<KK, true>, g, dim3(kThreads), 0, st, R, c->d_PBP, c->d_pinv, c->d_levels, c->d_primes, K,  \
-                                                             c->N, chunks);                                         \
+        if (mode == kTailRescale)                                                                                   \
+            launch_k(c->pdl, k_moddown_conv<KK, kTailRescale>, g, dim3(kThreads), 0, st, R, c->d_PBP, c->d_pinv,    \
+                     c->d_levels, c->d_primes, K, c->N, chunks);                                                    \
+        else if (mode == kTailRescalePQ)                                                                            \
+            launch_k(c->pdl, k_moddown_conv<KK, kTailRescalePQ>, g, dim3(kThreads), 0, st, R, c->d_PB, c->d_pinv,   \
+                     c->d_levels, c->d_primes, K, c->N, chunks);                                                    \
         else                                                                                                        \
-            launch_k(c->pdl, k_moddown_conv<KK, false>, g, dim3(kThreads), 0, st, R, c->d_PB, c->d_pinv, c->d_levels, c->d_primes, K,  \
-                                                              c->N, chunks);                                        \
+            launch_k(c->pdl, k_moddown_conv<KK, kTailPlain>, g, dim3(kThreads), 0, st, R, c->d_PB, c->d_pinv,       \
+                     c->d_levels, c->d_primes, K, c->N, chunks);                                                    \
     } while (0)
     const int kp = c->KP;
     if (kp == 1) HE_MD(1);

@@ -113,4 +113,6 @@ def test_single_division_decrypts_n12():
     c2 = oracle.encrypt_poly(prm, pk, encode(m2, prm.logN, sc), L, s2)
     c3 = oracle.he_mul_rescale_pq(prm, c1, c2, evk, L)
     z = oracle.decrypt(prm, sk, c3, L - 1, sc * sc / int(prm.q[L - 1]))
+    # n12 has K = 1: the conversion's overflow term adds at most 2 per
+    # coefficient, within the two-floor bound's margin
     assert 2.0 ** -40 < np.abs(z - m1 * m2).max() < 2.0 ** -14
