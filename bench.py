@@ -418,17 +418,20 @@ def run_single(g, preset, level, dev, stream, rank, reps=300, npairs=2):
     torch.cuda.synchronize()
     z = g.he_decrypt(ctx, sk, g.to_host(outs[0]), level - 1, sc * sc / float(ctx.q[level - 1]))
     err = float(np.abs(z - si.messages(N // 2, s1) * si.messages(N // 2, s2)).max())
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t0.record(stream)
     for k in range(reps):
-        ev[k][0].record(stream)
         step(k)
-        ev[k][1].record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / reps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for k in range(reps):
+        ev[k][0].record(stream)
+        step(k)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
     lat = np.array([a.elapsed_time(b) for a, b in ev])
     g.he_profile(ctx, True)
     for k in range(10):
