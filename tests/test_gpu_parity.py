@@ -269,15 +269,20 @@ def test_batch_matches_single_and_oracle(g):
         assert np.array_equal(host(g, jobs[k][2]), want)
 
 
-def test_batch_graph_replays_match_single(g):
+@pytest.mark.parametrize("capture_cap,replay_cap", [(4, 4), (1, 3)])
+def test_batch_graph_replays_match_single(g, capture_cap, replay_cap):
     """One captured graph, replayed with two different batches (sizes, levels,
-    operands): every result equals he_mul_rescale on the job alone."""
+    operands): every result equals he_mul_rescale on the job alone.  Captured
+    at limb-group cap 1 (single-buffered NTT tiles) and replayed at cap 3, the
+    NTT kernels get groups of several limbs and load them one after another."""
     import torch
     name = "n16"
     ctx = ctx_for(g, name)
     op = oracle.preset(name)
     evk_t = dev(g, rand_evk(op, 130))
+    g.he_set_shape(ctx, capture_cap, 8, 1)
     graph = g.BatchGraph(ctx, 8, evk_t)
+    g.he_set_shape(ctx, replay_cap, 8, 1)
     for rnd, levels in enumerate([[24, 5, 13, 2, 18, 9], [3, 24, 11]]):
         jobs, singles = [], []
         for k, lv in enumerate(levels):
@@ -292,6 +297,7 @@ def test_batch_graph_replays_match_single(g):
     with pytest.raises(g.HeError):
         graph.launch([jobs[0]] * 9)  # more jobs than captured
     graph.close()
+    g.he_set_shape(ctx, 4, 8, 1)
 
 
 def test_server_continuous_batching_matches_single(g):
