@@ -385,6 +385,11 @@ k_ntt_pass(const NttArgs P)
             const BatchItem it = job_item(P.R, (int)G.job[i]);
             const int ci = (int)(G.ci[i] & 0x7fffffffu), hh = (int)(G.ci[i] >> 31);
             const ulonglong2 pv = P.pinv[ci], qv = P.levels[it.level].qinv_last[ci];
+            // above any forward-NTT output (values grow by < 4q per stage from
+            // canonical inputs): d + KS P^-1 (lazy, < 2q) + Cz - z stays in
+            // (0, (4 + 4 log N) q), below 2^64, and one Shoup product by
+            // q_{l-1}^-1 reduces it
+            const u64 Cz = pr.q * (u64)(1 + 4 * P.logN);
             u64 *o = it.out + ((size_t)hh * (it.level - 1) + ci) * N;
             const u64 *dd = P.dst + (size_t)G.cd[i] * N, *kk = P.dst + (size_t)G.cks[i] * N;
             // four pairs per step: their d and KS loads are all in flight before the first product
@@ -402,9 +407,8 @@ k_ntt_pass(const NttArgs P)
                 for (int k = 0; k < B4; k++) {
                     const int e = 2 * (threadIdx.x + (b0 + k) * NT);
                     const size_t gi = tile_gi<LOGM, TE, STRIDED>(e, tile, stride);
-                    const u64 zx = shoup(sm[padi(e)], 1, pr.r64, pr.q), zy = shoup(sm[padi(e + 1)], 1, pr.r64, pr.q);
-                    const u64 x = sub_mod(add_mod(dv[k].x, shoup(kv[k].x, pv.x, pv.y, pr.q), pr.q), zx, pr.q);
-                    const u64 y = sub_mod(add_mod(dv[k].y, shoup(kv[k].y, pv.x, pv.y, pr.q), pr.q), zy, pr.q);
+                    const u64 x = dv[k].x + shoup_lazy(kv[k].x, pv.x, pv.y, pr.q) + Cz - sm[padi(e)];
+                    const u64 y = dv[k].y + shoup_lazy(kv[k].y, pv.x, pv.y, pr.q) + Cz - sm[padi(e + 1)];
                     *reinterpret_cast<ulonglong2 *>(o + gi) =
                         make_ulonglong2(shoup(x, qv.x, qv.y, pr.q), shoup(y, qv.x, qv.y, pr.q));
                 }
