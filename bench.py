@@ -324,6 +324,16 @@ def run_batched(g, ctx, evk_t, dev, stream, wsz, count=64, reps=20):
                      "batch_latency_ms_p50": float(np.percentile(lat, 50)),
                      "batch_latency_ms_p99": float(np.percentile(lat, 99))}
     graph.close()
+    # per-kernel device time of one batch (CUDA events between the launches)
+    g.he_profile(ctx, True)
+    for _ in range(5):
+        batch()
+    prof = g.he_profile_read(ctx)
+    g.he_profile(ctx, False)
+    res["kernels_us"] = {k: v[0] / v[1] * 1e3 for k, v in prof.items()}
+    if "inner_product" in prof:
+        ip_bytes = sum(kernel_work("inner_product", ctx.prm, lv)[1] for lv in levels)
+        res["inner_product_gbs"] = ip_bytes / (res["kernels_us"]["inner_product"] * 1e-6) / 1e9
     g.he_set_shape(ctx, *shape_before)
     res["autotune"] = {"group_cap": best[0], "modup_chunk": best[1], "pdl": best[2], "ntt_r8": best[3],
                        "ms_per_batch": best[4],
