@@ -51,7 +51,7 @@ struct NttGroup {
 };
 
 // Group single-limb jobs by prime, at most `cap` limbs per group (order
-// within a prime is kept).
+// within a prime is kept); the groups come out sorted by prime.
 std::vector<NttGroup> group_jobs(const std::vector<NttJob> &jobs, int cap = kGroupMax);
 
 // Per-level constants on the device.

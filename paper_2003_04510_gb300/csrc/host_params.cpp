@@ -87,6 +87,9 @@ std::vector<NttGroup> group_jobs(const std::vector<NttJob> &jobs, int cap)
         G.cks[G.nl] = j.cks;
         G.nl++;
     }
+    // groups of one prime next to each other: their CTAs run at the same time
+    // and read that prime's twiddle runs from L2 instead of each from DRAM
+    std::stable_sort(out.begin(), out.end(), [](const NttGroup &a, const NttGroup &b) { return a.prime < b.prime; });
     return out;
 }
 
