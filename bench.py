@@ -12,7 +12,10 @@ Printed JSON line (rank 0):
   e2e         HE Mul/s through he_mul_rescale_host: host->device copy of both
               operands, the path, device->host copy of the result, per step
   latency     p50 / p99 per-step device latency (ms)
-  roofline    the dominant kernel against its ceiling
+  roofline    the dominant kernel of the event profile against its ceiling:
+              NTT passes in butterflies/s against the measured butterfly probe,
+              base conversions in MACs/s against 7/3 of it, streaming kernels
+              in GB/s against the measured HBM copy rate
   cpu_baseline  the CPU oracle on the host cores, bounded sample
   clocks      SM clocks sampled with nvidia-smi during the timed region
 
