@@ -522,7 +522,10 @@ cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, 
             launch_k(c->pdl, k_inner_product<B, false>, g, dim3(kThreads), 0, st, R, evk, c->d_levels, c->d_primes,  \
                      c->K, c->L, c->N, ss);                                                                          \
     } while (0)
+    // three digits get their own width: 64 registers, four CTAs per SM
+    // (the four-digit width takes 78 and fits three)
     if (bm <= 2) HE_IP(2);
+    else if (bm == 3) HE_IP(3);
     else if (bm <= 4) HE_IP(4);
     else if (bm <= 8) HE_IP(8);
     else HE_IP(16);
