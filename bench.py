@@ -13,9 +13,10 @@ Printed JSON line (rank 0):
               operands, the path, device->host copy of the result, per step
   latency     p50 / p99 per-step device latency (ms)
   roofline    the dominant kernel of the event profile against its ceiling:
-              NTT passes in butterflies/s against the measured butterfly probe,
-              base conversions in MACs/s against 7/3 of it, streaming kernels
-              in GB/s against the measured HBM copy rate
+              NTT passes in butterflies/s against the measured butterfly probe
+              (the NTT's own butterfly), base conversions in MACs/s against the
+              measured conversion probe (their own inner loop), streaming
+              kernels in GB/s against the measured HBM copy rate
   cpu_baseline  the CPU oracle on the host cores, bounded sample
   clocks      SM clocks sampled with nvidia-smi during the timed region
 
@@ -251,6 +252,19 @@ def kernel_work(name: str, prm, level: int):
     return None, 0
 
 
+def kernel_width(n: int) -> int:
+    """The padded term count a conversion kernel is instantiated for (1, 2, 4, 8, 12, 16)."""
+    return next(w for w in (1, 2, 4, 8, 12, 16) if w >= n)
+
+
+def shape_dict(t) -> dict:
+    """A launch shape (group_cap, modup_chunk, pdl, ntt_r8, ip_jobs[, ms]) as a dict."""
+    d = dict(zip(("group_cap", "modup_chunk", "pdl", "ntt_r8", "ip_jobs"), t[:5]))
+    if len(t) > 5:
+        d["ms"] = t[5]
+    return d
+
+
 def committed_traffic(kernel: str):
     """Per-launch DRAM bytes of `kernel` (a name of the bench's event profile)
     from a committed ncu summary under profiles/ that names it ("bench kernel:
@@ -338,10 +352,7 @@ def run_batched(g, ctx, evk_t, dev, stream, wsz, count=64, reps=20):
         ip_bytes = sum(kernel_work("inner_product", ctx.prm, lv)[1] for lv in levels)
         res["inner_product_gbs"] = ip_bytes / (res["kernels_us"]["inner_product"] * 1e-6) / 1e9
     g.he_set_shape(ctx, *shape_before)
-    res["autotune"] = {"group_cap": best[0], "modup_chunk": best[1], "pdl": best[2], "ntt_r8": best[3],
-                       "ms_per_batch": best[4],
-                       "tried": [{"group_cap": t[0], "modup_chunk": t[1], "pdl": t[2], "ntt_r8": t[3], "ms": t[4]}
-                                 for t in tried]}
+    res["autotune"] = dict(shape_dict(best), ms_per_batch=best[5], tried=[shape_dict(t) for t in tried])
     res["config"] = {"jobs": count, "N": N, "levels": "uniform 4..24 (seed 1604)", "mean_level": float(np.mean(levels)),
                      "operands": "uniform residues"}
     return res
@@ -458,7 +469,7 @@ def run_single(g, preset, level, dev, stream, rank, reps=300, npairs=2):
         ip = b / (kernels_us["inner_product"] * 1e-6) / 1e9
     res = {"workload": WORKLOADS[preset][2], "HE_Mul_per_s": 1e3 / ms, "ms": ms, "reps": reps,
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-           "autotune": {"group_cap": best[0], "modup_chunk": best[1], "pdl": best[2], "ntt_r8": best[3]},
+           "autotune": shape_dict(best),
            "kernels_us": kernels_us, "inner_product_gbs": ip,
            "evk_bytes": int(evk_t.numel() * 8), "decrypt_max_err": err,
            "l2": f"{npairs} ciphertext pairs + evk rotated "
@@ -510,9 +521,9 @@ def run_ours(args):
     # launch shapes picked by the library's autotuner for this single HE Mul
     # (or fixed by --shape, e.g. for a profiler run)
     if args.shape:
-        cap, chunk, pdl, r8 = ([int(v) for v in args.shape.split(",")] + [0])[:4]
-        g.he_set_shape(ctx, cap, chunk, pdl, r8)
-        tune_best, tune_tried = (cap, chunk, pdl, r8, 0.0), []
+        cap, chunk, pdl, r8, ipj = ([int(v) for v in args.shape.split(",")] + [0, 8][len(args.shape.split(",")) - 3:])[:5]
+        g.he_set_shape(ctx, cap, chunk, pdl, r8, ipj)
+        tune_best, tune_tried = (cap, chunk, pdl, r8, ipj, 0.0), []
     else:
         tune_best, tune_tried = g.he_autotune(ctx, [(ct_t[0][0], ct_t[0][1], outs[0], level)], evk_t, ws, reps=20,
                                               stream=stream)
@@ -545,6 +556,18 @@ def run_ours(args):
     if wsz > 1:
         torch.distributed.barrier()
     elapsed_ms = reduce_max(t0.elapsed_time(t1), dev)
+    # the same K-step region repeated: its spread says how steady the first is
+    rep_ms = [elapsed_ms]
+    for _ in range(4):
+        if wsz > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for k in range(args.steps):
+            step(k)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        rep_ms.append(reduce_max(t0.elapsed_time(t1), dev))
     # per-step latency: a separate pass, each step between its own two events
     lat_steps = max(10, min(args.steps, 1000))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(lat_steps)]
@@ -579,18 +602,23 @@ def run_ours(args):
     # and downloads its result, overlapped with the neighbouring steps' kernels
     slots = 3
     sws = torch.empty(g.he_host_stream_workspace_bytes(ctx, level, slots) // 8, dtype=torch.int64, device=dev)
-    e2e_steps = max(3, min(args.steps, 200))
+    e2e_steps = 200  # fixed, independent of --steps: a few tenths of a second of host wall clock per run
     s_ct1 = [pin_np[k % 2][0] for k in range(e2e_steps)]
     s_ct2 = [pin_np[k % 2][1] for k in range(e2e_steps)]
     g.he_mul_rescale_host_stream(ctx, s_ct1[:4], s_ct2[:4], [level] * 4, [out_np] * 4, evk_t, sws, slots, stream)
     if wsz > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    te = time.perf_counter()
-    g.he_mul_rescale_host_stream(ctx, s_ct1, s_ct2, [level] * e2e_steps, [out_np] * e2e_steps, evk_t, sws, slots,
-                                 stream)
-    e2e_s = reduce_max(time.perf_counter() - te, dev)
-    e2e_val = job_rate(e2e_steps, wsz, e2e_s)
+    e2e_runs = []
+    for _ in range(3):
+        if wsz > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        te = time.perf_counter()
+        g.he_mul_rescale_host_stream(ctx, s_ct1, s_ct2, [level] * e2e_steps, [out_np] * e2e_steps, evk_t, sws,
+                                     slots, stream)
+        e2e_runs.append(job_rate(e2e_steps, wsz, reduce_max(time.perf_counter() - te, dev)))
+    e2e_val = float(np.median(e2e_runs))
     zs = g.he_decrypt(ctx, sk, out_np, level - 1, sc * sc / float(ctx.q[level - 1]))
     m_last = si.messages(N // 2, s1 + 17 * ((e2e_steps - 1) % 2)) * si.messages(N // 2, s2 + 17 * ((e2e_steps - 1) % 2))
     e2e_err = float(np.abs(zs - m_last).max())
@@ -774,9 +802,17 @@ def run_ours(args):
         plan.close()
         del nws, prep, nevk, nct, nout
 
-    # ALU ceiling: register-resident butterfly probe
+    # ALU ceilings: the NTT's butterfly and the conversions' inner loop,
+    # register-resident, measured in this run at its clocks
     bfly_peak = g.he_probe_butterfly_rate(152 * 8, 4096, stream)
-    probe = {"butterfly_per_s": bfly_peak}
+    conv_width = {"modup": kernel_width(prm.alpha), "moddown_conv": kernel_width(prm.K)}
+    conv_peak = {k: g.he_probe_conversion_rate(w, 152 * 8, max(64, 4096 // w), stream) for k, w in conv_width.items()}
+    probe = {"butterfly_per_s": bfly_peak, "conversion_mac_per_s": conv_peak, "conversion_width": conv_width}
+    for k, d in per_kernel.items():
+        if d["kind"] == "alu":
+            d["frac_of_probe"] = d["Gbutterfly_s"] * 1e9 / bfly_peak
+        elif d["kind"] == "mac" and k.split(".")[0] in conv_peak:
+            d["frac_of_probe"] = d["GMAC_s"] * 1e9 / conv_peak[k.split(".")[0]]
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -794,13 +830,13 @@ def run_ours(args):
                     "peak_source": "measured: the NTT's own butterfly on register-resident data "
                                    "(he_probe_butterfly_rate), same clocks, same run"}
         elif kind == "mac":
-            # one Karatsuba base-conversion MAC is three 32x32->64 multiply-adds;
-            # the probe's butterfly costs seven in wide-multiply units (five
-            # wide products plus four 32-bit ones at half the cost)
             ach = work / avg_s / 1e9
-            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": 7.0 / 3.0 * bfly_peak / 1e9,
-                    "unit": "GMAC/s", "frac": ach / (7.0 / 3.0 * bfly_peak / 1e9), "traffic": committed_traffic(dom),
-                    "peak_source": "derived: 7/3 x measured butterfly probe rate (wide-multiply count ratio)"}
+            pk = conv_peak[dom.split(".")[0]] / 1e9
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk,
+                    "unit": "GMAC/s", "frac": ach / pk, "traffic": committed_traffic(dom),
+                    "peak_source": f"measured: the conversion's own inner loop (split-28 Karatsuba multiply-"
+                                   f"accumulates, 128-bit assembly, Barrett) at width {conv_width[dom.split('.')[0]]}, "
+                                   f"register-resident (he_probe_conversion_rate), same clocks, same run"}
         elif kind == "hbm":
             ach = work / avg_s / 1e9
             roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
@@ -849,10 +885,15 @@ def run_ours(args):
                        "dnum": ctx.dnum, "l2": f"{NPAIRS} distinct ciphertext pairs + evk rotated "
                        f"({(NPAIRS * 4 * level + 2 * ctx.dnum * (prm.K + prm.L)) * N * 8 / 1e6:.0f} MB > 129 MB L2)",
                        "parallelism": f"replicas x{wsz}"},
+            "repeats": {"regions": len(rep_ms), "steps_each": args.steps,
+                        "value_median": job_rate(args.steps, wsz, float(np.median(rep_ms)) * 1e-3),
+                        "values": [job_rate(args.steps, wsz, m * 1e-3) for m in rep_ms]},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(lat.mean()), "steps": lat_steps},
             "e2e": {"value": e2e_val, "unit": "HE Mul/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "api": f"he_mul_rescale_host_stream, {e2e_steps} steps from pinned host buffers, {slots} slots",
+                    "api": f"he_mul_rescale_host_stream, {e2e_steps} steps from pinned host buffers, {slots} slots, "
+                           f"median of {len(e2e_runs)} runs",
+                    "runs": e2e_runs,
                     "decrypt_max_err": e2e_err,
                     "single_call": {"value": single_val, "unit": "HE Mul/s", "api": "he_mul_rescale_host",
                                     "steps": single_steps}},
@@ -861,10 +902,7 @@ def run_ours(args):
             "inner_product_hbm": ip,
             "probe": probe,
             "kernels": per_kernel,
-            "autotune": {"group_cap": tune_best[0], "modup_chunk": tune_best[1], "pdl": tune_best[2],
-                         "ntt_r8": tune_best[3], "ms": tune_best[4],
-                         "tried": [{"group_cap": t[0], "modup_chunk": t[1], "pdl": t[2], "ntt_r8": t[3], "ms": t[4]}
-                                   for t in tune_tried]},
+            "autotune": dict(shape_dict(tune_best), tried=[shape_dict(t) for t in tune_tried]),
             "n17_single": n17,
             "rescale_pq": pq,
             "seeded_evk": seeded,

@@ -173,9 +173,11 @@ int he_mul_rescale_pq(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, con
  *  - Limit: levels whose he_workspace_bytes exceeds HE_STATIC_SCRATCH_BYTES
  *    (64 MiB: every level of logN <= 15 parameter sets of this size, logN 16
  *    up to level 8) return HE_ENOMEM; use he_mul_rescale for those.
- *  - The first call with a device current looks up that device's scratch
- *    address (cudaGetSymbolAddress), which may load the library's device
- *    code; make that first call outside any stream capture.
+ *  - Every call looks up the current device's scratch address
+ *    (cudaGetSymbolAddress); the first lookup on a device may load the
+ *    library's device code, so make the first call outside any stream
+ *    capture.
+ *  - HE_ELEVEL for a level outside 2..L, as he_mul_rescale.
  *  - The current device must be the context's (HE_EINVAL otherwise).
  *  - Nothing in the scratch needs to start at zero.
  *  - All calls on one device share the scratch: calls whose executions
@@ -252,7 +254,9 @@ size_t he_batch_workspace_bytes(const he_ctx *ctx, int count, const int *levels)
  * twiddle tile serves limbs of several jobs.  The first bytes of ws receive
  * the batch's job table and NTT job lists (one host-to-device copy on the
  * stream); the rest holds the jobs' workspaces.  Results are bit-identical
- * to he_mul_rescale on each job.  count <= 65535. */
+ * to he_mul_rescale on each job.  count <= 65535.  HE_EINVAL while `stream`
+ * is being captured into a CUDA graph (the header copy reads this call's host
+ * memory; capture batches with he_batch_graph_create). */
 int he_mul_batch(he_ctx *ctx, int count, const he_job *jobs, const uint64_t *evk_dev, void *ws,
                  size_t ws_bytes, void *stream);
 
@@ -276,13 +280,20 @@ int he_batch_graph_destroy(he_batch_graph *g);
 /* ---- serving (continuous batching) ------------------------------------------ */
 
 /* A served request: HE Mul + rescale of device-resident operands on ring
- * ctx_index of the server (ct1, ct2: [2][level][N]; out: [2][level-1][N]). */
+ * ctx_index of the server (ct1, ct2: [2][level][N]; out: [2][level-1][N]).
+ * The server runs batches on streams of its own: operands written on another
+ * stream must either be complete before he_server_submit (synchronise that
+ * stream) or come with `ready`, a cudaEvent_t (passed as void*) recorded after
+ * the writes, which the batch waits for on the device before its first
+ * kernel; NULL means the operands are already complete.  The event must stay
+ * valid until the request completes. */
 typedef struct {
     int ctx_index;
     int level;
     const uint64_t *ct1;
     const uint64_t *ct2;
     uint64_t *out;
+    void *ready;
 } he_request;
 
 typedef struct {
@@ -310,10 +321,15 @@ int he_server_create(he_server **out, he_ctx *const *ctxs, const uint64_t *const
  * whole budget (it could never be admitted), HE_ELEVEL / HE_EINVAL for bad
  * arguments. */
 int he_server_submit(he_server *s, const he_request *r, uint64_t *ticket);
-/* done = 1 once the request completed; returns its error code if it failed. */
+/* done = 1 once the request completed; returns its error code if it failed.
+ * The status of finished tickets is kept for the 2^20 most recent tickets;
+ * an older or unknown ticket gives HE_EINVAL. */
 int he_server_poll(he_server *s, uint64_t ticket, int *done);
-/* Wait up to timeout_ms for a request; HE_ETIMEOUT if it has not completed. */
+/* Wait up to timeout_ms (0: do not wait) for a request; HE_ETIMEOUT if it has
+ * not completed by then, its error code if it failed. */
 int he_server_wait(he_server *s, uint64_t ticket, int timeout_ms);
+/* Counters since creation; latency percentiles over the last 65536
+ * completions. */
 int he_server_stats(he_server *s, he_server_report *stats);
 /* Stops the scheduler after the batches in flight finish; queued requests
  * that were never launched are dropped. */
@@ -369,6 +385,11 @@ int he_add_plain(he_ctx *ctx, const uint64_t *ct, const uint64_t *pt, int level,
  * `steps`, which may be negative).  2N - 1 conjugates every slot.  0 if ctx
  * is NULL. */
 uint64_t he_galois_elt(const he_ctx *ctx, int steps);
+/* g = 2N - 1: kappa_g = X -> X^(-1) takes every slot to its complex conjugate
+ * (the canonical embedding's roots zeta^(5^k) map to their inverses, i.e.
+ * their conjugates).  Used with he_keygen_rot / he_rotate like a rotation.
+ * 0 if ctx is NULL. */
+uint64_t he_conj_elt(const he_ctx *ctx);
 /* Rotation key for kappa_g: rk [dnum][2][K+L][N] host, same layout as evk;
  * b_j = a_j s + e_j + [t in digit j] P kappa_g(s), a_j and e_j drawn from
  * `seed` (streams distinct from the evaluation key's).  HE_EINVAL for an even
@@ -428,14 +449,18 @@ int he_nr_rescale(he_nr_plan *plan, const uint64_t *ct, int logq, uint64_t *out,
  * the special limbs, 3 the NTT of the ModDown limbs) use the radix-8 plan
  * (rounds of at most three stages, 256 threads per tile) instead of the
  * radix-16 one (128 threads per tile).  Speed only: every shape gives
- * bit-identical results.  Default {4, 8, 1, 0}.  A batch graph keeps the
+ * bit-identical results.  Default {4, 8, 1, 0, 8}.  A batch graph keeps the
  * shape it was captured with, except the limb-group cap. */
 typedef struct {
     int group_cap;
     int modup_chunk;
     int pdl;
-    int ntt_r8; /* 0..15 */
-    double ms;  /* he_autotune: measured milliseconds per call; else 0 */
+    int ntt_r8;  /* 0..15 */
+    int ip_jobs; /* batches of 2 or more jobs: 4 or 8 jobs of similar level share each CTA of the inner
+                    product, which reads the evaluation key's words once for all of them (Fig. 2 region 2's
+                    key stream, read once per group instead of once per job); 1 = one job per CTA.  Used
+                    while the context has at most four digits (dnum <= 4), else 1. */
+    double ms;   /* he_autotune: measured milliseconds per call; else 0 */
 } he_shape;
 
 /* HE_EINVAL for a NULL context or an unsupported value. */
@@ -443,7 +468,8 @@ int he_set_shape(he_ctx *ctx, const he_shape *shape);
 int he_get_shape(const he_ctx *ctx, he_shape *shape);
 /* Time shapes on the caller's own work and keep the fastest in ctx: every
  * (group_cap, modup_chunk, pdl) with the radix-16 NTT plan, then every
- * nonzero ntt_r8 mask on the best of those (39 shapes);
+ * nonzero ntt_r8 mask on the best of those (39 shapes), then, for a batch,
+ * the other two ip_jobs values on the best (41 shapes);
  * count == 1 times he_mul_rescale on jobs[0] (ws of he_workspace_bytes),
  * count > 1 times he_mul_batch on the jobs (ws of he_batch_workspace_bytes),
  * `reps` calls per shape after one warm-up call, CUDA events on `stream`.
@@ -463,11 +489,23 @@ int he_autotune(he_ctx *ctx, const he_job *jobs, int count, const uint64_t *evk_
 int he_profile(he_ctx *ctx, int enable);
 int he_profile_read(he_ctx *ctx, int max, char *names, double *total_ms, int *calls, int *count);
 
-/* Measurement helper: rate (butterflies per second) of the NTT's lazy
- * Cooley-Tukey butterfly (one Shoup product, Algo 2, plus adds) on
- * register-resident data, `blocks` x 256 threads x 8 chains x `iters`.  The
- * ALU ceiling the NTT kernels are compared against. */
+/* Measurement helper: rate (butterflies per second) of the NTT's own lazy
+ * Cooley-Tukey butterfly (Algo 4 with the modified Shoup product of Sec. 5.2;
+ * the same device function the NTT passes call) on register-resident data,
+ * `blocks` x 256 threads x 8 chains x `iters`.  The ALU ceiling the NTT
+ * kernels are compared against.  Allocates a small output buffer with
+ * cudaMallocAsync on `stream`; HE_EINVAL for a non-positive count. */
 int he_probe_butterfly_rate(int blocks, int iters, double *bfly_per_s, void *stream);
+/* Measurement helper: rate (multiply-accumulates per second) of the base
+ * conversion's inner loop (Sec. 7's mod up / mod down as fast base conversion
+ * with Sec. 5.3's delayed-modulo accumulation): per output, `width` terms
+ * (1, 2, 4, 8, 12 or 16: the kernels' padded digit or special-prime count)
+ * of the split-28 Karatsuba multiply-accumulate with the constant read from
+ * shared memory, then one 128-bit assembly and Barrett reduction, on two
+ * coefficients per thread held in registers; `blocks` x 256 threads x 16
+ * outputs x `iters`.  The ALU ceiling the ModUp and ModDown conversions are
+ * compared against.  HE_EINVAL for another width or a non-positive count. */
+int he_probe_conversion_rate(int width, int blocks, int iters, double *mac_per_s, void *stream);
 
 const char *he_strerror(int code);
 /* Name of the CUDA error behind the calling thread's last HE_ECUDA. */

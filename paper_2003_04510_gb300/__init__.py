@@ -39,7 +39,7 @@ class he_params(ctypes.Structure):
 
 class he_request(ctypes.Structure):
     _fields_ = [("ctx_index", ctypes.c_int), ("level", ctypes.c_int), ("ct1", ctypes.c_void_p),
-                ("ct2", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+                ("ct2", ctypes.c_void_p), ("out", ctypes.c_void_p), ("ready", ctypes.c_void_p)]
 
 
 class he_server_report(ctypes.Structure):
@@ -126,7 +126,10 @@ _SIGS = {
     "he_batch_graph_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "he_batch_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "he_probe_butterfly_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "he_probe_conversion_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
     "he_galois_elt": (ctypes.c_uint64, [ctypes.c_void_p, ctypes.c_int]),
+    "he_conj_elt": (ctypes.c_uint64, [ctypes.c_void_p]),
     "he_nr_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "he_nr_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "he_nr_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -398,25 +401,29 @@ def he_add_plain(ctx, ct, pt, level, out, stream=None):
 
 class he_shape(ctypes.Structure):
     _fields_ = [("group_cap", ctypes.c_int), ("modup_chunk", ctypes.c_int), ("pdl", ctypes.c_int),
-                ("ntt_r8", ctypes.c_int), ("ms", ctypes.c_double)]
+                ("ntt_r8", ctypes.c_int), ("ip_jobs", ctypes.c_int), ("ms", ctypes.c_double)]
 
 
-def he_set_shape(ctx, group_cap: int, modup_chunk: int, pdl: int = 1, ntt_r8: int = 0):
-    sh = he_shape(group_cap, modup_chunk, pdl, ntt_r8, 0.0)
+def _shape_tuple(sh) -> tuple:
+    return sh.group_cap, sh.modup_chunk, sh.pdl, sh.ntt_r8, sh.ip_jobs
+
+
+def he_set_shape(ctx, group_cap: int, modup_chunk: int, pdl: int = 1, ntt_r8: int = 0, ip_jobs: int = 8):
+    sh = he_shape(group_cap, modup_chunk, pdl, ntt_r8, ip_jobs, 0.0)
     _check(lib().he_set_shape(ctx.ptr, ctypes.byref(sh)), "he_set_shape")
 
 
-def he_get_shape(ctx) -> tuple[int, int, int, int]:
-    """(group_cap, modup_chunk, pdl, ntt_r8)"""
+def he_get_shape(ctx) -> tuple[int, int, int, int, int]:
+    """(group_cap, modup_chunk, pdl, ntt_r8, ip_jobs)"""
     sh = he_shape()
     _check(lib().he_get_shape(ctx.ptr, ctypes.byref(sh)), "he_get_shape")
-    return sh.group_cap, sh.modup_chunk, sh.pdl, sh.ntt_r8
+    return _shape_tuple(sh)
 
 
 def he_autotune(ctx, jobs, evk, ws, reps: int = 3, stream=None):
     """jobs: list of (ct1, ct2, out, level) device tensors (one job: the single
-    path).  Returns (best (cap, chunk, pdl, ntt_r8, ms), [the same for every
-    shape tried])."""
+    path).  Returns (best (cap, chunk, pdl, ntt_r8, ip_jobs, ms), [the same for
+    every shape tried])."""
     arr = (he_job * len(jobs))()
     for i, (a, b, o, lv) in enumerate(jobs):
         arr[i] = he_job(_dev_ptr(a), _dev_ptr(b), _dev_ptr(o), int(lv))
@@ -426,8 +433,7 @@ def he_autotune(ctx, jobs, evk, ws, reps: int = 3, stream=None):
     _check(lib().he_autotune(ctx.ptr, ctypes.cast(arr, ctypes.c_void_p), len(jobs), _dev_ptr(evk), _dev_ptr(ws),
                              ws.numel() * 8, reps, _stream_ptr(stream), ctypes.byref(best),
                              ctypes.cast(tried, ctypes.c_void_p), 64, ctypes.byref(n)), "he_autotune")
-    return ((best.group_cap, best.modup_chunk, best.pdl, best.ntt_r8, best.ms),
-            [(t.group_cap, t.modup_chunk, t.pdl, t.ntt_r8, t.ms) for t in tried[: n.value]])
+    return (_shape_tuple(best) + (best.ms,), [_shape_tuple(t) + (t.ms,) for t in tried[: n.value]])
 
 
 def he_keygen_seeded(ctx, seed: int, sk: np.ndarray) -> np.ndarray:
@@ -497,7 +503,7 @@ def he_galois_elt(ctx, steps: int) -> int:
 
 def he_conj_elt(ctx) -> int:
     """2N - 1 (slot-wise complex conjugation)."""
-    return 2 * ctx.N - 1
+    return int(lib().he_conj_elt(ctx.ptr))
 
 
 def he_keygen_rot(ctx, seed: int, sk: np.ndarray, galois: int) -> np.ndarray:
@@ -618,6 +624,13 @@ def he_probe_butterfly_rate(blocks: int, iters: int, stream=None) -> float:
     return r.value
 
 
+def he_probe_conversion_rate(width: int, blocks: int, iters: int, stream=None) -> float:
+    r = ctypes.c_double()
+    _check(lib().he_probe_conversion_rate(width, blocks, iters, ctypes.byref(r), _stream_ptr(stream)),
+           "he_probe_conversion_rate")
+    return r.value
+
+
 class BatchGraph:
     """he_batch_graph: the batched path captured once in a CUDA graph."""
 
@@ -662,8 +675,11 @@ class Server:
         _check(lib().he_server_create(ctypes.byref(self.ptr), self._ctxs, self._evks, n, hbm_budget, max_batch,
                                       streams), "he_server_create")
 
-    def submit(self, ctx_index: int, level: int, ct1, ct2, out) -> int:
-        r = he_request(ctx_index, level, _dev_ptr(ct1), _dev_ptr(ct2), _dev_ptr(out))
+    def submit(self, ctx_index: int, level: int, ct1, ct2, out, ready=None) -> int:
+        """ready: optional torch.cuda.Event recorded after the operands were written
+        (the batch waits for it on the device); None if they are complete."""
+        r = he_request(ctx_index, level, _dev_ptr(ct1), _dev_ptr(ct2), _dev_ptr(out),
+                       ready.cuda_event if ready is not None else None)
         t = ctypes.c_uint64()
         _check(lib().he_server_submit(self.ptr, ctypes.byref(r), ctypes.byref(t)), "he_server_submit")
         return t.value

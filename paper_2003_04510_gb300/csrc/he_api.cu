@@ -23,6 +23,24 @@ void prof_mark(const he_ctx *c, cudaStream_t st, const char *tag, const char *su
     c->prof_used++;
 }
 
+std::vector<IpGroup> ip_groups(const int *levels, int count, int per)
+{
+    per = std::max(1, std::min(per, kIpJobsMax));
+    std::vector<int> order(count);
+    for (int i = 0; i < count; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return levels[a] > levels[b]; });
+    std::vector<IpGroup> out;
+    for (int i = 0; i < count; i += per) {
+        IpGroup g;
+        memset(&g, 0, sizeof(g));
+        g.n = std::min(per, count - i);
+        g.level = levels[order[i]];
+        for (int k = 0; k < g.n; k++) g.job[k] = order[i + k];
+        out.push_back(g);
+    }
+    return out;
+}
+
 }  // namespace he
 
 namespace {
@@ -63,7 +81,8 @@ struct Stages {
     const NttGroup *ntt_up;   int n_ntt_up;    // NTT of the ModUp outputs
     const NttGroup *intt2;    int n_intt2;     // iNTT of the special limbs (+ KS last limb when fused)
     const NttGroup *ntt_last; int n_ntt_last;  // NTT of the ModDown (fused: ModDown + rescale) limbs
-    const int *counts = nullptr;               // optional device-side counts of the four lists
+    const int *counts = nullptr;               // optional device-side counts of the four lists (+ ipg's)
+    const IpGroup *ipg = nullptr;  int n_ipg = 0;  // batches: inner product with shared key words
 };
 
 // The HE Mul pipeline for one job or a batch (JobRef).  mode (TailMode):
@@ -95,7 +114,10 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
     HE_TRY(run_modup(c, R, st));
     prof_mark(c, st, "modup");
     HE_TRY(launch_ntt(c, ntt_base, S.ntt_up, S.n_ntt_up, false, st, "ntt_modup", cnt ? cnt + 1 : nullptr, r8(1)));
-    HE_TRY(run_inner_product(c, R, evk, st));
+    if (S.ipg)
+        HE_TRY(run_inner_product_shared(c, R, S.ipg, S.n_ipg, cnt ? cnt + 4 : nullptr, evk, st));
+    else
+        HE_TRY(run_inner_product(c, R, evk, st));
     prof_mark(c, st, "inner_product");
     // ModDown: iNTT of the special limbs (times N^-1 Phat^-1), conversion, NTT
     HE_TRY(launch_ntt(c, ntt_base, S.intt2, S.n_intt2, true, st, "intt_special", cnt ? cnt + 2 : nullptr, r8(2)));
@@ -152,8 +174,9 @@ int hemul_pipeline(he_ctx *c, const u64 *ct1, const u64 *ct2, const u64 *evk, in
 }
 
 // ---- batches -------------------------------------------------------------
-// Batch workspace: [header: items | four NTT group lists] [job 0 ws] [job 1 ws] ...
-// Group offsets are relative to the first job's ws.
+// Batch workspace: [header: items | four NTT group lists | inner-product job
+// groups] [job 0 ws] [job 1 ws] ...  Group offsets are relative to the first
+// job's ws.
 size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t batch_header_bytes(const he_ctx *c, int count, const int *levels)
@@ -163,8 +186,12 @@ size_t batch_header_bytes(const he_ctx *c, int count, const int *levels)
         const HostLevel &H = c->host_levels[levels[i]];
         limbs += H.intt1f.size() + H.ntt_up.size() + H.intt2f.size() + H.ntt_z.size();
     }
-    return round_up(sizeof(BatchItem) * count) + round_up(sizeof(NttGroup) * limbs);
+    return round_up(sizeof(BatchItem) * count) + round_up(sizeof(NttGroup) * limbs) +
+           round_up(sizeof(IpGroup) * count);
 }
+
+// Whether a batch of `count` jobs runs the inner product with shared key words.
+bool use_shared_ip(const he_ctx *c, int count) { return count > 1 && c->ip_jobs > 1 && inner_product_shared_fits(c); }
 
 size_t batch_bytes(const he_ctx *c, int count, const int *levels)
 {
@@ -514,7 +541,20 @@ int he_mul_batch(he_ctx *c, int count, const he_job *jobs, const uint64_t *evk, 
     put(g2, Sg.ntt_up, Sg.n_ntt_up);
     put(g3, Sg.intt2, Sg.n_intt2);
     put(g4, Sg.ntt_last, Sg.n_ntt_last);
+    if (use_shared_ip(c, count)) {
+        const std::vector<IpGroup> ipg = ip_groups(levels.data(), count, c->ip_jobs);
+        const size_t ip_off = items_bytes + round_up(sizeof(NttGroup) * gi);
+        memcpy(head.data() + ip_off, ipg.data(), sizeof(IpGroup) * ipg.size());
+        Sg.ipg = (const IpGroup *)(wsb + ip_off);
+        Sg.n_ipg = (int)ipg.size();
+    }
     cudaStream_t st = S(stream);
+    // the header is staged from this call's own host memory, which a captured
+    // copy would read after it is gone: batches are captured with
+    // he_batch_graph_create instead
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    HE_TRY(cudaStreamIsCapturing(st, &capturing));
+    if (capturing != cudaStreamCaptureStatusNone) return HE_EINVAL;
     HE_TRY(cudaMemcpyAsync(ws, head.data(), hdr, cudaMemcpyHostToDevice, st));
     JobRef R;
     R.items = (const BatchItem *)ws;
@@ -578,10 +618,12 @@ int he_set_shape(he_ctx *c, const he_shape *sh)
     if (sh->modup_chunk != 4 && sh->modup_chunk != 8 && sh->modup_chunk != 16) return HE_EINVAL;
     if (sh->pdl != 0 && sh->pdl != 1) return HE_EINVAL;
     if (sh->ntt_r8 < 0 || sh->ntt_r8 > 15) return HE_EINVAL;
+    if (sh->ip_jobs != 1 && sh->ip_jobs != 4 && sh->ip_jobs != 8) return HE_EINVAL;
     c->group_cap = sh->group_cap;
     c->modup_chunk = sh->modup_chunk;
     c->pdl = sh->pdl != 0;
     c->ntt_r8 = sh->ntt_r8;
+    c->ip_jobs = sh->ip_jobs;
     if (c->device) c->jobs = c->jobs_cap[c->group_cap - 1];
     return HE_OK;
 }
@@ -593,6 +635,7 @@ int he_get_shape(const he_ctx *c, he_shape *sh)
     sh->modup_chunk = c->modup_chunk;
     sh->pdl = c->pdl ? 1 : 0;
     sh->ntt_r8 = c->ntt_r8;
+    sh->ip_jobs = c->ip_jobs;
     sh->ms = 0;
     return HE_OK;
 }
@@ -636,17 +679,28 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
         return HE_OK;
     };
     // first the limb-group cap, ModUp chunk and PDL with the radix-16 NTT
-    // plan, then the NTT plan of each of the four pipeline sites on that shape
+    // plan, then the NTT plan of each of the four pipeline sites on that shape,
+    // then (batches) the jobs sharing the inner product's key words
     const int caps[] = {1, 2, 3, 4}, chunks[] = {4, 8, 16}, pdls[] = {1, 0};
+    const int ipj = keep.ip_jobs;
     for (int pdl : pdls)
         for (int cap : caps)
             for (int ch : chunks)
-                if (rc == HE_OK) rc = time_shape({cap, ch, pdl, 0, 0});
+                if (rc == HE_OK) rc = time_shape({cap, ch, pdl, 0, ipj, 0});
     const he_shape base = top;
     for (int mask = 1; mask < 16 && rc == HE_OK; mask++) {
         he_shape sh = base;
         sh.ntt_r8 = mask;
         rc = time_shape(sh);
+    }
+    if (count > 1 && inner_product_shared_fits(c)) {
+        const he_shape b2 = top;
+        for (int per : {1, 4, 8}) {
+            if (per == b2.ip_jobs || rc != HE_OK) continue;
+            he_shape sh = b2;
+            sh.ip_jobs = per;
+            rc = time_shape(sh);
+        }
     }
     c->prof = prof;
     cudaEventDestroy(e0);
@@ -799,8 +853,9 @@ struct he_batch_graph {
     const u64 *evk = nullptr;
     char *ws = nullptr;
     size_t hdr = 0, slot_limbs = 0;
-    size_t items_bytes = 0, counts_off = 0, lists_off[4] = {0, 0, 0, 0};
+    size_t items_bytes = 0, counts_off = 0, lists_off[4] = {0, 0, 0, 0}, ipg_off = 0;
     int list_max[4] = {0, 0, 0, 0};
+    int ip_jobs = 0;  // jobs per inner-product group captured (0: one job per CTA)
     unsigned char *pinned = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -828,6 +883,8 @@ void graph_layout(const he_ctx *c, int max_jobs, he_batch_graph *g)
         g->lists_off[t] = off;
         off += round_up(sizeof(NttGroup) * (size_t)g->list_max[t]);
     }
+    g->ipg_off = off;
+    off += round_up(sizeof(IpGroup) * (size_t)max_jobs);
     g->hdr = off;
     size_t slot = 0;
     for (int l = 2; l <= c->L; l++) slot = std::max(slot, c->host_levels[l].ws.total);
@@ -891,6 +948,11 @@ int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws
         *np[t] = g->list_max[t];
     }
     Sg.counts = (const int *)(g->ws + g->counts_off);
+    if (use_shared_ip(c, max_jobs)) {
+        g->ip_jobs = c->ip_jobs;
+        Sg.ipg = (const IpGroup *)(g->ws + g->ipg_off);
+        Sg.n_ipg = (max_jobs + g->ip_jobs - 1) / g->ip_jobs;
+    }
     u64 *data = (u64 *)(g->ws + g->hdr);
     int rc = HE_OK;
     cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
@@ -960,6 +1022,13 @@ int he_batch_graph_launch(he_batch_graph *g, int count, const he_job *jobs, void
         if ((int)grp.size() > g->list_max[t]) return HE_EINVAL;
         memcpy(g->pinned + g->lists_off[t], grp.data(), sizeof(NttGroup) * grp.size());
         counts[t] = (int)grp.size();
+    }
+    if (g->ip_jobs) {
+        std::vector<int> lv(count);
+        for (int i = 0; i < count; i++) lv[i] = jobs[i].level;
+        const std::vector<IpGroup> ipg = ip_groups(lv.data(), count, g->ip_jobs);
+        memcpy(g->pinned + g->ipg_off, ipg.data(), sizeof(IpGroup) * ipg.size());
+        counts[4] = (int)ipg.size();
     }
     cudaStream_t st = S(stream);
     if (cudaGraphLaunch(g->exec, st) != cudaSuccess) return HE_ECUDA;

@@ -84,6 +84,20 @@ struct JobRef {
 __device__ __forceinline__ BatchItem job_item(const JobRef &R, int z) { return R.items ? R.items[z] : R.one; }
 #endif
 
+// Batched inner product with shared key tiles: the jobs of a batch, sorted by
+// level (highest first), are cut into groups of at most kIpJobsMax; one CTA
+// loads the evaluation-key words of its (limb, coefficients) once and forms
+// the products of every job of its group with them.  `level` is the group's
+// highest level (its first job's).
+constexpr int kIpJobsMax = 8;
+struct IpGroup {
+    int n, level, pad0, pad1;
+    int job[kIpJobsMax];
+};
+// Groups of at most `per` jobs (1..kIpJobsMax) over jobs sorted by level,
+// highest first (ties keep the batch order).
+std::vector<IpGroup> ip_groups(const int *levels, int count, int per);
+
 // Workspace layout of one HE Mul at level l (offsets in limbs).
 struct WsLayout {
     size_t d0, d1, d2, y, u, ks, ys, r, z, total;
@@ -125,6 +139,7 @@ struct he_ctx {
     int modup_chunk = 8;
     bool pdl = true;                     // programmatic dependent launch between the path's kernels
     int ntt_r8 = 0;                      // bit s: the radix-8 NTT plan at pipeline NTT site s (0..3)
+    int ip_jobs = he::kIpJobsMax;        // batches: jobs sharing one CTA's key words in the inner product (1: none)
     std::vector<u64> ext;                // moduli, ext order
     std::vector<u64> psi;                // smallest primitive 2N-th roots, ext order
     // host tables (for the host NTT used by keygen / encrypt / decrypt)
@@ -204,6 +219,15 @@ inline void launch_k(bool dep, void (*k)(KArgs...), dim3 grid, dim3 block, size_
 // dependency).
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Exit of a CTA with no work.  It still waits for the previous kernel first:
+// a kernel launched after this one waits only for this kernel's completion,
+// so this kernel must not complete before its own predecessor has, even when
+// none of its CTAs has work (ordering is then transitive along the stream).
+// Tables that only the host writes (job items, NTT group lists and their
+// counts, copied before a launch sequence's first kernel) may be read before
+// the wait; nothing a kernel writes is.
+__device__ __forceinline__ void idle_exit() { griddep_wait(); }
+
 // L2 eviction policies.  Streams read once per HE Mul (the evaluation key,
 // the input ciphertexts, ModUp outputs) are marked evict-first, so they pass
 // through L2 without displacing the NTT twiddle tables, which every HE Mul
@@ -254,6 +278,11 @@ cudaError_t run_elementwise(const he_ctx *c, int op, const u64 *x, const u64 *y,
 // Rotation's first step: d0 = kappa_g(b), d1 = 0, d2 = -kappa_g(a) into ws (level l).
 cudaError_t run_automorph(const he_ctx *c, const u64 *ct, u64 *ws, int l, u64 g, cudaStream_t st);
 cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st);
+// The batched inner product with key words shared by the jobs of each group
+// (ngroups launched; dev_count, optional, bounds the groups on the device).
+bool inner_product_shared_fits(const he_ctx *c);  // the shared kernel covers at most four digits
+cudaError_t run_inner_product_shared(const he_ctx *c, const JobRef &R, const IpGroup *groups, int ngroups,
+                                     const int *dev_count, const u64 *evk, cudaStream_t st);
 // The key switch's tail: ModDown alone, ModDown then rescale (two floors,
 // bit-identical to he_mul then he_rescale), or one division by P q_{l-1}.
 enum TailMode { kTailPlain = 0, kTailRescale = 1, kTailRescalePQ = 2 };

@@ -5,11 +5,13 @@
 // a thin foreign-language binding with no device allocator of its own).
 //
 // The scratch is a file-scope __device__ array of HE_STATIC_SCRATCH_BYTES
-// (one instance per device).  Its address is looked up once per device with
-// cudaGetSymbolAddress on the first call made with that device current; that
-// lookup may load this file's device module, so the first call on a device
-// should be made outside any stream capture.  Nothing here calls cudaMalloc,
-// cudaFree or any allocating routine.
+// (one instance per device).  In host code its name is only a stand-in, not a
+// device address, so every call looks the address up with
+// cudaGetSymbolAddress for the current device (cheap once the module is
+// loaded, and never stale, even after the device's context was torn down
+// and recreated).  The first lookup on a device may load this file's device
+// module, so the first call on a device should be made outside any stream
+// capture.  Nothing here calls cudaMalloc, cudaFree or any allocating routine.
 //
 // Nothing in the scratch has to start at zero: every word the HE Mul pipeline
 // reads from its workspace is written earlier in the same call.
@@ -18,9 +20,6 @@
 // executions overlap (different streams, or different host threads without
 // ordering between their streams) race on it and give wrong results.  Calls
 // issued to the same stream are ordered and safe.
-#include <atomic>
-#include <mutex>
-
 #include "he_internal.h"
 
 using namespace he;
@@ -32,24 +31,11 @@ static_assert((size_t)HE_STATIC_SCRATCH_BYTES % 256 == 0, "scratch size must kee
 
 static __device__ __align__(256) u64 g_scratch[kScratchWords];
 
-constexpr int kMaxDevices = 64;
-std::atomic<void *> g_scratch_addr[kMaxDevices];
-std::mutex g_scratch_mu;
-
-// Device address of the scratch on `dev`, the current device (looked up on
-// first use).
-int scratch_address(int dev, void **out)
+// Device address of the scratch on the current device.
+int scratch_address(void **out)
 {
-    if (dev < 0 || dev >= kMaxDevices) return HE_EINVAL;
-    void *p = g_scratch_addr[dev].load(std::memory_order_acquire);
-    if (!p) {
-        std::lock_guard<std::mutex> lk(g_scratch_mu);
-        p = g_scratch_addr[dev].load(std::memory_order_relaxed);
-        if (!p) {
-            if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return HE_ECUDA;
-            g_scratch_addr[dev].store(p, std::memory_order_release);
-        }
-    }
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return HE_ECUDA;
     *out = p;
     return HE_OK;
 }
@@ -66,7 +52,7 @@ extern "C" int he_mul_rescale_static(he_ctx *c, const uint64_t *ct1, const uint6
     if (cudaGetDevice(&dev) != cudaSuccess) return HE_ECUDA;
     if (dev != c->device_id) return HE_EINVAL;  // the context's tables live on another device
     void *ws = nullptr;
-    const int rc = scratch_address(dev, &ws);
+    const int rc = scratch_address(&ws);
     if (rc != HE_OK) return rc;
     return he_mul_rescale(c, ct1, ct2, evk, level, out, ws, (size_t)HE_STATIC_SCRATCH_BYTES, stream);
 }

@@ -320,6 +320,12 @@ uint64_t he_galois_elt(const he_ctx *c, int steps)
     return g;
 }
 
+uint64_t he_conj_elt(const he_ctx *c)
+{
+    if (!c) return 0;
+    return 2 * (u64)c->N - 1;  // X -> X^(-1) = X^(2N-1) mod X^N + 1
+}
+
 int he_keygen_seeded(he_ctx *c, uint64_t seed, const int64_t *sk, uint64_t *evk_b)
 {
     if (!c || !sk || !evk_b) return HE_EINVAL;

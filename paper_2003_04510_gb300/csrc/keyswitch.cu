@@ -49,7 +49,7 @@ k_tensor(const JobRef R, const DevPrime *__restrict__ primes, const DevLevel *__
 {
     const BatchItem it = job_of(R, blockIdx.z);
     const int l = it.level, i = blockIdx.y;
-    if (i >= l) return;
+    if (i >= l) return idle_exit();
     const DevLevel &lv = lv_arr[l];
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[K + i];
@@ -82,12 +82,12 @@ k_modup(const JobRef R, const DevLevel *__restrict__ lv_arr, const DevPrime *__r
     const BatchItem it = job_of(R, blockIdx.z);
     const DevLevel &lv = lv_arr[it.level];
     const int j = blockIdx.y / chunks;
-    if (j >= lv.beta) return;
+    if (j >= lv.beta) return idle_exit();
     const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
     const int E = lv.E;
     const int u0 = (blockIdx.y - j * chunks) * CH;
     const int cnt = min(CH, E - nj - u0);
-    if (cnt <= 0) return;
+    if (cnt <= 0) return idle_exit();
     __shared__ u64 sB[CH][A];
     __shared__ u64 sq[CH], smu[CH];
     __shared__ unsigned ss[CH];
@@ -169,7 +169,7 @@ k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__r
     const DevLevel &lv = lv_arr[it.level];
     const int e = blockIdx.y;
     const int E = lv.E, EL = K + L, beta = lv.beta;
-    if (e >= E) return;
+    if (e >= E) return idle_exit();
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[e];
     const u64 *U = it.ws + (size_t)lv.o_u * N, *d2 = it.ws + (size_t)lv.o_d2 * N;
@@ -208,6 +208,98 @@ k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__r
     u64 *KS = it.ws + (size_t)lv.o_ks * N;
     st2(KS + (size_t)e * N + n, barrett128(bx, pr.q, pr.mu, pr.s), barrett128(by, pr.q, pr.mu, pr.s));
     st2(KS + ((size_t)E + e) * N + n, barrett128(ax, pr.q, pr.mu, pr.s), barrett128(ay, pr.q, pr.mu, pr.s));
+}
+
+// The U words of one job for ext limb e at coefficients n, n+1 (digits j <
+// the job's beta; own-digit rows from d2, as above).
+template <int BM>
+__device__ __forceinline__ void ip_load_u(const BatchItem &it, const DevLevel &lv, int e, int K, int N, size_t n,
+                                          u64 pol, ulonglong2 (&u)[BM])
+{
+    const u64 *U = it.ws + (size_t)lv.o_u * N, *d2 = it.ws + (size_t)lv.o_d2 * N;
+#pragma unroll
+    for (int j = 0; j < BM; j++) {
+        if (j < lv.beta) {
+            const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
+            const bool own = e >= K && e - K >= lo && e - K < lo + nj;
+            u[j] = own ? ld2(d2 + (size_t)(e - K) * N + n) : ld2_hint(U + ((size_t)j * lv.E + e) * N + n, pol);
+        }
+    }
+}
+
+// Batched inner product with key words shared across jobs.  grid: x over
+// N/2/kThreads, y over ext limbs (up to K + lmax), z over job groups
+// (IpGroup: at most kIpJobsMax jobs, highest level first).  A CTA loads the
+// key words of digits j < beta(group's highest level) at (e, n) once, then
+// forms KS of each job of its group that has limb e (the jobs whose level
+// exceeds e - K), its next job's U words in flight while the current job's
+// products run.  Per job the words are those of k_inner_product: the key
+// limbs and digits do not depend on the level (one full-level key serves every
+// level), only U, d2, KS and beta do.
+template <int BM, bool SEEDED>
+__global__ void __launch_bounds__(kThreads)
+k_inner_product_shared(const JobRef R, const IpGroup *__restrict__ groups, const int *count,
+                       const u64 *__restrict__ evk, const DevLevel *__restrict__ lv_arr,
+                       const DevPrime *__restrict__ primes, int K, int L, int N, const SeedStates seeds)
+{
+    const int gz = blockIdx.z;
+    if (count && gz >= *count) return idle_exit();
+    const IpGroup &gr = groups[gz];
+    const int e = blockIdx.y;
+    const DevLevel &lv0 = lv_arr[gr.level];
+    if (gr.n < 1 || e >= lv0.E) return idle_exit();
+    const int EL = K + L, beta0 = lv0.beta;
+    const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
+    const DevPrime pr = primes[e];
+    griddep_wait();
+    const u64 pol = l2_policy_stream();
+    ulonglong2 kb[BM], ka[BM];
+#pragma unroll
+    for (int j = 0; j < BM; j++) {
+        if (j < beta0) {
+            if (SEEDED) {
+                kb[j] = ld2_hint(evk + ((size_t)j * EL + e) * N + n, pol);
+                const u64 idx = (u64)e * (u64)N + n;
+                ka[j] = make_ulonglong2(seeded_a(seeds.s[j], idx, pr.q), seeded_a(seeds.s[j], idx + 1, pr.q));
+            } else {
+                kb[j] = ld2_hint(evk + ((size_t)(2 * j) * EL + e) * N + n, pol);
+                ka[j] = ld2_hint(evk + ((size_t)(2 * j + 1) * EL + e) * N + n, pol);
+            }
+        }
+    }
+    BatchItem it = job_item(R, gr.job[0]);
+    ulonglong2 u[BM];
+    ip_load_u<BM>(it, lv_arr[it.level], e, K, N, n, pol, u);
+    for (int g = 0;;) {
+        const DevLevel &lv = lv_arr[it.level];
+        // the next job of the group, if it has limb e
+        BatchItem nx = it;
+        bool more = g + 1 < gr.n;
+        if (more) {
+            nx = job_item(R, gr.job[g + 1]);
+            more = e < K + nx.level;
+        }
+        ulonglong2 v[BM];
+        if (more) ip_load_u<BM>(nx, lv_arr[nx.level], e, K, N, n, pol, v);
+        U128 bx = {0, 0}, by = {0, 0}, ax = {0, 0}, ay = {0, 0};
+#pragma unroll
+        for (int j = 0; j < BM; j++) {
+            if (j < lv.beta) {
+                mac(bx, u[j].x, kb[j].x);
+                mac(by, u[j].y, kb[j].y);
+                mac(ax, u[j].x, ka[j].x);
+                mac(ay, u[j].y, ka[j].y);
+            }
+        }
+        u64 *KS = it.ws + (size_t)lv.o_ks * N;
+        st2(KS + (size_t)e * N + n, barrett128(bx, pr.q, pr.mu, pr.s), barrett128(by, pr.q, pr.mu, pr.s));
+        st2(KS + ((size_t)lv.E + e) * N + n, barrett128(ax, pr.q, pr.mu, pr.s), barrett128(ay, pr.q, pr.mu, pr.s));
+        if (!more) break;
+        it = nx;
+#pragma unroll
+        for (int j = 0; j < BM; j++) u[j] = v[j];
+        g++;
+    }
 }
 
 // grid: x over N/2/kThreads, y over (h in {0,1}, chunk of kModdownChunk
@@ -256,7 +348,7 @@ k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__r
     const int nout = MODE != kTailPlain ? l - 1 : l;
     const int i0 = (blockIdx.y - h * chunks) * kModdownChunk;
     const int cnt = min(kModdownChunk, nout - i0);
-    if (cnt <= 0) return;
+    if (cnt <= 0) return idle_exit();
     const u64 *PBt = PQ ? lv.pbpq : PB;
     // rows 0..cnt-1: this chunk's outputs; row kModdownChunk: q_{l-1} (fused)
     __shared__ u64 sB[kModdownChunk + 1][KM];
@@ -335,7 +427,7 @@ k_combine_plain(const JobRef R, const ulonglong2 *__restrict__ pinv, const DevLe
 {
     const BatchItem it = job_of(R, blockIdx.z >> 1);
     const int h = blockIdx.z & 1, l = it.level, i = blockIdx.y;
-    if (i >= l) return;
+    if (i >= l) return idle_exit();
     const DevLevel &lv = lv_arr[l];
     const int E = K + l;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
@@ -530,6 +622,40 @@ cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, 
     else if (bm <= 8) HE_IP(8);
     else HE_IP(16);
 #undef HE_IP
+    return cudaGetLastError();
+}
+
+bool inner_product_shared_fits(const he_ctx *c) { return (c->L + c->alpha - 1) / c->alpha <= 4; }
+
+cudaError_t run_inner_product_shared(const he_ctx *c, const JobRef &R, const IpGroup *groups, int ngroups,
+                                     const int *dev_count, const u64 *evk, cudaStream_t st)
+{
+    if (!inner_product_shared_fits(c)) return cudaErrorInvalidValue;
+    dim3 g = grid_x(c->N);
+    g.y = c->K + R.lmax;
+    g.z = ngroups;
+    const int bm = (c->L + c->alpha - 1) / c->alpha;
+    SeedStates ss;
+    memset(&ss, 0, sizeof(ss));
+    bool seeded = false;
+    for (const auto &k : c->seeded)
+        if (k.ptr == evk) {
+            seeded = true;
+            memcpy(ss.s, k.state, sizeof(ss.s));
+        }
+#define HE_IPS(B)                                                                                                  \
+    do {                                                                                                           \
+        if (seeded)                                                                                                \
+            launch_k(c->pdl, k_inner_product_shared<B, true>, g, dim3(kThreads), 0, st, R, groups, dev_count, evk, \
+                     c->d_levels, c->d_primes, c->K, c->L, c->N, ss);                                              \
+        else                                                                                                       \
+            launch_k(c->pdl, k_inner_product_shared<B, false>, g, dim3(kThreads), 0, st, R, groups, dev_count,     \
+                     evk, c->d_levels, c->d_primes, c->K, c->L, c->N, ss);                                         \
+    } while (0)
+    if (bm <= 2) HE_IPS(2);
+    else if (bm == 3) HE_IPS(3);
+    else HE_IPS(4);
+#undef HE_IPS
     return cudaGetLastError();
 }
 

@@ -83,6 +83,31 @@ __device__ __forceinline__ u64 shoup_approx_nq(u64 x, u64 w, u64 wp, u64 nq)
 
 __device__ __forceinline__ u64 shoup(u64 x, u64 w, u64 wp, u64 q) { return csub(shoup_lazy(x, w, wp, q), q); }
 
+// The NTT's butterflies (ntt.cu; the throughput probe runs the same ones).
+// Forward (Cooley-Tukey, Algo 4) with no correction step: the modified
+// Shoup product t lies in [0, 4q), so each stage adds at most 4q to the
+// range.  From canonical inputs, values stay below (1 + 4 log N) q < 2^64 for
+// q < 2^57.9 and are reduced once, on the final store.  w = (value, Shoup
+// companion), nq = 2^64 - q.
+__device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, ulonglong2 w, u64 nq, u64 q4)
+{
+    const u64 t = shoup_approx_nq(y, w.x, w.y, nq);
+    y = x + q4 - t;
+    x = x + t;
+}
+
+// Inverse (Gentleman-Sande) butterfly on values in [0, 4q): the sum is
+// brought back below 4q with one conditional subtraction, the difference
+// goes through the modified Shoup product, which lands in [0, 4q).
+__device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, ulonglong2 w, u64 nq, u64 q4)
+{
+    u64 s = x + y;
+    s = s >= q4 ? s - q4 : s;
+    const u64 d = x + q4 - y;
+    y = shoup_approx_nq(d, w.x, w.y, nq);
+    x = s;
+}
+
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
 
 __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }

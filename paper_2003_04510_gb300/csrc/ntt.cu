@@ -58,29 +58,6 @@ struct NttArgs {
     const ulonglong2 *pinv;
 };
 
-// Forward (Cooley-Tukey) butterfly with no correction step: the modified
-// Shoup product t lies in [0, 4q), so each stage adds at most 4q to the
-// range.  From canonical inputs, values stay below (1 + 4 log N) q < 2^64 for
-// q < 2^57.9 and are reduced once, on the final store.  nq = 2^64 - q.
-__device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, ulonglong2 w, u64 nq, u64 q4)
-{
-    const u64 t = shoup_approx_nq(y, w.x, w.y, nq);
-    y = x + q4 - t;
-    x = x + t;
-}
-
-// Inverse (Gentleman-Sande) butterfly on values in [0, 4q): the sum is
-// brought back below 4q with one conditional subtraction, the difference
-// goes through the modified Shoup product, which lands in [0, 4q).
-__device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, ulonglong2 w, u64 nq, u64 q4)
-{
-    u64 s = x + y;
-    s = s >= q4 ? s - q4 : s;
-    const u64 d = x + q4 - y;
-    y = shoup_approx_nq(d, w.x, w.y, nq);
-    x = s;
-}
-
 // 16-byte read-only load that does not allocate in L1 (twiddles read once).
 // The table's lines are kept in L2 (evict-last): every HE Mul rereads them.
 __device__ __forceinline__ ulonglong2 ld_tw(const ulonglong2 *p) { return ld2_hint(p, l2_policy_keep()); }
@@ -287,7 +264,7 @@ k_ntt_pass(const NttArgs P)
 
     const int gidx = blockIdx.x / P.tiles;
     const int tile = blockIdx.x - gidx * P.tiles;
-    if (P.count && gidx >= *P.count) return;
+    if (P.count && gidx >= *P.count) return idle_exit();
     const NttGroup &G = P.groups[gidx];
     const int nl = (int)G.nl;
     const DevPrime pr = P.primes[G.prime];

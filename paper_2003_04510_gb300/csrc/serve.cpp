@@ -75,6 +75,12 @@ struct Req {
     clk::time_point t_submit;
 };
 
+// Finished tickets whose status is kept for he_server_poll / he_server_wait,
+// and completion latencies kept for he_server_stats: the most recent ones
+// (older entries are dropped, so a long-running server's memory stays bounded).
+constexpr uint64_t kKeepTickets = 1u << 20;
+constexpr size_t kKeepLatencies = 1u << 16;
+
 struct Flight {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -98,7 +104,8 @@ struct he_server {
     std::condition_variable cv;
     std::deque<Req> pending;
     std::map<uint64_t, int> status;  // ticket -> 0 pending/in flight, 1 done, <0 -error
-    std::vector<double> latencies_ms;
+    std::vector<double> latencies_ms;  // ring of the last kKeepLatencies completions
+    size_t lat_next = 0;
     uint64_t next_ticket = 1;
     uint64_t completed = 0, batches = 0, batched_requests = 0;
     clk::time_point t_first, t_last;
@@ -131,8 +138,15 @@ bool step(he_server *s)
         const int st = (q == cudaSuccess && f.rc == HE_OK) ? 1 : -(f.rc == HE_OK ? HE_ECUDA : f.rc);
         for (size_t i = 0; i < f.tickets.size(); i++) {
             s->status[f.tickets[i]] = st;
-            s->latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - f.t_submit[i]).count());
+            const double ms = std::chrono::duration<double, std::milli>(now - f.t_submit[i]).count();
+            if (s->latencies_ms.size() < kKeepLatencies) s->latencies_ms.push_back(ms);
+            else s->latencies_ms[s->lat_next] = ms;
+            s->lat_next = (s->lat_next + 1) % kKeepLatencies;
         }
+        // forget finished tickets that are more than kKeepTickets old
+        while (!s->status.empty() && s->status.begin()->first + kKeepTickets < s->next_ticket &&
+               s->status.begin()->second != 0)
+            s->status.erase(s->status.begin());
         s->completed += f.tickets.size();
         s->t_last = now;
         s->arena->release(f.ws_off, f.ws_bytes);
@@ -176,6 +190,11 @@ bool step(he_server *s)
             }
         }
         he_ctx *c = s->ctxs[take[0].r.ctx_index];
+        // operands written on other streams: the batch waits for their events
+        int rc_wait = HE_OK;
+        for (const Req &q : take)
+            if (q.r.ready && cudaStreamWaitEvent(f.stream, (cudaEvent_t)q.r.ready, 0) != cudaSuccess)
+                rc_wait = HE_ECUDA;
         std::vector<he_job> jobs(take.size());
         for (size_t i = 0; i < take.size(); i++) {
             jobs[i].ct1 = take[i].r.ct1;
@@ -183,8 +202,9 @@ bool step(he_server *s)
             jobs[i].out = take[i].r.out;
             jobs[i].level = take[i].r.level;
         }
-        f.rc = he_mul_batch(c, (int)jobs.size(), jobs.data(), s->evks[take[0].r.ctx_index],
-                            (char *)s->arena_mem + off, bytes, f.stream);
+        f.rc = rc_wait != HE_OK ? rc_wait
+                                : he_mul_batch(c, (int)jobs.size(), jobs.data(), s->evks[take[0].r.ctx_index],
+                                               (char *)s->arena_mem + off, bytes, f.stream);
         cudaEventRecord(f.done, f.stream);
         f.busy = true;
         f.ws_off = off;

@@ -269,6 +269,46 @@ def test_batch_matches_single_and_oracle(g):
         assert np.array_equal(host(g, jobs[k][2]), want)
 
 
+@pytest.mark.parametrize("levels,ip_jobs", [
+    ([3, 5], 8), ([5, 3], 4), ([3, 5, 2, 4, 5, 3, 2, 8, 9], 4),
+    ([24, 4, 9, 17, 2, 13, 24, 23, 16, 8, 3], 8), ([24, 9, 17, 2], 1)])
+def test_batch_shared_key_words_bit_exact(g, levels, ip_jobs):
+    """Batches whose inner product shares each CTA's evaluation-key words among
+    up to ip_jobs jobs of similar level (groups cut from the jobs sorted by
+    level, ragged last group, jobs of a group at different levels and digit
+    counts): every result equals he_mul_rescale on the job alone, bit for bit,
+    and the lowest-level job equals the oracle."""
+    import torch
+    name = "n16"
+    ctx = ctx_for(g, name)
+    op = oracle.preset(name)
+    evk = rand_evk(op, 160)
+    evk_t = dev(g, evk)
+    jobs, singles, cts = [], [], []
+    for k, lv in enumerate(levels):
+        c1, c2 = rand_ct(op, lv, 1200 + 2 * k), rand_ct(op, lv, 1300 + 2 * k)
+        cts.append((c1, c2))
+        out = torch.full((2, lv - 1, op.N), -1, dtype=torch.int64, device="cuda")
+        jobs.append((dev(g, c1), dev(g, c2), out, lv))
+        singles.append(gpu_mul(g, ctx, c1, c2, evk_t, lv, fused=True))
+    ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
+    try:
+        g.he_set_shape(ctx, 4, 8, 1, 0, ip_jobs)
+        for rnd in range(2):  # twice on the same workspace
+            for j in jobs:
+                j[2].fill_(-1)
+            g.he_mul_batch(ctx, jobs, evk_t, ws)
+            torch.cuda.synchronize()
+            for (t1, t2, out, lv), single in zip(jobs, singles):
+                assert np.array_equal(host(g, out), single), (rnd, lv)
+    finally:
+        g.he_set_shape(ctx, 4, 8, 1)
+    k = int(np.argmin(levels))
+    c1, c2 = cts[k]
+    want = oracle.rescale(op, oracle.he_mul(op, c1, c2, evk, levels[k]), levels[k])
+    assert np.array_equal(host(g, jobs[k][2]), want)
+
+
 @pytest.mark.parametrize("capture_cap,replay_cap", [(4, 4), (1, 3)])
 def test_batch_graph_replays_match_single(g, capture_cap, replay_cap):
     """One captured graph, replayed with two different batches (sizes, levels,
@@ -357,10 +397,52 @@ def test_server_admission_errors(g):
     assert e.value.code == g.HE_ELEVEL
     b = torch.zeros((2, 8, op.N), dtype=torch.int64, device="cuda")
     o2 = torch.zeros((2, 7, op.N), dtype=torch.int64, device="cuda")
-    tk = srv.submit(0, 8, b, b, o2)
-    rc = g.lib().he_server_wait(srv.ptr, tk, 0)
-    assert rc in (g.HE_OK, g.HE_ETIMEOUT)
+    # the budget admits one level-8 request at a time: the last of eight
+    # queued back to back waits behind seven HE Muls run one after another,
+    # so a zero-timeout wait on it right after submitting must time out
+    tks = [srv.submit(0, 8, b, b, o2) for _ in range(8)]
+    assert g.lib().he_server_wait(srv.ptr, tks[-1], 0) == g.HE_ETIMEOUT
+    for tk in tks:
+        srv.wait(tk, 60000)
+    assert g.lib().he_server_wait(srv.ptr, tks[-1], 0) == g.HE_OK
+    st = srv.stats()
+    assert st["batches"] == 8 and st["completed"] == 8  # one request per batch under this budget
+    with pytest.raises(g.HeError) as e:
+        srv.poll(123456789)  # never issued
+    assert e.value.code == g.HE_EINVAL
+    srv.close()
+
+
+def test_server_waits_for_request_events(g):
+    """Operands written on another stream and submitted at once, with the
+    event recorded after the writes: the batch waits for the event on the
+    device, and the result equals he_mul_rescale on the same operands."""
+    import torch
+    ctx = ctx_for(g, "n16")
+    op = oracle.preset("n16")
+    evk_t = dev(g, rand_evk(op, 170))
+    lv = 20
+    srv = g.Server([ctx], [evk_t], hbm_budget=2 * g.he_batch_workspace_bytes(ctx, [lv]), max_batch=4, streams=2)
+    src1, src2 = dev(g, rand_ct(op, lv, 1400)), dev(g, rand_ct(op, lv, 1402))
+    writer = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    a, b = torch.empty_like(src1), torch.empty_like(src2)
+    out = torch.full((2, lv - 1, op.N), -1, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(writer):
+        for _ in range(20):  # keep the writer busy for a while before the copies land
+            a.copy_(src2)
+            b.copy_(src1)
+        a.copy_(src1)
+        b.copy_(src2)
+        ev = torch.cuda.Event()
+        ev.record(writer)
+    tk = srv.submit(0, lv, a, b, out, ready=ev)
     srv.wait(tk, 60000)
+    torch.cuda.synchronize()
+    ref = torch.empty_like(out)
+    g.he_mul_rescale(ctx, src1, src2, evk_t, lv, ref, g.workspace(ctx, lv))
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
     srv.close()
 
 
@@ -591,9 +673,10 @@ def test_autotune_batch_keeps_results(g):
     ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
     try:
         best, tried = g.he_autotune(ctx, jobs, evk_t, ws, reps=2)
-        assert len(tried) == 39 and all(t[4] > 0 for t in tried)
-        assert best[:4] == g.he_get_shape(ctx) and best[4] == min(t[4] for t in tried)
-        assert sorted(t[3] for t in tried[24:]) == list(range(1, 16))
+        assert len(tried) == 41 and all(t[5] > 0 for t in tried)
+        assert best[:5] == g.he_get_shape(ctx) and best[5] == min(t[5] for t in tried)
+        assert sorted(t[3] for t in tried[24:39]) == list(range(1, 16))
+        assert sorted(t[4] for t in tried[39:]) == [1, 4]  # the other two ip_jobs values
         for j in jobs:
             j[2].zero_()
         g.he_mul_batch(ctx, jobs, evk_t, ws)

@@ -68,3 +68,32 @@ def test_static_rejects_levels_beyond_scratch(g):
     evk_t = g.to_device(rand_evk(ctx, 530))
     ref, got = both(g, ctx, rand_ct(ctx, fits, 540), rand_ct(ctx, fits, 550), evk_t, fits)
     assert np.array_equal(got, ref)
+
+
+def test_static_back_to_back_on_one_stream(g):
+    """Calls issued in order on one non-default stream share the scratch
+    safely: two calls back to back at different levels and on different
+    inputs, synchronised only at the end, each equal the workspace entry
+    point's result.  A level below 2 is rejected before anything runs."""
+    import torch
+    ctx = g.Context(g.PRESETS["n15"][0], device=True)
+    evk_t = g.to_device(rand_evk(ctx, 560))
+    st = torch.cuda.Stream()
+    cases = []
+    for k, level in enumerate((16, 7)):
+        a = g.to_device(rand_ct(ctx, level, 570 + 10 * k))
+        b = g.to_device(rand_ct(ctx, level, 575 + 10 * k))
+        cases.append((level, a, b, torch.full((2, level - 1, ctx.N), -1, dtype=torch.int64, device="cuda")))
+    torch.cuda.synchronize()
+    for level, a, b, out in cases:
+        g.he_mul_rescale_static(ctx, a, b, evk_t, level, out, st)
+    st.synchronize()
+    for level, a, b, out in cases:
+        ref = torch.empty_like(out)
+        g.he_mul_rescale(ctx, a, b, evk_t, level, ref, g.workspace(ctx, level))
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), level
+    level, a, b, out = cases[0]
+    with pytest.raises(g.HeError) as e:
+        g.he_mul_rescale_static(ctx, a, b, evk_t, 1, out, st)
+    assert e.value.code == g.HE_ELEVEL
