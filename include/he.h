@@ -449,7 +449,7 @@ int he_nr_rescale(he_nr_plan *plan, const uint64_t *ct, int logq, uint64_t *out,
  * the special limbs, 3 the NTT of the ModDown limbs) use the radix-8 plan
  * (rounds of at most three stages, 256 threads per tile) instead of the
  * radix-16 one (128 threads per tile).  Speed only: every shape gives
- * bit-identical results.  Default {4, 8, 1, 0, 8}.  A batch graph keeps the
+ * bit-identical results.  Default {4, 8, 1, 0, 8, 1}.  A batch graph keeps the
  * shape it was captured with, except the limb-group cap. */
 typedef struct {
     int group_cap;
@@ -460,6 +460,9 @@ typedef struct {
                     product, which reads the evaluation key's words once for all of them (Fig. 2 region 2's
                     key stream, read once per group instead of once per job); 1 = one job per CTA.  Used
                     while the context has at most four digits (dnum <= 4), else 1. */
+    int fuse;    /* bit 0: the tensor product (Fig. 2 region 1) is formed inside the first inverse-NTT pass
+                    of d2, which loads the ciphertexts instead of d2 and also stores d0, d1, d2 (one launch
+                    and one read of d2 fewer); 0: its own kernel.  0..1 */
     double ms;   /* he_autotune: measured milliseconds per call; else 0 */
 } he_shape;
 
@@ -469,7 +472,8 @@ int he_get_shape(const he_ctx *ctx, he_shape *shape);
 /* Time shapes on the caller's own work and keep the fastest in ctx: every
  * (group_cap, modup_chunk, pdl) with the radix-16 NTT plan, then every
  * nonzero ntt_r8 mask on the best of those (39 shapes), then, for a batch,
- * the other two ip_jobs values on the best (41 shapes);
+ * the other two ip_jobs values on the best, then the other fuse value on the
+ * best (40 shapes for one job, 42 for a batch);
  * count == 1 times he_mul_rescale on jobs[0] (ws of he_workspace_bytes),
  * count > 1 times he_mul_batch on the jobs (ws of he_batch_workspace_bytes),
  * `reps` calls per shape after one warm-up call, CUDA events on `stream`.

@@ -91,26 +91,33 @@ struct Stages {
 // he_rescale); kTailRescalePQ, one division by P q_{l-1} (out [2][l-1][N]).
 // NTT group offsets are relative to ntt_base.
 int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, int mode,
-                  cudaStream_t st);
+                  cudaStream_t st, bool tensor_fused = false);
 
 int run_pipeline(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, int mode,
                  cudaStream_t st)
 {
     prof_mark(c, st, "");
-    // Region 1: tensor product
-    HE_TRY(run_tensor(c, R, st));
-    prof_mark(c, st, "tensor");
-    return run_keyswitch(c, R, ntt_base, S, evk, mode, st);
+    // Region 1: tensor product, on its own or inside the first iNTT pass of d2
+    const bool fused = (c->fuse & 1) != 0;
+    if (!fused) {
+        HE_TRY(run_tensor(c, R, st));
+        prof_mark(c, st, "tensor");
+    }
+    return run_keyswitch(c, R, ntt_base, S, evk, mode, st, fused);
 }
 
-// Region 2 and the final additions, on d0, d1, d2 already in the workspace.
+// Region 2 and the final additions, on d0, d1, d2 already in the workspace
+// (tensor_fused: the first iNTT pass forms d0, d1, d2 itself).
 int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, const u64 *evk, int mode,
-                  cudaStream_t st)
+                  cudaStream_t st, bool tensor_fused)
 {
     // key switching: iNTT(d2) (times N^-1 Qhat^-1), ModUp, NTT, inner product
     const int *cnt = S.counts;
     auto r8 = [c](int site) { return ((c->ntt_r8 >> site) & 1) != 0; };
-    HE_TRY(launch_ntt(c, ntt_base, S.intt1, S.n_intt1, true, st, "intt_d2", cnt ? cnt + 0 : nullptr, r8(0)));
+    if (tensor_fused)
+        HE_TRY(launch_ntt_tensor(c, ntt_base, S.intt1, S.n_intt1, R, st, "intt_d2", cnt ? cnt + 0 : nullptr, r8(0)));
+    else
+        HE_TRY(launch_ntt(c, ntt_base, S.intt1, S.n_intt1, true, st, "intt_d2", cnt ? cnt + 0 : nullptr, r8(0)));
     HE_TRY(run_modup(c, R, st));
     prof_mark(c, st, "modup");
     HE_TRY(launch_ntt(c, ntt_base, S.ntt_up, S.n_ntt_up, false, st, "ntt_modup", cnt ? cnt + 1 : nullptr, r8(1)));
@@ -619,11 +626,13 @@ int he_set_shape(he_ctx *c, const he_shape *sh)
     if (sh->pdl != 0 && sh->pdl != 1) return HE_EINVAL;
     if (sh->ntt_r8 < 0 || sh->ntt_r8 > 15) return HE_EINVAL;
     if (sh->ip_jobs != 1 && sh->ip_jobs != 4 && sh->ip_jobs != 8) return HE_EINVAL;
+    if (sh->fuse < 0 || sh->fuse > 1) return HE_EINVAL;
     c->group_cap = sh->group_cap;
     c->modup_chunk = sh->modup_chunk;
     c->pdl = sh->pdl != 0;
     c->ntt_r8 = sh->ntt_r8;
     c->ip_jobs = sh->ip_jobs;
+    c->fuse = sh->fuse;
     if (c->device) c->jobs = c->jobs_cap[c->group_cap - 1];
     return HE_OK;
 }
@@ -636,6 +645,7 @@ int he_get_shape(const he_ctx *c, he_shape *sh)
     sh->pdl = c->pdl ? 1 : 0;
     sh->ntt_r8 = c->ntt_r8;
     sh->ip_jobs = c->ip_jobs;
+    sh->fuse = c->fuse;
     sh->ms = 0;
     return HE_OK;
 }
@@ -680,13 +690,14 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
     };
     // first the limb-group cap, ModUp chunk and PDL with the radix-16 NTT
     // plan, then the NTT plan of each of the four pipeline sites on that shape,
-    // then (batches) the jobs sharing the inner product's key words
+    // then (batches) the jobs sharing the inner product's key words, then the
+    // tensor product fused or not
     const int caps[] = {1, 2, 3, 4}, chunks[] = {4, 8, 16}, pdls[] = {1, 0};
-    const int ipj = keep.ip_jobs;
+    const int ipj = keep.ip_jobs, fz = keep.fuse;
     for (int pdl : pdls)
         for (int cap : caps)
             for (int ch : chunks)
-                if (rc == HE_OK) rc = time_shape({cap, ch, pdl, 0, ipj, 0});
+                if (rc == HE_OK) rc = time_shape({cap, ch, pdl, 0, ipj, fz, 0});
     const he_shape base = top;
     for (int mask = 1; mask < 16 && rc == HE_OK; mask++) {
         he_shape sh = base;
@@ -701,6 +712,11 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
             sh.ip_jobs = per;
             rc = time_shape(sh);
         }
+    }
+    if (rc == HE_OK) {
+        he_shape sh = top;
+        sh.fuse = top.fuse ^ 1;
+        rc = time_shape(sh);
     }
     c->prof = prof;
     cudaEventDestroy(e0);

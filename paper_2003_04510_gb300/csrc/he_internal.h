@@ -140,6 +140,7 @@ struct he_ctx {
     bool pdl = true;                     // programmatic dependent launch between the path's kernels
     int ntt_r8 = 0;                      // bit s: the radix-8 NTT plan at pipeline NTT site s (0..3)
     int ip_jobs = he::kIpJobsMax;        // batches: jobs sharing one CTA's key words in the inner product (1: none)
+    int fuse = 1;                        // bit 0: the tensor product inside the first inverse NTT pass of d2
     std::vector<u64> ext;                // moduli, ext order
     std::vector<u64> psi;                // smallest primitive 2N-th roots, ext order
     // host tables (for the host NTT used by keygen / encrypt / decrypt)
@@ -268,6 +269,13 @@ cudaError_t configure_ntt(const he_ctx *ctx);
 cudaError_t launch_ntt_combine(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
                                cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr,
                                bool r8 = false);
+// Inverse NTT of d2 (and the rescale limbs of d0, d1) whose first pass forms
+// its input tiles with the tensor product from each job's ciphertexts and
+// stores d0, d1, d2 to the job's workspace (groups carry job and ci = limb |
+// product << 16 | keep << 18).
+cudaError_t launch_ntt_tensor(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
+                              cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr,
+                              bool r8 = false);
 // Number of final stages (the contiguous pass's last round) whose twiddle
 // runs the device table stores transposed; 0 for an unsupported logN.
 int ntt_direct_stages(int logN);

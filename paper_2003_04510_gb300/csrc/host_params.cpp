@@ -221,8 +221,9 @@ int build_context(he_ctx *c, const he_params *p, bool device)
                 for (int i2 = lo; i2 < hi; i2++)
                     if (i2 != i) qh = mul(qh, c->ext[K + i2] % qi, qi);
                 u64 sc = mul(c->ninv[K + i], inv(qh, qi), qi);
+                // tensor fields (the fused first pass): limb i, product d2, keep d0..d2
                 H.intt1.push_back(NttJob{(unsigned)(W.d2 + i), (unsigned)(W.y + i), (unsigned)(K + i), 0, sc,
-                                         shoup(sc, qi)});
+                                         shoup(sc, qi), 0, (unsigned)i | (2u << 16) | (1u << 18), 0, 0});
             }
             for (int e = 0; e < El; e++) {
                 bool own = e >= K && (e - K) >= lo && (e - K) < hi;
@@ -242,7 +243,8 @@ int build_context(he_ctx *c, const he_params *p, bool device)
         H.intt1f = H.intt1;
         for (int h = 0; h < 2; h++)
             H.intt1f.push_back(NttJob{(unsigned)((h ? W.d1 : W.d0) + l - 1), (unsigned)(W.r + h), (unsigned)(K + l - 1),
-                                      0, c->ninv[K + l - 1], c->ninv_sh[K + l - 1]});
+                                      0, c->ninv[K + l - 1], c->ninv_sh[K + l - 1], 0,
+                                      (unsigned)(l - 1) | ((unsigned)h << 16), 0, 0});
         for (int h = 0; h < 2; h++)
             for (int k = 0; k < K; k++) {
                 u64 pk = c->ext[k];

@@ -210,38 +210,29 @@ k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__r
     st2(KS + ((size_t)E + e) * N + n, barrett128(ax, pr.q, pr.mu, pr.s), barrett128(ay, pr.q, pr.mu, pr.s));
 }
 
-// The U words of one job for ext limb e at coefficients n, n+1 (digits j <
-// the job's beta; own-digit rows from d2, as above).
-template <int BM>
-__device__ __forceinline__ void ip_load_u(const BatchItem &it, const DevLevel &lv, int e, int K, int N, size_t n,
-                                          u64 pol, ulonglong2 (&u)[BM])
-{
-    const u64 *U = it.ws + (size_t)lv.o_u * N, *d2 = it.ws + (size_t)lv.o_d2 * N;
-#pragma unroll
-    for (int j = 0; j < BM; j++) {
-        if (j < lv.beta) {
-            const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
-            const bool own = e >= K && e - K >= lo && e - K < lo + nj;
-            u[j] = own ? ld2(d2 + (size_t)(e - K) * N + n) : ld2_hint(U + ((size_t)j * lv.E + e) * N + n, pol);
-        }
-    }
-}
-
 // Batched inner product with key words shared across jobs.  grid: x over
 // N/2/kThreads, y over ext limbs (up to K + lmax), z over job groups
 // (IpGroup: at most kIpJobsMax jobs, highest level first).  A CTA loads the
-// key words of digits j < beta(group's highest level) at (e, n) once, then
+// key words of digits j < beta(group's highest level) at (e, n) once and
 // forms KS of each job of its group that has limb e (the jobs whose level
-// exceeds e - K), its next job's U words in flight while the current job's
-// products run.  Per job the words are those of k_inner_product: the key
-// limbs and digits do not depend on the level (one full-level key serves every
-// level), only U, d2, KS and beta do.
+// exceeds e - K: a prefix of the group).  Per job the words are those of
+// k_inner_product: the key limbs and digits do not depend on the level (one
+// full-level key serves every level), only U, d2, KS and beta do.  The jobs'
+// row addresses are gathered into shared memory before the wait for the
+// previous kernel (they come from host-written tables); after it, the U words
+// of a chunk of jobs (four; two at four digits, for registers) are loaded
+// together with the key words, so a thread has every load of a chunk in
+// flight before its first product.
+
 template <int BM, bool SEEDED>
 __global__ void __launch_bounds__(kThreads)
 k_inner_product_shared(const JobRef R, const IpGroup *__restrict__ groups, const int *count,
                        const u64 *__restrict__ evk, const DevLevel *__restrict__ lv_arr,
                        const DevPrime *__restrict__ primes, int K, int L, int N, const SeedStates seeds)
 {
+    __shared__ const u64 *s_row[kIpJobsMax][BM];  // U row of digit j at limb e (own digit: d2's row)
+    __shared__ u64 *s_ks[kIpJobsMax][2];          // KS_b, KS_a rows of limb e
+    __shared__ int s_beta[kIpJobsMax];            // the job's digits; 0: the job has no limb e
     const int gz = blockIdx.z;
     if (count && gz >= *count) return idle_exit();
     const IpGroup &gr = groups[gz];
@@ -249,8 +240,33 @@ k_inner_product_shared(const JobRef R, const IpGroup *__restrict__ groups, const
     const DevLevel &lv0 = lv_arr[gr.level];
     if (gr.n < 1 || e >= lv0.E) return idle_exit();
     const int EL = K + L, beta0 = lv0.beta;
+    if (threadIdx.x < kIpJobsMax) {
+        const int g = threadIdx.x;
+        int b = 0;
+        if (g < gr.n) {
+            const BatchItem it = job_item(R, gr.job[g]);
+            if (e < K + it.level) {
+                const DevLevel &lv = lv_arr[it.level];
+                b = lv.beta;
+                const u64 *U = it.ws + (size_t)lv.o_u * N, *d2 = it.ws + (size_t)lv.o_d2 * N;
+                for (int j = 0; j < BM; j++) {
+                    const int lo = lv.dig_lo[j], nj = lv.dig_n[j];
+                    const bool own = j < b && e >= K && e - K >= lo && e - K < lo + nj;
+                    s_row[g][j] = own ? d2 + (size_t)(e - K) * N : U + ((size_t)j * lv.E + e) * N;
+                }
+                u64 *KS = it.ws + (size_t)lv.o_ks * N;
+                s_ks[g][0] = KS + (size_t)e * N;
+                s_ks[g][1] = KS + ((size_t)lv.E + e) * N;
+            }
+        }
+        s_beta[g] = b;
+    }
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[e];
+    __syncthreads();
+    int njobs = 0;  // jobs sorted by level, highest first: those with limb e are a prefix
+#pragma unroll
+    for (int g = 0; g < kIpJobsMax; g++) njobs += s_beta[g] > 0 ? 1 : 0;
     griddep_wait();
     const u64 pol = l2_policy_stream();
     ulonglong2 kb[BM], ka[BM];
@@ -267,38 +283,37 @@ k_inner_product_shared(const JobRef R, const IpGroup *__restrict__ groups, const
             }
         }
     }
-    BatchItem it = job_item(R, gr.job[0]);
-    ulonglong2 u[BM];
-    ip_load_u<BM>(it, lv_arr[it.level], e, K, N, n, pol, u);
-    for (int g = 0;;) {
-        const DevLevel &lv = lv_arr[it.level];
-        // the next job of the group, if it has limb e
-        BatchItem nx = it;
-        bool more = g + 1 < gr.n;
-        if (more) {
-            nx = job_item(R, gr.job[g + 1]);
-            more = e < K + nx.level;
-        }
-        ulonglong2 v[BM];
-        if (more) ip_load_u<BM>(nx, lv_arr[nx.level], e, K, N, n, pol, v);
-        U128 bx = {0, 0}, by = {0, 0}, ax = {0, 0}, ay = {0, 0};
+    constexpr int CJ = BM >= 4 ? 2 : 4;
+    for (int c0 = 0; c0 < njobs; c0 += CJ) {
+        ulonglong2 u[CJ][BM];
 #pragma unroll
-        for (int j = 0; j < BM; j++) {
-            if (j < lv.beta) {
-                mac(bx, u[j].x, kb[j].x);
-                mac(by, u[j].y, kb[j].y);
-                mac(ax, u[j].x, ka[j].x);
-                mac(ay, u[j].y, ka[j].y);
+        for (int g = 0; g < CJ; g++) {
+            const int gg = c0 + g;
+            if (gg < njobs) {
+#pragma unroll
+                for (int j = 0; j < BM; j++)
+                    if (j < s_beta[gg]) u[g][j] = ld2_hint(s_row[gg][j] + n, pol);
             }
         }
-        u64 *KS = it.ws + (size_t)lv.o_ks * N;
-        st2(KS + (size_t)e * N + n, barrett128(bx, pr.q, pr.mu, pr.s), barrett128(by, pr.q, pr.mu, pr.s));
-        st2(KS + ((size_t)lv.E + e) * N + n, barrett128(ax, pr.q, pr.mu, pr.s), barrett128(ay, pr.q, pr.mu, pr.s));
-        if (!more) break;
-        it = nx;
 #pragma unroll
-        for (int j = 0; j < BM; j++) u[j] = v[j];
-        g++;
+        for (int g = 0; g < CJ; g++) {
+            const int gg = c0 + g;
+            if (gg < njobs) {
+                U128 bx = {0, 0}, by = {0, 0}, ax = {0, 0}, ay = {0, 0};
+                const int b = s_beta[gg];
+#pragma unroll
+                for (int j = 0; j < BM; j++) {
+                    if (j < b) {
+                        mac(bx, u[g][j].x, kb[j].x);
+                        mac(by, u[g][j].y, kb[j].y);
+                        mac(ax, u[g][j].x, ka[j].x);
+                        mac(ay, u[g][j].y, ka[j].y);
+                    }
+                }
+                st2(s_ks[gg][0] + n, barrett128(bx, pr.q, pr.mu, pr.s), barrett128(by, pr.q, pr.mu, pr.s));
+                st2(s_ks[gg][1] + n, barrett128(ax, pr.q, pr.mu, pr.s), barrett128(ay, pr.q, pr.mu, pr.s));
+            }
+        }
     }
 }
 

@@ -232,6 +232,71 @@ __device__ __forceinline__ size_t tile_gi(int e, int tile, int stride)
     return (size_t)tile * TE + e;
 }
 
+// The tensor product (Fig. 2 region 1 in RNS form: d0 = b1 b2, d1 = a1 b2 +
+// a2 b1, d2 = a1 a2 mod q_i) of the contiguous tile `tile` of limb i, as the
+// tile load of an inverse contiguous first pass.  The group's limb k carries
+// the job (job[k]) and ci[k] = i | comp << 16 | keep << 18: the product comp
+// (0: d0, 1: d1, 2: d2) goes to shared memory for the transform, and with
+// keep all three are also stored to the job's workspace (d0, d1 for the final
+// additions, d2 in the NTT domain for the inner product's own-digit rows).
+// Without keep only the product needed is formed (the rescale limbs of d0,
+// d1, whose d2 job stores them).
+template <int TE, int NT>
+__device__ __forceinline__ void tensor_tile(const NttArgs &P, const NttGroup &G, int k, int tile, const DevPrime &pr,
+                                            u64 *b)
+{
+    const int N = 1 << P.logN;
+    const BatchItem it = job_item(P.R, (int)G.job[k]);
+    const unsigned spec = G.ci[k];
+    const int li = (int)(spec & 0xffffu), comp = (int)((spec >> 16) & 3u);
+    const bool keep = ((spec >> 18) & 1u) != 0;
+    const int l = it.level;
+    const DevLevel &lv = P.levels[l];
+    const u64 *c1b = it.ct1 + (size_t)li * N, *c1a = it.ct1 + ((size_t)l + li) * N;
+    const u64 *c2b = it.ct2 + (size_t)li * N, *c2a = it.ct2 + ((size_t)l + li) * N;
+    u64 *w0 = it.ws + ((size_t)lv.o_d0 + li) * N, *w1 = it.ws + ((size_t)lv.o_d1 + li) * N;
+    u64 *w2 = it.ws + ((size_t)lv.o_d2 + li) * N;
+    const u64 pol = l2_policy_stream();  // the ciphertexts are read once
+    constexpr int PAIRS = TE / 2 / NT;
+    static_assert(PAIRS % 2 == 0, "pairs per thread");
+#pragma unroll 2
+    for (int s = 0; s < PAIRS; s++) {
+        const int e = 2 * (threadIdx.x + s * NT);
+        const size_t gi = (size_t)tile * TE + e;
+        u64 x, y;
+        if (keep) {
+            const ulonglong2 b1 = ld2_hint(c1b + gi, pol), a1 = ld2_hint(c1a + gi, pol), b2 = ld2_hint(c2b + gi, pol),
+                             a2 = ld2_hint(c2a + gi, pol);
+            U128 sx = mul_wide(a1.x, b2.x), sy = mul_wide(a1.y, b2.y);
+            mac(sx, a2.x, b1.x);
+            mac(sy, a2.y, b1.y);
+            const u64 d0x = mul_mod(b1.x, b2.x, pr.q, pr.mu, pr.s), d0y = mul_mod(b1.y, b2.y, pr.q, pr.mu, pr.s);
+            const u64 d1x = barrett128(sx, pr.q, pr.mu, pr.s), d1y = barrett128(sy, pr.q, pr.mu, pr.s);
+            const u64 d2x = mul_mod(a1.x, a2.x, pr.q, pr.mu, pr.s), d2y = mul_mod(a1.y, a2.y, pr.q, pr.mu, pr.s);
+            *reinterpret_cast<ulonglong2 *>(w0 + gi) = make_ulonglong2(d0x, d0y);
+            *reinterpret_cast<ulonglong2 *>(w1 + gi) = make_ulonglong2(d1x, d1y);
+            *reinterpret_cast<ulonglong2 *>(w2 + gi) = make_ulonglong2(d2x, d2y);
+            x = comp == 0 ? d0x : comp == 1 ? d1x : d2x;
+            y = comp == 0 ? d0y : comp == 1 ? d1y : d2y;
+        } else if (comp == 1) {
+            const ulonglong2 b1 = ld2_hint(c1b + gi, pol), a1 = ld2_hint(c1a + gi, pol), b2 = ld2_hint(c2b + gi, pol),
+                             a2 = ld2_hint(c2a + gi, pol);
+            U128 sx = mul_wide(a1.x, b2.x), sy = mul_wide(a1.y, b2.y);
+            mac(sx, a2.x, b1.x);
+            mac(sy, a2.y, b1.y);
+            x = barrett128(sx, pr.q, pr.mu, pr.s);
+            y = barrett128(sy, pr.q, pr.mu, pr.s);
+        } else {
+            const u64 *u1 = comp == 0 ? c1b : c1a, *u2 = comp == 0 ? c2b : c2a;
+            const ulonglong2 v1 = ld2_hint(u1 + gi, pol), v2 = ld2_hint(u2 + gi, pol);
+            x = mul_mod(v1.x, v2.x, pr.q, pr.mu, pr.s);
+            y = mul_mod(v1.y, v2.y, pr.q, pr.mu, pr.s);
+        }
+        b[padi(e)] = x;
+        b[padi(e + 1)] = y;
+    }
+}
+
 // One pass of LOGM stages over a group of limbs.  Rounds RA, RB, RC (RC may
 // be 0) in forward order; the inverse runs them in reverse.  FIRST: read
 // group.src (else group.dst); LAST: apply the output reduction / scaling.
@@ -246,11 +311,19 @@ __host__ __device__ constexpr int ntt_min_blocks(int nt, int logm, bool inv)
     return logm >= 12 ? 0 : nt >= 256 ? 5 : inv ? 0 : 6;
 }
 
-template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE, bool COMBINE = false>
+// FUSE: kFuseNone; kFuseCombine, the final combine in the store loop of the
+// forward contiguous last pass (ModDown + rescale limbs); kFuseTensor, the
+// tensor product computed in place of the inverse contiguous first pass's
+// tile load (d2 limbs and the rescale limbs of d0, d1).
+enum { kFuseNone = 0, kFuseCombine = 1, kFuseTensor = 2 };
+
+template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE, int FUSE = kFuseNone>
 __global__ void __launch_bounds__(TE >> cmax(RA, cmax(RB, RC)), ntt_min_blocks(TE >> cmax(RA, cmax(RB, RC)), LOGM, INV))
 k_ntt_pass(const NttArgs P)
 {
+    constexpr bool COMBINE = FUSE == kFuseCombine, TENSOR = FUSE == kFuseTensor;
     static_assert(!COMBINE || (LAST && !INV && !STRIDED), "the combine follows a forward contiguous last pass");
+    static_assert(!TENSOR || (FIRST && INV && !STRIDED), "the tensor product feeds an inverse contiguous first pass");
     constexpr int NT = TE >> cmax(RA, cmax(RB, RC));
     constexpr int RL = RC ? RC : RB;  // last round in forward order
     constexpr int L0 = LOGM - RL;     // its first stage
@@ -275,9 +348,13 @@ k_ntt_pass(const NttArgs P)
 
     // data tile of limb i of the group -> shared memory (8-byte async copies)
     auto load_tile = [&](int i, u64 *b) {
-        const u64 *src = FIRST ? P.src + (size_t)G.src[i] * N : P.dst + (size_t)G.dst[i] * N;
-        for (int e = threadIdx.x; e < TE; e += NT)
-            __pipeline_memcpy_async(&b[padi(e)], src + tile_gi<LOGM, TE, STRIDED>(e, tile, stride), 8);
+        if constexpr (TENSOR) {
+            tensor_tile<TE, NT>(P, G, i, tile, pr, b);
+        } else {
+            const u64 *src = FIRST ? P.src + (size_t)G.src[i] * N : P.dst + (size_t)G.dst[i] * N;
+            for (int e = threadIdx.x; e < TE; e += NT)
+                __pipeline_memcpy_async(&b[padi(e)], src + tile_gi<LOGM, TE, STRIDED>(e, tile, stride), 8);
+        }
     };
     // staged twiddles of this tile -> shared memory (16-byte async copies)
     const ulonglong2 *twg = INV ? pr.iw : pr.w;
@@ -416,12 +493,12 @@ k_ntt_pass(const NttArgs P)
 }
 
 // ngroups == 0 only sets the kernel's shared-memory limit (no launch).
-template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE, bool COMBINE = false>
+template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE, int FUSE = kFuseNone>
 cudaError_t run_pass(const NttArgs &a, int ngroups, cudaStream_t st)
 {
     constexpr int NT = TE >> cmax(RA, cmax(RB, RC));
     constexpr size_t smem = Geometry<LOGM, TE, STRIDED, (RC ? RC : RB)>::SMEM;
-    auto kern = k_ntt_pass<LOGM, RA, RB, RC, STRIDED, INV, FIRST, LAST, TE, COMBINE>;
+    auto kern = k_ntt_pass<LOGM, RA, RB, RC, STRIDED, INV, FIRST, LAST, TE, FUSE>;
     static bool configured = false;  // once per instantiation
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -517,11 +594,11 @@ cudaError_t combine_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t s
 {
     constexpr int TE = 2048;
     a.tiles = (1 << LOGN) / TE;
-    if (ngroups == 0) return run_pass<P::S2, P::A2, P::B2, P::C2, false, false, false, true, TE, true>(a, 0, st);
+    if (ngroups == 0) return run_pass<P::S2, P::A2, P::B2, P::C2, false, false, false, true, TE, kFuseCombine>(a, 0, st);
     cudaError_t e = run_pass<P::S1, P::A1, P::B1, P::C1, true, false, true, false, TE>(a, ngroups, st);
     if (e != cudaSuccess) return e;
     prof_mark(c, st, tag, ".fwd_pass1");
-    e = run_pass<P::S2, P::A2, P::B2, P::C2, false, false, false, true, TE, true>(a, ngroups, st);
+    e = run_pass<P::S2, P::A2, P::B2, P::C2, false, false, false, true, TE, kFuseCombine>(a, ngroups, st);
     prof_mark(c, st, tag, ".fwd_pass2_combine");
     return e;
 }
@@ -533,7 +610,62 @@ cudaError_t combine_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st
               : combine_plan<LOGN, Plan<LOGN>>(c, a, ngroups, st, tag);
 }
 
+// Inverse transform whose first pass forms its input with the tensor product.
+template <int LOGN, class P>
+cudaError_t tensor_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag)
+{
+    constexpr int TE = 2048;
+    a.tiles = (1 << LOGN) / TE;
+    if (ngroups == 0) return run_pass<P::S2, P::A2, P::B2, P::C2, false, true, true, false, TE, kFuseTensor>(a, 0, st);
+    cudaError_t e = run_pass<P::S2, P::A2, P::B2, P::C2, false, true, true, false, TE, kFuseTensor>(a, ngroups, st);
+    if (e != cudaSuccess) return e;
+    prof_mark(c, st, tag, ".tensor_inv_pass1");
+    e = run_pass<P::S1, P::A1, P::B1, P::C1, true, true, false, true, TE>(a, ngroups, st);
+    prof_mark(c, st, tag, ".inv_pass2");
+    return e;
+}
+
+template <int LOGN>
+cudaError_t tensor_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, bool r8)
+{
+    return r8 ? tensor_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, st, tag)
+              : tensor_plan<LOGN, Plan<LOGN>>(c, a, ngroups, st, tag);
+}
+
 }  // namespace
+
+cudaError_t launch_ntt_tensor(const he_ctx *c, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
+                              cudaStream_t st, const char *tag, const int *dev_count, bool r8)
+{
+    if (ngroups < 0) return cudaSuccess;  // ngroups == 0: configure the kernels only
+    NttArgs a;
+    memset(&a, 0, sizeof(a));
+    a.src = base;
+    a.dst = base;
+    a.groups = groups;
+    a.primes = c->d_primes;
+    a.logN = c->logN;
+    a.ts = c->logN - ntt_direct_stages(c->logN);
+    a.tiles = 1;
+    a.count = dev_count;
+    a.pdl = c->pdl;
+    a.R = R;
+    a.levels = c->d_levels;
+    a.pinv = c->d_pinv;
+    switch (c->logN) {
+    case 12: {
+        cudaError_t e = run_pass<12, 4, 4, 4, false, true, true, true, 4096, kFuseTensor>(a, ngroups, st);
+        if (ngroups) prof_mark(c, st, tag, ".tensor_inv");
+        return e;
+    }
+    case 13: return tensor_any<13>(c, a, ngroups, st, tag, r8);
+    case 14: return tensor_any<14>(c, a, ngroups, st, tag, r8);
+    case 15: return tensor_any<15>(c, a, ngroups, st, tag, r8);
+    case 16: return tensor_any<16>(c, a, ngroups, st, tag, r8);
+    case 17: return tensor_any<17>(c, a, ngroups, st, tag, r8);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_ntt_combine(const he_ctx *c, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
                                cudaStream_t st, const char *tag, const int *dev_count, bool r8)
@@ -554,7 +686,7 @@ cudaError_t launch_ntt_combine(const he_ctx *c, u64 *base, const NttGroup *group
     a.pinv = c->d_pinv;
     switch (c->logN) {
     case 12: {
-        cudaError_t e = run_pass<12, 4, 4, 4, false, false, true, true, 4096, true>(a, ngroups, st);
+        cudaError_t e = run_pass<12, 4, 4, 4, false, false, true, true, 4096, kFuseCombine>(a, ngroups, st);
         if (ngroups) prof_mark(c, st, tag, ".fwd_combine");
         return e;
     }
@@ -630,6 +762,8 @@ cudaError_t configure_ntt(const he_ctx *c)
         cudaError_t e = launch_ntt2(c, nullptr, nullptr, nullptr, 0, false, nullptr, nullptr, nullptr, r8 != 0);
         if (e != cudaSuccess) return e;
         e = launch_ntt_combine(c, nullptr, nullptr, 0, R, nullptr, nullptr, nullptr, r8 != 0);
+        if (e != cudaSuccess) return e;
+        e = launch_ntt_tensor(c, nullptr, nullptr, 0, R, nullptr, nullptr, nullptr, r8 != 0);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -269,10 +269,10 @@ def test_batch_matches_single_and_oracle(g):
         assert np.array_equal(host(g, jobs[k][2]), want)
 
 
-@pytest.mark.parametrize("levels,ip_jobs", [
-    ([3, 5], 8), ([5, 3], 4), ([3, 5, 2, 4, 5, 3, 2, 8, 9], 4),
-    ([24, 4, 9, 17, 2, 13, 24, 23, 16, 8, 3], 8), ([24, 9, 17, 2], 1)])
-def test_batch_shared_key_words_bit_exact(g, levels, ip_jobs):
+@pytest.mark.parametrize("levels,ip_jobs,fuse", [
+    ([3, 5], 8, 1), ([5, 3], 4, 0), ([3, 5, 2, 4, 5, 3, 2, 8, 9], 4, 1),
+    ([24, 4, 9, 17, 2, 13, 24, 23, 16, 8, 3], 8, 1), ([24, 9, 17, 2], 1, 0), ([24, 9, 17, 2], 1, 1)])
+def test_batch_shared_key_words_bit_exact(g, levels, ip_jobs, fuse):
     """Batches whose inner product shares each CTA's evaluation-key words among
     up to ip_jobs jobs of similar level (groups cut from the jobs sorted by
     level, ragged last group, jobs of a group at different levels and digit
@@ -293,7 +293,7 @@ def test_batch_shared_key_words_bit_exact(g, levels, ip_jobs):
         singles.append(gpu_mul(g, ctx, c1, c2, evk_t, lv, fused=True))
     ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
     try:
-        g.he_set_shape(ctx, 4, 8, 1, 0, ip_jobs)
+        g.he_set_shape(ctx, 4, 8, 1, 0, ip_jobs, fuse)
         for rnd in range(2):  # twice on the same workspace
             for j in jobs:
                 j[2].fill_(-1)
@@ -632,12 +632,14 @@ def test_every_shape_is_bit_identical_n16(g):
     c2 = np.ascontiguousarray(np.stack([ct2[0, :level], ct2[1, :level]]))
     want = oracle.rescale(op, oracle.he_mul(op, c1, c2, evk, level), level)
     try:
-        for shape in ((1, 4, 1, 15), (2, 16, 0, 5), (3, 8, 1, 10), (4, 16, 0, 0), (4, 8, 1, 0), (1, 8, 1, 3)):
+        for shape in ((1, 4, 1, 15), (2, 16, 0, 5), (3, 8, 1, 10), (4, 16, 0, 0), (4, 8, 1, 0), (1, 8, 1, 3),
+                      (1, 8, 1, 8, 8, 0), (3, 4, 0, 1, 8, 0), (2, 8, 1, 15, 8, 0)):
             g.he_set_shape(ctx, *shape)
             assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want), shape
-        g.he_set_shape(ctx, 2, 8, 1, 15)  # the plain ModDown path with the radix-8 plans
         want_plain = oracle.he_mul(op, c1, c2, evk, level)
-        assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=False), want_plain)
+        for fz in (1, 0):  # the plain ModDown path with the radix-8 plans, tensor fused or not
+            g.he_set_shape(ctx, 2, 8, 1, 15, 8, fz)
+            assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=False), want_plain), fz
     finally:
         g.he_set_shape(ctx, 4, 8, 1)
 
@@ -673,10 +675,11 @@ def test_autotune_batch_keeps_results(g):
     ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
     try:
         best, tried = g.he_autotune(ctx, jobs, evk_t, ws, reps=2)
-        assert len(tried) == 41 and all(t[5] > 0 for t in tried)
-        assert best[:5] == g.he_get_shape(ctx) and best[5] == min(t[5] for t in tried)
+        assert len(tried) == 42 and all(t[6] > 0 for t in tried)
+        assert best[:6] == g.he_get_shape(ctx) and best[6] == min(t[6] for t in tried)
         assert sorted(t[3] for t in tried[24:39]) == list(range(1, 16))
-        assert sorted(t[4] for t in tried[39:]) == [1, 4]  # the other two ip_jobs values
+        assert sorted(t[4] for t in tried[39:41]) == [1, 4]  # the other two ip_jobs values
+        assert tried[41][5] == 0  # the tensor product on its own
         for j in jobs:
             j[2].zero_()
         g.he_mul_batch(ctx, jobs, evk_t, ws)
