@@ -261,10 +261,13 @@ int he_mul_batch(he_ctx *ctx, int count, const he_job *jobs, const uint64_t *evk
                  size_t ws_bytes, void *stream);
 
 /* The batched path captured once in a CUDA graph for up to max_jobs jobs:
- * every launch is sized for max_jobs jobs at level L and reads the job table
- * and NTT job lists (and their counts) that the graph's first node copies from
- * a pinned host buffer, so he_batch_graph_launch with any batch of at most
- * max_jobs jobs (levels 2..L) is one graph launch.  ws (device, at least
+ * every launch is sized for max_jobs jobs at level L (the NTT launches for
+ * the most limb groups they can form at the limb-group cap in effect at
+ * creation; launches group at that cap or the context's current one,
+ * whichever is larger) and reads the job table and NTT job lists (and their
+ * counts) that the graph's first node copies from a pinned host buffer, so
+ * he_batch_graph_launch with any batch of at most max_jobs jobs (levels
+ * 2..L) is one graph launch.  ws (device, at least
  * he_batch_graph_workspace_bytes(max_jobs)) and evk_dev are bound at
  * creation and must outlive the graph.  Creation captures `stream` (no work
  * runs).  A launch waits on the host for the previous launch of the same graph

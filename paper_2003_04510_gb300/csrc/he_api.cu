@@ -858,7 +858,9 @@ int he_mul_rescale_host_stream(he_ctx *c, int count, const uint64_t *const *ct1,
 
 // ---- batch graphs ----------------------------------------------------------
 // The batched pipeline captured once in a CUDA graph for up to max_jobs jobs:
-// every grid is sized for max_jobs jobs at level L, the job table and NTT
+// the per-job grids are sized for max_jobs jobs at level L, the NTT grids for
+// the most groups max_jobs jobs can form at the limb-group cap in effect at
+// capture (at least that cap is used at every launch), the job table and NTT
 // group lists (and their counts) live at the head of the workspace and are
 // refreshed from a pinned host copy by the graph's first node, so a replay
 // with a different batch (count, levels, operands) is one graph launch.
@@ -870,7 +872,9 @@ struct he_batch_graph {
     char *ws = nullptr;
     size_t hdr = 0, slot_limbs = 0;
     size_t items_bytes = 0, counts_off = 0, lists_off[4] = {0, 0, 0, 0}, ipg_off = 0;
-    int list_max[4] = {0, 0, 0, 0};
+    size_t hdr_copy = 0;  // header bytes the graph's first node copies (up to the last list's end)
+    int list_max[4] = {0, 0, 0, 0};  // groups each NTT list may hold (and its launch's grid) at `cap`
+    int cap = 1;                     // limb-group cap at capture
     int ip_jobs = 0;  // jobs per inner-product group captured (0: one job per CTA)
     unsigned char *pinned = nullptr;
     cudaGraph_t graph = nullptr;
@@ -881,27 +885,45 @@ struct he_batch_graph {
 
 namespace {
 
-void graph_layout(const he_ctx *c, int max_jobs, he_batch_graph *g)
+// Most groups NTT list t (0..3: the four sites) can hold for max_jobs jobs
+// at limb-group cap `cap`: per prime, the most limbs one job of any level has
+// in that list, times max_jobs, in groups of cap (group_jobs never mixes
+// primes).
+int graph_list_bound(const he_ctx *c, int max_jobs, int t, int cap)
 {
-    int mx[4] = {0, 0, 0, 0};
+    std::vector<int> most(c->E, 0), cnt(c->E, 0);
     for (int l = 2; l <= c->L; l++) {
         const HostLevel &H = c->host_levels[l];
-        mx[0] = std::max(mx[0], (int)H.intt1f.size());
-        mx[1] = std::max(mx[1], (int)H.ntt_up.size());
-        mx[2] = std::max(mx[2], (int)H.intt2f.size());
-        mx[3] = std::max(mx[3], (int)H.ntt_z.size());
+        const std::vector<NttJob> *lists[4] = {&H.intt1f, &H.ntt_up, &H.intt2f, &H.ntt_z};
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (const NttJob &j : *lists[t]) cnt[j.prime]++;
+        for (int p = 0; p < c->E; p++) most[p] = std::max(most[p], cnt[p]);
     }
+    long long groups = 0;
+    for (int p = 0; p < c->E; p++) groups += ((long long)most[p] * max_jobs + cap - 1) / cap;
+    return (int)groups;
+}
+
+// Header layout: [items | counts | inner-product groups | four NTT lists at
+// the capture cap's bounds | room up to the bounds at cap 1], then the jobs'
+// workspaces; the workspace size does not depend on the cap.
+void graph_layout(const he_ctx *c, int max_jobs, he_batch_graph *g, int cap)
+{
+    g->cap = cap;
     g->items_bytes = round_up(sizeof(BatchItem) * max_jobs);
     g->counts_off = g->items_bytes;
     size_t off = g->counts_off + 256;
-    for (int t = 0; t < 4; t++) {
-        g->list_max[t] = mx[t] * max_jobs;  // one group per limb at worst
-        g->lists_off[t] = off;
-        off += round_up(sizeof(NttGroup) * (size_t)g->list_max[t]);
-    }
     g->ipg_off = off;
     off += round_up(sizeof(IpGroup) * (size_t)max_jobs);
-    g->hdr = off;
+    size_t room = off;
+    for (int t = 0; t < 4; t++) {
+        g->list_max[t] = graph_list_bound(c, max_jobs, t, cap);
+        g->lists_off[t] = off;
+        off += round_up(sizeof(NttGroup) * (size_t)g->list_max[t]);
+        room += round_up(sizeof(NttGroup) * (size_t)graph_list_bound(c, max_jobs, t, 1));
+    }
+    g->hdr_copy = off;
+    g->hdr = std::max(off, room);
     size_t slot = 0;
     for (int l = 2; l <= c->L; l++) slot = std::max(slot, c->host_levels[l].ws.total);
     g->slot_limbs = slot;
@@ -915,7 +937,7 @@ size_t he_batch_graph_workspace_bytes(const he_ctx *c, int max_jobs)
 {
     if (!c || max_jobs < 1 || max_jobs > 65535 || c->L < 2) return 0;
     he_batch_graph g;
-    graph_layout(c, max_jobs, &g);
+    graph_layout(c, max_jobs, &g, 1);
     return g.hdr + (size_t)max_jobs * g.slot_limbs * c->N * sizeof(u64);
 }
 
@@ -931,7 +953,7 @@ int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws
     g->max_jobs = max_jobs;
     g->evk = evk;
     g->ws = (char *)ws;
-    graph_layout(c, max_jobs, g);
+    graph_layout(c, max_jobs, g, c->group_cap);
     // capture runs nothing, so it uses a private stream: capture is not
     // permitted on the legacy default stream the caller may be using
     (void)stream;
@@ -977,7 +999,7 @@ int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws
         g_last_cuda_error = cudaGetErrorName(ce);
         return fail(HE_ECUDA);
     }
-    ce = cudaMemcpyAsync(g->ws, g->pinned, g->hdr, cudaMemcpyHostToDevice, st);
+    ce = cudaMemcpyAsync(g->ws, g->pinned, g->hdr_copy, cudaMemcpyHostToDevice, st);
     if (ce != cudaSuccess) {
         g_last_cuda_error = cudaGetErrorName(ce);
         rc = HE_ECUDA;
@@ -1034,8 +1056,8 @@ int he_batch_graph_launch(he_batch_graph *g, int count, const he_job *jobs, void
     }
     int *counts = (int *)(g->pinned + g->counts_off);
     for (int t = 0; t < 4; t++) {
-        std::vector<NttGroup> grp = group_jobs(lists[t], c->group_cap);
-        if ((int)grp.size() > g->list_max[t]) return HE_EINVAL;
+        std::vector<NttGroup> grp = group_jobs(lists[t], std::max(c->group_cap, g->cap));
+        if ((int)grp.size() > g->list_max[t]) return HE_EINVAL;  // cannot happen: bounded at capture
         memcpy(g->pinned + g->lists_off[t], grp.data(), sizeof(NttGroup) * grp.size());
         counts[t] = (int)grp.size();
     }

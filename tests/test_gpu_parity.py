@@ -309,7 +309,7 @@ def test_batch_shared_key_words_bit_exact(g, levels, ip_jobs, fuse):
     assert np.array_equal(host(g, jobs[k][2]), want)
 
 
-@pytest.mark.parametrize("capture_cap,replay_cap", [(4, 4), (1, 3)])
+@pytest.mark.parametrize("capture_cap,replay_cap", [(4, 4), (1, 3), (4, 1)])
 def test_batch_graph_replays_match_single(g, capture_cap, replay_cap):
     """One captured graph, replayed with two different batches (sizes, levels,
     operands): every result equals he_mul_rescale on the job alone.  Captured
