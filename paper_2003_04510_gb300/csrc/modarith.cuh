@@ -83,6 +83,27 @@ __device__ __forceinline__ u64 shoup_approx_nq(u64 x, u64 w, u64 wp, u64 nq)
 
 __device__ __forceinline__ u64 shoup(u64 x, u64 w, u64 wp, u64 q) { return csub(shoup_lazy(x, w, wp, q), q); }
 
+// x w mod q, canonical: the modified Shoup product (remainder in [0, 4q))
+// and two conditional subtractions.  Fewer wide multiplies than shoup()
+// (which forms the exact Shoup quotient); nq = 2^64 - q, q < 2^62.
+__device__ __forceinline__ u64 shoup_canon(u64 x, u64 w, u64 wp, u64 q, u64 nq)
+{
+    return csub(csub(shoup_approx_nq(x, w, wp, nq), 2 * q), q);
+}
+
+// x mod q for x below 2^64 and below a small multiple of q (at most 2^32 q),
+// q > 2^32, r64 = floor(2^64 / q) (then below 2^32): the quotient estimate
+// floor((x >> 32) r64 / 2^32) is floor(x / q) minus 0, 1 or 2 (the dropped
+// low word of x is below q, and (x >> 32)(2^64 / q - r64) / 2^32 < 1), so
+// the remainder lies in [0, 3q) and two conditional subtractions finish.
+// One 32 x 32 high multiply and a 32 x 64 product instead of a Shoup product.
+__device__ __forceinline__ u64 reduce_small(u64 x, u64 q, u64 r64)
+{
+    const uint32_t qh = mul_hi32((uint32_t)(x >> 32), (uint32_t)r64);
+    const u64 r = x - (u64)qh * q;
+    return csub(csub(r, 2 * q), q);
+}
+
 // The NTT's butterflies (ntt.cu; the throughput probe runs the same ones).
 // Forward (Cooley-Tukey, Algo 4) with no correction step: the modified
 // Shoup product t lies in [0, 4q), so each stage adds at most 4q to the

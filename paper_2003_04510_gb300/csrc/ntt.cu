@@ -223,15 +223,6 @@ __device__ __forceinline__ void prefetch_direct_tw(const ulonglong2 *twg, int ti
     }
 }
 
-// global index of tile element e
-template <int LOGM, int TE, bool STRIDED>
-__device__ __forceinline__ size_t tile_gi(int e, int tile, int stride)
-{
-    constexpr int NG = TE / (1 << LOGM);
-    if (STRIDED) return (size_t)(e / NG) * stride + (size_t)tile * NG + (e % NG);
-    return (size_t)tile * TE + e;
-}
-
 // The tensor product (Fig. 2 region 1 in RNS form: d0 = b1 b2, d1 = a1 b2 +
 // a2 b1, d2 = a1 a2 mod q_i) of the contiguous tile `tile` of limb i, as the
 // tile load of an inverse contiguous first pass.  The group's limb k carries
@@ -245,24 +236,26 @@ template <int TE, int NT>
 __device__ __forceinline__ void tensor_tile(const NttArgs &P, const NttGroup &G, int k, int tile, const DevPrime &pr,
                                             u64 *b)
 {
-    const int N = 1 << P.logN;
+    const int lg = P.logN;
     const BatchItem it = job_item(P.R, (int)G.job[k]);
     const unsigned spec = G.ci[k];
     const int li = (int)(spec & 0xffffu), comp = (int)((spec >> 16) & 3u);
     const bool keep = ((spec >> 18) & 1u) != 0;
     const int l = it.level;
     const DevLevel &lv = P.levels[l];
-    const u64 *c1b = it.ct1 + (size_t)li * N, *c1a = it.ct1 + ((size_t)l + li) * N;
-    const u64 *c2b = it.ct2 + (size_t)li * N, *c2a = it.ct2 + ((size_t)l + li) * N;
-    u64 *w0 = it.ws + ((size_t)lv.o_d0 + li) * N, *w1 = it.ws + ((size_t)lv.o_d1 + li) * N;
-    u64 *w2 = it.ws + ((size_t)lv.o_d2 + li) * N;
+    const size_t t0 = (size_t)tile * TE;
+    const u64 *c1b = it.ct1 + ((size_t)li << lg) + t0, *c1a = it.ct1 + (((size_t)l + li) << lg) + t0;
+    const u64 *c2b = it.ct2 + ((size_t)li << lg) + t0, *c2a = it.ct2 + (((size_t)l + li) << lg) + t0;
+    u64 *w0 = it.ws + (((size_t)lv.o_d0 + li) << lg) + t0, *w1 = it.ws + (((size_t)lv.o_d1 + li) << lg) + t0;
+    u64 *w2 = it.ws + (((size_t)lv.o_d2 + li) << lg) + t0;
     const u64 pol = l2_policy_stream();  // the ciphertexts are read once
     constexpr int PAIRS = TE / 2 / NT;
     static_assert(PAIRS % 2 == 0, "pairs per thread");
-#pragma unroll 2
+    constexpr int UNROLL = NT >= 256 ? 1 : 2;  // registers: the 256-thread tiles run at 64
+#pragma unroll UNROLL
     for (int s = 0; s < PAIRS; s++) {
         const int e = 2 * (threadIdx.x + s * NT);
-        const size_t gi = (size_t)tile * TE + e;
+        const int gi = e;
         u64 x, y;
         if (keep) {
             const ulonglong2 b1 = ld2_hint(c1b + gi, pol), a1 = ld2_hint(c1a + gi, pol), b2 = ld2_hint(c2b + gi, pol),
@@ -301,14 +294,16 @@ __device__ __forceinline__ void tensor_tile(const NttArgs &P, const NttGroup &G,
 // be 0) in forward order; the inverse runs them in reverse.  FIRST: read
 // group.src (else group.dst); LAST: apply the output reduction / scaling.
 // Resident CTAs per SM the register allocation is bounded for (0: no bound):
-// 256-thread tiles (radix-8 rounds) five (51 registers), forward 128-thread
+// 256-thread tiles (radix-8 rounds) five (51 registers; inverse ones four, 64
+// registers, as their first pass holds the direct round's twiddles from the
+// start and the tensor-fused variant its products), forward 128-thread
 // tiles six (85 registers, what their shared memory allows; measured faster
 // than the compiler's own choice), inverse 128-thread tiles unbounded (their
 // first pass holds the direct round's fifteen twiddles from the start and
 // spills under a bound).
 __host__ __device__ constexpr int ntt_min_blocks(int nt, int logm, bool inv)
 {
-    return logm >= 12 ? 0 : nt >= 256 ? 5 : inv ? 0 : 6;
+    return logm >= 12 ? 0 : nt >= 256 ? (inv ? 4 : 5) : inv ? 0 : 6;
 }
 
 // FUSE: kFuseNone; kFuseCombine, the final combine in the store loop of the
@@ -342,18 +337,36 @@ k_ntt_pass(const NttArgs P)
     const int nl = (int)G.nl;
     const DevPrime pr = P.primes[G.prime];
     const u64 nq = 0ull - pr.q;
-    const int N = 1 << P.logN;
-    const int stride = N >> LOGM;
     const int s0 = STRIDED ? 0 : P.logN - LOGM;
+
+    // Thread walks over the tile: element threadIdx.x + k NT sits at global
+    // index g1 + k gs1 and shared word padi(threadIdx.x) + k (NT + NT / 16)
+    // (NT is a multiple of 16 and of NG); the pair 2 (threadIdx.x + k NT),
+    // +1 at g2 + k gs2 and padi(2 threadIdx.x) + k (2 NT + NT / 8).  Index
+    // arithmetic by shifts and additions only, which leaves the wide-multiply
+    // pipe to the butterflies.
+    const int lsh = P.logN - LOGM;  // log2 of the strided pass's row stride
+    const size_t g1 = STRIDED ? (((size_t)(threadIdx.x / NG) << lsh) + (size_t)tile * NG + threadIdx.x % NG)
+                              : (size_t)tile * TE + threadIdx.x;
+    const size_t gs1 = STRIDED ? ((size_t)(NT / NG) << lsh) : (size_t)NT;
+    const size_t g2 = STRIDED ? (((size_t)(2 * threadIdx.x / NG) << lsh) + (size_t)tile * NG + 2 * threadIdx.x % NG)
+                              : (size_t)tile * TE + 2 * threadIdx.x;
+    const size_t gs2 = STRIDED ? ((size_t)(2 * NT / NG) << lsh) : (size_t)(2 * NT);
+    static_assert(NT % 16 == 0 && NT % NG == 0 && (2 * NT) % NG == 0, "tile walk");
 
     // data tile of limb i of the group -> shared memory (8-byte async copies)
     auto load_tile = [&](int i, u64 *b) {
         if constexpr (TENSOR) {
             tensor_tile<TE, NT>(P, G, i, tile, pr, b);
         } else {
-            const u64 *src = FIRST ? P.src + (size_t)G.src[i] * N : P.dst + (size_t)G.dst[i] * N;
-            for (int e = threadIdx.x; e < TE; e += NT)
-                __pipeline_memcpy_async(&b[padi(e)], src + tile_gi<LOGM, TE, STRIDED>(e, tile, stride), 8);
+            const u64 *src = (FIRST ? P.src + ((size_t)G.src[i] << P.logN) : P.dst + ((size_t)G.dst[i] << P.logN)) + g1;
+            u64 *d = b + padi(threadIdx.x);
+#pragma unroll
+            for (int k = 0; k < TE / NT; k++) {
+                __pipeline_memcpy_async(d, src, 8);
+                d += NT + NT / 16;
+                src += gs1;
+            }
         }
     };
     // staged twiddles of this tile -> shared memory (16-byte async copies)
@@ -404,7 +417,9 @@ k_ntt_pass(const NttArgs P)
     for (int i = 0; i < nl; i++) {
         u64 *sm = buf + (i & 1) * Gm::DATA;
         TwReg<RL, SPT> TR;
-        if (DIRECT && INV) load_direct(TR);  // the inverse starts with the direct round
+        // the inverse starts with the direct round (its twiddles are loaded
+        // after the next limb's tensor product, which needs the registers)
+        if (DIRECT && INV && !TENSOR) load_direct(TR);
         if (i + 1 < nl) {
             load_tile(i + 1, buf + ((i + 1) & 1) * Gm::DATA);
             __pipeline_commit();
@@ -412,6 +427,7 @@ k_ntt_pass(const NttArgs P)
         } else {
             __pipeline_wait_prior(0);
         }
+        if (DIRECT && INV && TENSOR) load_direct(TR);
         __syncthreads();
         if (!INV) {
             ntt_round<LOGM, TE, RA, STRIDED, false, NT, false>(sm, tw, TR, 0, nq, pr.q4);
@@ -444,8 +460,9 @@ k_ntt_pass(const NttArgs P)
             // (0, (4 + 4 log N) q), below 2^64, and one Shoup product by
             // q_{l-1}^-1 reduces it
             const u64 Cz = pr.q * (u64)(1 + 4 * P.logN);
-            u64 *o = it.out + ((size_t)hh * (it.level - 1) + ci) * N;
-            const u64 *dd = P.dst + (size_t)G.cd[i] * N, *kk = P.dst + (size_t)G.cks[i] * N;
+            u64 *o = it.out + ((((size_t)hh * (it.level - 1) + ci)) << P.logN) + g2;
+            const u64 *dd = P.dst + ((size_t)G.cd[i] << P.logN) + g2, *kk = P.dst + ((size_t)G.cks[i] << P.logN) + g2;
+            const u64 *sp = sm + padi(2 * threadIdx.x);
             // four pairs per step: their d and KS loads are all in flight before the first product
             constexpr int PAIRS = TE / 2 / NT, B4 = PAIRS >= 4 ? 4 : PAIRS;
             static_assert(PAIRS % B4 == 0, "pairs per thread");
@@ -453,40 +470,47 @@ k_ntt_pass(const NttArgs P)
                 ulonglong2 dv[B4], kv[B4];
 #pragma unroll
                 for (int k = 0; k < B4; k++) {
-                    const size_t gi = tile_gi<LOGM, TE, STRIDED>(2 * (threadIdx.x + (b0 + k) * NT), tile, stride);
-                    dv[k] = __ldg(reinterpret_cast<const ulonglong2 *>(dd + gi));
-                    kv[k] = __ldg(reinterpret_cast<const ulonglong2 *>(kk + gi));
+                    dv[k] = __ldg(reinterpret_cast<const ulonglong2 *>(dd + (b0 + k) * gs2));
+                    kv[k] = __ldg(reinterpret_cast<const ulonglong2 *>(kk + (b0 + k) * gs2));
                 }
 #pragma unroll
                 for (int k = 0; k < B4; k++) {
-                    const int e = 2 * (threadIdx.x + (b0 + k) * NT);
-                    const size_t gi = tile_gi<LOGM, TE, STRIDED>(e, tile, stride);
-                    const u64 x = dv[k].x + shoup_lazy(kv[k].x, pv.x, pv.y, pr.q) + Cz - sm[padi(e)];
-                    const u64 y = dv[k].y + shoup_lazy(kv[k].y, pv.x, pv.y, pr.q) + Cz - sm[padi(e + 1)];
-                    *reinterpret_cast<ulonglong2 *>(o + gi) =
-                        make_ulonglong2(shoup(x, qv.x, qv.y, pr.q), shoup(y, qv.x, qv.y, pr.q));
+                    // KS P^-1 lazily in [0, 4q): x < (6 + 4 log N) q < 2^64
+                    const u64 *z = sp + (b0 + k) * (2 * NT + NT / 8);
+                    const u64 x = dv[k].x + shoup_approx_nq(kv[k].x, pv.x, pv.y, nq) + Cz - z[0];
+                    const u64 y = dv[k].y + shoup_approx_nq(kv[k].y, pv.x, pv.y, nq) + Cz - z[1];
+                    *reinterpret_cast<ulonglong2 *>(o + (b0 + k) * gs2) =
+                        make_ulonglong2(shoup_canon(x, qv.x, qv.y, pr.q, nq), shoup_canon(y, qv.x, qv.y, pr.q, nq));
                 }
             }
             __syncthreads();  // the next prefetch reuses this buffer
             continue;
         }
         // shared memory -> HBM, 16-byte stores, output reduction on the last pass
-        u64 *dst = P.dst + (size_t)G.dst[i] * N;
+        u64 *dst = P.dst + ((size_t)G.dst[i] << P.logN) + g2;
         const u64 sc = G.scale[i], scs = G.scale_sh[i];
-        for (int h = threadIdx.x; h < TE / 2; h += NT) {
-            const int e = 2 * h;
-            u64 x = sm[padi(e)], y = sm[padi(e + 1)];
+        const bool small_red = (pr.r64 >> 32) == 0;  // q > 2^32: reduce_small applies
+        const u64 *sp = sm + padi(2 * threadIdx.x);
+#pragma unroll
+        for (int k = 0; k < TE / 2 / NT; k++) {
+            u64 x = sp[0], y = sp[1];
             if (LAST) {
-                if (!INV) {  // x < (1 + 4 log N) q: one Shoup product by 1 reduces it
-                    x = shoup(x, 1, pr.r64, pr.q);
-                    y = shoup(y, 1, pr.r64, pr.q);
+                if (!INV) {  // x < (1 + 4 log N) q
+                    if (small_red) {
+                        x = reduce_small(x, pr.q, pr.r64);
+                        y = reduce_small(y, pr.q, pr.r64);
+                    } else {
+                        x = shoup(x, 1, pr.r64, pr.q);
+                        y = shoup(y, 1, pr.r64, pr.q);
+                    }
                 } else {
-                    x = shoup(x, sc, scs, pr.q);
-                    y = shoup(y, sc, scs, pr.q);
+                    x = shoup_canon(x, sc, scs, pr.q, nq);
+                    y = shoup_canon(y, sc, scs, pr.q, nq);
                 }
             }
-            *reinterpret_cast<ulonglong2 *>(dst + tile_gi<LOGM, TE, STRIDED>(e, tile, stride)) =
-                make_ulonglong2(x, y);
+            *reinterpret_cast<ulonglong2 *>(dst) = make_ulonglong2(x, y);
+            dst += gs2;
+            sp += 2 * NT + NT / 8;
         }
         __syncthreads();  // the next prefetch reuses this buffer
     }
