@@ -13,6 +13,9 @@ using namespace he;
 
 namespace he {
 
+thread_local std::vector<int> *capture_log = nullptr;
+thread_local int capture_tag = kTagFixed;
+
 void prof_mark(const he_ctx *c, cudaStream_t st, const char *tag, const char *suffix)
 {
     if (!c->prof || c->prof_used >= c->prof_pool.size()) return;
@@ -100,6 +103,7 @@ int run_pipeline(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, con
     // Region 1: tensor product, on its own or inside the first iNTT pass of d2
     const bool fused = (c->fuse & 1) != 0;
     if (!fused) {
+        capture_tag = kTagJobs;
         HE_TRY(run_tensor(c, R, st));
         prof_mark(c, st, "tensor");
     }
@@ -114,22 +118,31 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
     // key switching: iNTT(d2) (times N^-1 Qhat^-1), ModUp, NTT, inner product
     const int *cnt = S.counts;
     auto r8 = [c](int site) { return ((c->ntt_r8 >> site) & 1) != 0; };
+    capture_tag = kTagNtt0 + 0;
     if (tensor_fused)
         HE_TRY(launch_ntt_tensor(c, ntt_base, S.intt1, S.n_intt1, R, st, "intt_d2", cnt ? cnt + 0 : nullptr, r8(0)));
     else
         HE_TRY(launch_ntt(c, ntt_base, S.intt1, S.n_intt1, true, st, "intt_d2", cnt ? cnt + 0 : nullptr, r8(0)));
+    capture_tag = kTagJobs;
     HE_TRY(run_modup(c, R, st));
     prof_mark(c, st, "modup");
+    capture_tag = kTagNtt0 + 1;
     HE_TRY(launch_ntt(c, ntt_base, S.ntt_up, S.n_ntt_up, false, st, "ntt_modup", cnt ? cnt + 1 : nullptr, r8(1)));
-    if (S.ipg)
+    if (S.ipg) {
+        capture_tag = kTagIpGroups;
         HE_TRY(run_inner_product_shared(c, R, S.ipg, S.n_ipg, cnt ? cnt + 4 : nullptr, evk, st));
-    else
+    } else {
+        capture_tag = kTagJobs;
         HE_TRY(run_inner_product(c, R, evk, st));
+    }
     prof_mark(c, st, "inner_product");
     // ModDown: iNTT of the special limbs (times N^-1 Phat^-1), conversion, NTT
+    capture_tag = kTagNtt0 + 2;
     HE_TRY(launch_ntt(c, ntt_base, S.intt2, S.n_intt2, true, st, "intt_special", cnt ? cnt + 2 : nullptr, r8(2)));
+    capture_tag = kTagJobs;
     HE_TRY(run_moddown_conv(c, R, mode, st));
     prof_mark(c, st, "moddown_conv");
+    capture_tag = kTagNtt0 + 3;
     if (mode != kTailPlain) {
         // the final combine runs in the last NTT pass (writes each job's output)
         HE_TRY(launch_ntt_combine(c, ntt_base, S.ntt_last, S.n_ntt_last, R, st, "ntt_moddown", cnt ? cnt + 3 : nullptr,
@@ -137,9 +150,11 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
     } else {
         HE_TRY(launch_ntt(c, ntt_base, S.ntt_last, S.n_ntt_last, false, st, "ntt_moddown", cnt ? cnt + 3 : nullptr,
                           r8(3)));
+        capture_tag = kTagFixed;
         HE_TRY(run_combine_plain(c, R, st));
         prof_mark(c, st, "combine");
     }
+    capture_tag = kTagFixed;
     return HE_OK;
 }
 
@@ -876,6 +891,16 @@ struct he_batch_graph {
     int list_max[4] = {0, 0, 0, 0};  // groups each NTT list may hold (and its launch's grid) at `cap`
     int cap = 1;                     // limb-group cap at capture
     int ip_jobs = 0;  // jobs per inner-product group captured (0: one job per CTA)
+    // kernel nodes resized at every launch to the batch it runs (NTT nodes to
+    // its limb groups, per-job nodes to its jobs); empty if the captured
+    // launches could not be matched to the graph's nodes
+    struct NodeFix {
+        cudaGraphNode_t node;
+        cudaKernelNodeParams p;
+        int tag;
+        unsigned tiles;
+    };
+    std::vector<NodeFix> fixes;
     unsigned char *pinned = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -927,6 +952,62 @@ void graph_layout(const he_ctx *c, int max_jobs, he_batch_graph *g, int cap)
     size_t slot = 0;
     for (int l = 2; l <= c->L; l++) slot = std::max(slot, c->host_levels[l].ws.total);
     g->slot_limbs = slot;
+}
+
+// The graph's kernel nodes in launch order (a topological walk of the
+// captured chain), matched one to one with the tags logged at capture.
+void graph_match_nodes(he_batch_graph *g, const std::vector<int> &log, const Stages &S)
+{
+    size_t n = 0;
+    if (cudaGraphGetNodes(g->graph, nullptr, &n) != cudaSuccess || n == 0) return;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g->graph, nodes.data(), &n) != cudaSuccess) return;
+    // Kahn's order over the dependency edges
+    std::vector<size_t> indeg(n, 0);
+    std::vector<std::vector<size_t>> out(n);
+    for (size_t i = 0; i < n; i++) {
+        size_t nd = 0;
+        if (cudaGraphNodeGetDependentNodes(nodes[i], nullptr, nullptr, &nd) != cudaSuccess) return;
+        std::vector<cudaGraphNode_t> dep(nd);
+        if (nd && cudaGraphNodeGetDependentNodes(nodes[i], dep.data(), nullptr, &nd) != cudaSuccess) return;
+        for (cudaGraphNode_t d : dep)
+            for (size_t j = 0; j < n; j++)
+                if (nodes[j] == d) {
+                    out[i].push_back(j);
+                    indeg[j]++;
+                }
+    }
+    std::vector<size_t> order, ready;
+    for (size_t i = 0; i < n; i++)
+        if (!indeg[i]) ready.push_back(i);
+    while (!ready.empty()) {
+        if (ready.size() != 1) return;  // not a chain: leave the nodes as captured
+        const size_t i = ready.back();
+        ready.pop_back();
+        order.push_back(i);
+        for (size_t j : out[i])
+            if (--indeg[j] == 0) ready.push_back(j);
+    }
+    std::vector<he_batch_graph::NodeFix> fixes;
+    const int lists[4] = {S.n_intt1, S.n_ntt_up, S.n_intt2, S.n_ntt_last};
+    for (size_t i : order) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nodes[i], &ty) != cudaSuccess) return;
+        if (ty != cudaGraphNodeTypeKernel) continue;
+        he_batch_graph::NodeFix f;
+        f.node = nodes[i];
+        if (cudaGraphKernelNodeGetParams(nodes[i], &f.p) != cudaSuccess) return;
+        if (fixes.size() >= log.size()) return;
+        f.tag = log[fixes.size()];
+        f.tiles = 1;
+        if (f.tag >= kTagNtt0 && f.tag < kTagNtt0 + 4) {
+            const int t = f.tag - kTagNtt0;
+            if (lists[t] < 1 || f.p.gridDim.x % (unsigned)lists[t]) return;
+            f.tiles = f.p.gridDim.x / (unsigned)lists[t];
+        }
+        fixes.push_back(f);
+    }
+    if (fixes.size() == log.size()) g->fixes = fixes;
 }
 
 }  // namespace
@@ -1004,7 +1085,11 @@ int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws
         g_last_cuda_error = cudaGetErrorName(ce);
         rc = HE_ECUDA;
     }
+    std::vector<int> log;
+    capture_log = &log;
     if (rc == HE_OK) rc = run_pipeline(c, R, data, Sg, evk, kTailRescale, st);
+    capture_log = nullptr;
+    capture_tag = kTagFixed;
     ce = cudaStreamEndCapture(st, &g->graph);
     c->prof = prof;
     if (ce != cudaSuccess) g_last_cuda_error = cudaGetErrorName(ce);
@@ -1014,6 +1099,7 @@ int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws
         g_last_cuda_error = cudaGetErrorName(ce);
         return fail(HE_ECUDA);
     }
+    graph_match_nodes(g, log, Sg);
     cudaStreamDestroy(st);
     *out = g;
     return HE_OK;
@@ -1067,6 +1153,19 @@ int he_batch_graph_launch(he_batch_graph *g, int count, const he_job *jobs, void
         const std::vector<IpGroup> ipg = ip_groups(lv.data(), count, g->ip_jobs);
         memcpy(g->pinned + g->ipg_off, ipg.data(), sizeof(IpGroup) * ipg.size());
         counts[4] = (int)ipg.size();
+    }
+    // every kernel node sized to this batch
+    for (const he_batch_graph::NodeFix &f : g->fixes) {
+        cudaKernelNodeParams p = f.p;
+        if (f.tag >= kTagNtt0 && f.tag < kTagNtt0 + 4)
+            p.gridDim.x = (unsigned)std::max(1, counts[f.tag - kTagNtt0]) * f.tiles;
+        else if (f.tag == kTagJobs)
+            p.gridDim.z = (unsigned)count;
+        else if (f.tag == kTagIpGroups)
+            p.gridDim.z = (unsigned)std::max(1, counts[4]);
+        else
+            continue;
+        if (cudaGraphExecKernelNodeSetParams(g->exec, f.node, &p) != cudaSuccess) return HE_ECUDA;
     }
     cudaStream_t st = S(stream);
     if (cudaGraphLaunch(g->exec, st) != cudaSuccess) return HE_ECUDA;

@@ -198,10 +198,24 @@ void prof_mark(const he_ctx *ctx, cudaStream_t st, const char *tag, const char *
 // stream drains, so every such kernel executes griddep_wait() before it
 // touches memory that earlier work on the stream produces or reads (static
 // tables may be read before).  Errors are left for cudaGetLastError().
+//
+// While a batch graph is being captured (capture_log set on this thread),
+// every launch appends capture_tag, the kind of grid the caller set before
+// it, so that the graph can resize each kernel node to the batch it runs.
+enum LaunchTag {
+    kTagNtt0 = 0,   // NTT launches over group list t (0..3): grid.x = groups x tiles
+    kTagJobs = 8,   // per-job kernels: grid.z = jobs
+    kTagIpGroups,   // the shared-key inner product: grid.z = its job groups
+    kTagFixed       // not resized
+};
+extern thread_local std::vector<int> *capture_log;
+extern thread_local int capture_tag;
+
 template <typename... KArgs, typename... Args>
 inline void launch_k(bool dep, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                      Args... args)
 {
+    if (capture_log) capture_log->push_back(capture_tag);
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
@@ -217,8 +231,16 @@ inline void launch_k(bool dep, void (*k)(KArgs...), dim3 grid, dim3 block, size_
 
 #ifdef __CUDACC__
 // Wait for the previous kernel on the stream (a no-op without a programmatic
-// dependency).
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// dependency), then allow the next kernel to be launched: once every CTA of
+// this grid has passed this point (the grid's last wave is running), the
+// next kernel's CTAs may occupy the SMs this grid's tail leaves idle and run
+// their prologue; they wait in their own griddep_wait for this grid's
+// completion and memory flush before touching its data.
+__device__ __forceinline__ void griddep_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // Exit of a CTA with no work.  It still waits for the previous kernel first:
 // a kernel launched after this one waits only for this kernel's completion,
