@@ -959,23 +959,36 @@ void graph_layout(const he_ctx *c, int max_jobs, he_batch_graph *g, int cap)
 void graph_match_nodes(he_batch_graph *g, const std::vector<int> &log, const Stages &S)
 {
     size_t n = 0;
-    if (cudaGraphGetNodes(g->graph, nullptr, &n) != cudaSuccess || n == 0) return;
+    if (cudaGraphGetNodes(g->graph, nullptr, &n) != cudaSuccess || n == 0) {
+        (void)cudaGetLastError();
+        return;
+    }
     std::vector<cudaGraphNode_t> nodes(n);
-    if (cudaGraphGetNodes(g->graph, nodes.data(), &n) != cudaSuccess) return;
-    // Kahn's order over the dependency edges
+    if (cudaGraphGetNodes(g->graph, nodes.data(), &n) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    // Kahn's order over the dependency edges (programmatic edges carry edge
+    // data, so the query passes room for it; a failed query leaves the nodes
+    // as captured and clears the error it raised)
     std::vector<size_t> indeg(n, 0);
     std::vector<std::vector<size_t>> out(n);
+    std::vector<cudaGraphNode_t> dep(n);
+    std::vector<cudaGraphEdgeData> edata(n);
     for (size_t i = 0; i < n; i++) {
-        size_t nd = 0;
-        if (cudaGraphNodeGetDependentNodes(nodes[i], nullptr, nullptr, &nd) != cudaSuccess) return;
-        std::vector<cudaGraphNode_t> dep(nd);
-        if (nd && cudaGraphNodeGetDependentNodes(nodes[i], dep.data(), nullptr, &nd) != cudaSuccess) return;
-        for (cudaGraphNode_t d : dep)
+        size_t nd = n;
+        if (cudaGraphNodeGetDependentNodes(nodes[i], dep.data(), edata.data(), &nd) != cudaSuccess || nd > n) {
+            (void)cudaGetLastError();
+            return;
+        }
+        for (size_t k = 0; k < nd; k++) {
+            const cudaGraphNode_t d = dep[k];
             for (size_t j = 0; j < n; j++)
                 if (nodes[j] == d) {
                     out[i].push_back(j);
                     indeg[j]++;
                 }
+        }
     }
     std::vector<size_t> order, ready;
     for (size_t i = 0; i < n; i++)
@@ -992,11 +1005,17 @@ void graph_match_nodes(he_batch_graph *g, const std::vector<int> &log, const Sta
     const int lists[4] = {S.n_intt1, S.n_ntt_up, S.n_intt2, S.n_ntt_last};
     for (size_t i : order) {
         cudaGraphNodeType ty;
-        if (cudaGraphNodeGetType(nodes[i], &ty) != cudaSuccess) return;
+        if (cudaGraphNodeGetType(nodes[i], &ty) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return;
+        }
         if (ty != cudaGraphNodeTypeKernel) continue;
         he_batch_graph::NodeFix f;
         f.node = nodes[i];
-        if (cudaGraphKernelNodeGetParams(nodes[i], &f.p) != cudaSuccess) return;
+        if (cudaGraphKernelNodeGetParams(nodes[i], &f.p) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return;
+        }
         if (fixes.size() >= log.size()) return;
         f.tag = log[fixes.size()];
         f.tiles = 1;
