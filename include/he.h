@@ -447,17 +447,19 @@ int he_nr_rescale(he_nr_plan *plan, const uint64_t *ct, int logq, uint64_t *out,
  * staged twiddles; 1..4), ModUp targets per CTA (4, 8 or 16), whether the
  * path's kernels use programmatic dependent launch (1: a kernel's CTAs may be
  * scheduled while its predecessor drains; each waits for it in hardware
- * before touching its data), and which of the four NTT sites of the key
+ * before touching its data; 2: as 1, and a kernel allows its successor to be
+ * launched as soon as its own last wave runs, so the successor's CTAs fill
+ * the SMs its tail leaves idle; 0: off), and which of the four NTT sites of the key
  * switch (bit 0 the iNTT of d2, 1 the NTT of the ModUp outputs, 2 the iNTT of
  * the special limbs, 3 the NTT of the ModDown limbs) use the radix-8 plan
  * (rounds of at most three stages, 256 threads per tile) instead of the
  * radix-16 one (128 threads per tile).  Speed only: every shape gives
- * bit-identical results.  Default {4, 8, 1, 0, 8, 1}.  A batch graph keeps the
+ * bit-identical results.  Default {4, 8, 1, 0, 8, 3}.  A batch graph keeps the
  * shape it was captured with, except the limb-group cap. */
 typedef struct {
     int group_cap;
     int modup_chunk;
-    int pdl;
+    int pdl;     /* 0..2 */
     int ntt_r8;  /* 0..15 */
     int ip_jobs; /* batches of 2 or more jobs: 4 or 8 jobs of similar level share each CTA of the inner
                     product, which reads the evaluation key's words once for all of them (Fig. 2 region 2's
@@ -465,7 +467,11 @@ typedef struct {
                     while the context has at most four digits (dnum <= 4), else 1. */
     int fuse;    /* bit 0: the tensor product (Fig. 2 region 1) is formed inside the first inverse-NTT pass
                     of d2, which loads the ciphertexts instead of d2 and also stores d0, d1, d2 (one launch
-                    and one read of d2 fewer); 0: its own kernel.  0..1 */
+                    and one read of d2 fewer); else its own kernel.  bit 1 (single HE Mul with rescale):
+                    the key-switch sums of Fig. 2 region 2 are split: those of the special primes and of
+                    q_{level-1} (the next iNTT's inputs) first, those of the other q primes (read only by
+                    the final additions) in the same launch as the ModDown conversion, so the key stream
+                    overlaps the conversion's arithmetic.  0..3 */
     double ms;   /* he_autotune: measured milliseconds per call; else 0 */
 } he_shape;
 
@@ -475,8 +481,9 @@ int he_get_shape(const he_ctx *ctx, he_shape *shape);
 /* Time shapes on the caller's own work and keep the fastest in ctx: every
  * (group_cap, modup_chunk, pdl) with the radix-16 NTT plan, then every
  * nonzero ntt_r8 mask on the best of those (39 shapes), then, for a batch,
- * the other two ip_jobs values on the best, then the other fuse value on the
- * best (40 shapes for one job, 42 for a batch);
+ * the other two ip_jobs values on the best, then each fuse bit toggled on the
+ * best, then pdl = 2 if the best has pdl = 1 (41 or 42 shapes for one job, 43
+ * or 44 for a batch);
  * count == 1 times he_mul_rescale on jobs[0] (ws of he_workspace_bytes),
  * count > 1 times he_mul_batch on the jobs (ws of he_batch_workspace_bytes),
  * `reps` calls per shape after one warm-up call, CUDA events on `stream`.

@@ -409,7 +409,7 @@ def _shape_tuple(sh) -> tuple:
 
 
 def he_set_shape(ctx, group_cap: int, modup_chunk: int, pdl: int = 1, ntt_r8: int = 0, ip_jobs: int = 8,
-                 fuse: int = 1):
+                 fuse: int = 3):
     sh = he_shape(group_cap, modup_chunk, pdl, ntt_r8, ip_jobs, fuse, 0.0)
     _check(lib().he_set_shape(ctx.ptr, ctypes.byref(sh)), "he_set_shape")
 

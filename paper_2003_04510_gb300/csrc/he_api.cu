@@ -128,20 +128,29 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
     prof_mark(c, st, "modup");
     capture_tag = kTagNtt0 + 1;
     HE_TRY(launch_ntt(c, ntt_base, S.ntt_up, S.n_ntt_up, false, st, "ntt_modup", cnt ? cnt + 1 : nullptr, r8(1)));
+    // a single job's q-limb sums (read only by the final combine) may run
+    // beside the ModDown conversion: the sums of the special limbs and the
+    // last q limb (the next iNTT's inputs) come first
+    const bool split = (c->fuse & 2) && !S.ipg && !R.items && mode != kTailPlain && moddown_ipq_fits(c);
     if (S.ipg) {
         capture_tag = kTagIpGroups;
         HE_TRY(run_inner_product_shared(c, R, S.ipg, S.n_ipg, cnt ? cnt + 4 : nullptr, evk, st));
     } else {
         capture_tag = kTagJobs;
-        HE_TRY(run_inner_product(c, R, evk, st));
+        HE_TRY(run_inner_product(c, R, evk, st, split ? kIpSpecialLastRows : kIpAllRows));
     }
-    prof_mark(c, st, "inner_product");
+    prof_mark(c, st, split ? "inner_product_special" : "inner_product");
     // ModDown: iNTT of the special limbs (times N^-1 Phat^-1), conversion, NTT
     capture_tag = kTagNtt0 + 2;
     HE_TRY(launch_ntt(c, ntt_base, S.intt2, S.n_intt2, true, st, "intt_special", cnt ? cnt + 2 : nullptr, r8(2)));
     capture_tag = kTagJobs;
-    HE_TRY(run_moddown_conv(c, R, mode, st));
-    prof_mark(c, st, "moddown_conv");
+    if (split) {
+        HE_TRY(run_moddown_ipq(c, R, mode, evk, st));
+        prof_mark(c, st, "moddown_conv_ipq");
+    } else {
+        HE_TRY(run_moddown_conv(c, R, mode, st));
+        prof_mark(c, st, "moddown_conv");
+    }
     capture_tag = kTagNtt0 + 3;
     if (mode != kTailPlain) {
         // the final combine runs in the last NTT pass (writes each job's output)
@@ -158,9 +167,10 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
     return HE_OK;
 }
 
-JobRef single_job(const u64 *ct1, const u64 *ct2, u64 *out, u64 *ws, int l)
+JobRef single_job(const he_ctx *c, const u64 *ct1, const u64 *ct2, u64 *out, u64 *ws, int l)
 {
     JobRef R;
+    R.trigger = c->pdl >= 2;
     R.items = nullptr;
     R.one.ct1 = ct1;
     R.one.ct2 = ct2;
@@ -192,7 +202,7 @@ Stages level_stages(const he_ctx *c, int l, int mode)
 int hemul_pipeline(he_ctx *c, const u64 *ct1, const u64 *ct2, const u64 *evk, int l, u64 *out, u64 *ws,
                    int mode, cudaStream_t st)
 {
-    return run_pipeline(c, single_job(ct1, ct2, out, ws, l), ws, level_stages(c, l, mode), evk, mode, st);
+    return run_pipeline(c, single_job(c, ct1, ct2, out, ws, l), ws, level_stages(c, l, mode), evk, mode, st);
 }
 
 // ---- batches -------------------------------------------------------------
@@ -371,7 +381,7 @@ int he_rotate(he_ctx *c, const uint64_t *ct, const uint64_t *rk, int level, uint
     prof_mark(c, st, "");
     HE_TRY(run_automorph(c, ct, w, level, galois, st));
     prof_mark(c, st, "automorph");
-    return run_keyswitch(c, single_job(nullptr, nullptr, out, w, level), w, level_stages(c, level, kTailPlain), rk, kTailPlain,
+    return run_keyswitch(c, single_job(c, nullptr, nullptr, out, w, level), w, level_stages(c, level, kTailPlain), rk, kTailPlain,
                          st);
 }
 
@@ -416,7 +426,7 @@ int he_step_tensor(he_ctx *c, const uint64_t *ct1, const uint64_t *ct2, int leve
     if (check_dev(c) || !ct1 || !ct2 || !d) return HE_EINVAL;
     if (level < 1 || level > c->L) return HE_ELEVEL;
     // d0, d1, d2 sit at limb offsets 0, l, 2l of a workspace: d serves as one
-    HE_TRY(run_tensor(c, single_job(ct1, ct2, nullptr, (u64 *)d, level), S(stream)));
+    HE_TRY(run_tensor(c, single_job(c, ct1, ct2, nullptr, (u64 *)d, level), S(stream)));
     return HE_OK;
 }
 
@@ -434,7 +444,7 @@ int he_step_modup(he_ctx *c, const uint64_t *d2, int level, uint64_t *U, void *w
     HE_TRY(cudaMemcpyAsync(w + W.d2 * N, d2, (size_t)level * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
     HE_TRY(cudaMemcpyAsync(w + W.u * N, U, beta * E * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
     HE_TRY(launch_ntt(c, w, J.intt1, J.n_intt1, true, st));
-    HE_TRY(run_modup(c, single_job(nullptr, nullptr, nullptr, w, level), st));
+    HE_TRY(run_modup(c, single_job(c, nullptr, nullptr, nullptr, w, level), st));
     HE_TRY(cudaMemcpyAsync(U, w + W.u * N, beta * E * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
     return HE_OK;
 }
@@ -452,7 +462,7 @@ int he_step_inner_product(he_ctx *c, const uint64_t *U, const uint64_t *d2, cons
     cudaStream_t st = S(stream);
     HE_TRY(cudaMemcpyAsync(w + W.d2 * N, d2, (size_t)level * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
     HE_TRY(cudaMemcpyAsync(w + W.u * N, U, beta * E * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
-    HE_TRY(run_inner_product(c, single_job(nullptr, nullptr, nullptr, w, level), evk, st));
+    HE_TRY(run_inner_product(c, single_job(c, nullptr, nullptr, nullptr, w, level), evk, st));
     HE_TRY(cudaMemcpyAsync(KS, w + W.ks * N, 2 * E * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
     return HE_OK;
 }
@@ -473,7 +483,7 @@ int he_step_moddown(he_ctx *c, const uint64_t *X, int level, uint64_t *out, void
     HE_TRY(cudaMemsetAsync(w + (W.ks + E) * N, 0, (size_t)E * N * sizeof(u64), st));
     HE_TRY(cudaMemsetAsync(w + W.d0 * N, 0, 2 * (size_t)level * N * sizeof(u64), st));
     HE_TRY(launch_ntt(c, w, J.intt2, J.n_intt2, true, st));
-    const JobRef R = single_job(nullptr, nullptr, w + W.y * N, w, level);  // both halves land at y, u
+    const JobRef R = single_job(c, nullptr, nullptr, w + W.y * N, w, level);  // both halves land at y, u
     HE_TRY(run_moddown_conv(c, R, false, st));
     HE_TRY(launch_ntt(c, w, J.ntt_conv, J.n_ntt_conv, false, st));
     HE_TRY(run_combine_plain(c, R, st));
@@ -583,6 +593,7 @@ int he_mul_batch(he_ctx *c, int count, const he_job *jobs, const uint64_t *evk, 
     memset(&R.one, 0, sizeof(R.one));
     R.B = count;
     R.lmax = lmax;
+    R.trigger = c->pdl >= 2;
     return run_pipeline(c, R, data, Sg, evk, kTailRescale, st);
 }
 
@@ -638,13 +649,13 @@ int he_set_shape(he_ctx *c, const he_shape *sh)
     if (!c || !sh) return HE_EINVAL;
     if (sh->group_cap < 1 || sh->group_cap > kGroupMax) return HE_EINVAL;
     if (sh->modup_chunk != 4 && sh->modup_chunk != 8 && sh->modup_chunk != 16) return HE_EINVAL;
-    if (sh->pdl != 0 && sh->pdl != 1) return HE_EINVAL;
+    if (sh->pdl < 0 || sh->pdl > 2) return HE_EINVAL;
     if (sh->ntt_r8 < 0 || sh->ntt_r8 > 15) return HE_EINVAL;
     if (sh->ip_jobs != 1 && sh->ip_jobs != 4 && sh->ip_jobs != 8) return HE_EINVAL;
-    if (sh->fuse < 0 || sh->fuse > 1) return HE_EINVAL;
+    if (sh->fuse < 0 || sh->fuse > 3) return HE_EINVAL;
     c->group_cap = sh->group_cap;
     c->modup_chunk = sh->modup_chunk;
-    c->pdl = sh->pdl != 0;
+    c->pdl = sh->pdl;
     c->ntt_r8 = sh->ntt_r8;
     c->ip_jobs = sh->ip_jobs;
     c->fuse = sh->fuse;
@@ -657,7 +668,7 @@ int he_get_shape(const he_ctx *c, he_shape *sh)
     if (!c || !sh) return HE_EINVAL;
     sh->group_cap = c->group_cap;
     sh->modup_chunk = c->modup_chunk;
-    sh->pdl = c->pdl ? 1 : 0;
+    sh->pdl = c->pdl;
     sh->ntt_r8 = c->ntt_r8;
     sh->ip_jobs = c->ip_jobs;
     sh->fuse = c->fuse;
@@ -728,9 +739,14 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
             rc = time_shape(sh);
         }
     }
-    if (rc == HE_OK) {
+    for (int bit = 1; bit <= 2 && rc == HE_OK; bit <<= 1) {  // each fusion on the best, toggled
         he_shape sh = top;
-        sh.fuse = top.fuse ^ 1;
+        sh.fuse = top.fuse ^ bit;
+        rc = time_shape(sh);
+    }
+    if (rc == HE_OK && top.pdl == 1) {  // early dependent launch on the best
+        he_shape sh = top;
+        sh.pdl = 2;
         rc = time_shape(sh);
     }
     c->prof = prof;
@@ -1078,6 +1094,7 @@ int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws
     memset(&R.one, 0, sizeof(R.one));
     R.B = max_jobs;
     R.lmax = c->L;
+    R.trigger = c->pdl >= 2;
     Stages Sg;
     const NttGroup **lp[4] = {&Sg.intt1, &Sg.ntt_up, &Sg.intt2, &Sg.ntt_last};
     int *np[4] = {&Sg.n_intt1, &Sg.n_ntt_up, &Sg.n_intt2, &Sg.n_ntt_last};

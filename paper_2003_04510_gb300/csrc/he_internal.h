@@ -79,6 +79,7 @@ struct JobRef {
     BatchItem one;
     int B;                   // number of jobs
     int lmax;                // largest level among them
+    int trigger;             // early dependent launch (the shape's pdl = 2): see griddep_wait
 };
 #ifdef __CUDACC__
 __device__ __forceinline__ BatchItem job_item(const JobRef &R, int z) { return R.items ? R.items[z] : R.one; }
@@ -137,10 +138,12 @@ struct he_ctx {
     // group (1..kGroupMax) and ModUp targets per CTA (4, 8 or 16)
     int group_cap = he::kGroupMax;
     int modup_chunk = 8;
-    bool pdl = true;                     // programmatic dependent launch between the path's kernels
+    int pdl = 1;                         // programmatic dependent launch between the path's kernels:
+                                         // 0 off, 1 on, 2 on with early dependent launch (griddep_wait)
     int ntt_r8 = 0;                      // bit s: the radix-8 NTT plan at pipeline NTT site s (0..3)
     int ip_jobs = he::kIpJobsMax;        // batches: jobs sharing one CTA's key words in the inner product (1: none)
-    int fuse = 1;                        // bit 0: the tensor product inside the first inverse NTT pass of d2
+    int fuse = 3;                        // bit 0: the tensor product inside the first inverse NTT pass of d2;
+                                         // bit 1: the q limbs' key-switch sums beside the ModDown conversion
     std::vector<u64> ext;                // moduli, ext order
     std::vector<u64> psi;                // smallest primitive 2N-th roots, ext order
     // host tables (for the host NTT used by keygen / encrypt / decrypt)
@@ -231,15 +234,16 @@ inline void launch_k(bool dep, void (*k)(KArgs...), dim3 grid, dim3 block, size_
 
 #ifdef __CUDACC__
 // Wait for the previous kernel on the stream (a no-op without a programmatic
-// dependency), then allow the next kernel to be launched: once every CTA of
-// this grid has passed this point (the grid's last wave is running), the
-// next kernel's CTAs may occupy the SMs this grid's tail leaves idle and run
-// their prologue; they wait in their own griddep_wait for this grid's
-// completion and memory flush before touching its data.
-__device__ __forceinline__ void griddep_wait()
+// dependency).  With `trigger`, then allow the next kernel to be launched:
+// once every CTA of this grid has passed this point (the grid's last wave is
+// running), the next kernel's CTAs may occupy the SMs this grid's tail leaves
+// idle and run their prologue; they wait in their own griddep_wait for this
+// grid's completion and memory flush before touching its data.  Without it
+// the next kernel is launched as this grid's CTAs exit.
+__device__ __forceinline__ void griddep_wait(bool trigger = false)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (trigger) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Exit of a CTA with no work.  It still waits for the previous kernel first:
@@ -307,7 +311,17 @@ cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st);
 cudaError_t run_elementwise(const he_ctx *c, int op, const u64 *x, const u64 *y, u64 *out, int l, cudaStream_t st);
 // Rotation's first step: d0 = kappa_g(b), d1 = 0, d2 = -kappa_g(a) into ws (level l).
 cudaError_t run_automorph(const he_ctx *c, const u64 *ct, u64 *ws, int l, u64 g, cudaStream_t st);
-cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st);
+// rows (IpRows in keyswitch.cu): 0 every ext limb; 1 the special limbs and the
+// last q limb; 2 the special limbs; 3 the q limbs but the last; 4 the q limbs.
+enum { kIpAllRows = 0, kIpSpecialLastRows = 1 };
+cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st,
+                              int rows = kIpAllRows);
+// The ModDown conversion (rescaling tails) and the key-switch sums of the q
+// limbs but the last in one launch (after run_inner_product of the special
+// limbs and the last q limb).  Single jobs; moddown_ipq_fits says whether the
+// context's sizes have an instantiation.
+bool moddown_ipq_fits(const he_ctx *c);
+cudaError_t run_moddown_ipq(const he_ctx *c, const JobRef &R, int mode, const u64 *evk, cudaStream_t st);
 // The batched inner product with key words shared by the jobs of each group
 // (ngroups launched; dev_count, optional, bounds the groups on the device).
 bool inner_product_shared_fits(const he_ctx *c);  // the shared kernel covers at most four digits

@@ -54,7 +54,7 @@ k_tensor(const JobRef R, const DevPrime *__restrict__ primes, const DevLevel *__
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[K + i];
     const size_t ob = (size_t)i * N + n, oa = ((size_t)l + i) * N + n;
-    griddep_wait();
+    griddep_wait(R.trigger);
     const u64 pol = l2_policy_stream();  // the inputs are read once
     const ulonglong2 b1 = ld2_hint(it.ct1 + ob, pol), a1 = ld2_hint(it.ct1 + oa, pol),
                      b2 = ld2_hint(it.ct2 + ob, pol), a2 = ld2_hint(it.ct2 + oa, pol);
@@ -108,7 +108,7 @@ k_modup(const JobRef R, const DevLevel *__restrict__ lv_arr, const DevPrime *__r
     }
     const u64 *y = it.ws + (size_t)lv.o_y * N;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
-    griddep_wait();
+    griddep_wait(R.trigger);
     uint32_t x0[A], x1[A], z0[A], z1[A];
 #pragma unroll
     for (int i = 0; i < A; i++) {
@@ -160,20 +160,35 @@ __device__ __forceinline__ u64 seeded_a(u64 state, u64 idx, u64 t)
 // (SEEDED: [dnum][K+L][N], b halves only, a halves regenerated), KS: [2][E][N].
 // The digit loop is unrolled to BM >= beta with guards, so every operand
 // load of a thread is issued before the first product.
-template <int BM, bool SEEDED>
-__global__ void __launch_bounds__(kThreads)
-k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__restrict__ lv_arr,
-                const DevPrime *__restrict__ primes, int K, int L, int N, const SeedStates seeds)
+//
+// Rows: the key-switch sum of ext limb e of one job.  Which limb a CTA takes
+// (IpRows): every limb (grid.y over K + lmax); the special limbs and, for the
+// rescaling tails, the last q limb (their iNTT comes next: grid.y = K + 1);
+// or the q limbs (only the final combine reads them, so their sum can run
+// beside the ModDown conversion: all l, or l - 1 for the rescaling tails).
+enum IpRows { kIpAll = 0, kIpSpecialLast = 1, kIpSpecial = 2, kIpQButLast = 3, kIpQ = 4 };
+
+__device__ __forceinline__ int ip_row(int rows, int y, int K, int l)
 {
-    const BatchItem it = job_of(R, blockIdx.z);
-    const DevLevel &lv = lv_arr[it.level];
-    const int e = blockIdx.y;
+    switch (rows) {
+    case kIpAll: return y < K + l ? y : -1;
+    case kIpSpecialLast: return y < K ? y : y == K ? K + l - 1 : -1;
+    case kIpSpecial: return y < K ? y : -1;
+    case kIpQButLast: return y < l - 1 ? K + y : -1;
+    default: return y < l ? K + y : -1;
+    }
+}
+
+template <int BM, bool SEEDED>
+__device__ __forceinline__ void ip_body(const JobRef &R, const BatchItem &it, const DevLevel &lv, int e,
+                                        const u64 *__restrict__ evk, const DevPrime *__restrict__ primes, int K,
+                                        int L, int N, const SeedStates &seeds)
+{
     const int E = lv.E, EL = K + L, beta = lv.beta;
-    if (e >= E) return idle_exit();
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
     const DevPrime pr = primes[e];
     const u64 *U = it.ws + (size_t)lv.o_u * N, *d2 = it.ws + (size_t)lv.o_d2 * N;
-    griddep_wait();
+    griddep_wait(R.trigger);
     // the key and the ModUp outputs are read once: evict-first keeps them from
     // displacing the twiddle tables in L2
     const u64 pol = l2_policy_stream();
@@ -208,6 +223,19 @@ k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__r
     u64 *KS = it.ws + (size_t)lv.o_ks * N;
     st2(KS + (size_t)e * N + n, barrett128(bx, pr.q, pr.mu, pr.s), barrett128(by, pr.q, pr.mu, pr.s));
     st2(KS + ((size_t)E + e) * N + n, barrett128(ax, pr.q, pr.mu, pr.s), barrett128(ay, pr.q, pr.mu, pr.s));
+}
+
+// grid: x over N/2/kThreads, y over the rows selected (IpRows), z over jobs.
+template <int BM, bool SEEDED>
+__global__ void __launch_bounds__(kThreads)
+k_inner_product(const JobRef R, const u64 *__restrict__ evk, const DevLevel *__restrict__ lv_arr,
+                const DevPrime *__restrict__ primes, int K, int L, int N, const SeedStates seeds, int rows)
+{
+    const BatchItem it = job_of(R, blockIdx.z);
+    const DevLevel &lv = lv_arr[it.level];
+    const int e = ip_row(rows, blockIdx.y, K, it.level);
+    if (e < 0) return idle_exit();
+    ip_body<BM, SEEDED>(R, it, lv, e, evk, primes, K, L, N, seeds);
 }
 
 // Batched inner product with key words shared across jobs.  grid: x over
@@ -267,7 +295,7 @@ k_inner_product_shared(const JobRef R, const IpGroup *__restrict__ groups, const
     int njobs = 0;  // jobs sorted by level, highest first: those with limb e are a prefix
 #pragma unroll
     for (int g = 0; g < kIpJobsMax; g++) njobs += s_beta[g] > 0 ? 1 : 0;
-    griddep_wait();
+    griddep_wait(R.trigger);
     const u64 pol = l2_policy_stream();
     ulonglong2 kb[BM], ka[BM];
 #pragma unroll
@@ -351,17 +379,17 @@ __device__ __forceinline__ void conv_one(const uint32_t *x0, const uint32_t *x1,
 // the per-level constants lv.pbpq: the combine pass then forms
 // (P d + KS - NTT(conv)) / M exactly as for two floors.
 template <int KM, int MODE>
-__global__ void __launch_bounds__(kThreads, KM <= 8 ? 3 : 2)  // 85 / 128 registers
-k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__restrict__ pinv,
-               const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int N, int chunks)
+__device__ __forceinline__ void moddown_body(const JobRef &R, const u64 *__restrict__ PB,
+                                             const ulonglong2 *__restrict__ pinv, const DevLevel *__restrict__ lv_arr,
+                                             const DevPrime *__restrict__ primes, int K, int N, int chunks, int y)
 {
     constexpr bool FUSED = MODE == kTailRescale, PQ = MODE == kTailRescalePQ;
     const BatchItem it = job_of(R, blockIdx.z);
     const int l = it.level;
     const DevLevel &lv = lv_arr[l];
-    const int h = blockIdx.y / chunks;
+    const int h = y / chunks;
     const int nout = MODE != kTailPlain ? l - 1 : l;
-    const int i0 = (blockIdx.y - h * chunks) * kModdownChunk;
+    const int i0 = (y - h * chunks) * kModdownChunk;
     const int cnt = min(kModdownChunk, nout - i0);
     if (cnt <= 0) return idle_exit();
     const u64 *PBt = PQ ? lv.pbpq : PB;
@@ -388,7 +416,7 @@ k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__r
     const u64 *ys = it.ws + (size_t)lv.o_ys * N, *rr = it.ws + (size_t)lv.o_r * N;
     u64 *z = it.ws + (size_t)lv.o_z * N;
     const size_t n = 2 * ((size_t)blockIdx.x * kThreads + threadIdx.x);
-    griddep_wait();
+    griddep_wait(R.trigger);
     uint32_t x0[KM], x1[KM], z0[KM], z1[KM];
 #pragma unroll
     for (int k = 0; k < KM; k++) {
@@ -434,6 +462,37 @@ k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__r
     }
 }
 
+template <int KM, int MODE>
+__global__ void __launch_bounds__(kThreads, KM <= 8 ? 3 : 2)  // 85 / 128 registers
+k_moddown_conv(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__restrict__ pinv,
+               const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int N, int chunks)
+{
+    moddown_body<KM, MODE>(R, PB, pinv, lv_arr, primes, K, N, chunks, blockIdx.y);
+}
+
+// The ModDown conversion and the key-switch sums of the q limbs in one
+// launch: grid.y below 2 chunks runs the conversion (compute-bound), above it
+// the sums of the q limbs (a stream of key and ModUp words), so the SMs run
+// both kinds of CTA side by side.  The conversion reads only the special
+// limbs' iNTT (and the rescale limbs), the q-limb sums only U, d2 and the
+// key: the two parts touch disjoint data.
+template <int KM, int MODE, int BM, bool SEEDED>
+__global__ void __launch_bounds__(kThreads, KM <= 8 ? 3 : 2)
+k_moddown_ipq(const JobRef R, const u64 *__restrict__ PB, const ulonglong2 *__restrict__ pinv,
+              const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int N, int chunks,
+              const u64 *__restrict__ evk, int L, const SeedStates seeds)
+{
+    const int y = blockIdx.y;
+    if (y < 2 * chunks) {
+        moddown_body<KM, MODE>(R, PB, pinv, lv_arr, primes, K, N, chunks, y);
+        return;
+    }
+    const BatchItem it = job_of(R, blockIdx.z);
+    const int e = ip_row(MODE == kTailPlain ? kIpQ : kIpQButLast, y - 2 * chunks, K, it.level);
+    if (e < 0) return idle_exit();
+    ip_body<BM, SEEDED>(R, it, lv_arr[it.level], e, evk, primes, K, L, N, seeds);
+}
+
 // grid: x over N/2/kThreads, y over limbs, z over 2 * jobs (h = z & 1).
 // out[h][i] = d_h[i] + (KS_h[K+i] - C[h][i]) P^-1 mod q_i, i < l
 __global__ void __launch_bounds__(kThreads)
@@ -450,7 +509,7 @@ k_combine_plain(const JobRef R, const ulonglong2 *__restrict__ pinv, const DevLe
     const ulonglong2 pv = pinv[i];
     const u64 *d = it.ws + (size_t)(h ? lv.o_d1 : lv.o_d0) * N;
     const u64 *KS = it.ws + (size_t)lv.o_ks * N, *C = it.ws + (size_t)lv.o_z * N;
-    griddep_wait();
+    griddep_wait(R.trigger);
     const ulonglong2 dv = ld2(d + (size_t)i * N + n);
     const ulonglong2 ks = ld2(KS + ((size_t)h * E + K + i) * N + n);
     const ulonglong2 c = ld2(C + ((size_t)h * l + i) * N + n);
@@ -606,10 +665,24 @@ cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st)
     return launch_modup<8>(c, R, st);
 }
 
-cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st)
+SeedStates seed_states(const he_ctx *c, const u64 *evk, bool *seeded)
+{
+    SeedStates ss;
+    memset(&ss, 0, sizeof(ss));
+    *seeded = false;
+    for (const auto &k : c->seeded)
+        if (k.ptr == evk) {
+            *seeded = true;
+            memcpy(ss.s, k.state, sizeof(ss.s));
+        }
+    return ss;
+}
+
+cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st, int rows)
 {
     dim3 g = grid_x(c->N);
-    g.y = c->K + R.lmax;
+    g.y = rows == kIpAll ? c->K + R.lmax : rows == kIpSpecialLast ? c->K + 1 : rows == kIpSpecial ? c->K
+        : rows == kIpQButLast ? R.lmax - 1 : R.lmax;
     g.z = R.B;
     const int bm = (c->L + c->alpha - 1) / c->alpha;  // the most digits any level has
     SeedStates ss;
@@ -624,10 +697,10 @@ cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, 
     do {                                                                                                             \
         if (seeded)                                                                                                  \
             launch_k(c->pdl, k_inner_product<B, true>, g, dim3(kThreads), 0, st, R, evk, c->d_levels, c->d_primes,   \
-                     c->K, c->L, c->N, ss);                                                                          \
+                     c->K, c->L, c->N, ss, rows);                                                                    \
         else                                                                                                         \
             launch_k(c->pdl, k_inner_product<B, false>, g, dim3(kThreads), 0, st, R, evk, c->d_levels, c->d_primes,  \
-                     c->K, c->L, c->N, ss);                                                                          \
+                     c->K, c->L, c->N, ss, rows);                                                                    \
     } while (0)
     // three digits get their own width: 64 registers, four CTAs per SM
     // (the four-digit width takes 78 and fits three)
@@ -701,6 +774,45 @@ cudaError_t run_moddown_conv(const he_ctx *c, const JobRef &R, int mode, cudaStr
     else if (kp == 12) HE_MD(12);
     else HE_MD(16);
 #undef HE_MD
+    return cudaGetLastError();
+}
+
+bool moddown_ipq_fits(const he_ctx *c)
+{
+    return (c->L + c->alpha - 1) / c->alpha <= 4 && (c->KP == 1 || c->KP == 8 || c->KP == 12);
+}
+
+cudaError_t run_moddown_ipq(const he_ctx *c, const JobRef &R, int mode, const u64 *evk, cudaStream_t st)
+{
+    if (!moddown_ipq_fits(c) || mode == kTailPlain) return cudaErrorInvalidValue;
+    const int chunks = (R.lmax + kModdownChunk - 1) / kModdownChunk;
+    dim3 g = grid_x(c->N);
+    g.y = 2 * chunks + R.lmax - 1;
+    g.z = R.B;
+    const int K = c->K, bm = (c->L + c->alpha - 1) / c->alpha;
+    bool seeded;
+    const SeedStates ss = seed_states(c, evk, &seeded);
+    const u64 *PB = mode == kTailRescale ? c->d_PBP : c->d_PB;
+#define HE_MDQ(KK, MM, BB, SS)                                                                                       \
+    launch_k(c->pdl, k_moddown_ipq<KK, MM, BB, SS>, g, dim3(kThreads), 0, st, R, PB, c->d_pinv, c->d_levels,         \
+             c->d_primes, K, c->N, chunks, evk, c->L, ss)
+#define HE_MDQ_B(KK, MM)                                                                                             \
+    do {                                                                                                             \
+        if (bm <= 2) { if (seeded) HE_MDQ(KK, MM, 2, true); else HE_MDQ(KK, MM, 2, false); }                         \
+        else if (bm == 3) { if (seeded) HE_MDQ(KK, MM, 3, true); else HE_MDQ(KK, MM, 3, false); }                    \
+        else { if (seeded) HE_MDQ(KK, MM, 4, true); else HE_MDQ(KK, MM, 4, false); }                                 \
+    } while (0)
+#define HE_MDQ_M(KK)                                                                                                 \
+    do {                                                                                                             \
+        if (mode == kTailRescale) HE_MDQ_B(KK, kTailRescale);                                                        \
+        else HE_MDQ_B(KK, kTailRescalePQ);                                                                           \
+    } while (0)
+    if (c->KP == 1) HE_MDQ_M(1);
+    else if (c->KP == 8) HE_MDQ_M(8);
+    else HE_MDQ_M(12);
+#undef HE_MDQ_M
+#undef HE_MDQ_B
+#undef HE_MDQ
     return cudaGetLastError();
 }
 

@@ -51,7 +51,7 @@ struct NttArgs {
     int ts;          // first stage whose twiddle runs the table stores transposed
     int tiles;       // tiles per limb
     const int *count;  // optional device-side group count (grids sized for a maximum)
-    bool pdl;          // launched with programmatic dependent launch
+    int pdl;           // programmatic dependent launch: 0 off, 1 on, 2 with early dependent launch
     // fused final combine (COMBINE passes only)
     JobRef R;
     const DevLevel *levels;
@@ -389,7 +389,7 @@ k_ntt_pass(const NttArgs P)
         }
     }
     if (DIRECT) prefetch_direct_tw<LOGM, TE, RL, NT>(twg, tile, s0, P.ts);
-    griddep_wait();  // the limbs come from the previous kernels
+    griddep_wait(P.pdl >= 2);  // the limbs come from the previous kernels
     load_tile(0, buf);
     __pipeline_commit();
 
@@ -530,7 +530,7 @@ cudaError_t run_pass(const NttArgs &a, int ngroups, cudaStream_t st)
         configured = true;
     }
     if (ngroups == 0) return cudaSuccess;
-    launch_k(a.pdl, kern, dim3(ngroups * a.tiles), dim3(NT), smem, st, a);
+    launch_k(a.pdl != 0, kern, dim3(ngroups * a.tiles), dim3(NT), smem, st, a);
     return cudaGetLastError();
 }
 

@@ -269,10 +269,10 @@ def test_batch_matches_single_and_oracle(g):
         assert np.array_equal(host(g, jobs[k][2]), want)
 
 
-@pytest.mark.parametrize("levels,ip_jobs,fuse", [
-    ([3, 5], 8, 1), ([5, 3], 4, 0), ([3, 5, 2, 4, 5, 3, 2, 8, 9], 4, 1),
-    ([24, 4, 9, 17, 2, 13, 24, 23, 16, 8, 3], 8, 1), ([24, 9, 17, 2], 1, 0), ([24, 9, 17, 2], 1, 1)])
-def test_batch_shared_key_words_bit_exact(g, levels, ip_jobs, fuse):
+@pytest.mark.parametrize("levels,ip_jobs,fuse,pdl", [
+    ([3, 5], 8, 1, 1), ([5, 3], 4, 0, 2), ([3, 5, 2, 4, 5, 3, 2, 8, 9], 4, 1, 2),
+    ([24, 4, 9, 17, 2, 13, 24, 23, 16, 8, 3], 8, 1, 2), ([24, 9, 17, 2], 1, 0, 0), ([24, 9, 17, 2], 1, 1, 1)])
+def test_batch_shared_key_words_bit_exact(g, levels, ip_jobs, fuse, pdl):
     """Batches whose inner product shares each CTA's evaluation-key words among
     up to ip_jobs jobs of similar level (groups cut from the jobs sorted by
     level, ragged last group, jobs of a group at different levels and digit
@@ -293,7 +293,7 @@ def test_batch_shared_key_words_bit_exact(g, levels, ip_jobs, fuse):
         singles.append(gpu_mul(g, ctx, c1, c2, evk_t, lv, fused=True))
     ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
     try:
-        g.he_set_shape(ctx, 4, 8, 1, 0, ip_jobs, fuse)
+        g.he_set_shape(ctx, 4, 8, pdl, 0, ip_jobs, fuse)
         for rnd in range(2):  # twice on the same workspace
             for j in jobs:
                 j[2].fill_(-1)
@@ -309,8 +309,8 @@ def test_batch_shared_key_words_bit_exact(g, levels, ip_jobs, fuse):
     assert np.array_equal(host(g, jobs[k][2]), want)
 
 
-@pytest.mark.parametrize("capture_cap,replay_cap", [(4, 4), (1, 3), (4, 1)])
-def test_batch_graph_replays_match_single(g, capture_cap, replay_cap):
+@pytest.mark.parametrize("capture_cap,replay_cap,pdl", [(4, 4, 1), (1, 3, 2), (4, 1, 2)])
+def test_batch_graph_replays_match_single(g, capture_cap, replay_cap, pdl):
     """One captured graph, replayed with two different batches (sizes, levels,
     operands): every result equals he_mul_rescale on the job alone.  Captured
     at limb-group cap 1 (single-buffered NTT tiles) and replayed at cap 3, the
@@ -320,9 +320,9 @@ def test_batch_graph_replays_match_single(g, capture_cap, replay_cap):
     ctx = ctx_for(g, name)
     op = oracle.preset(name)
     evk_t = dev(g, rand_evk(op, 130))
-    g.he_set_shape(ctx, capture_cap, 8, 1)
+    g.he_set_shape(ctx, capture_cap, 8, pdl)
     graph = g.BatchGraph(ctx, 8, evk_t)
-    g.he_set_shape(ctx, replay_cap, 8, 1)
+    g.he_set_shape(ctx, replay_cap, 8, pdl)
     for rnd, levels in enumerate([[24, 5, 13, 2, 18, 9], [3, 24, 11]]):
         jobs, singles = [], []
         for k, lv in enumerate(levels):
@@ -633,7 +633,8 @@ def test_every_shape_is_bit_identical_n16(g):
     want = oracle.rescale(op, oracle.he_mul(op, c1, c2, evk, level), level)
     try:
         for shape in ((1, 4, 1, 15), (2, 16, 0, 5), (3, 8, 1, 10), (4, 16, 0, 0), (4, 8, 1, 0), (1, 8, 1, 3),
-                      (1, 8, 1, 8, 8, 0), (3, 4, 0, 1, 8, 0), (2, 8, 1, 15, 8, 0)):
+                      (1, 8, 1, 8, 8, 0), (3, 4, 0, 1, 8, 0), (2, 8, 1, 15, 8, 0), (1, 8, 2, 9, 8, 1),
+                      (4, 16, 2, 0, 8, 0), (1, 8, 2, 9, 8, 2), (2, 16, 1, 6, 8, 3), (1, 4, 0, 0, 8, 2)):
             g.he_set_shape(ctx, *shape)
             assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want), shape
         want_plain = oracle.he_mul(op, c1, c2, evk, level)
@@ -675,11 +676,13 @@ def test_autotune_batch_keeps_results(g):
     ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
     try:
         best, tried = g.he_autotune(ctx, jobs, evk_t, ws, reps=2)
-        assert len(tried) == 42 and all(t[6] > 0 for t in tried)
+        assert len(tried) in (43, 44) and all(t[6] > 0 for t in tried)
         assert best[:6] == g.he_get_shape(ctx) and best[6] == min(t[6] for t in tried)
         assert sorted(t[3] for t in tried[24:39]) == list(range(1, 16))
         assert sorted(t[4] for t in tried[39:41]) == [1, 4]  # the other two ip_jobs values
-        assert tried[41][5] == 0  # the tensor product on its own
+        assert tried[41][5] in (2, 0) and tried[42][5] in (1, 0)  # each fusion bit toggled
+        if len(tried) == 44:
+            assert tried[43][2] == 2  # early dependent launch
         for j in jobs:
             j[2].zero_()
         g.he_mul_batch(ctx, jobs, evk_t, ws)
