@@ -200,8 +200,9 @@ int he_mul_rescale_host(he_ctx *ctx, const uint64_t *ct1, const uint64_t *ct2, c
 /* A stream of HE Mul + rescale jobs from host buffers: job k's operands
  * ct1[k], ct2[k] (host, [2][levels[k]][N]) are copied to the device, run
  * through the path (he_mul_rescale) and the result copied to out[k] (host,
- * [2][levels[k]-1][N]).  Uploads and downloads run on two copy streams the
- * context owns, the path on `stream`, and `slots` (2..4) device staging slots
+ * [2][levels[k]-1][N]).  Uploads (one stream per operand) and downloads run
+ * on three copy streams the context owns, the path on `stream`, and `slots`
+ * (2..4) device staging slots
  * let job k+1's upload and job k-1's download overlap job k's kernels (the
  * host buffers should be pinned for that).  ws: device memory of at least
  * he_host_stream_workspace_bytes(max level, slots) (one path workspace plus
@@ -270,8 +271,11 @@ int he_mul_batch(he_ctx *ctx, int count, const he_job *jobs, const uint64_t *evk
  * 2..L) is one graph launch.  ws (device, at least
  * he_batch_graph_workspace_bytes(max_jobs)) and evk_dev are bound at
  * creation and must outlive the graph.  Creation captures `stream` (no work
- * runs).  A launch waits on the host for the previous launch of the same graph
- * to finish before it rewrites the pinned table.  Results are bit-identical to
+ * runs).  Launches alternate between two pinned tables: a launch waits on the
+ * host only for the launch before the previous one (which read the table it
+ * rewrites), so the host prepares a batch while the previous one runs.
+ * Launches of one graph share its workspace: issue them on one stream (or
+ * order their streams), as overlapping launches would race on it.  Results are bit-identical to
  * he_mul_rescale per job. */
 typedef struct he_batch_graph he_batch_graph;
 size_t he_batch_graph_workspace_bytes(const he_ctx *ctx, int max_jobs);

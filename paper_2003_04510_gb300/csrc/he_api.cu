@@ -278,6 +278,7 @@ int he_ctx_destroy(he_ctx *c)
         for (cudaEvent_t e : slot)
             if (e) cudaEventDestroy(e);
     if (c->io_h2d) cudaStreamDestroy(c->io_h2d);
+    if (c->io_h2d2) cudaStreamDestroy(c->io_h2d2);
     if (c->io_d2h) cudaStreamDestroy(c->io_d2h);
     if (c->arena) cudaFree(c->arena);
     delete c;
@@ -849,6 +850,8 @@ int he_mul_rescale_host_stream(he_ctx *c, int count, const uint64_t *const *ct1,
     {
         std::lock_guard<std::mutex> lk(c->io_mu);
         if (!c->io_h2d && cudaStreamCreateWithFlags(&c->io_h2d, cudaStreamNonBlocking) != cudaSuccess) return HE_ECUDA;
+        if (!c->io_h2d2 && cudaStreamCreateWithFlags(&c->io_h2d2, cudaStreamNonBlocking) != cudaSuccess)
+            return HE_ECUDA;
         if (!c->io_d2h && cudaStreamCreateWithFlags(&c->io_d2h, cudaStreamNonBlocking) != cudaSuccess) return HE_ECUDA;
         for (auto &slot : c->io_ev)
             for (cudaEvent_t &e : slot)
@@ -859,19 +862,26 @@ int he_mul_rescale_host_stream(he_ctx *c, int count, const uint64_t *const *ct1,
     const size_t limb = (size_t)c->N * sizeof(u64);
     const size_t slot_bytes = (6 * (size_t)ml - 2) * limb;
     u64 *w = (u64 *)ws;
-    cudaStream_t st = S(stream), up = c->io_h2d, down = c->io_d2h;
+    cudaStream_t st = S(stream), up = c->io_h2d, up2 = c->io_h2d2, down = c->io_d2h;
     for (int k = 0; k < count; k++) {
         const int s = k % slots, l = levels[k];
-        cudaEvent_t *ev = c->io_ev[s];  // 0: inputs copied, 1: path done, 2: result copied
+        // 0: ct1 copied, 3: ct2 copied, 1: path done, 2: result copied
+        cudaEvent_t *ev = c->io_ev[s];
         char *sb = (char *)ws + path + (size_t)s * slot_bytes;
         u64 *a = (u64 *)sb, *b = (u64 *)(sb + 2 * (size_t)ml * limb), *o = (u64 *)(sb + 4 * (size_t)ml * limb);
-        // the slot's inputs are free once the path of job k - slots has run
-        if (k >= slots) HE_TRY(cudaStreamWaitEvent(up, ev[1], 0));
+        // the slot's inputs are free once the path of job k - slots has run;
+        // the two operands travel on two streams, side by side
+        if (k >= slots) {
+            HE_TRY(cudaStreamWaitEvent(up, ev[1], 0));
+            HE_TRY(cudaStreamWaitEvent(up2, ev[1], 0));
+        }
         HE_TRY(cudaMemcpyAsync(a, ct1[k], 2 * (size_t)l * limb, cudaMemcpyHostToDevice, up));
-        HE_TRY(cudaMemcpyAsync(b, ct2[k], 2 * (size_t)l * limb, cudaMemcpyHostToDevice, up));
+        HE_TRY(cudaMemcpyAsync(b, ct2[k], 2 * (size_t)l * limb, cudaMemcpyHostToDevice, up2));
         HE_TRY(cudaEventRecord(ev[0], up));
+        HE_TRY(cudaEventRecord(ev[3], up2));
         // the path waits for its inputs and for the slot's previous result to be read back
         HE_TRY(cudaStreamWaitEvent(st, ev[0], 0));
+        HE_TRY(cudaStreamWaitEvent(st, ev[3], 0));
         if (k >= slots) HE_TRY(cudaStreamWaitEvent(st, ev[2], 0));
         int rc = hemul_pipeline(c, a, b, evk, l, o, w, kTailRescale, st);
         if (rc) return rc;
@@ -917,11 +927,16 @@ struct he_batch_graph {
         unsigned tiles;
     };
     std::vector<NodeFix> fixes;
-    unsigned char *pinned = nullptr;
+    // the graph's first node copies the header from pinned[b]; with its node
+    // found, launches alternate between two pinned headers, so the host fills
+    // one while the previous launch (which read the other) may still run
+    cudaGraphNode_t memcpy_node = nullptr;
+    unsigned char *pinned[2] = {nullptr, nullptr};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaEvent_t done = nullptr;
-    bool launched = false;
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    bool launched[2] = {false, false};
+    unsigned nlaunch = 0;
 };
 
 namespace {
@@ -1018,6 +1033,7 @@ void graph_match_nodes(he_batch_graph *g, const std::vector<int> &log, const Sta
             if (--indeg[j] == 0) ready.push_back(j);
     }
     std::vector<he_batch_graph::NodeFix> fixes;
+    cudaGraphNode_t copy = nullptr;
     const int lists[4] = {S.n_intt1, S.n_ntt_up, S.n_intt2, S.n_ntt_last};
     for (size_t i : order) {
         cudaGraphNodeType ty;
@@ -1025,6 +1041,7 @@ void graph_match_nodes(he_batch_graph *g, const std::vector<int> &log, const Sta
             (void)cudaGetLastError();
             return;
         }
+        if (ty == cudaGraphNodeTypeMemcpy && i == order[0]) copy = nodes[i];
         if (ty != cudaGraphNodeTypeKernel) continue;
         he_batch_graph::NodeFix f;
         f.node = nodes[i];
@@ -1042,7 +1059,10 @@ void graph_match_nodes(he_batch_graph *g, const std::vector<int> &log, const Sta
         }
         fixes.push_back(f);
     }
-    if (fixes.size() == log.size()) g->fixes = fixes;
+    if (fixes.size() == log.size()) {
+        g->fixes = fixes;
+        g->memcpy_node = copy;
+    }
 }
 
 }  // namespace
@@ -1078,15 +1098,19 @@ int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws
         if (st) cudaStreamDestroy(st);
         if (g->exec) cudaGraphExecDestroy(g->exec);
         if (g->graph) cudaGraphDestroy(g->graph);
-        if (g->done) cudaEventDestroy(g->done);
-        if (g->pinned) cudaFreeHost(g->pinned);
+        for (int b = 0; b < 2; b++) {
+            if (g->done[b]) cudaEventDestroy(g->done[b]);
+            if (g->pinned[b]) cudaFreeHost(g->pinned[b]);
+        }
         delete g;
         return rc;
     };
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return fail(HE_ECUDA);
-    if (cudaMallocHost((void **)&g->pinned, g->hdr) != cudaSuccess) return fail(HE_ENOMEM);
-    memset(g->pinned, 0, g->hdr);  // level-0 items: every block exits
-    if (cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess) return fail(HE_ECUDA);
+    for (int b = 0; b < 2; b++) {
+        if (cudaMallocHost((void **)&g->pinned[b], g->hdr) != cudaSuccess) return fail(HE_ENOMEM);
+        memset(g->pinned[b], 0, g->hdr);  // level-0 items: every block exits
+        if (cudaEventCreateWithFlags(&g->done[b], cudaEventDisableTiming) != cudaSuccess) return fail(HE_ECUDA);
+    }
     const bool prof = c->prof;
     c->prof = false;
     JobRef R;
@@ -1116,7 +1140,7 @@ int he_batch_graph_create(he_ctx *c, int max_jobs, const uint64_t *evk, void *ws
         g_last_cuda_error = cudaGetErrorName(ce);
         return fail(HE_ECUDA);
     }
-    ce = cudaMemcpyAsync(g->ws, g->pinned, g->hdr_copy, cudaMemcpyHostToDevice, st);
+    ce = cudaMemcpyAsync(g->ws, g->pinned[0], g->hdr_copy, cudaMemcpyHostToDevice, st);
     if (ce != cudaSuccess) {
         g_last_cuda_error = cudaGetErrorName(ce);
         rc = HE_ECUDA;
@@ -1150,11 +1174,13 @@ int he_batch_graph_launch(he_batch_graph *g, int count, const he_job *jobs, void
         if (!j.ct1 || !j.ct2 || !j.out || !aligned(j.ct1) || !aligned(j.ct2) || !aligned(j.out)) return HE_EINVAL;
         if (j.level < 2 || j.level > c->L) return HE_ELEVEL;
     }
-    // the previous replay must have consumed the pinned header
-    if (g->launched && cudaEventSynchronize(g->done) != cudaSuccess) return HE_ECUDA;
+    // the launch that last read this pinned header must have finished
+    const int b = g->memcpy_node ? (int)(g->nlaunch & 1u) : 0;
+    if (g->launched[b] && cudaEventSynchronize(g->done[b]) != cudaSuccess) return HE_ECUDA;
+    unsigned char *pin = g->pinned[b];
     const size_t N = (size_t)c->N;
     u64 *data = (u64 *)(g->ws + g->hdr);
-    BatchItem *items = (BatchItem *)g->pinned;
+    BatchItem *items = (BatchItem *)pin;
     memset(items, 0, sizeof(BatchItem) * g->max_jobs);
     std::vector<NttJob> lists[4];
     for (int i = 0; i < count; i++) {
@@ -1176,21 +1202,27 @@ int he_batch_graph_launch(he_batch_graph *g, int count, const he_job *jobs, void
                 lists[t].push_back(j);
             }
     }
-    int *counts = (int *)(g->pinned + g->counts_off);
+    int *counts = (int *)(pin + g->counts_off);
     for (int t = 0; t < 4; t++) {
         std::vector<NttGroup> grp = group_jobs(lists[t], std::max(c->group_cap, g->cap));
         if ((int)grp.size() > g->list_max[t]) return HE_EINVAL;  // cannot happen: bounded at capture
-        memcpy(g->pinned + g->lists_off[t], grp.data(), sizeof(NttGroup) * grp.size());
+        memcpy(pin + g->lists_off[t], grp.data(), sizeof(NttGroup) * grp.size());
         counts[t] = (int)grp.size();
     }
     if (g->ip_jobs) {
         std::vector<int> lv(count);
         for (int i = 0; i < count; i++) lv[i] = jobs[i].level;
         const std::vector<IpGroup> ipg = ip_groups(lv.data(), count, g->ip_jobs);
-        memcpy(g->pinned + g->ipg_off, ipg.data(), sizeof(IpGroup) * ipg.size());
+        memcpy(pin + g->ipg_off, ipg.data(), sizeof(IpGroup) * ipg.size());
         counts[4] = (int)ipg.size();
     }
-    // every kernel node sized to this batch
+    // the header copy reads this launch's pinned buffer; every kernel node is
+    // sized to this batch (the updates apply to this launch, not to one that
+    // is still running)
+    if (g->memcpy_node &&
+        cudaGraphExecMemcpyNodeSetParams1D(g->exec, g->memcpy_node, g->ws, pin, g->hdr_copy,
+                                           cudaMemcpyHostToDevice) != cudaSuccess)
+        return HE_ECUDA;
     for (const he_batch_graph::NodeFix &f : g->fixes) {
         cudaKernelNodeParams p = f.p;
         if (f.tag >= kTagNtt0 && f.tag < kTagNtt0 + 4)
@@ -1205,19 +1237,23 @@ int he_batch_graph_launch(he_batch_graph *g, int count, const he_job *jobs, void
     }
     cudaStream_t st = S(stream);
     if (cudaGraphLaunch(g->exec, st) != cudaSuccess) return HE_ECUDA;
-    if (cudaEventRecord(g->done, st) != cudaSuccess) return HE_ECUDA;
-    g->launched = true;
+    if (cudaEventRecord(g->done[b], st) != cudaSuccess) return HE_ECUDA;
+    g->launched[b] = true;
+    g->nlaunch++;
     return HE_OK;
 }
 
 int he_batch_graph_destroy(he_batch_graph *g)
 {
     if (!g) return HE_EINVAL;
-    if (g->launched) cudaEventSynchronize(g->done);
+    for (int b = 0; b < 2; b++)
+        if (g->launched[b]) cudaEventSynchronize(g->done[b]);
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
-    if (g->done) cudaEventDestroy(g->done);
-    if (g->pinned) cudaFreeHost(g->pinned);
+    for (int b = 0; b < 2; b++) {
+        if (g->done[b]) cudaEventDestroy(g->done[b]);
+        if (g->pinned[b]) cudaFreeHost(g->pinned[b]);
+    }
     delete g;
     return HE_OK;
 }

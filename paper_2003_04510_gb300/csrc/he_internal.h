@@ -180,12 +180,13 @@ struct he_ctx {
     mutable std::vector<cudaEvent_t> prof_pool;
     mutable std::vector<std::string> prof_names;  // prof_names[i] = kernel ended by event i ("" = a start mark)
     mutable size_t prof_used = 0;
-    // host-stream entry point: an upload and a download stream and, per
-    // staging slot, the events ordering a job's upload, path and download
+    // host-stream entry point: two upload streams (one per operand, so both
+    // copies run at once) and a download stream and, per staging slot, the
+    // events ordering a job's uploads, path and download
     // (created on first use, under io_mu)
     std::mutex io_mu;
-    cudaStream_t io_h2d = nullptr, io_d2h = nullptr;
-    cudaEvent_t io_ev[4][3] = {};
+    cudaStream_t io_h2d = nullptr, io_h2d2 = nullptr, io_d2h = nullptr;
+    cudaEvent_t io_ev[4][4] = {};
 };
 
 namespace he {
