@@ -482,12 +482,11 @@ typedef struct {
 /* HE_EINVAL for a NULL context or an unsupported value. */
 int he_set_shape(he_ctx *ctx, const he_shape *shape);
 int he_get_shape(const he_ctx *ctx, he_shape *shape);
-/* Time shapes on the caller's own work and keep the fastest in ctx: every
- * (group_cap, modup_chunk, pdl) with the radix-16 NTT plan, then every
- * nonzero ntt_r8 mask on the best of those (39 shapes), then, for a batch,
- * the other two ip_jobs values on the best, then each fuse bit toggled on the
- * best, then pdl = 2 if the best has pdl = 1 (41 or 42 shapes for one job, 43
- * or 44 for a batch);
+/* Time shapes on the caller's own work and keep the fastest in ctx, by
+ * coordinate descent from the context's current shape: each knob in turn
+ * (group_cap, modup_chunk, pdl, ntt_r8, ip_jobs for a batch, fuse) takes
+ * every value with the others held at the best shape so far, sweep after
+ * sweep until one changes nothing (at most four; no shape is timed twice);
  * count == 1 times he_mul_rescale on jobs[0] (ws of he_workspace_bytes),
  * count > 1 times he_mul_batch on the jobs (ws of he_batch_workspace_bytes),
  * `reps` calls per shape after one warm-up call, CUDA events on `stream`.

@@ -715,40 +715,43 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
         if (top.ms < 0 || sh.ms < top.ms) top = sh;
         return HE_OK;
     };
-    // first the limb-group cap, ModUp chunk and PDL with the radix-16 NTT
-    // plan, then the NTT plan of each of the four pipeline sites on that shape,
-    // then (batches) the jobs sharing the inner product's key words, then the
-    // tensor product fused or not
-    const int caps[] = {1, 2, 3, 4}, chunks[] = {4, 8, 16}, pdls[] = {1, 0};
-    const int ipj = keep.ip_jobs, fz = keep.fuse;
-    for (int pdl : pdls)
-        for (int cap : caps)
-            for (int ch : chunks)
-                if (rc == HE_OK) rc = time_shape({cap, ch, pdl, 0, ipj, fz, 0});
-    const he_shape base = top;
-    for (int mask = 1; mask < 16 && rc == HE_OK; mask++) {
-        he_shape sh = base;
-        sh.ntt_r8 = mask;
-        rc = time_shape(sh);
-    }
-    if (count > 1 && inner_product_shared_fits(c)) {
-        const he_shape b2 = top;
-        for (int per : {1, 4, 8}) {
-            if (per == b2.ip_jobs || rc != HE_OK) continue;
-            he_shape sh = b2;
-            sh.ip_jobs = per;
-            rc = time_shape(sh);
+    // coordinate descent over the knobs, from the context's shape: each knob
+    // in turn takes every value with the others held at the best so far,
+    // until a full sweep changes nothing (at most four sweeps); shapes
+    // already timed are not timed again
+    std::vector<he_shape> seen;
+    auto same = [](const he_shape &a, const he_shape &b) {
+        return a.group_cap == b.group_cap && a.modup_chunk == b.modup_chunk && a.pdl == b.pdl &&
+               a.ntt_r8 == b.ntt_r8 && a.ip_jobs == b.ip_jobs && a.fuse == b.fuse;
+    };
+    auto try_shape = [&](he_shape sh) -> int {
+        for (const he_shape &t : seen)
+            if (same(t, sh)) return HE_OK;
+        seen.push_back(sh);
+        return time_shape(sh);
+    };
+    rc = try_shape(keep);
+    const bool batch = count > 1 && inner_product_shared_fits(c);
+    for (int sweep = 0; sweep < 4 && rc == HE_OK; sweep++) {
+        const he_shape before = top;
+        for (int knob = 0; knob < 6 && rc == HE_OK; knob++) {
+            const he_shape base = top;
+            const int nv = knob == 0 ? kGroupMax : knob == 1 ? 3 : knob == 2 ? 3 : knob == 3 ? 16 : knob == 4 ? 3 : 4;
+            if (knob == 4 && !batch) continue;
+            for (int v = 0; v < nv && rc == HE_OK; v++) {
+                he_shape sh = base;
+                switch (knob) {
+                case 0: sh.group_cap = v + 1; break;
+                case 1: sh.modup_chunk = v == 0 ? 4 : v == 1 ? 8 : 16; break;
+                case 2: sh.pdl = v; break;
+                case 3: sh.ntt_r8 = v; break;
+                case 4: sh.ip_jobs = v == 0 ? 1 : v == 1 ? 4 : 8; break;
+                default: sh.fuse = v; break;
+                }
+                rc = try_shape(sh);
+            }
         }
-    }
-    for (int bit = 1; bit <= 2 && rc == HE_OK; bit <<= 1) {  // each fusion on the best, toggled
-        he_shape sh = top;
-        sh.fuse = top.fuse ^ bit;
-        rc = time_shape(sh);
-    }
-    if (rc == HE_OK && top.pdl == 1) {  // early dependent launch on the best
-        he_shape sh = top;
-        sh.pdl = 2;
-        rc = time_shape(sh);
+        if (same(before, top)) break;
     }
     c->prof = prof;
     cudaEventDestroy(e0);

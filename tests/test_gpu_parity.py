@@ -676,13 +676,11 @@ def test_autotune_batch_keeps_results(g):
     ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
     try:
         best, tried = g.he_autotune(ctx, jobs, evk_t, ws, reps=2)
-        assert len(tried) in (43, 44) and all(t[6] > 0 for t in tried)
+        assert all(t[6] > 0 for t in tried) and len(set(t[:6] for t in tried)) == len(tried)
         assert best[:6] == g.he_get_shape(ctx) and best[6] == min(t[6] for t in tried)
-        assert sorted(t[3] for t in tried[24:39]) == list(range(1, 16))
-        assert sorted(t[4] for t in tried[39:41]) == [1, 4]  # the other two ip_jobs values
-        assert tried[41][5] in (2, 0) and tried[42][5] in (1, 0)  # each fusion bit toggled
-        if len(tried) == 44:
-            assert tried[43][2] == 2  # early dependent launch
+        # the first sweep gives every knob every value
+        for k, vals in enumerate(((1, 2, 3, 4), (4, 8, 16), (0, 1, 2), tuple(range(16)), (1, 4, 8), (0, 1, 2, 3))):
+            assert set(vals) <= {t[k] for t in tried}, k
         for j in jobs:
             j[2].zero_()
         g.he_mul_batch(ctx, jobs, evk_t, ws)
