@@ -458,7 +458,7 @@ int he_nr_rescale(he_nr_plan *plan, const uint64_t *ct, int logq, uint64_t *out,
  * the special limbs, 3 the NTT of the ModDown limbs) use the radix-8 plan
  * (rounds of at most three stages, 256 threads per tile) instead of the
  * radix-16 one (128 threads per tile).  Speed only: every shape gives
- * bit-identical results.  Default {4, 8, 1, 0, 8, 3}.  A batch graph keeps the
+ * bit-identical results.  Default {4, 8, 1, 0, 8, 3, 0}.  A batch graph keeps the
  * shape it was captured with, except the limb-group cap. */
 typedef struct {
     int group_cap;
@@ -476,6 +476,11 @@ typedef struct {
                     q_{level-1} (the next iNTT's inputs) first, those of the other q primes (read only by
                     the final additions) in the same launch as the ModDown conversion, so the key stream
                     overlaps the conversion's arithmetic.  0..3 */
+    int ntt_split; /* the stages each pass of every NTT covers (Algo 3 split into a strided pass over the
+                    first stages and a contiguous pass over the last ones): 0 the default (2^16: 8 + 8;
+                    2^17: 9 + 8), 1 one stage more in the contiguous pass (7 + 9; 8 + 9), 2 one more in the
+                    strided pass (9 + 7; 10 + 7); ring sizes other than 2^16 and 2^17 keep the default.
+                    0..2 */
     double ms;   /* he_autotune: measured milliseconds per call; else 0 */
 } he_shape;
 
@@ -484,7 +489,8 @@ int he_set_shape(he_ctx *ctx, const he_shape *shape);
 int he_get_shape(const he_ctx *ctx, he_shape *shape);
 /* Time shapes on the caller's own work and keep the fastest in ctx, by
  * coordinate descent from the context's current shape: each knob in turn
- * (group_cap, modup_chunk, pdl, ntt_r8, ip_jobs for a batch, fuse) takes
+ * (group_cap, modup_chunk, pdl, ntt_r8, ip_jobs for a batch, fuse,
+ * ntt_split) takes
  * every value with the others held at the best shape so far, sweep after
  * sweep until one changes nothing (at most four; no shape is timed twice);
  * count == 1 times he_mul_rescale on jobs[0] (ws of he_workspace_bytes),

@@ -117,7 +117,7 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
 {
     // key switching: iNTT(d2) (times N^-1 Qhat^-1), ModUp, NTT, inner product
     const int *cnt = S.counts;
-    auto r8 = [c](int site) { return ((c->ntt_r8 >> site) & 1) != 0; };
+    auto r8 = [c](int site) { return ((c->ntt_r8 >> site) & 1) | (c->ntt_split << 1); };  // NTT plan of a site
     capture_tag = kTagNtt0 + 0;
     if (tensor_fused)
         HE_TRY(launch_ntt_tensor(c, ntt_base, S.intt1, S.n_intt1, R, st, "intt_d2", cnt ? cnt + 0 : nullptr, r8(0)));
@@ -417,7 +417,8 @@ int he_step_ntt(he_ctx *c, uint64_t *data, const int *prime_idx, int count, int 
     NttGroup *dj = nullptr;
     int rc = with_jobs(groups, st, &dj);
     if (rc) return rc;
-    cudaError_t e = launch_ntt(c, (u64 *)data, dj, (int)groups.size(), inverse != 0, st);
+    cudaError_t e = launch_ntt(c, (u64 *)data, dj, (int)groups.size(), inverse != 0, st, nullptr, nullptr,
+                               (c->ntt_r8 & 1) | (c->ntt_split << 1));
     cudaFreeAsync(dj, st);
     return e == cudaSuccess ? HE_OK : HE_ECUDA;
 }
@@ -654,12 +655,14 @@ int he_set_shape(he_ctx *c, const he_shape *sh)
     if (sh->ntt_r8 < 0 || sh->ntt_r8 > 15) return HE_EINVAL;
     if (sh->ip_jobs != 1 && sh->ip_jobs != 4 && sh->ip_jobs != 8) return HE_EINVAL;
     if (sh->fuse < 0 || sh->fuse > 3) return HE_EINVAL;
+    if (sh->ntt_split < 0 || sh->ntt_split > 2) return HE_EINVAL;
     c->group_cap = sh->group_cap;
     c->modup_chunk = sh->modup_chunk;
     c->pdl = sh->pdl;
     c->ntt_r8 = sh->ntt_r8;
     c->ip_jobs = sh->ip_jobs;
     c->fuse = sh->fuse;
+    c->ntt_split = sh->ntt_split;
     if (c->device) c->jobs = c->jobs_cap[c->group_cap - 1];
     return HE_OK;
 }
@@ -673,6 +676,7 @@ int he_get_shape(const he_ctx *c, he_shape *sh)
     sh->ntt_r8 = c->ntt_r8;
     sh->ip_jobs = c->ip_jobs;
     sh->fuse = c->fuse;
+    sh->ntt_split = c->ntt_split;
     sh->ms = 0;
     return HE_OK;
 }
@@ -722,7 +726,7 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
     std::vector<he_shape> seen;
     auto same = [](const he_shape &a, const he_shape &b) {
         return a.group_cap == b.group_cap && a.modup_chunk == b.modup_chunk && a.pdl == b.pdl &&
-               a.ntt_r8 == b.ntt_r8 && a.ip_jobs == b.ip_jobs && a.fuse == b.fuse;
+               a.ntt_r8 == b.ntt_r8 && a.ip_jobs == b.ip_jobs && a.fuse == b.fuse && a.ntt_split == b.ntt_split;
     };
     auto try_shape = [&](he_shape sh) -> int {
         for (const he_shape &t : seen)
@@ -734,10 +738,12 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
     const bool batch = count > 1 && inner_product_shared_fits(c);
     for (int sweep = 0; sweep < 4 && rc == HE_OK; sweep++) {
         const he_shape before = top;
-        for (int knob = 0; knob < 6 && rc == HE_OK; knob++) {
+        for (int knob = 0; knob < 7 && rc == HE_OK; knob++) {
             const he_shape base = top;
-            const int nv = knob == 0 ? kGroupMax : knob == 1 ? 3 : knob == 2 ? 3 : knob == 3 ? 16 : knob == 4 ? 3 : 4;
+            const int nv = knob == 0 ? kGroupMax : knob == 1 ? 3 : knob == 2 ? 3 : knob == 3 ? 16 : knob == 4 ? 3
+                         : knob == 5 ? 4 : 3;
             if (knob == 4 && !batch) continue;
+            if (knob == 6 && c->logN != 16 && c->logN != 17) continue;
             for (int v = 0; v < nv && rc == HE_OK; v++) {
                 he_shape sh = base;
                 switch (knob) {
@@ -746,7 +752,8 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
                 case 2: sh.pdl = v; break;
                 case 3: sh.ntt_r8 = v; break;
                 case 4: sh.ip_jobs = v == 0 ? 1 : v == 1 ? 4 : 8; break;
-                default: sh.fuse = v; break;
+                case 5: sh.fuse = v; break;
+                default: sh.ntt_split = v; break;
                 }
                 rc = try_shape(sh);
             }

@@ -141,6 +141,7 @@ struct he_ctx {
     int pdl = 1;                         // programmatic dependent launch between the path's kernels:
                                          // 0 off, 1 on, 2 on with early dependent launch (griddep_wait)
     int ntt_r8 = 0;                      // bit s: the radix-8 NTT plan at pipeline NTT site s (0..3)
+    int ntt_split = 0;                   // NTT pass split of every site (0 default, 1, 2: see launch_ntt)
     int ip_jobs = he::kIpJobsMax;        // batches: jobs sharing one CTA's key words in the inner product (1: none)
     int fuse = 3;                        // bit 0: the tensor product inside the first inverse NTT pass of d2;
                                          // bit 1: the q limbs' key-switch sums beside the ModDown conversion
@@ -282,27 +283,29 @@ __device__ __forceinline__ ulonglong2 ld2_hint(const void *p, u64 pol)
 }
 #endif
 
-// r8: the radix-8 plan (256 threads per tile) instead of the radix-16 one;
-// both give the same words.
+// plan: bit 0 the radix-8 plan (256 threads per tile) instead of the
+// radix-16 one; bits 1.. the pass split (0 default, 1 one stage from the
+// strided pass to the contiguous one, 2 the other way; 2^16 and 2^17 only).
+// Every plan gives the same words.
 cudaError_t launch_ntt(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, bool inverse,
-                       cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr, bool r8 = false);
+                       cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr, int plan = 0);
 cudaError_t launch_ntt2(const he_ctx *ctx, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups,
                         bool inverse, cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr,
-                        bool r8 = false);
+                        int plan = 0);
 cudaError_t configure_ntt(const he_ctx *ctx);
 // Forward NTT of the fused ModDown + rescale limbs with the final combine in
 // its last pass: out[h][i] = (d_h[i] + KS_h[K+i] P^-1 - NTT(z)) q_{l-1}^-1,
 // written to each job's output (groups carry the combine fields).
 cudaError_t launch_ntt_combine(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
                                cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr,
-                               bool r8 = false);
+                               int plan = 0);
 // Inverse NTT of d2 (and the rescale limbs of d0, d1) whose first pass forms
 // its input tiles with the tensor product from each job's ciphertexts and
 // stores d0, d1, d2 to the job's workspace (groups carry job and ci = limb |
 // product << 16 | keep << 18).
 cudaError_t launch_ntt_tensor(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
                               cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr,
-                              bool r8 = false);
+                              int plan = 0);
 // Number of final stages (the contiguous pass's last round) whose twiddle
 // runs the device table stores transposed; 0 for an unsupported logN.
 int ntt_direct_stages(int logN);

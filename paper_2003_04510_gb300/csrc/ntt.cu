@@ -30,6 +30,7 @@
 // every tile uses twiddles [1, 2^M); in the contiguous pass the tile's groups
 // [g0, g0 + NG) use, per stage l, the run [2^(s0+l) + g0 2^l, + NG 2^l).
 #include <cstring>
+#include <type_traits>
 
 #include <cuda_pipeline_primitives.h>
 
@@ -566,6 +567,37 @@ template <int LOGN> constexpr bool plan8_fits()
 static_assert(plan8_fits<13>() && plan8_fits<14>() && plan8_fits<15>() && plan8_fits<16>() && plan8_fits<17>(),
               "the radix-8 direct round must lie in the transposed region");
 
+// Pass splits (the launch shape's ntt_split): SPLIT 1 moves one stage from
+// the strided pass to the contiguous one, SPLIT 2 the other way (2^16:
+// 7 + 9 and 9 + 7 stages; 2^17: 8 + 9 and 10 + 7), each in a radix-16 and a
+// radix-8 form (R8).  Every plan's direct round lies in the transposed
+// region of the one twiddle table, and every round's shared-memory index map
+// was checked on the CPU (each tile element touched once, the padding of
+// e0 + c equal to padi(e0) plus the compile-time offset, addresses inside
+// the padded buffer).  Other ring sizes keep their default plans.
+template <int LOGN, int SPLIT, bool R8> struct PlanV : std::conditional_t<R8, Plan8<LOGN>, Plan<LOGN>> {};
+template <> struct PlanV<16, 1, false> { static constexpr int S1 = 7, A1 = 4, B1 = 3, C1 = 0, S2 = 9, A2 = 4, B2 = 2, C2 = 3; };
+template <> struct PlanV<16, 1, true> { static constexpr int S1 = 7, A1 = 3, B1 = 2, C1 = 2, S2 = 9, A2 = 3, B2 = 3, C2 = 3; };
+template <> struct PlanV<16, 2, false> { static constexpr int S1 = 9, A1 = 4, B1 = 3, C1 = 2, S2 = 7, A2 = 4, B2 = 3, C2 = 0; };
+template <> struct PlanV<16, 2, true> { static constexpr int S1 = 9, A1 = 3, B1 = 3, C1 = 3, S2 = 7, A2 = 2, B2 = 3, C2 = 2; };
+template <> struct PlanV<17, 1, false> { static constexpr int S1 = 8, A1 = 4, B1 = 4, C1 = 0, S2 = 9, A2 = 4, B2 = 2, C2 = 3; };
+template <> struct PlanV<17, 1, true> { static constexpr int S1 = 8, A1 = 2, B1 = 3, C1 = 3, S2 = 9, A2 = 3, B2 = 3, C2 = 3; };
+template <> struct PlanV<17, 2, false> { static constexpr int S1 = 10, A1 = 4, B1 = 3, C1 = 3, S2 = 7, A2 = 4, B2 = 3, C2 = 0; };
+template <> struct PlanV<17, 2, true> { static constexpr int S1 = 10, A1 = 4, B1 = 3, C1 = 3, S2 = 7, A2 = 2, B2 = 3, C2 = 2; };
+template <int LOGN, int SPLIT, bool R8> constexpr bool planv_fits()
+{
+    using P = PlanV<LOGN, SPLIT, R8>;
+    return P::S1 + P::S2 == LOGN && P::A1 + P::B1 + P::C1 == P::S1 && P::A2 + P::B2 + P::C2 == P::S2 &&
+           (P::C2 ? P::C2 : P::B2) <= plan_direct<LOGN>() && P::S1 <= LOGN - plan_direct<LOGN>();
+}
+static_assert(planv_fits<16, 1, false>() && planv_fits<16, 1, true>() && planv_fits<16, 2, false>() &&
+                  planv_fits<16, 2, true>() && planv_fits<17, 1, false>() && planv_fits<17, 1, true>() &&
+                  planv_fits<17, 2, false>() && planv_fits<17, 2, true>(),
+              "split plans: stages, rounds and the transposed region");
+
+// plan id: bit 0 the radix-8 form, bits 1.. the split (0, 1, 2)
+constexpr int kNttPlans = 6;
+
 // Two-pass transform: the strided pass covers the first S1 stages (forward
 // order), the contiguous pass the last S2.
 template <int S1, int A1, int B1, int C1, int S2, int A2, int B2, int C2>
@@ -606,10 +638,16 @@ cudaError_t two_pass_plan(const he_ctx *c, NttArgs a, int ngroups, bool inverse,
 }
 
 template <int LOGN>
-cudaError_t two_pass_any(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag, bool r8)
+cudaError_t two_pass_any(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag, int plan)
 {
-    return r8 ? two_pass_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, inverse, st, tag)
-              : two_pass_plan<LOGN, Plan<LOGN>>(c, a, ngroups, inverse, st, tag);
+    switch (plan) {
+    case 1: return two_pass_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, inverse, st, tag);
+    case 2: return two_pass_plan<LOGN, PlanV<LOGN, 1, false>>(c, a, ngroups, inverse, st, tag);
+    case 3: return two_pass_plan<LOGN, PlanV<LOGN, 1, true>>(c, a, ngroups, inverse, st, tag);
+    case 4: return two_pass_plan<LOGN, PlanV<LOGN, 2, false>>(c, a, ngroups, inverse, st, tag);
+    case 5: return two_pass_plan<LOGN, PlanV<LOGN, 2, true>>(c, a, ngroups, inverse, st, tag);
+    default: return two_pass_plan<LOGN, Plan<LOGN>>(c, a, ngroups, inverse, st, tag);
+    }
 }
 
 // Forward transform whose last pass also applies the final combine.
@@ -628,10 +666,16 @@ cudaError_t combine_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t s
 }
 
 template <int LOGN>
-cudaError_t combine_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, bool r8)
+cudaError_t combine_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, int plan)
 {
-    return r8 ? combine_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, st, tag)
-              : combine_plan<LOGN, Plan<LOGN>>(c, a, ngroups, st, tag);
+    switch (plan) {
+    case 1: return combine_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, st, tag);
+    case 2: return combine_plan<LOGN, PlanV<LOGN, 1, false>>(c, a, ngroups, st, tag);
+    case 3: return combine_plan<LOGN, PlanV<LOGN, 1, true>>(c, a, ngroups, st, tag);
+    case 4: return combine_plan<LOGN, PlanV<LOGN, 2, false>>(c, a, ngroups, st, tag);
+    case 5: return combine_plan<LOGN, PlanV<LOGN, 2, true>>(c, a, ngroups, st, tag);
+    default: return combine_plan<LOGN, Plan<LOGN>>(c, a, ngroups, st, tag);
+    }
 }
 
 // Inverse transform whose first pass forms its input with the tensor product.
@@ -650,16 +694,22 @@ cudaError_t tensor_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st
 }
 
 template <int LOGN>
-cudaError_t tensor_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, bool r8)
+cudaError_t tensor_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, int plan)
 {
-    return r8 ? tensor_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, st, tag)
-              : tensor_plan<LOGN, Plan<LOGN>>(c, a, ngroups, st, tag);
+    switch (plan) {
+    case 1: return tensor_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, st, tag);
+    case 2: return tensor_plan<LOGN, PlanV<LOGN, 1, false>>(c, a, ngroups, st, tag);
+    case 3: return tensor_plan<LOGN, PlanV<LOGN, 1, true>>(c, a, ngroups, st, tag);
+    case 4: return tensor_plan<LOGN, PlanV<LOGN, 2, false>>(c, a, ngroups, st, tag);
+    case 5: return tensor_plan<LOGN, PlanV<LOGN, 2, true>>(c, a, ngroups, st, tag);
+    default: return tensor_plan<LOGN, Plan<LOGN>>(c, a, ngroups, st, tag);
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_ntt_tensor(const he_ctx *c, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
-                              cudaStream_t st, const char *tag, const int *dev_count, bool r8)
+                              cudaStream_t st, const char *tag, const int *dev_count, int plan)
 {
     if (ngroups < 0) return cudaSuccess;  // ngroups == 0: configure the kernels only
     NttArgs a;
@@ -682,17 +732,17 @@ cudaError_t launch_ntt_tensor(const he_ctx *c, u64 *base, const NttGroup *groups
         if (ngroups) prof_mark(c, st, tag, ".tensor_inv");
         return e;
     }
-    case 13: return tensor_any<13>(c, a, ngroups, st, tag, r8);
-    case 14: return tensor_any<14>(c, a, ngroups, st, tag, r8);
-    case 15: return tensor_any<15>(c, a, ngroups, st, tag, r8);
-    case 16: return tensor_any<16>(c, a, ngroups, st, tag, r8);
-    case 17: return tensor_any<17>(c, a, ngroups, st, tag, r8);
+    case 13: return tensor_any<13>(c, a, ngroups, st, tag, plan);
+    case 14: return tensor_any<14>(c, a, ngroups, st, tag, plan);
+    case 15: return tensor_any<15>(c, a, ngroups, st, tag, plan);
+    case 16: return tensor_any<16>(c, a, ngroups, st, tag, plan);
+    case 17: return tensor_any<17>(c, a, ngroups, st, tag, plan);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_ntt_combine(const he_ctx *c, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
-                               cudaStream_t st, const char *tag, const int *dev_count, bool r8)
+                               cudaStream_t st, const char *tag, const int *dev_count, int plan)
 {
     if (ngroups < 0) return cudaSuccess;  // ngroups == 0: configure the kernels only
     NttArgs a;
@@ -714,17 +764,17 @@ cudaError_t launch_ntt_combine(const he_ctx *c, u64 *base, const NttGroup *group
         if (ngroups) prof_mark(c, st, tag, ".fwd_combine");
         return e;
     }
-    case 13: return combine_any<13>(c, a, ngroups, st, tag, r8);
-    case 14: return combine_any<14>(c, a, ngroups, st, tag, r8);
-    case 15: return combine_any<15>(c, a, ngroups, st, tag, r8);
-    case 16: return combine_any<16>(c, a, ngroups, st, tag, r8);
-    case 17: return combine_any<17>(c, a, ngroups, st, tag, r8);
+    case 13: return combine_any<13>(c, a, ngroups, st, tag, plan);
+    case 14: return combine_any<14>(c, a, ngroups, st, tag, plan);
+    case 15: return combine_any<15>(c, a, ngroups, st, tag, plan);
+    case 16: return combine_any<16>(c, a, ngroups, st, tag, plan);
+    case 17: return combine_any<17>(c, a, ngroups, st, tag, plan);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups, bool inverse,
-                        cudaStream_t st, const char *tag, const int *dev_count, bool r8)
+                        cudaStream_t st, const char *tag, const int *dev_count, int plan)
 {
     if (ngroups < 0) return cudaSuccess;  // ngroups == 0: configure the kernels only
     NttArgs a;
@@ -748,11 +798,11 @@ cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGrou
         prof_mark(c, st, tag, inverse ? ".inv" : ".fwd");
         return e;
     }
-    case 13: return two_pass_any<13>(c, a, ngroups, inverse, st, tag, r8);
-    case 14: return two_pass_any<14>(c, a, ngroups, inverse, st, tag, r8);
-    case 15: return two_pass_any<15>(c, a, ngroups, inverse, st, tag, r8);
-    case 16: return two_pass_any<16>(c, a, ngroups, inverse, st, tag, r8);
-    case 17: return two_pass_any<17>(c, a, ngroups, inverse, st, tag, r8);
+    case 13: return two_pass_any<13>(c, a, ngroups, inverse, st, tag, plan);
+    case 14: return two_pass_any<14>(c, a, ngroups, inverse, st, tag, plan);
+    case 15: return two_pass_any<15>(c, a, ngroups, inverse, st, tag, plan);
+    case 16: return two_pass_any<16>(c, a, ngroups, inverse, st, tag, plan);
+    case 17: return two_pass_any<17>(c, a, ngroups, inverse, st, tag, plan);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -771,23 +821,23 @@ int ntt_direct_stages(int logN)
 }
 
 cudaError_t launch_ntt(const he_ctx *c, u64 *base, const NttGroup *groups, int ngroups, bool inverse, cudaStream_t st,
-                       const char *tag, const int *dev_count, bool r8)
+                       const char *tag, const int *dev_count, int plan)
 {
-    return launch_ntt2(c, base, base, groups, ngroups, inverse, st, tag, dev_count, r8);
+    return launch_ntt2(c, base, base, groups, ngroups, inverse, st, tag, dev_count, plan);
 }
 
 // Set the dynamic shared-memory limit of every NTT pass this ring size uses,
-// in both plans (done once per context, before any launch or stream capture).
+// in every plan (done once per context, before any launch or stream capture).
 cudaError_t configure_ntt(const he_ctx *c)
 {
     JobRef R;
     memset(&R, 0, sizeof(R));
-    for (int r8 = 0; r8 < 2; r8++) {
-        cudaError_t e = launch_ntt2(c, nullptr, nullptr, nullptr, 0, false, nullptr, nullptr, nullptr, r8 != 0);
+    for (int plan = 0; plan < kNttPlans; plan++) {
+        cudaError_t e = launch_ntt2(c, nullptr, nullptr, nullptr, 0, false, nullptr, nullptr, nullptr, plan);
         if (e != cudaSuccess) return e;
-        e = launch_ntt_combine(c, nullptr, nullptr, 0, R, nullptr, nullptr, nullptr, r8 != 0);
+        e = launch_ntt_combine(c, nullptr, nullptr, 0, R, nullptr, nullptr, nullptr, plan);
         if (e != cudaSuccess) return e;
-        e = launch_ntt_tensor(c, nullptr, nullptr, 0, R, nullptr, nullptr, nullptr, r8 != 0);
+        e = launch_ntt_tensor(c, nullptr, nullptr, 0, R, nullptr, nullptr, nullptr, plan);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
