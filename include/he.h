@@ -489,10 +489,10 @@ int he_set_shape(he_ctx *ctx, const he_shape *shape);
 int he_get_shape(const he_ctx *ctx, he_shape *shape);
 /* Time shapes on the caller's own work and keep the fastest in ctx, by
  * coordinate descent from the context's current shape: each knob in turn
- * (group_cap, modup_chunk, pdl, ntt_r8, ip_jobs for a batch, fuse,
- * ntt_split) takes
- * every value with the others held at the best shape so far, sweep after
- * sweep until one changes nothing (at most four; no shape is timed twice);
+ * (group_cap; modup_chunk; pdl and fuse together; ntt_r8 and ntt_split
+ * together; ip_jobs for a batch) takes every value with the others held at
+ * the best shape so far, sweep after sweep until one changes nothing (at
+ * most four; no shape is timed twice);
  * count == 1 times he_mul_rescale on jobs[0] (ws of he_workspace_bytes),
  * count > 1 times he_mul_batch on the jobs (ws of he_batch_workspace_bytes),
  * `reps` calls per shape after one warm-up call, CUDA events on `stream`.

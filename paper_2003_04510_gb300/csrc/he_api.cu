@@ -736,24 +736,23 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
     };
     rc = try_shape(keep);
     const bool batch = count > 1 && inner_product_shared_fits(c);
+    const int nsplit = (c->logN == 16 || c->logN == 17) ? 3 : 1;
+    // knobs whose best values depend on each other move together: the PDL
+    // mode with the fusions, the NTT radix mask with the pass split
     for (int sweep = 0; sweep < 4 && rc == HE_OK; sweep++) {
         const he_shape before = top;
-        for (int knob = 0; knob < 7 && rc == HE_OK; knob++) {
+        for (int knob = 0; knob < 5 && rc == HE_OK; knob++) {
             const he_shape base = top;
-            const int nv = knob == 0 ? kGroupMax : knob == 1 ? 3 : knob == 2 ? 3 : knob == 3 ? 16 : knob == 4 ? 3
-                         : knob == 5 ? 4 : 3;
+            const int nv = knob == 0 ? kGroupMax : knob == 1 ? 3 : knob == 2 ? 3 * 4 : knob == 3 ? 16 * nsplit : 3;
             if (knob == 4 && !batch) continue;
-            if (knob == 6 && c->logN != 16 && c->logN != 17) continue;
             for (int v = 0; v < nv && rc == HE_OK; v++) {
                 he_shape sh = base;
                 switch (knob) {
                 case 0: sh.group_cap = v + 1; break;
                 case 1: sh.modup_chunk = v == 0 ? 4 : v == 1 ? 8 : 16; break;
-                case 2: sh.pdl = v; break;
-                case 3: sh.ntt_r8 = v; break;
-                case 4: sh.ip_jobs = v == 0 ? 1 : v == 1 ? 4 : 8; break;
-                case 5: sh.fuse = v; break;
-                default: sh.ntt_split = v; break;
+                case 2: sh.pdl = v / 4; sh.fuse = v % 4; break;
+                case 3: sh.ntt_r8 = v % 16; sh.ntt_split = v / 16; break;
+                default: sh.ip_jobs = v == 0 ? 1 : v == 1 ? 4 : 8; break;
                 }
                 rc = try_shape(sh);
             }

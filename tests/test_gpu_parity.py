@@ -714,9 +714,11 @@ def test_autotune_batch_keeps_results(g):
         best, tried = g.he_autotune(ctx, jobs, evk_t, ws, reps=2)
         assert all(t[7] > 0 for t in tried) and len(set(t[:7] for t in tried)) == len(tried)
         assert best[:7] == g.he_get_shape(ctx) and best[7] == min(t[7] for t in tried)
-        # the first sweep gives every knob every value (N = 2^15: no pass splits)
+        # the first sweep gives every knob every value (N = 2^15: no pass splits);
+        # pdl with fuse and ntt_r8 with ntt_split take every pair
         for k, vals in enumerate(((1, 2, 3, 4), (4, 8, 16), (0, 1, 2), tuple(range(16)), (1, 4, 8), (0, 1, 2, 3), (0,))):
             assert set(vals) <= {t[k] for t in tried}, k
+        assert {(p, f) for p in range(3) for f in range(4)} <= {(t[2], t[5]) for t in tried}
         for j in jobs:
             j[2].zero_()
         g.he_mul_batch(ctx, jobs, evk_t, ws)
