@@ -846,7 +846,7 @@ def run_ours(args):
             roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk,
                     "unit": "GMAC/s", "frac": ach / pk, "traffic": committed_traffic(dom),
                     "peak_source": f"measured: the conversion's own inner loop (split-28 Karatsuba multiply-"
-                                   f"accumulates, 128-bit assembly, Barrett) at width {conv_width[dom.split('.')[0]]}, "
+                                   f"accumulates, reduction from the accumulators) at width {conv_width[dom.split('.')[0]]}, "
                                    f"register-resident (he_probe_conversion_rate), same clocks, same run"}
         elif kind == "hbm":
             ach = work / avg_s / 1e9

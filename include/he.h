@@ -524,7 +524,7 @@ int he_probe_butterfly_rate(int blocks, int iters, double *bfly_per_s, void *str
  * with Sec. 5.3's delayed-modulo accumulation): per output, `width` terms
  * (1, 2, 4, 8, 12 or 16: the kernels' padded digit or special-prime count)
  * of the split-28 Karatsuba multiply-accumulate with the constant read from
- * shared memory, then one 128-bit assembly and Barrett reduction, on two
+ * shared memory, then one reduction straight from the accumulators, on two
  * coefficients per thread held in registers; `blocks` x 256 threads x 16
  * outputs x `iters`.  The ALU ceiling the ModUp and ModDown conversions are
  * compared against.  HE_EINVAL for another width or a non-positive count. */

@@ -446,7 +446,7 @@ int he_step_modup(he_ctx *c, const uint64_t *d2, int level, uint64_t *U, void *w
     HE_TRY(cudaMemcpyAsync(w + W.d2 * N, d2, (size_t)level * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
     HE_TRY(cudaMemcpyAsync(w + W.u * N, U, beta * E * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
     HE_TRY(launch_ntt(c, w, J.intt1, J.n_intt1, true, st));
-    HE_TRY(run_modup(c, single_job(c, nullptr, nullptr, nullptr, w, level), st));
+    HE_TRY(run_modup(c, single_job(c, nullptr, nullptr, nullptr, w, level), st, true));
     HE_TRY(cudaMemcpyAsync(U, w + W.u * N, beta * E * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
     return HE_OK;
 }

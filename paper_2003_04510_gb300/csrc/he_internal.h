@@ -310,7 +310,9 @@ cudaError_t launch_ntt_tensor(const he_ctx *ctx, u64 *base, const NttGroup *grou
 // runs the device table stores transposed; 0 for an unsupported logN.
 int ntt_direct_stages(int logN);
 cudaError_t run_tensor(const he_ctx *c, const JobRef &R, cudaStream_t st);
-cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st);
+// ModUp outputs lazily in [0, 3q) (the forward NTT that follows reduces them),
+// or canonical residues (the per-step entry point).
+cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st, bool canonical = false);
 // Element-wise ops: 0 add, 1 sub, 2 times plaintext, 3 plus plaintext (b half).
 cudaError_t run_elementwise(const he_ctx *c, int op, const u64 *x, const u64 *y, u64 *out, int l, cudaStream_t st);
 // Rotation's first step: d0 = kappa_g(b), d1 = 0, d2 = -kappa_g(a) into ws (level l).

@@ -68,13 +68,15 @@ k_tensor(const JobRef R, const DevPrime *__restrict__ primes, const DevLevel *__
 }
 
 // grid: x over N/2/kThreads, y over (digit, chunk of CH targets),
-// z over jobs.  Input: the scaled iNTT of d2 (y region), output U: [beta][E][N].
+// z over jobs.  Input: the scaled iNTT of d2 (y region), output U: [beta][E][N],
+// canonical with CANON, else lazily in [0, 3q) (the forward NTT that follows
+// takes inputs below 4q; see acc3k_reduce_lazy).
 // Target u of digit j (u < E - n_j) is ext limb u below the digit's own limbs,
 // u + n_j above.  Digits are padded to A limbs with zero constants (the padding
 // loads reread a real limb, whose value is multiplied by zero), so the MAC loop
 // has no predicates; the chunk's constants and prime parameters sit in shared
 // memory.
-template <int A, int CH>
+template <int A, int CH, bool CANON>
 __global__ void __launch_bounds__(kThreads)
 k_modup(const JobRef R, const DevLevel *__restrict__ lv_arr, const DevPrime *__restrict__ primes, int K, int N,
         int chunks)
@@ -129,7 +131,11 @@ k_modup(const JobRef R, const DevLevel *__restrict__ lv_arr, const DevPrime *__r
         }
         const u64 q = sq[u], mu = smu[u];
         const unsigned sh = ss[u];
-        st2(Uj + (size_t)se[u] * N + n, barrett128(acc3k_value(ax), q, mu, sh), barrett128(acc3k_value(ay), q, mu, sh));
+        if (CANON)
+            st2(Uj + (size_t)se[u] * N + n, barrett128(acc3k_value(ax), q, mu, sh),
+                barrett128(acc3k_value(ay), q, mu, sh));
+        else
+            st2(Uj + (size_t)se[u] * N + n, acc3k_reduce_lazy(ax, q, mu, sh), acc3k_reduce_lazy(ay, q, mu, sh));
     }
 }
 
@@ -353,7 +359,8 @@ k_inner_product_shared(const JobRef R, const IpGroup *__restrict__ groups, const
 // PB rows are zero-padded to KM constants, so the MAC loop has no predicates.
 constexpr int kModdownChunk = 8;
 
-template <int KM>
+// LAZY: the conversion in [0, 3q) (acc3k_reduce_lazy), else canonical.
+template <int KM, bool LAZY = false>
 __device__ __forceinline__ void conv_one(const uint32_t *x0, const uint32_t *x1, const uint32_t *z0,
                                          const uint32_t *z1, const u64 *b, u64 q, u64 mu, unsigned sh, u64 &cx,
                                          u64 &cy)
@@ -365,8 +372,13 @@ __device__ __forceinline__ void conv_one(const uint32_t *x0, const uint32_t *x1,
         mac28k(ax, x0[k], x1[k], x0[k] + x1[k], c);
         mac28k(ay, z0[k], z1[k], z0[k] + z1[k], c);
     }
-    cx = barrett128(acc3k_value(ax), q, mu, sh);
-    cy = barrett128(acc3k_value(ay), q, mu, sh);
+    if (LAZY) {
+        cx = acc3k_reduce_lazy(ax, q, mu, sh);
+        cy = acc3k_reduce_lazy(ay, q, mu, sh);
+    } else {
+        cx = barrett128(acc3k_value(ax), q, mu, sh);
+        cy = barrett128(acc3k_value(ay), q, mu, sh);
+    }
 }
 
 // MODE (TailMode): kTailPlain: z[h][i] = conv_i for i < l.  kTailRescale:
@@ -447,16 +459,17 @@ __device__ __forceinline__ void moddown_body(const JobRef &R, const u64 *__restr
         rx = add_mod(r0.x, shoup(r1.x, pv.x, pv.y, q), q);
         ry = add_mod(r0.y, shoup(r1.y, pv.x, pv.y, q), q);
     }
+    // z feeds a forward NTT, which takes inputs below 4q: the conversion is
+    // left lazily in [0, 3q) and r (or y_last, below q_{l-1} < q_i) added
+    // without a reduction
 #pragma unroll kConvUnroll
     for (int r = 0; r < cnt; r++) {
         const u64 q = sq[r];
         u64 cx, cy;
-        conv_one<KM>(x0, x1, z0, z1, sB[r], q, smu[r], ss[r], cx, cy);
+        conv_one<KM, true>(x0, x1, z0, z1, sB[r], q, smu[r], ss[r], cx, cy);
         if (FUSED || PQ) {
-            // conv_i P^-1 + r (two floors) or + y_last (one division); both are
-            // below q_{l-1} < q_i, so already residues mod q_i
-            cx = add_mod(cx, rx, q);
-            cy = add_mod(cy, ry, q);
+            cx += rx;
+            cy += ry;
         }
         st2(z + ((size_t)h * nout + i0 + r) * N + n, cx, cy);
     }
@@ -637,7 +650,7 @@ cudaError_t run_automorph(const he_ctx *c, const u64 *ct, u64 *ws, int l, u64 g,
     return cudaGetLastError();
 }
 
-template <int CH>
+template <int CH, bool CANON>
 cudaError_t launch_modup(const he_ctx *c, const JobRef &R, cudaStream_t st)
 {
     // the most targets any digit of any level up to lmax has: K + (beta - 1) alpha
@@ -647,7 +660,8 @@ cudaError_t launch_modup(const he_ctx *c, const JobRef &R, cudaStream_t st)
     g.y = beta * chunks;
     g.z = R.B;
     const int a = c->AP;
-#define HE_MODUP(AA) launch_k(c->pdl, k_modup<AA, CH>, g, dim3(kThreads), 0, st, R, c->d_levels, c->d_primes, c->K, c->N, chunks)
+#define HE_MODUP(AA) \
+    launch_k(c->pdl, k_modup<AA, CH, CANON>, g, dim3(kThreads), 0, st, R, c->d_levels, c->d_primes, c->K, c->N, chunks)
     if (a == 1) HE_MODUP(1);
     else if (a == 2) HE_MODUP(2);
     else if (a == 4) HE_MODUP(4);
@@ -658,11 +672,12 @@ cudaError_t launch_modup(const he_ctx *c, const JobRef &R, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st)
+cudaError_t run_modup(const he_ctx *c, const JobRef &R, cudaStream_t st, bool canonical)
 {
-    if (c->modup_chunk == 4) return launch_modup<4>(c, R, st);
-    if (c->modup_chunk == 16) return launch_modup<16>(c, R, st);
-    return launch_modup<8>(c, R, st);
+    if (canonical) return launch_modup<8, true>(c, R, st);
+    if (c->modup_chunk == 4) return launch_modup<4, false>(c, R, st);
+    if (c->modup_chunk == 16) return launch_modup<16, false>(c, R, st);
+    return launch_modup<8, false>(c, R, st);
 }
 
 SeedStates seed_states(const he_ctx *c, const u64 *evk, bool *seeded)

@@ -107,9 +107,10 @@ __device__ __forceinline__ u64 reduce_small(u64 x, u64 q, u64 r64)
 // The NTT's butterflies (ntt.cu; the throughput probe runs the same ones).
 // Forward (Cooley-Tukey, Algo 4) with no correction step: the modified
 // Shoup product t lies in [0, 4q), so each stage adds at most 4q to the
-// range.  From canonical inputs, values stay below (1 + 4 log N) q < 2^64 for
-// q < 2^57.9 and are reduced once, on the final store.  w = (value, Shoup
-// companion), nq = 2^64 - q.
+// range.  From inputs below 4q (the base conversions leave their outputs
+// lazily reduced), values stay below (4 + 4 log N) q < 2^64 for q < 2^57.8
+// and are reduced once, on the final store.  w = (value, Shoup companion),
+// nq = 2^64 - q.
 __device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, ulonglong2 w, u64 nq, u64 q4)
 {
     const u64 t = shoup_approx_nq(y, w.x, w.y, nq);
@@ -227,4 +228,22 @@ __device__ __forceinline__ U128 acc3k_value(const Acc3 &k)
     t.a1 = k.a1 - k.a0 - k.a2;
     t.a2 = k.a2;
     return acc3_value(t);
+}
+
+// V mod q, lazily in [0, 3q), straight from the Karatsuba accumulators
+// (V = a0 + m 2^28 + a2 2^56, m = a1 - a0 - a2 >= 0, V < 2^(b+61)), without
+// assembling the 128-bit value.  With s = b - 2 (28 <= s <= 56) and
+// mu = floor(2^(64+s) / q) as for barrett128: the shifted value
+// u' = a2 2^(56-s) + floor(m / 2^(s-28)) + floor(a0 / 2^s) is floor(V / 2^s)
+// or one less (two dropped fractions, each below one), so
+// floor(u' mu / 2^64) is floor(V / q) minus 0, 1 or 2 (Barrett's own estimate
+// is the true quotient or one less), and V minus that multiple of q, formed
+// modulo 2^64 from V's low word, lies in [0, 3q).  Every term fits a word:
+// a2 2^(56-s) <= V / 2^s < 2^63.
+__device__ __forceinline__ u64 acc3k_reduce_lazy(const Acc3 &k, u64 q, u64 mu, unsigned s)
+{
+    const u64 m = k.a1 - k.a0 - k.a2;
+    const u64 u = (k.a2 << (56 - s)) + (m >> (s - 28)) + (k.a0 >> s);
+    const u64 vlo = k.a0 + (m << 28) + (k.a2 << 56);
+    return vlo - __umul64hi(u, mu) * q;
 }

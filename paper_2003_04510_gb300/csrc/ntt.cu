@@ -457,10 +457,10 @@ k_ntt_pass(const NttArgs P)
             const int ci = (int)(G.ci[i] & 0x7fffffffu), hh = (int)(G.ci[i] >> 31);
             const ulonglong2 pv = P.pinv[ci], qv = P.levels[it.level].qinv_last[ci];
             // above any forward-NTT output (values grow by < 4q per stage from
-            // canonical inputs): d + KS P^-1 (lazy, < 2q) + Cz - z stays in
-            // (0, (4 + 4 log N) q), below 2^64, and one Shoup product by
+            // inputs below 4q): d + KS P^-1 (lazy, < 4q) + Cz - z stays in
+            // (0, (9 + 4 log N) q), below 2^64, and one Shoup product by
             // q_{l-1}^-1 reduces it
-            const u64 Cz = pr.q * (u64)(1 + 4 * P.logN);
+            const u64 Cz = pr.q * (u64)(4 + 4 * P.logN);
             u64 *o = it.out + ((((size_t)hh * (it.level - 1) + ci)) << P.logN) + g2;
             const u64 *dd = P.dst + ((size_t)G.cd[i] << P.logN) + g2, *kk = P.dst + ((size_t)G.cks[i] << P.logN) + g2;
             const u64 *sp = sm + padi(2 * threadIdx.x);
@@ -496,7 +496,7 @@ k_ntt_pass(const NttArgs P)
         for (int k = 0; k < TE / 2 / NT; k++) {
             u64 x = sp[0], y = sp[1];
             if (LAST) {
-                if (!INV) {  // x < (1 + 4 log N) q
+                if (!INV) {  // x < (4 + 4 log N) q
                     if (small_red) {
                         x = reduce_small(x, pr.q, pr.r64);
                         y = reduce_small(y, pr.q, pr.r64);

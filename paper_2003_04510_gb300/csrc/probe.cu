@@ -14,8 +14,9 @@
 //  * base conversion: the inner loop of k_modup / k_moddown_conv (Sec. 7's
 //    mod up / mod down as fast base conversion, with the delayed-modulo
 //    accumulation of Sec. 5.3): per output, A terms of mac28k on two
-//    coefficients with the constant read from shared memory, then
-//    acc3k_value and barrett128 per coefficient.  A thread keeps its A split
+//    coefficients with the constant read from shared memory, then the lazy
+//    reduction straight from the accumulators (acc3k_reduce_lazy) per
+//    coefficient.  A thread keeps its A split
 //    inputs in registers, as the kernels do, and walks a table of constant
 //    rows; the outputs are folded into a checksum instead of stored.
 #include "he_internal.h"
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(256) k_probe_conv(u64 *out, const u64 *rows, u
                 mac28k(ax, x0[i], x1[i], x0[i] + x1[i], c);
                 mac28k(ay, z0[i], z1[i], z0[i] + z1[i], c);
             }
-            acc ^= barrett128(acc3k_value(ax), q, mu, sh) + barrett128(acc3k_value(ay), q, mu, sh);
+            acc ^= acc3k_reduce_lazy(ax, q, mu, sh) + acc3k_reduce_lazy(ay, q, mu, sh);
         }
     }
     out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
