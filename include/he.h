@@ -492,7 +492,8 @@ int he_get_shape(const he_ctx *ctx, he_shape *shape);
  * (group_cap; modup_chunk; pdl and fuse together; ntt_r8 and ntt_split
  * together; ip_jobs for a batch) takes every value with the others held at
  * the best shape so far, sweep after sweep until one changes nothing (at
- * most four; no shape is timed twice);
+ * most four); then every (pdl, fuse, ntt_split) with the radix masks {best,
+ * 0, 15}, and descent sweeps again from the best (no shape is timed twice);
  * count == 1 times he_mul_rescale on jobs[0] (ws of he_workspace_bytes),
  * count > 1 times he_mul_batch on the jobs (ws of he_batch_workspace_bytes),
  * `reps` calls per shape after one warm-up call, CUDA events on `stream`.

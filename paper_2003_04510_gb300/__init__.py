@@ -430,11 +430,11 @@ def he_autotune(ctx, jobs, evk, ws, reps: int = 3, stream=None):
     for i, (a, b, o, lv) in enumerate(jobs):
         arr[i] = he_job(_dev_ptr(a), _dev_ptr(b), _dev_ptr(o), int(lv))
     best = he_shape()
-    tried = (he_shape * 256)()
+    tried = (he_shape * 1024)()
     n = ctypes.c_int()
     _check(lib().he_autotune(ctx.ptr, ctypes.cast(arr, ctypes.c_void_p), len(jobs), _dev_ptr(evk), _dev_ptr(ws),
                              ws.numel() * 8, reps, _stream_ptr(stream), ctypes.byref(best),
-                             ctypes.cast(tried, ctypes.c_void_p), 256, ctypes.byref(n)), "he_autotune")
+                             ctypes.cast(tried, ctypes.c_void_p), 1024, ctypes.byref(n)), "he_autotune")
     return (_shape_tuple(best) + (best.ms,), [_shape_tuple(t) + (t.ms,) for t in tried[: n.value]])
 
 

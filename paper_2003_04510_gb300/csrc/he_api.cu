@@ -759,6 +759,47 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
         }
         if (same(before, top)) break;
     }
+    // the knobs whose best values interact most, exhaustively: every PDL
+    // mode, fusion set and pass split with the radix masks {best, none, all},
+    // then descent sweeps again from the best
+    for (int pass = 0; pass < 2 && rc == HE_OK; pass++) {
+        if (pass == 0) {
+            const he_shape base = top;
+            const int masks[3] = {base.ntt_r8, 0, 15};
+            for (int m = 0; m < 3 && rc == HE_OK; m++)
+                for (int pdl = 0; pdl < 3 && rc == HE_OK; pdl++)
+                    for (int fz = 0; fz < 4 && rc == HE_OK; fz++)
+                        for (int sp = 0; sp < nsplit && rc == HE_OK; sp++) {
+                            he_shape sh = base;
+                            sh.ntt_r8 = masks[m];
+                            sh.pdl = pdl;
+                            sh.fuse = fz;
+                            sh.ntt_split = sp;
+                            rc = try_shape(sh);
+                        }
+            continue;
+        }
+        for (int sweep = 0; sweep < 4 && rc == HE_OK; sweep++) {
+            const he_shape before = top;
+            for (int knob = 0; knob < 5 && rc == HE_OK; knob++) {
+                const he_shape base = top;
+                const int nv = knob == 0 ? kGroupMax : knob == 1 ? 3 : knob == 2 ? 3 * 4 : knob == 3 ? 16 * nsplit : 3;
+                if (knob == 4 && !batch) continue;
+                for (int v = 0; v < nv && rc == HE_OK; v++) {
+                    he_shape sh = base;
+                    switch (knob) {
+                    case 0: sh.group_cap = v + 1; break;
+                    case 1: sh.modup_chunk = v == 0 ? 4 : v == 1 ? 8 : 16; break;
+                    case 2: sh.pdl = v / 4; sh.fuse = v % 4; break;
+                    case 3: sh.ntt_r8 = v % 16; sh.ntt_split = v / 16; break;
+                    default: sh.ip_jobs = v == 0 ? 1 : v == 1 ? 4 : 8; break;
+                    }
+                    rc = try_shape(sh);
+                }
+            }
+            if (same(before, top)) break;
+        }
+    }
     c->prof = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
