@@ -125,12 +125,17 @@ int he_decrypt(he_ctx *ctx, const int64_t *sk, const uint64_t *ct, int level, do
 
 /* ---- device side: caller-owned device memory, caller's stream ------------ */
 
-/* Copy an evaluation key from host to device memory (evk_dev holds
- * dnum*2*(K+L)*N words). */
+/* Copy an evaluation key (Fig. 2, region 2: the key switch's evk, as
+ * he_keygen writes it) from host to device memory; evk_dev holds
+ * dnum*2*(K+L)*N words.  Asynchronous on `stream`.  HE_EINVAL for a NULL
+ * pointer or a host-only context, HE_ECUDA if the copy cannot be queued. */
 int he_evk_upload(he_ctx *ctx, const uint64_t *evk_host, uint64_t *evk_dev, void *stream);
 
 /* Bytes of device workspace one he_mul / he_rescale / he_mul_rescale call at
- * `level` needs (the largest of the three). */
+ * `level` needs (the largest of the three): the intermediates of Fig. 2 in
+ * RNS form (region 1's d0, d1, d2; region 2's ModUp limbs of every digit,
+ * key-switch sums and special limbs' iNTT) and the rescale's (Sec. 3.1).  0
+ * for a level outside 1..L. */
 size_t he_workspace_bytes(const he_ctx *ctx, int level);
 
 /* HE Mul (Fig. 2, full-RNS form): out = (d0 + ModDown(KS_b), d1 + ModDown(KS_a))
@@ -247,7 +252,10 @@ typedef struct {
     int level;           /* 2 .. L */
 } he_job;
 
-/* Workspace bytes for a batch of `count` jobs at the given levels. */
+/* Batches have no counterpart in the paper, which times one HE Mul at a
+ * time; each job is the HE Mul of Fig. 2 followed by Sec. 3.1's rescale.
+ * Workspace bytes for a batch of `count` jobs at the given levels (0 for a
+ * level outside 2..L). */
 size_t he_batch_workspace_bytes(const he_ctx *ctx, int count, const int *levels);
 /* Run B independent HE Mul + rescale jobs (uneven levels allowed) as one
  * batch: each stage is one launch over every job's work (grid.z = job), and
@@ -261,7 +269,8 @@ size_t he_batch_workspace_bytes(const he_ctx *ctx, int count, const int *levels)
 int he_mul_batch(he_ctx *ctx, int count, const he_job *jobs, const uint64_t *evk_dev, void *ws,
                  size_t ws_bytes, void *stream);
 
-/* The batched path captured once in a CUDA graph for up to max_jobs jobs:
+/* The batched path (each job Fig. 2 + Sec. 3.1's rescale; no counterpart in
+ * the paper) captured once in a CUDA graph for up to max_jobs jobs:
  * every launch is sized for max_jobs jobs at level L (the NTT launches for
  * the most limb groups they can form at the limb-group cap in effect at
  * creation; launches group at that cap or the context's current one,
@@ -275,8 +284,8 @@ int he_mul_batch(he_ctx *ctx, int count, const he_job *jobs, const uint64_t *evk
  * host only for the launch before the previous one (which read the table it
  * rewrites), so the host prepares a batch while the previous one runs.
  * Launches of one graph share its workspace: issue them on one stream (or
- * order their streams), as overlapping launches would race on it.  Results are bit-identical to
- * he_mul_rescale per job. */
+ * order their streams), as overlapping launches would race on it.  Results
+ * are bit-identical to he_mul_rescale per job. */
 typedef struct he_batch_graph he_batch_graph;
 size_t he_batch_graph_workspace_bytes(const he_ctx *ctx, int max_jobs);
 int he_batch_graph_create(he_ctx *ctx, int max_jobs, const uint64_t *evk_dev, void *ws, size_t ws_bytes,
@@ -312,8 +321,9 @@ typedef struct {
 
 typedef struct he_server he_server;
 
-/* Create a server over nctx rings (contexts) with their device-resident
- * evaluation keys.  It allocates one device arena of hbm_budget bytes for
+/* Serving has no counterpart in the paper; every request is the HE Mul of
+ * Fig. 2 followed by Sec. 3.1's rescale.  Create a server over nctx rings
+ * (contexts) with their device-resident evaluation keys.  It allocates one device arena of hbm_budget bytes for
  * request workspaces and `streams` CUDA streams, and starts a scheduler
  * thread.  The scheduler admits queued requests in arrival order as arena
  * space and streams free up, groups admitted requests of one ring into a
