@@ -262,10 +262,10 @@ def kernel_width(n: int) -> int:
 
 
 def shape_dict(t) -> dict:
-    """A launch shape (group_cap, modup_chunk, pdl, ntt_r8, ip_jobs, fuse, ntt_split[, ms]) as a dict."""
-    d = dict(zip(("group_cap", "modup_chunk", "pdl", "ntt_r8", "ip_jobs", "fuse", "ntt_split"), t[:7]))
-    if len(t) > 7:
-        d["ms"] = t[7]
+    """A launch shape (group_cap, modup_chunk, pdl, ntt_r8, ip_jobs, fuse, ntt_split, ntt_small[, ms]) as a dict."""
+    d = dict(zip(("group_cap", "modup_chunk", "pdl", "ntt_r8", "ip_jobs", "fuse", "ntt_split", "ntt_small"), t[:8]))
+    if len(t) > 8:
+        d["ms"] = t[8]
     return d
 
 
@@ -362,7 +362,7 @@ def run_batched(g, ctx, evk_t, dev, stream, wsz, count=64, reps=20):
         ip_bytes = sum(kernel_work("inner_product", ctx.prm, lv)[1] for lv in levels)
         res["inner_product_gbs"] = ip_bytes / (res["kernels_us"]["inner_product"] * 1e-6) / 1e9
     g.he_set_shape(ctx, *shape_before)
-    res["autotune"] = dict(shape_dict(best), ms_per_batch=best[7], tried=[shape_dict(t) for t in tried])
+    res["autotune"] = dict(shape_dict(best), ms_per_batch=best[8], tried=[shape_dict(t) for t in tried])
     res["config"] = {"jobs": count, "N": N, "levels": "uniform 4..24 (seed 1604)", "mean_level": float(np.mean(levels)),
                      "operands": "uniform residues"}
     return res
@@ -532,7 +532,7 @@ def run_ours(args):
     # (or fixed by --shape, e.g. for a profiler run)
     if args.shape:
         given = [int(v) for v in args.shape.split(",")]
-        shape = (given + [0, 8, 3, 0][len(given) - 3:])[:7]
+        shape = (given + [0, 8, 3, 0, 0][len(given) - 3:])[:8]
         g.he_set_shape(ctx, *shape)
         tune_best, tune_tried = tuple(shape) + (0.0,), []
     else:
@@ -949,7 +949,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-rotate", action="store_true")
     ap.add_argument("--no-n17", action="store_true", help="skip the N=2^17 single HE Mul section")
-    ap.add_argument("--shape", default="", help="fixed launch shape CAP,CHUNK,PDL[,R8[,IPJOBS[,FUSE[,SPLIT]]]] "
+    ap.add_argument("--shape", default="", help="fixed launch shape CAP,CHUNK,PDL[,R8[,IPJOBS[,FUSE[,SPLIT[,SMALL]]]]] "
                                                  "instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

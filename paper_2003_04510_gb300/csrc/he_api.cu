@@ -117,7 +117,9 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
 {
     // key switching: iNTT(d2) (times N^-1 Qhat^-1), ModUp, NTT, inner product
     const int *cnt = S.counts;
-    auto r8 = [c](int site) { return ((c->ntt_r8 >> site) & 1) | (c->ntt_split << 1); };  // NTT plan of a site
+    auto r8 = [c](int site) {  // NTT plan of a site
+        return ((c->ntt_r8 >> site) & 1) | (c->ntt_split << 1) | (((c->ntt_small >> site) & 1) << 3);
+    };
     capture_tag = kTagNtt0 + 0;
     if (tensor_fused)
         HE_TRY(launch_ntt_tensor(c, ntt_base, S.intt1, S.n_intt1, R, st, "intt_d2", cnt ? cnt + 0 : nullptr, r8(0)));
@@ -418,7 +420,7 @@ int he_step_ntt(he_ctx *c, uint64_t *data, const int *prime_idx, int count, int 
     int rc = with_jobs(groups, st, &dj);
     if (rc) return rc;
     cudaError_t e = launch_ntt(c, (u64 *)data, dj, (int)groups.size(), inverse != 0, st, nullptr, nullptr,
-                               (c->ntt_r8 & 1) | (c->ntt_split << 1));
+                               (c->ntt_r8 & 1) | (c->ntt_split << 1) | ((c->ntt_small & 1) << 3));
     cudaFreeAsync(dj, st);
     return e == cudaSuccess ? HE_OK : HE_ECUDA;
 }
@@ -656,6 +658,7 @@ int he_set_shape(he_ctx *c, const he_shape *sh)
     if (sh->ip_jobs != 1 && sh->ip_jobs != 4 && sh->ip_jobs != 8) return HE_EINVAL;
     if (sh->fuse < 0 || sh->fuse > 3) return HE_EINVAL;
     if (sh->ntt_split < 0 || sh->ntt_split > 2) return HE_EINVAL;
+    if (sh->ntt_small < 0 || sh->ntt_small > 15) return HE_EINVAL;
     c->group_cap = sh->group_cap;
     c->modup_chunk = sh->modup_chunk;
     c->pdl = sh->pdl;
@@ -663,6 +666,7 @@ int he_set_shape(he_ctx *c, const he_shape *sh)
     c->ip_jobs = sh->ip_jobs;
     c->fuse = sh->fuse;
     c->ntt_split = sh->ntt_split;
+    c->ntt_small = sh->ntt_small;
     if (c->device) c->jobs = c->jobs_cap[c->group_cap - 1];
     return HE_OK;
 }
@@ -677,6 +681,7 @@ int he_get_shape(const he_ctx *c, he_shape *sh)
     sh->ip_jobs = c->ip_jobs;
     sh->fuse = c->fuse;
     sh->ntt_split = c->ntt_split;
+    sh->ntt_small = c->ntt_small;
     sh->ms = 0;
     return HE_OK;
 }
@@ -726,7 +731,8 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
     std::vector<he_shape> seen;
     auto same = [](const he_shape &a, const he_shape &b) {
         return a.group_cap == b.group_cap && a.modup_chunk == b.modup_chunk && a.pdl == b.pdl &&
-               a.ntt_r8 == b.ntt_r8 && a.ip_jobs == b.ip_jobs && a.fuse == b.fuse && a.ntt_split == b.ntt_split;
+               a.ntt_r8 == b.ntt_r8 && a.ip_jobs == b.ip_jobs && a.fuse == b.fuse && a.ntt_split == b.ntt_split &&
+               a.ntt_small == b.ntt_small;
     };
     auto try_shape = [&](he_shape sh) -> int {
         for (const he_shape &t : seen)
@@ -741,10 +747,12 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
     // mode with the fusions, the NTT radix mask with the pass split
     for (int sweep = 0; sweep < 4 && rc == HE_OK; sweep++) {
         const he_shape before = top;
-        for (int knob = 0; knob < 5 && rc == HE_OK; knob++) {
+        for (int knob = 0; knob < 6 && rc == HE_OK; knob++) {
             const he_shape base = top;
-            const int nv = knob == 0 ? kGroupMax : knob == 1 ? 3 : knob == 2 ? 3 * 4 : knob == 3 ? 16 * nsplit : 3;
+            const int nv = knob == 0 ? kGroupMax : knob == 1 ? 3 : knob == 2 ? 3 * 4 : knob == 3 ? 16 * nsplit
+                         : knob == 4 ? 3 : 16;
             if (knob == 4 && !batch) continue;
+            if (knob == 5 && nsplit == 1) continue;  // 1024-element tiles: 2^16 and 2^17
             for (int v = 0; v < nv && rc == HE_OK; v++) {
                 he_shape sh = base;
                 switch (knob) {
@@ -752,7 +760,8 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
                 case 1: sh.modup_chunk = v == 0 ? 4 : v == 1 ? 8 : 16; break;
                 case 2: sh.pdl = v / 4; sh.fuse = v % 4; break;
                 case 3: sh.ntt_r8 = v % 16; sh.ntt_split = v / 16; break;
-                default: sh.ip_jobs = v == 0 ? 1 : v == 1 ? 4 : 8; break;
+                case 4: sh.ip_jobs = v == 0 ? 1 : v == 1 ? 4 : 8; break;
+                default: sh.ntt_small = v; break;
                 }
                 rc = try_shape(sh);
             }
@@ -781,10 +790,12 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
         }
         for (int sweep = 0; sweep < 4 && rc == HE_OK; sweep++) {
             const he_shape before = top;
-            for (int knob = 0; knob < 5 && rc == HE_OK; knob++) {
+            for (int knob = 0; knob < 6 && rc == HE_OK; knob++) {
                 const he_shape base = top;
-                const int nv = knob == 0 ? kGroupMax : knob == 1 ? 3 : knob == 2 ? 3 * 4 : knob == 3 ? 16 * nsplit : 3;
+                const int nv = knob == 0 ? kGroupMax : knob == 1 ? 3 : knob == 2 ? 3 * 4 : knob == 3 ? 16 * nsplit
+                             : knob == 4 ? 3 : 16;
                 if (knob == 4 && !batch) continue;
+                if (knob == 5 && nsplit == 1) continue;
                 for (int v = 0; v < nv && rc == HE_OK; v++) {
                     he_shape sh = base;
                     switch (knob) {
@@ -792,7 +803,8 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
                     case 1: sh.modup_chunk = v == 0 ? 4 : v == 1 ? 8 : 16; break;
                     case 2: sh.pdl = v / 4; sh.fuse = v % 4; break;
                     case 3: sh.ntt_r8 = v % 16; sh.ntt_split = v / 16; break;
-                    default: sh.ip_jobs = v == 0 ? 1 : v == 1 ? 4 : 8; break;
+                    case 4: sh.ip_jobs = v == 0 ? 1 : v == 1 ? 4 : 8; break;
+                    default: sh.ntt_small = v; break;
                     }
                     rc = try_shape(sh);
                 }

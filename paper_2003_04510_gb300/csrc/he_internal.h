@@ -142,6 +142,7 @@ struct he_ctx {
                                          // 0 off, 1 on, 2 on with early dependent launch (griddep_wait)
     int ntt_r8 = 0;                      // bit s: the radix-8 NTT plan at pipeline NTT site s (0..3)
     int ntt_split = 0;                   // NTT pass split of every site (0 default, 1, 2: see launch_ntt)
+    int ntt_small = 0;                   // bit s: 1024-element NTT tiles at pipeline NTT site s (2^16, 2^17)
     int ip_jobs = he::kIpJobsMax;        // batches: jobs sharing one CTA's key words in the inner product (1: none)
     int fuse = 3;                        // bit 0: the tensor product inside the first inverse NTT pass of d2;
                                          // bit 1: the q limbs' key-switch sums beside the ModDown conversion
@@ -284,9 +285,10 @@ __device__ __forceinline__ ulonglong2 ld2_hint(const void *p, u64 pol)
 #endif
 
 // plan: bit 0 the radix-8 plan (256 threads per tile) instead of the
-// radix-16 one; bits 1.. the pass split (0 default, 1 one stage from the
-// strided pass to the contiguous one, 2 the other way; 2^16 and 2^17 only).
-// Every plan gives the same words.
+// radix-16 one; bits 1-2 the pass split (0 default, 1 one stage from the
+// strided pass to the contiguous one, 2 the other way; 2^16 and 2^17 only);
+// bit 3 tiles of 1024 elements instead of 2048 (2^16 and 2^17 only).  Every
+// plan gives the same words.
 cudaError_t launch_ntt(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, bool inverse,
                        cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr, int plan = 0);
 cudaError_t launch_ntt2(const he_ctx *ctx, const u64 *src, u64 *dst, const NttGroup *groups, int ngroups,

@@ -304,7 +304,9 @@ __device__ __forceinline__ void tensor_tile(const NttArgs &P, const NttGroup &G,
 // spills under a bound).
 __host__ __device__ constexpr int ntt_min_blocks(int nt, int logm, bool inv)
 {
-    return logm >= 12 ? 0 : nt >= 256 ? (inv ? 4 : 5) : inv ? 0 : 6;
+    // 64-thread tiles (radix-16 rounds on 1024 elements): twelve forward (85
+    // registers), inverse unbounded
+    return logm >= 12 ? 0 : nt >= 256 ? (inv ? 4 : 5) : nt <= 64 ? (inv ? 0 : 12) : inv ? 0 : 6;
 }
 
 // FUSE: kFuseNone; kFuseCombine, the final combine in the store loop of the
@@ -595,15 +597,20 @@ static_assert(planv_fits<16, 1, false>() && planv_fits<16, 1, true>() && planv_f
                   planv_fits<17, 2, false>() && planv_fits<17, 2, true>(),
               "split plans: stages, rounds and the transposed region");
 
-// plan id: bit 0 the radix-8 form, bits 1.. the split (0, 1, 2)
-constexpr int kNttPlans = 6;
+// plan id: bit 0 the radix-8 form, bits 1-2 the split (0, 1, 2), bit 3
+// 1024-element tiles (twice the CTAs, each half the work, for launches with
+// few limbs; every round's index map at that tile size was checked on the
+// CPU as for 2048)
+constexpr int kNttPlans = 16;
+// 1024-element tiles of a plan: a strided pass of 2^10 stages would be one
+// column wide, so that plan keeps 2048
+template <class P> constexpr int small_te() { return P::S1 >= 10 ? 2048 : 1024; }
 
 // Two-pass transform: the strided pass covers the first S1 stages (forward
 // order), the contiguous pass the last S2.
-template <int S1, int A1, int B1, int C1, int S2, int A2, int B2, int C2>
+template <int S1, int A1, int B1, int C1, int S2, int A2, int B2, int C2, int TE>
 cudaError_t two_pass(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag)
 {
-    constexpr int TE = 2048;
     a.tiles = (1 << (S1 + S2)) / TE;
     cudaError_t e;
     const char *t1 = inverse ? ".inv_pass1" : ".fwd_pass1";
@@ -631,16 +638,28 @@ cudaError_t two_pass(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cuda
     return e;
 }
 
-template <int LOGN, class P = Plan<LOGN>>
+template <int LOGN, class P = Plan<LOGN>, int TE = 2048>
 cudaError_t two_pass_plan(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag)
 {
-    return two_pass<P::S1, P::A1, P::B1, P::C1, P::S2, P::A2, P::B2, P::C2>(c, a, ngroups, inverse, st, tag);
+    return two_pass<P::S1, P::A1, P::B1, P::C1, P::S2, P::A2, P::B2, P::C2, TE>(c, a, ngroups, inverse, st, tag);
 }
 
 template <int LOGN>
 cudaError_t two_pass_any(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag, int plan)
 {
-    switch (plan) {
+    // bit 3: 1024-element tiles (2^16 and 2^17; a pass over 2^10 stages keeps 2048)
+    constexpr bool SMALL_OK = LOGN == 16 || LOGN == 17;
+    if (SMALL_OK && (plan & 8)) {
+        switch (plan & 7) {
+        case 1: return two_pass_plan<LOGN, Plan8<LOGN>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, inverse, st, tag);
+        case 2: return two_pass_plan<LOGN, PlanV<LOGN, 1, false>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, inverse, st, tag);
+        case 3: return two_pass_plan<LOGN, PlanV<LOGN, 1, true>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, inverse, st, tag);
+        case 4: return two_pass_plan<LOGN, PlanV<LOGN, 2, false>, small_te<PlanV<LOGN, 2, false>>()>(c, a, ngroups, inverse, st, tag);
+        case 5: return two_pass_plan<LOGN, PlanV<LOGN, 2, true>, small_te<PlanV<LOGN, 2, true>>()>(c, a, ngroups, inverse, st, tag);
+        default: return two_pass_plan<LOGN, Plan<LOGN>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, inverse, st, tag);
+        }
+    }
+    switch (plan & 7) {
     case 1: return two_pass_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, inverse, st, tag);
     case 2: return two_pass_plan<LOGN, PlanV<LOGN, 1, false>>(c, a, ngroups, inverse, st, tag);
     case 3: return two_pass_plan<LOGN, PlanV<LOGN, 1, true>>(c, a, ngroups, inverse, st, tag);
@@ -651,10 +670,9 @@ cudaError_t two_pass_any(const he_ctx *c, NttArgs a, int ngroups, bool inverse, 
 }
 
 // Forward transform whose last pass also applies the final combine.
-template <int LOGN, class P>
+template <int LOGN, class P, int TE = 2048>
 cudaError_t combine_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag)
 {
-    constexpr int TE = 2048;
     a.tiles = (1 << LOGN) / TE;
     if (ngroups == 0) return run_pass<P::S2, P::A2, P::B2, P::C2, false, false, false, true, TE, kFuseCombine>(a, 0, st);
     cudaError_t e = run_pass<P::S1, P::A1, P::B1, P::C1, true, false, true, false, TE>(a, ngroups, st);
@@ -668,7 +686,19 @@ cudaError_t combine_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t s
 template <int LOGN>
 cudaError_t combine_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, int plan)
 {
-    switch (plan) {
+    // bit 3: 1024-element tiles (2^16 and 2^17; a pass over 2^10 stages keeps 2048)
+    constexpr bool SMALL_OK = LOGN == 16 || LOGN == 17;
+    if (SMALL_OK && (plan & 8)) {
+        switch (plan & 7) {
+        case 1: return combine_plan<LOGN, Plan8<LOGN>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, st, tag);
+        case 2: return combine_plan<LOGN, PlanV<LOGN, 1, false>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, st, tag);
+        case 3: return combine_plan<LOGN, PlanV<LOGN, 1, true>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, st, tag);
+        case 4: return combine_plan<LOGN, PlanV<LOGN, 2, false>, small_te<PlanV<LOGN, 2, false>>()>(c, a, ngroups, st, tag);
+        case 5: return combine_plan<LOGN, PlanV<LOGN, 2, true>, small_te<PlanV<LOGN, 2, true>>()>(c, a, ngroups, st, tag);
+        default: return combine_plan<LOGN, Plan<LOGN>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, st, tag);
+        }
+    }
+    switch (plan & 7) {
     case 1: return combine_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, st, tag);
     case 2: return combine_plan<LOGN, PlanV<LOGN, 1, false>>(c, a, ngroups, st, tag);
     case 3: return combine_plan<LOGN, PlanV<LOGN, 1, true>>(c, a, ngroups, st, tag);
@@ -679,10 +709,9 @@ cudaError_t combine_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st
 }
 
 // Inverse transform whose first pass forms its input with the tensor product.
-template <int LOGN, class P>
+template <int LOGN, class P, int TE = 2048>
 cudaError_t tensor_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag)
 {
-    constexpr int TE = 2048;
     a.tiles = (1 << LOGN) / TE;
     if (ngroups == 0) return run_pass<P::S2, P::A2, P::B2, P::C2, false, true, true, false, TE, kFuseTensor>(a, 0, st);
     cudaError_t e = run_pass<P::S2, P::A2, P::B2, P::C2, false, true, true, false, TE, kFuseTensor>(a, ngroups, st);
@@ -696,7 +725,19 @@ cudaError_t tensor_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st
 template <int LOGN>
 cudaError_t tensor_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, int plan)
 {
-    switch (plan) {
+    // bit 3: 1024-element tiles (2^16 and 2^17; a pass over 2^10 stages keeps 2048)
+    constexpr bool SMALL_OK = LOGN == 16 || LOGN == 17;
+    if (SMALL_OK && (plan & 8)) {
+        switch (plan & 7) {
+        case 1: return tensor_plan<LOGN, Plan8<LOGN>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, st, tag);
+        case 2: return tensor_plan<LOGN, PlanV<LOGN, 1, false>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, st, tag);
+        case 3: return tensor_plan<LOGN, PlanV<LOGN, 1, true>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, st, tag);
+        case 4: return tensor_plan<LOGN, PlanV<LOGN, 2, false>, small_te<PlanV<LOGN, 2, false>>()>(c, a, ngroups, st, tag);
+        case 5: return tensor_plan<LOGN, PlanV<LOGN, 2, true>, small_te<PlanV<LOGN, 2, true>>()>(c, a, ngroups, st, tag);
+        default: return tensor_plan<LOGN, Plan<LOGN>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, st, tag);
+        }
+    }
+    switch (plan & 7) {
     case 1: return tensor_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, st, tag);
     case 2: return tensor_plan<LOGN, PlanV<LOGN, 1, false>>(c, a, ngroups, st, tag);
     case 3: return tensor_plan<LOGN, PlanV<LOGN, 1, true>>(c, a, ngroups, st, tag);

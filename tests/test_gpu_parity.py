@@ -645,12 +645,14 @@ def test_every_shape_is_bit_identical_n16(g):
         g.he_set_shape(ctx, 4, 8, 1)
 
 
-@pytest.mark.parametrize("name,level,split", [("n16", 24, 1), ("n16", 9, 2), ("n17", 44, 1), ("n17", 13, 2)])
+@pytest.mark.parametrize("name,level,split", [("n16", 24, 0), ("n16", 24, 1), ("n16", 9, 2), ("n17", 44, 1),
+                                              ("n17", 13, 2)])
 def test_ntt_pass_splits_bit_identical(g, name, level, split):
     """Every NTT of the path on a pass split (one stage moved between the
-    strided and the contiguous pass), in the radix-16 and the radix-8 form:
-    the same words as the oracle.  The raw transforms too (he_step_ntt takes
-    the context's split and the radix bit of site 0)."""
+    strided and the contiguous pass), in the radix-16 and the radix-8 form,
+    on 2048- and 1024-element tiles (all sites, or sites 1 and 3): the same
+    words as the oracle.  The raw transforms too (he_step_ntt takes the
+    context's split and site 0's radix and tile bits)."""
     import torch
     op = oracle.preset(name)
     ctx = ctx_for(g, name)
@@ -660,23 +662,24 @@ def test_ntt_pass_splits_bit_identical(g, name, level, split):
     want = oracle.rescale(op, oracle.he_mul(op, c1, c2, evk, level), level)
     try:
         for r8 in (0, 15, 5):
-            g.he_set_shape(ctx, 1, 8, 1, r8, 8, 3, split)
-            assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want), (split, r8)
+            for small in (0, 15, 10):
+                g.he_set_shape(ctx, 1, 8, 1, r8, 8, 3, split, small)
+                assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want), (split, r8, small)
         E = op.K + op.L
         idx = [0, op.K, E - 1]
         mods = [op.ext[e] for e in idx]
         psis = [int(op.psi_p[e]) if e < op.K else int(op.psi_q[e - op.K]) for e in idx]
         a = rand_polys(mods, op.N, 960 + split)
-        for r8 in (0, 1):
-            g.he_set_shape(ctx, 1, 8, 1, r8, 8, 3, split)
+        for r8, small in ((0, 0), (1, 0), (0, 1), (1, 1)):
+            g.he_set_shape(ctx, 1, 8, 1, r8, 8, 3, split, small)
             t = dev(g, a)
             g.he_step_ntt(ctx, t, idx, inverse=False)
             torch.cuda.synchronize()
             assert np.array_equal(host(g, t), np.stack([oracle.ntt(a[i], mods[i], psis[i], op.logN)
-                                                        for i in range(len(idx))])), (split, r8)
+                                                        for i in range(len(idx))])), (split, r8, small)
             g.he_step_ntt(ctx, t, idx, inverse=True)
             torch.cuda.synchronize()
-            assert np.array_equal(host(g, t), a), (split, r8)
+            assert np.array_equal(host(g, t), a), (split, r8, small)
     finally:
         g.he_set_shape(ctx, 4, 8, 1)
 
@@ -712,11 +715,12 @@ def test_autotune_batch_keeps_results(g):
     ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
     try:
         best, tried = g.he_autotune(ctx, jobs, evk_t, ws, reps=2)
-        assert all(t[7] > 0 for t in tried) and len(set(t[:7] for t in tried)) == len(tried)
-        assert best[:7] == g.he_get_shape(ctx) and best[7] == min(t[7] for t in tried)
-        # the first sweep gives every knob every value (N = 2^15: no pass splits);
-        # pdl with fuse and ntt_r8 with ntt_split take every pair
-        for k, vals in enumerate(((1, 2, 3, 4), (4, 8, 16), (0, 1, 2), tuple(range(16)), (1, 4, 8), (0, 1, 2, 3), (0,))):
+        assert all(t[8] > 0 for t in tried) and len(set(t[:8] for t in tried)) == len(tried)
+        assert best[:8] == g.he_get_shape(ctx) and best[8] == min(t[8] for t in tried)
+        # the first sweep gives every knob every value (N = 2^15: no pass splits
+        # or small tiles); pdl with fuse and ntt_r8 with ntt_split take every pair
+        for k, vals in enumerate(((1, 2, 3, 4), (4, 8, 16), (0, 1, 2), tuple(range(16)), (1, 4, 8), (0, 1, 2, 3), (0,),
+                                  (0,))):
             assert set(vals) <= {t[k] for t in tried}, k
         assert {(p, f) for p in range(3) for f in range(4)} <= {(t[2], t[5]) for t in tried}
         for j in jobs:
