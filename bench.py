@@ -219,14 +219,22 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def kernel_work(name: str, prm, level: int):
+# stages of the strided pass under the launch shape's NTT pass split (1, 2) at
+# the ring sizes that have one; the contiguous pass takes the rest
+SPLIT_STRIDED = {(16, 1): 7, (16, 2): 9, (17, 1): 8, (17, 2): 10}
+
+
+def kernel_work(name: str, prm, level: int, split: int = 0):
     """Algorithmic work of one launch of kernel `name` at this level:
-    ("alu", butterflies) for NTT passes, ("hbm", bytes) for the streaming kernels."""
+    ("alu", butterflies) for NTT passes, ("hbm", bytes) for the streaming kernels.
+    `split` is the launch shape's NTT pass split (stages per pass)."""
     N, K, alpha = 1 << prm.logN, prm.K, prm.alpha
     beta = -(-level // alpha)
     E = K + level
     limb = N * 8
     passes = {16: (8, 8), 17: (9, 8), 15: (8, 7), 14: (7, 7), 13: (7, 6), 12: (12, 0)}[prm.logN]
+    if (prm.logN, split) in SPLIT_STRIDED:
+        passes = (SPLIT_STRIDED[(prm.logN, split)], prm.logN - SPLIT_STRIDED[(prm.logN, split)])
     jobs = {"intt_d2": level + 2, "ntt_modup": beta * E - level, "intt_special": 2 * K + 2,
             "ntt_moddown": 2 * (level - 1)}
     base = name.split(".")[0]
@@ -589,10 +597,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     lat = np.array([a.elapsed_time(b) for a, b in ev])
     value = job_rate(args.steps, wsz, elapsed_ms * 1e-3)
-    # the final combine runs inside the last NTT pass; with the shape's fuse bit
-    # the tensor product runs inside the first one
+    # the final combine runs inside the last NTT pass; with fuse bit 0 the
+    # tensor product runs inside the first one (bit 1 moves the q rows of the
+    # inner product into the ModDown launch: the launch count stays)
     fz = g.he_get_shape(ctx)[5]
-    launches_per_step = (12 if prm.logN > 12 else 8) - (1 if fz & 1 else 0) + (1 if fz & 2 else 0)
+    launches_per_step = (12 if prm.logN > 12 else 8) - (1 if fz & 1 else 0)
 
     # ---- end to end: host buffers through he_mul_rescale_host ----
     hws = torch.empty(g.he_host_workspace_bytes(ctx, level) // 8, dtype=torch.int64, device=dev)
@@ -665,8 +674,9 @@ def run_ours(args):
     prof = g.he_profile_read(ctx)
     g.he_profile(ctx, False)
     per_kernel = {}
+    split = g.he_get_shape(ctx)[6]
     for k, v in prof.items():
-        kind, work = kernel_work(k, ctx.prm, level)
+        kind, work = kernel_work(k, ctx.prm, level, split)
         d = {"ms_total": v[0], "calls": v[1], "ms_avg": v[0] / v[1], "kind": kind}
         if kind == "alu":
             d["Gbutterfly_s"] = work / (d["ms_avg"] * 1e-3) / 1e9
@@ -855,7 +865,7 @@ def run_ours(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     roof = None
     if dom:
-        kind, work = kernel_work(dom, ctx.prm, level)
+        kind, work = kernel_work(dom, ctx.prm, level, split)
         avg_s = per_kernel[dom]["ms_avg"] * 1e-3
         if kind == "alu":
             ach = work / avg_s / 1e9

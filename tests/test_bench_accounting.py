@@ -19,8 +19,9 @@ NTT_KERNELS = ["intt_d2.inv_pass1", "intt_d2.inv_pass2", "ntt_modup.fwd_pass1", 
                "ntt_moddown.fwd_pass2_combine"]
 
 
-@pytest.mark.parametrize("name,level", [("n16", 24), ("n16", 9), ("n17", 44), ("n15", 16)])
-def test_ntt_butterflies_add_up_to_the_limb_transforms(name, level):
+@pytest.mark.parametrize("name,level,split", [("n16", 24, 0), ("n16", 9, 0), ("n17", 44, 0), ("n15", 16, 0),
+                                              ("n16", 24, 1), ("n16", 24, 2), ("n17", 44, 1), ("n17", 44, 2)])
+def test_ntt_butterflies_add_up_to_the_limb_transforms(name, level, split):
     prm = oracle.preset(name)
     N, K = prm.N, prm.K
     beta = -(-level // prm.alpha)
@@ -29,11 +30,18 @@ def test_ntt_butterflies_add_up_to_the_limb_transforms(name, level):
     # last KS limbs; NTT of the 2(l-1) ModDown limbs
     transforms = (level + 2) + (beta * (K + level) - level) + (2 * K + 2) + 2 * (level - 1)
     total = 0
+    per = {}
     for k in NTT_KERNELS:
-        kind, work = bench.kernel_work(k, prm, level)
+        kind, work = bench.kernel_work(k, prm, level, split)
         assert kind == "alu"
         total += work
+        per[k] = work
     assert total == transforms * (N // 2) * prm.logN
+    # the strided pass (first forward, second inverse) takes the split's stage count
+    strided = {0: {16: 8, 17: 9}, 1: {16: 7, 17: 8}, 2: {16: 9, 17: 10}}[split].get(prm.logN)
+    if strided is not None:
+        assert per["ntt_modup.fwd_pass1"] == (beta * (K + level) - level) * (N // 2) * strided
+        assert per["intt_special.inv_pass2"] == (2 * K + 2) * (N // 2) * strided
     if (name, level) == ("n16", 24):
         assert transforms == 162
 
