@@ -468,7 +468,7 @@ int he_nr_rescale(he_nr_plan *plan, const uint64_t *ct, int logq, uint64_t *out,
  * the special limbs, 3 the NTT of the ModDown limbs) use the radix-8 plan
  * (rounds of at most three stages, 256 threads per tile) instead of the
  * radix-16 one (128 threads per tile).  Speed only: every shape gives
- * bit-identical results.  Default {4, 8, 1, 0, 8, 3, 0, 0}.  A batch graph keeps the
+ * bit-identical results.  Default {4, 8, 1, 0, 8, 3, 0, 0, 0}.  A batch graph keeps the
  * shape it was captured with, except the limb-group cap. */
 typedef struct {
     int group_cap;
@@ -494,6 +494,10 @@ typedef struct {
     int ntt_small; /* bit s (the sites of ntt_r8): that site's NTT passes work on tiles of 1024 elements
                     instead of 2048 (twice the CTAs, each with half the work: launches over few limbs
                     then end sooner); 2^16 and 2^17 only (a 10-stage strided pass keeps 2048).  0..15 */
+    int ntt_onepass; /* bit s (the sites of ntt_r8), N = 2^16 only: that site's transform runs in one pass
+                    over memory (Algo 3 whole), each limb on a cluster of 8 CTAs that hold one eighth of it
+                    each in shared memory and exchange the first three stages through the cluster's
+                    distributed shared memory; else the two passes of ntt_split.  0..15 */
     double ms;   /* he_autotune: measured milliseconds per call; else 0 */
 } he_shape;
 
@@ -503,7 +507,7 @@ int he_get_shape(const he_ctx *ctx, he_shape *shape);
 /* Time shapes on the caller's own work and keep the fastest in ctx, by
  * coordinate descent from the context's current shape: each knob in turn
  * (group_cap; modup_chunk; pdl and fuse together; ntt_r8 and ntt_split
- * together; ip_jobs for a batch; ntt_small) takes every value with the others held at
+ * together; ip_jobs for a batch; ntt_small; ntt_onepass) takes every value with the others held at
  * the best shape so far, sweep after sweep until one changes nothing (at
  * most four); then every (pdl, fuse, ntt_split) with the radix masks {best,
  * 0, 15}, and descent sweeps again from the best (no shape is timed twice);

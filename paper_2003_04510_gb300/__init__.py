@@ -402,21 +402,22 @@ def he_add_plain(ctx, ct, pt, level, out, stream=None):
 class he_shape(ctypes.Structure):
     _fields_ = [("group_cap", ctypes.c_int), ("modup_chunk", ctypes.c_int), ("pdl", ctypes.c_int),
                 ("ntt_r8", ctypes.c_int), ("ip_jobs", ctypes.c_int), ("fuse", ctypes.c_int), ("ntt_split", ctypes.c_int),
-                ("ntt_small", ctypes.c_int), ("ms", ctypes.c_double)]
+                ("ntt_small", ctypes.c_int), ("ntt_onepass", ctypes.c_int), ("ms", ctypes.c_double)]
 
 
 def _shape_tuple(sh) -> tuple:
-    return sh.group_cap, sh.modup_chunk, sh.pdl, sh.ntt_r8, sh.ip_jobs, sh.fuse, sh.ntt_split, sh.ntt_small
+    return (sh.group_cap, sh.modup_chunk, sh.pdl, sh.ntt_r8, sh.ip_jobs, sh.fuse, sh.ntt_split, sh.ntt_small,
+            sh.ntt_onepass)
 
 
 def he_set_shape(ctx, group_cap: int, modup_chunk: int, pdl: int = 1, ntt_r8: int = 0, ip_jobs: int = 8,
-                 fuse: int = 3, ntt_split: int = 0, ntt_small: int = 0):
-    sh = he_shape(group_cap, modup_chunk, pdl, ntt_r8, ip_jobs, fuse, ntt_split, ntt_small, 0.0)
+                 fuse: int = 3, ntt_split: int = 0, ntt_small: int = 0, ntt_onepass: int = 0):
+    sh = he_shape(group_cap, modup_chunk, pdl, ntt_r8, ip_jobs, fuse, ntt_split, ntt_small, ntt_onepass, 0.0)
     _check(lib().he_set_shape(ctx.ptr, ctypes.byref(sh)), "he_set_shape")
 
 
-def he_get_shape(ctx) -> tuple[int, int, int, int, int, int, int, int]:
-    """(group_cap, modup_chunk, pdl, ntt_r8, ip_jobs, fuse, ntt_split, ntt_small)"""
+def he_get_shape(ctx) -> tuple[int, int, int, int, int, int, int, int, int]:
+    """(group_cap, modup_chunk, pdl, ntt_r8, ip_jobs, fuse, ntt_split, ntt_small, ntt_onepass)"""
     sh = he_shape()
     _check(lib().he_get_shape(ctx.ptr, ctypes.byref(sh)), "he_get_shape")
     return _shape_tuple(sh)
@@ -425,7 +426,7 @@ def he_get_shape(ctx) -> tuple[int, int, int, int, int, int, int, int]:
 def he_autotune(ctx, jobs, evk, ws, reps: int = 3, stream=None):
     """jobs: list of (ct1, ct2, out, level) device tensors (one job: the single
     path).  Returns (best (cap, chunk, pdl, ntt_r8, ip_jobs, fuse, ntt_split,
-    ntt_small, ms), [the same for every shape tried])."""
+    ntt_small, ntt_onepass, ms), [the same for every shape tried])."""
     arr = (he_job * len(jobs))()
     for i, (a, b, o, lv) in enumerate(jobs):
         arr[i] = he_job(_dev_ptr(a), _dev_ptr(b), _dev_ptr(o), int(lv))

@@ -118,7 +118,8 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
     // key switching: iNTT(d2) (times N^-1 Qhat^-1), ModUp, NTT, inner product
     const int *cnt = S.counts;
     auto r8 = [c](int site) {  // NTT plan of a site
-        return ((c->ntt_r8 >> site) & 1) | (c->ntt_split << 1) | (((c->ntt_small >> site) & 1) << 3);
+        return ((c->ntt_r8 >> site) & 1) | (c->ntt_split << 1) | (((c->ntt_small >> site) & 1) << 3) |
+               (((c->ntt_onepass >> site) & 1) << 4);
     };
     capture_tag = kTagNtt0 + 0;
     if (tensor_fused)
@@ -420,7 +421,8 @@ int he_step_ntt(he_ctx *c, uint64_t *data, const int *prime_idx, int count, int 
     int rc = with_jobs(groups, st, &dj);
     if (rc) return rc;
     cudaError_t e = launch_ntt(c, (u64 *)data, dj, (int)groups.size(), inverse != 0, st, nullptr, nullptr,
-                               (c->ntt_r8 & 1) | (c->ntt_split << 1) | ((c->ntt_small & 1) << 3));
+                               (c->ntt_r8 & 1) | (c->ntt_split << 1) | ((c->ntt_small & 1) << 3) |
+                                   ((c->ntt_onepass & 1) << 4));
     cudaFreeAsync(dj, st);
     return e == cudaSuccess ? HE_OK : HE_ECUDA;
 }
@@ -659,6 +661,7 @@ int he_set_shape(he_ctx *c, const he_shape *sh)
     if (sh->fuse < 0 || sh->fuse > 3) return HE_EINVAL;
     if (sh->ntt_split < 0 || sh->ntt_split > 2) return HE_EINVAL;
     if (sh->ntt_small < 0 || sh->ntt_small > 15) return HE_EINVAL;
+    if (sh->ntt_onepass < 0 || sh->ntt_onepass > 15) return HE_EINVAL;
     c->group_cap = sh->group_cap;
     c->modup_chunk = sh->modup_chunk;
     c->pdl = sh->pdl;
@@ -667,6 +670,7 @@ int he_set_shape(he_ctx *c, const he_shape *sh)
     c->fuse = sh->fuse;
     c->ntt_split = sh->ntt_split;
     c->ntt_small = sh->ntt_small;
+    c->ntt_onepass = sh->ntt_onepass;
     if (c->device) c->jobs = c->jobs_cap[c->group_cap - 1];
     return HE_OK;
 }
@@ -682,6 +686,7 @@ int he_get_shape(const he_ctx *c, he_shape *sh)
     sh->fuse = c->fuse;
     sh->ntt_split = c->ntt_split;
     sh->ntt_small = c->ntt_small;
+    sh->ntt_onepass = c->ntt_onepass;
     sh->ms = 0;
     return HE_OK;
 }
@@ -732,7 +737,7 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
     auto same = [](const he_shape &a, const he_shape &b) {
         return a.group_cap == b.group_cap && a.modup_chunk == b.modup_chunk && a.pdl == b.pdl &&
                a.ntt_r8 == b.ntt_r8 && a.ip_jobs == b.ip_jobs && a.fuse == b.fuse && a.ntt_split == b.ntt_split &&
-               a.ntt_small == b.ntt_small;
+               a.ntt_small == b.ntt_small && a.ntt_onepass == b.ntt_onepass;
     };
     auto try_shape = [&](he_shape sh) -> int {
         for (const he_shape &t : seen)
@@ -745,57 +750,24 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
     const int nsplit = (c->logN == 16 || c->logN == 17) ? 3 : 1;
     // knobs whose best values depend on each other move together: the PDL
     // mode with the fusions, the NTT radix mask with the pass split
-    for (int sweep = 0; sweep < 4 && rc == HE_OK; sweep++) {
-        const he_shape before = top;
-        for (int knob = 0; knob < 6 && rc == HE_OK; knob++) {
-            const he_shape base = top;
-            const int nv = knob == 0 ? kGroupMax : knob == 1 ? 3 : knob == 2 ? 3 * 4 : knob == 3 ? 16 * nsplit
-                         : knob == 4 ? 3 : 16;
-            if (knob == 4 && !batch) continue;
-            if (knob == 5 && nsplit == 1) continue;  // 1024-element tiles: 2^16 and 2^17
-            for (int v = 0; v < nv && rc == HE_OK; v++) {
-                he_shape sh = base;
-                switch (knob) {
-                case 0: sh.group_cap = v + 1; break;
-                case 1: sh.modup_chunk = v == 0 ? 4 : v == 1 ? 8 : 16; break;
-                case 2: sh.pdl = v / 4; sh.fuse = v % 4; break;
-                case 3: sh.ntt_r8 = v % 16; sh.ntt_split = v / 16; break;
-                case 4: sh.ip_jobs = v == 0 ? 1 : v == 1 ? 4 : 8; break;
-                default: sh.ntt_small = v; break;
-                }
-                rc = try_shape(sh);
-            }
+    constexpr int kKnobs = 7;
+    auto knob_values = [&](int knob) {
+        switch (knob) {
+        case 0: return kGroupMax;
+        case 1: return 3;
+        case 2: return 3 * 4;
+        case 3: return 16 * nsplit;
+        case 4: return batch ? 3 : 0;
+        case 5: return nsplit > 1 ? 16 : 0;           // 1024-element tiles: 2^16 and 2^17
+        default: return c->logN == 16 ? 16 : 0;       // one-pass cluster transforms: 2^16
         }
-        if (same(before, top)) break;
-    }
-    // the knobs whose best values interact most, exhaustively: every PDL
-    // mode, fusion set and pass split with the radix masks {best, none, all},
-    // then descent sweeps again from the best
-    for (int pass = 0; pass < 2 && rc == HE_OK; pass++) {
-        if (pass == 0) {
-            const he_shape base = top;
-            const int masks[3] = {base.ntt_r8, 0, 15};
-            for (int m = 0; m < 3 && rc == HE_OK; m++)
-                for (int pdl = 0; pdl < 3 && rc == HE_OK; pdl++)
-                    for (int fz = 0; fz < 4 && rc == HE_OK; fz++)
-                        for (int sp = 0; sp < nsplit && rc == HE_OK; sp++) {
-                            he_shape sh = base;
-                            sh.ntt_r8 = masks[m];
-                            sh.pdl = pdl;
-                            sh.fuse = fz;
-                            sh.ntt_split = sp;
-                            rc = try_shape(sh);
-                        }
-            continue;
-        }
+    };
+    auto descent = [&]() {
         for (int sweep = 0; sweep < 4 && rc == HE_OK; sweep++) {
             const he_shape before = top;
-            for (int knob = 0; knob < 6 && rc == HE_OK; knob++) {
+            for (int knob = 0; knob < kKnobs && rc == HE_OK; knob++) {
                 const he_shape base = top;
-                const int nv = knob == 0 ? kGroupMax : knob == 1 ? 3 : knob == 2 ? 3 * 4 : knob == 3 ? 16 * nsplit
-                             : knob == 4 ? 3 : 16;
-                if (knob == 4 && !batch) continue;
-                if (knob == 5 && nsplit == 1) continue;
+                const int nv = knob_values(knob);
                 for (int v = 0; v < nv && rc == HE_OK; v++) {
                     he_shape sh = base;
                     switch (knob) {
@@ -804,14 +776,35 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
                     case 2: sh.pdl = v / 4; sh.fuse = v % 4; break;
                     case 3: sh.ntt_r8 = v % 16; sh.ntt_split = v / 16; break;
                     case 4: sh.ip_jobs = v == 0 ? 1 : v == 1 ? 4 : 8; break;
-                    default: sh.ntt_small = v; break;
+                    case 5: sh.ntt_small = v; break;
+                    default: sh.ntt_onepass = v; break;
                     }
                     rc = try_shape(sh);
                 }
             }
             if (same(before, top)) break;
         }
+    };
+    descent();
+    // the knobs whose best values interact most, exhaustively: every PDL
+    // mode, fusion set and pass split with the radix masks {best, none, all},
+    // then descent sweeps again from the best
+    if (rc == HE_OK) {
+        const he_shape base = top;
+        const int masks[3] = {base.ntt_r8, 0, 15};
+        for (int m = 0; m < 3 && rc == HE_OK; m++)
+            for (int pdl = 0; pdl < 3 && rc == HE_OK; pdl++)
+                for (int fz = 0; fz < 4 && rc == HE_OK; fz++)
+                    for (int sp = 0; sp < nsplit && rc == HE_OK; sp++) {
+                        he_shape sh = base;
+                        sh.ntt_r8 = masks[m];
+                        sh.pdl = pdl;
+                        sh.fuse = fz;
+                        sh.ntt_split = sp;
+                        rc = try_shape(sh);
+                    }
     }
+    descent();
     c->prof = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -143,6 +143,7 @@ struct he_ctx {
     int ntt_r8 = 0;                      // bit s: the radix-8 NTT plan at pipeline NTT site s (0..3)
     int ntt_split = 0;                   // NTT pass split of every site (0 default, 1, 2: see launch_ntt)
     int ntt_small = 0;                   // bit s: 1024-element NTT tiles at pipeline NTT site s (2^16, 2^17)
+    int ntt_onepass = 0;                 // bit s: one-pass cluster transform at pipeline NTT site s (2^16)
     int ip_jobs = he::kIpJobsMax;        // batches: jobs sharing one CTA's key words in the inner product (1: none)
     int fuse = 3;                        // bit 0: the tensor product inside the first inverse NTT pass of d2;
                                          // bit 1: the q limbs' key-switch sums beside the ModDown conversion

@@ -291,6 +291,82 @@ __device__ __forceinline__ void tensor_tile(const NttArgs &P, const NttGroup &G,
     }
 }
 
+// Final combine in place of a forward last pass's store: for limb i of the
+// group (ModDown output (h, ci) of job G.job[i]),
+// out[h][ci] = (d_h[ci] + KS_h[K+ci] P^-1 - z) q_{l-1}^-1 with z the
+// transform in shared memory (thread pairs 2 t, +1 at g2 + k gs2 and shared
+// word padi(2 t) + k (2 NT + NT / 8)).
+template <int TE, int NT>
+__device__ __forceinline__ void combine_store(const NttArgs &P, const NttGroup &G, int i, const u64 *sm, size_t g2,
+                                              size_t gs2, const DevPrime &pr, u64 nq)
+{
+    const BatchItem it = job_item(P.R, (int)G.job[i]);
+    const int ci = (int)(G.ci[i] & 0x7fffffffu), hh = (int)(G.ci[i] >> 31);
+    const ulonglong2 pv = P.pinv[ci], qv = P.levels[it.level].qinv_last[ci];
+    // above any forward-NTT output (values grow by < 4q per stage from
+    // inputs below 4q): d + KS P^-1 (lazy, < 4q) + Cz - z stays in
+    // (0, (9 + 4 log N) q), below 2^64, and one Shoup product by
+    // q_{l-1}^-1 reduces it
+    const u64 Cz = pr.q * (u64)(4 + 4 * P.logN);
+    u64 *o = it.out + ((((size_t)hh * (it.level - 1) + ci)) << P.logN) + g2;
+    const u64 *dd = P.dst + ((size_t)G.cd[i] << P.logN) + g2, *kk = P.dst + ((size_t)G.cks[i] << P.logN) + g2;
+    const u64 *sp = sm + padi(2 * threadIdx.x);
+    // four pairs per step: their d and KS loads are all in flight before the first product
+    constexpr int PAIRS = TE / 2 / NT, B4 = PAIRS >= 4 ? 4 : PAIRS;
+    static_assert(PAIRS % B4 == 0, "pairs per thread");
+    for (int b0 = 0; b0 < PAIRS; b0 += B4) {
+        ulonglong2 dv[B4], kv[B4];
+#pragma unroll
+        for (int k = 0; k < B4; k++) {
+            dv[k] = __ldg(reinterpret_cast<const ulonglong2 *>(dd + (b0 + k) * gs2));
+            kv[k] = __ldg(reinterpret_cast<const ulonglong2 *>(kk + (b0 + k) * gs2));
+        }
+#pragma unroll
+        for (int k = 0; k < B4; k++) {
+            // KS P^-1 lazily in [0, 4q): x < (6 + 4 log N) q < 2^64
+            const u64 *z = sp + (b0 + k) * (2 * NT + NT / 8);
+            const u64 x = dv[k].x + shoup_approx_nq(kv[k].x, pv.x, pv.y, nq) + Cz - z[0];
+            const u64 y = dv[k].y + shoup_approx_nq(kv[k].y, pv.x, pv.y, nq) + Cz - z[1];
+            *reinterpret_cast<ulonglong2 *>(o + (b0 + k) * gs2) =
+                make_ulonglong2(shoup_canon(x, qv.x, qv.y, pr.q, nq), shoup_canon(y, qv.x, qv.y, pr.q, nq));
+        }
+    }
+}
+
+// Shared memory -> HBM for limb i of the group (same thread walk as
+// combine_store), 16-byte stores; LAST: the output reduction (forward: from
+// below (4 + 4 log N) q to [0, q); inverse: times the limb's scale).
+template <int TE, int NT, bool LAST, bool INV>
+__device__ __forceinline__ void final_store(const NttArgs &P, const NttGroup &G, int i, const u64 *sm, size_t g2,
+                                            size_t gs2, const DevPrime &pr, u64 nq)
+{
+    u64 *dst = P.dst + ((size_t)G.dst[i] << P.logN) + g2;
+    const u64 sc = G.scale[i], scs = G.scale_sh[i];
+    const bool small_red = (pr.r64 >> 32) == 0;  // q > 2^32: reduce_small applies
+    const u64 *sp = sm + padi(2 * threadIdx.x);
+#pragma unroll
+    for (int k = 0; k < TE / 2 / NT; k++) {
+        u64 x = sp[0], y = sp[1];
+        if (LAST) {
+            if (!INV) {  // x < (4 + 4 log N) q
+                if (small_red) {
+                    x = reduce_small(x, pr.q, pr.r64);
+                    y = reduce_small(y, pr.q, pr.r64);
+                } else {
+                    x = shoup(x, 1, pr.r64, pr.q);
+                    y = shoup(y, 1, pr.r64, pr.q);
+                }
+            } else {
+                x = shoup_canon(x, sc, scs, pr.q, nq);
+                y = shoup_canon(y, sc, scs, pr.q, nq);
+            }
+        }
+        *reinterpret_cast<ulonglong2 *>(dst) = make_ulonglong2(x, y);
+        dst += gs2;
+        sp += 2 * NT + NT / 8;
+    }
+}
+
 // One pass of LOGM stages over a group of limbs.  Rounds RA, RB, RC (RC may
 // be 0) in forward order; the inverse runs them in reverse.  FIRST: read
 // group.src (else group.dst); LAST: apply the output reduction / scaling.
@@ -454,67 +530,11 @@ k_ntt_pass(const NttArgs P)
             __syncthreads();
         }
         if (COMBINE) {
-            // out[h][ci] = (d_h[ci] + KS_h[K+ci] P^-1 - z) q_{l-1}^-1 for the job's output
-            const BatchItem it = job_item(P.R, (int)G.job[i]);
-            const int ci = (int)(G.ci[i] & 0x7fffffffu), hh = (int)(G.ci[i] >> 31);
-            const ulonglong2 pv = P.pinv[ci], qv = P.levels[it.level].qinv_last[ci];
-            // above any forward-NTT output (values grow by < 4q per stage from
-            // inputs below 4q): d + KS P^-1 (lazy, < 4q) + Cz - z stays in
-            // (0, (9 + 4 log N) q), below 2^64, and one Shoup product by
-            // q_{l-1}^-1 reduces it
-            const u64 Cz = pr.q * (u64)(4 + 4 * P.logN);
-            u64 *o = it.out + ((((size_t)hh * (it.level - 1) + ci)) << P.logN) + g2;
-            const u64 *dd = P.dst + ((size_t)G.cd[i] << P.logN) + g2, *kk = P.dst + ((size_t)G.cks[i] << P.logN) + g2;
-            const u64 *sp = sm + padi(2 * threadIdx.x);
-            // four pairs per step: their d and KS loads are all in flight before the first product
-            constexpr int PAIRS = TE / 2 / NT, B4 = PAIRS >= 4 ? 4 : PAIRS;
-            static_assert(PAIRS % B4 == 0, "pairs per thread");
-            for (int b0 = 0; b0 < PAIRS; b0 += B4) {
-                ulonglong2 dv[B4], kv[B4];
-#pragma unroll
-                for (int k = 0; k < B4; k++) {
-                    dv[k] = __ldg(reinterpret_cast<const ulonglong2 *>(dd + (b0 + k) * gs2));
-                    kv[k] = __ldg(reinterpret_cast<const ulonglong2 *>(kk + (b0 + k) * gs2));
-                }
-#pragma unroll
-                for (int k = 0; k < B4; k++) {
-                    // KS P^-1 lazily in [0, 4q): x < (6 + 4 log N) q < 2^64
-                    const u64 *z = sp + (b0 + k) * (2 * NT + NT / 8);
-                    const u64 x = dv[k].x + shoup_approx_nq(kv[k].x, pv.x, pv.y, nq) + Cz - z[0];
-                    const u64 y = dv[k].y + shoup_approx_nq(kv[k].y, pv.x, pv.y, nq) + Cz - z[1];
-                    *reinterpret_cast<ulonglong2 *>(o + (b0 + k) * gs2) =
-                        make_ulonglong2(shoup_canon(x, qv.x, qv.y, pr.q, nq), shoup_canon(y, qv.x, qv.y, pr.q, nq));
-                }
-            }
+            combine_store<TE, NT>(P, G, i, sm, g2, gs2, pr, nq);
             __syncthreads();  // the next prefetch reuses this buffer
             continue;
         }
-        // shared memory -> HBM, 16-byte stores, output reduction on the last pass
-        u64 *dst = P.dst + ((size_t)G.dst[i] << P.logN) + g2;
-        const u64 sc = G.scale[i], scs = G.scale_sh[i];
-        const bool small_red = (pr.r64 >> 32) == 0;  // q > 2^32: reduce_small applies
-        const u64 *sp = sm + padi(2 * threadIdx.x);
-#pragma unroll
-        for (int k = 0; k < TE / 2 / NT; k++) {
-            u64 x = sp[0], y = sp[1];
-            if (LAST) {
-                if (!INV) {  // x < (4 + 4 log N) q
-                    if (small_red) {
-                        x = reduce_small(x, pr.q, pr.r64);
-                        y = reduce_small(y, pr.q, pr.r64);
-                    } else {
-                        x = shoup(x, 1, pr.r64, pr.q);
-                        y = shoup(y, 1, pr.r64, pr.q);
-                    }
-                } else {
-                    x = shoup_canon(x, sc, scs, pr.q, nq);
-                    y = shoup_canon(y, sc, scs, pr.q, nq);
-                }
-            }
-            *reinterpret_cast<ulonglong2 *>(dst) = make_ulonglong2(x, y);
-            dst += gs2;
-            sp += 2 * NT + NT / 8;
-        }
+        final_store<TE, NT, LAST, INV>(P, G, i, sm, g2, gs2, pr, nq);
         __syncthreads();  // the next prefetch reuses this buffer
     }
 }
@@ -534,6 +554,263 @@ cudaError_t run_pass(const NttArgs &a, int ngroups, cudaStream_t st)
     }
     if (ngroups == 0) return cudaSuccess;
     launch_k(a.pdl != 0, kern, dim3(ngroups * a.tiles), dim3(NT), smem, st, a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// One-pass transform of N = 2^16 over a thread-block cluster.
+//
+// The limb is cut into kCl = 8 contiguous chunks of TE = N / 8 elements, one
+// per CTA of a cluster, each held in its CTA's shared memory.  Stages 0-2
+// pair elements of different chunks (stage sigma pairs j and
+// j + N / 2^(sigma+1) with twiddle 2^sigma + floor(j / 2^(16 - sigma)), which
+// depends only on the chunk of j): for every offset k of a chunk they form one
+// radix-8 set {v TE + k : v < 8} with the twiddles of entries 1..7.  CTA r
+// runs those sets for the offsets [r TE / 8, (r + 1) TE / 8) and moves the
+// values between the CTAs through distributed shared memory; stages 3-15 are
+// the contiguous pass of one group (s0 = 3, LOGM = 13, tile r of the limb).
+// Forward: the cross round reads HBM and writes every chunk into its CTA's
+// shared memory, then the local rounds, then the output reduction (or the
+// final combine) and the store.  Inverse: the chunk is loaded (or formed by
+// the tensor product), local rounds in reverse, then the cross round reads the
+// chunks from the cluster's shared memory, scales and stores.  The limb makes
+// one trip through HBM instead of two; every butterfly is the one the two-pass
+// plans apply to the same operands, so every output word equals theirs.
+constexpr int kCl = 8;                  // CTAs per cluster (portable size)
+constexpr int kClLogN = 16;             // ring size of the plan
+constexpr int kClTE = (1 << kClLogN) / kCl;
+constexpr int kClLogM = kClLogN - 3;    // local stages 3 .. 15
+
+__device__ __forceinline__ unsigned cl_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Barrier over every thread of the cluster; shared-memory writes before it
+// (local or remote) are visible to every thread after it.
+__device__ __forceinline__ void cl_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Address in the cluster's shared window of the word `p` of this CTA's
+// shared memory as held by CTA `rank`.
+__device__ __forceinline__ uint32_t cl_map(const void *p, unsigned rank)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void cl_st(uint32_t a, u64 v)
+{
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ u64 cl_ld(uint32_t a)
+{
+    u64 v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+
+// Stages 0-2 on one radix-8 set (element v of the set in a[v]), twiddle
+// entry 2^l + (v >> (3 - l)) of stage l at w[2^l - 1 + (v >> (3 - l))].
+__device__ __forceinline__ void cross_fwd(u64 (&a)[8], const ulonglong2 (&w)[7], u64 nq, u64 q4)
+{
+#pragma unroll
+    for (int l = 0; l < 3; l++) {
+        const int h = 4 >> l;
+#pragma unroll
+        for (int v = 0; v < 8; v++)
+            if (!(v & h)) ct_bfly(a[v], a[v + h], w[(1 << l) - 1 + (v >> (3 - l))], nq, q4);
+    }
+}
+
+__device__ __forceinline__ void cross_inv(u64 (&a)[8], const ulonglong2 (&w)[7], u64 nq, u64 q4)
+{
+#pragma unroll
+    for (int l = 2; l >= 0; l--) {
+        const int h = 4 >> l;
+#pragma unroll
+        for (int v = 0; v < 8; v++)
+            if (!(v & h)) gs_bfly(a[v], a[v + h], w[(1 << l) - 1 + (v >> (3 - l))], nq, q4);
+    }
+}
+
+template <int R0, int R1, int R2, int R3>
+struct ClGeom {
+    static constexpr int RMAX = cmax(cmax(R0, R1), cmax(R2, R3));
+    static constexpr int NT = kClTE >> RMAX;
+    using Gm = Geometry<kClLogM, kClTE, false, R3>;
+    static constexpr size_t SMEM = sizeof(ulonglong2) * Gm::TWN + sizeof(u64) * Gm::DATA;  // one data buffer
+};
+
+template <int R0, int R1, int R2, int R3, bool INV, int FUSE>
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(ClGeom<R0, R1, R2, R3>::NT, 1)
+k_ntt_cluster(const NttArgs P)
+{
+    constexpr bool COMBINE = FUSE == kFuseCombine, TENSOR = FUSE == kFuseTensor;
+    static_assert(!COMBINE || !INV, "the combine follows a forward transform");
+    static_assert(!TENSOR || INV, "the tensor product feeds an inverse transform");
+    using CG = ClGeom<R0, R1, R2, R3>;
+    using Gm = typename CG::Gm;
+    constexpr int LOGM = kClLogM, TE = kClTE, NT = CG::NT, RL = R3, L0 = LOGM - RL;
+    static_assert(R0 + R1 + R2 + R3 == LOGM, "rounds must cover the local stages");
+    static_assert(Gm::NG == 1, "one group per chunk");
+    constexpr int CK = TE / kCl;  // cross-round offsets per CTA
+    static_assert(CK == 2 * NT, "two consecutive offsets per thread in the cross round");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ulonglong2 *tw = reinterpret_cast<ulonglong2 *>(smem_raw);
+    u64 *sm = reinterpret_cast<u64 *>(smem_raw + sizeof(ulonglong2) * Gm::TWN);
+
+    const int tile = (int)cl_rank();  // the chunk this CTA holds
+    const int gidx = blockIdx.x / kCl;
+    if (P.count && gidx >= *P.count) return idle_exit();  // the whole cluster leaves
+    const NttGroup &G = P.groups[gidx];
+    const int nl = (int)G.nl;
+    const DevPrime pr = P.primes[G.prime];
+    const u64 nq = 0ull - pr.q;
+    constexpr int s0 = 3;
+    const ulonglong2 *twg = INV ? pr.iw : pr.w;
+    // the local rounds' staged twiddles (stages s0 + l, l < LS, of this tile)
+#pragma unroll
+    for (int l = 0; l < Gm::LS; l++) {
+        const int n = 1 << l;
+        if (s0 + l < P.ts) {
+            const ulonglong2 *g = twg + (1 << (s0 + l)) + (size_t)tile * n;
+            for (int f = threadIdx.x; f < n; f += NT) __pipeline_memcpy_async(&tw[n - 1 + f], &g[f], 16);
+        } else {
+            for (int f = threadIdx.x; f < n; f += NT)
+                __pipeline_memcpy_async(&tw[n - 1 + f], &twg[tw_pos(s0 + l, P.ts, (size_t)tile * n + f)], 16);
+        }
+    }
+    __pipeline_commit();
+    prefetch_direct_tw<LOGM, TE, RL, NT>(twg, tile, s0, P.ts);
+    // this thread's two cross-round offsets k0, k0 + 1 and their words in
+    // every CTA's shared memory
+    const int k0 = tile * CK + 2 * threadIdx.x;
+    const uint32_t ko0 = 8u * (uint32_t)padi(k0), ko1 = 8u * (uint32_t)padi(k0 + 1);
+    uint32_t rb[kCl];
+#pragma unroll
+    for (int v = 0; v < kCl; v++) rb[v] = cl_map(sm, (unsigned)v);
+    // the chunk's thread walk (as the contiguous pass with one tile per limb)
+    const size_t g2 = (size_t)tile * TE + 2 * threadIdx.x, gs2 = 2 * NT;
+
+    constexpr int SPT = (TE >> RL) / NT;
+    const int te = s0 + L0 - P.ts;
+    auto load_direct = [&](TwReg<RL, SPT> &T) {
+#pragma unroll
+        for (int si = 0; si < SPT; si++) {
+            const int s = threadIdx.x + si * NT;
+            const int Tn = ((tile + (s >> L0)) << L0) + (s & ((1 << L0) - 1));
+#pragma unroll
+            for (int lp = 0; lp < RL; lp++) {
+                const ulonglong2 *g = direct_base(twg, s0 + L0 + lp, P.ts, te, lp, Tn);
+#pragma unroll
+                for (int j = 0; j < (1 << lp); j++) T.t[si][(1 << lp) - 1 + j] = ld_tw(g + ((size_t)j << P.ts));
+            }
+        }
+    };
+
+    griddep_wait(P.pdl >= 2);  // the limbs come from the previous kernels
+    for (int i = 0; i < nl; i++) {
+        TwReg<RL, SPT> TR;
+        ulonglong2 cw[7];
+#pragma unroll
+        for (int t = 0; t < 7; t++) cw[t] = ld_tw(twg + 1 + t);
+        if (!INV) {
+            const u64 *src = P.src + ((size_t)G.src[i] << P.logN);
+            u64 a[8], b[8];
+#pragma unroll
+            for (int v = 0; v < 8; v++) {
+                const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(src + (size_t)v * TE + k0);
+                a[v] = x.x;
+                b[v] = x.y;
+            }
+            cross_fwd(a, cw, nq, pr.q4);
+            cross_fwd(b, cw, nq, pr.q4);
+            cl_sync();  // every CTA of the cluster runs and is done with its previous chunk
+#pragma unroll
+            for (int v = 0; v < 8; v++) {
+                cl_st(rb[v] + ko0, a[v]);
+                cl_st(rb[v] + ko1, b[v]);
+            }
+            __pipeline_wait_prior(0);  // this thread's staged twiddles
+            cl_sync();                 // every chunk complete, the twiddles visible
+            ntt_round<LOGM, TE, R0, false, false, NT, false>(sm, tw, TR, 0, nq, pr.q4);
+            __syncthreads();
+            ntt_round<LOGM, TE, R1, false, false, NT, false>(sm, tw, TR, R0, nq, pr.q4);
+            __syncthreads();
+            ntt_round<LOGM, TE, R2, false, false, NT, false>(sm, tw, TR, R0 + R1, nq, pr.q4);
+            load_direct(TR);
+            __syncthreads();
+            ntt_round<LOGM, TE, R3, false, false, NT, true>(sm, tw, TR, L0, nq, pr.q4);
+            __syncthreads();
+            if (COMBINE) combine_store<TE, NT>(P, G, i, sm, g2, gs2, pr, nq);
+            else final_store<TE, NT, true, false>(P, G, i, sm, g2, gs2, pr, nq);
+        } else {
+            if (i > 0) cl_sync();  // the peers are done reading this CTA's previous chunk
+            if constexpr (TENSOR) {
+                tensor_tile<TE, NT>(P, G, i, tile, pr, sm);
+            } else {
+                const u64 *src = P.src + ((size_t)G.src[i] << P.logN) + (size_t)tile * TE + threadIdx.x;
+                u64 *d = sm + padi(threadIdx.x);
+#pragma unroll
+                for (int k = 0; k < TE / NT; k++) {
+                    __pipeline_memcpy_async(d, src, 8);
+                    d += NT + NT / 16;
+                    src += NT;
+                }
+                __pipeline_commit();
+            }
+            load_direct(TR);
+            __pipeline_wait_prior(0);
+            __syncthreads();
+            ntt_round<LOGM, TE, R3, false, true, NT, true>(sm, tw, TR, L0, nq, pr.q4);
+            __syncthreads();
+            ntt_round<LOGM, TE, R2, false, true, NT, false>(sm, tw, TR, R0 + R1, nq, pr.q4);
+            __syncthreads();
+            ntt_round<LOGM, TE, R1, false, true, NT, false>(sm, tw, TR, R0, nq, pr.q4);
+            __syncthreads();
+            ntt_round<LOGM, TE, R0, false, true, NT, false>(sm, tw, TR, 0, nq, pr.q4);
+            cl_sync();  // every chunk transformed
+            u64 a[8], b[8];
+#pragma unroll
+            for (int v = 0; v < 8; v++) {
+                a[v] = cl_ld(rb[v] + ko0);
+                b[v] = cl_ld(rb[v] + ko1);
+            }
+            cross_inv(a, cw, nq, pr.q4);
+            cross_inv(b, cw, nq, pr.q4);
+            u64 *dst = P.dst + ((size_t)G.dst[i] << P.logN) + k0;
+            const u64 sc = G.scale[i], scs = G.scale_sh[i];
+#pragma unroll
+            for (int v = 0; v < 8; v++)
+                *reinterpret_cast<ulonglong2 *>(dst + (size_t)v * TE) =
+                    make_ulonglong2(shoup_canon(a[v], sc, scs, pr.q, nq), shoup_canon(b[v], sc, scs, pr.q, nq));
+        }
+    }
+    if (INV) cl_sync();  // no CTA leaves while a peer still reads its shared memory
+}
+
+// ngroups == 0 only sets the kernel's shared-memory limit (no launch).
+template <int R0, int R1, int R2, int R3, bool INV, int FUSE = kFuseNone>
+cudaError_t run_cluster(const NttArgs &a, int ngroups, cudaStream_t st)
+{
+    using CG = ClGeom<R0, R1, R2, R3>;
+    auto kern = k_ntt_cluster<R0, R1, R2, R3, INV, FUSE>;
+    static bool configured = false;  // once per instantiation
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG::SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    if (ngroups == 0) return cudaSuccess;
+    launch_k(a.pdl != 0, kern, dim3(ngroups * kCl), dim3(CG::NT), CG::SMEM, st, a);
     return cudaGetLastError();
 }
 
@@ -601,7 +878,10 @@ static_assert(planv_fits<16, 1, false>() && planv_fits<16, 1, true>() && planv_f
 // 1024-element tiles (twice the CTAs, each half the work, for launches with
 // few limbs; every round's index map at that tile size was checked on the
 // CPU as for 2048)
-constexpr int kNttPlans = 16;
+// bit 4: the one-pass transform over a cluster (N = 2^16; other sizes
+// ignore it)
+constexpr int kPlanOnePass = 16;
+constexpr int kNttPlans = 32;
 // 1024-element tiles of a plan: a strided pass of 2^10 stages would be one
 // column wide, so that plan keeps 2048
 template <class P> constexpr int small_te() { return P::S1 >= 10 ? 2048 : 1024; }
@@ -638,6 +918,37 @@ cudaError_t two_pass(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cuda
     return e;
 }
 
+// One-pass transforms over a cluster: local rounds (3, 3, 3, 4), which are
+// free of shared-memory bank conflicts with the one-word-per-16 padding and
+// keep the direct round inside the table's transposed region.
+#define HE_CL_ROUNDS 3, 3, 3, 4
+cudaError_t onepass(const he_ctx *c, const NttArgs &a, int ngroups, bool inverse, cudaStream_t st, const char *tag)
+{
+    if (ngroups == 0) {  // configure only
+        cudaError_t e = run_cluster<HE_CL_ROUNDS, false>(a, 0, st);
+        return e == cudaSuccess ? run_cluster<HE_CL_ROUNDS, true>(a, 0, st) : e;
+    }
+    const cudaError_t e = inverse ? run_cluster<HE_CL_ROUNDS, true>(a, ngroups, st)
+                                  : run_cluster<HE_CL_ROUNDS, false>(a, ngroups, st);
+    prof_mark(c, st, tag, inverse ? ".inv_onepass" : ".fwd_onepass");
+    return e;
+}
+
+cudaError_t onepass_combine(const he_ctx *c, const NttArgs &a, int ngroups, cudaStream_t st, const char *tag)
+{
+    const cudaError_t e = run_cluster<HE_CL_ROUNDS, false, kFuseCombine>(a, ngroups, st);
+    if (ngroups) prof_mark(c, st, tag, ".fwd_onepass_combine");
+    return e;
+}
+
+cudaError_t onepass_tensor(const he_ctx *c, const NttArgs &a, int ngroups, cudaStream_t st, const char *tag)
+{
+    const cudaError_t e = run_cluster<HE_CL_ROUNDS, true, kFuseTensor>(a, ngroups, st);
+    if (ngroups) prof_mark(c, st, tag, ".tensor_inv_onepass");
+    return e;
+}
+#undef HE_CL_ROUNDS
+
 template <int LOGN, class P = Plan<LOGN>, int TE = 2048>
 cudaError_t two_pass_plan(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag)
 {
@@ -647,6 +958,7 @@ cudaError_t two_pass_plan(const he_ctx *c, NttArgs a, int ngroups, bool inverse,
 template <int LOGN>
 cudaError_t two_pass_any(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag, int plan)
 {
+    if (LOGN == kClLogN && (plan & kPlanOnePass)) return onepass(c, a, ngroups, inverse, st, tag);
     // bit 3: 1024-element tiles (2^16 and 2^17; a pass over 2^10 stages keeps 2048)
     constexpr bool SMALL_OK = LOGN == 16 || LOGN == 17;
     if (SMALL_OK && (plan & 8)) {
@@ -686,6 +998,7 @@ cudaError_t combine_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t s
 template <int LOGN>
 cudaError_t combine_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, int plan)
 {
+    if (LOGN == kClLogN && (plan & kPlanOnePass)) return onepass_combine(c, a, ngroups, st, tag);
     // bit 3: 1024-element tiles (2^16 and 2^17; a pass over 2^10 stages keeps 2048)
     constexpr bool SMALL_OK = LOGN == 16 || LOGN == 17;
     if (SMALL_OK && (plan & 8)) {
@@ -725,6 +1038,7 @@ cudaError_t tensor_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st
 template <int LOGN>
 cudaError_t tensor_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, int plan)
 {
+    if (LOGN == kClLogN && (plan & kPlanOnePass)) return onepass_tensor(c, a, ngroups, st, tag);
     // bit 3: 1024-element tiles (2^16 and 2^17; a pass over 2^10 stages keeps 2048)
     constexpr bool SMALL_OK = LOGN == 16 || LOGN == 17;
     if (SMALL_OK && (plan & 8)) {

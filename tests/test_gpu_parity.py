@@ -684,6 +684,81 @@ def test_ntt_pass_splits_bit_identical(g, name, level, split):
         g.he_set_shape(ctx, 4, 8, 1)
 
 
+@pytest.mark.parametrize("level", [24, 3])
+def test_onepass_cluster_bit_identical(g, level):
+    """The one-pass transforms over a cluster of 8 CTAs (N = 2^16) at every
+    NTT site or at some, the other sites on radix-8 or radix-16 passes, with
+    and without the fusions (the tensor product in the first iNTT, the final
+    combine in the last NTT) and with groups of 1 to 4 limbs per cluster: the
+    same words as the oracle; the plain ModDown path and the raw transforms
+    (he_step_ntt takes site 0's bit) too."""
+    import torch
+    name = "n16"
+    op = oracle.preset(name)
+    ctx = ctx_for(g, name)
+    evk = rand_evk(op, 970 + level)
+    evk_t = dev(g, evk)
+    c1, c2 = rand_ct(op, level, 980 + level), rand_ct(op, level, 990 + level)
+    want = oracle.rescale(op, oracle.he_mul(op, c1, c2, evk, level), level)
+    try:
+        for onepass in (15, 5, 10):
+            for r8, fz, grp in ((15, 3, 1), (0, 0, 2), (5, 1, 4)):
+                g.he_set_shape(ctx, grp, 8, 1, r8, 8, fz, 1, 0, onepass)
+                got = gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True)
+                assert np.array_equal(got, want), (onepass, r8, fz, grp)
+        g.he_set_shape(ctx, 2, 8, 2, 15, 8, 1, 0, 0, 15)
+        assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=False), oracle.he_mul(op, c1, c2, evk, level))
+        E = op.K + op.L
+        idx = [0, op.K, E - 1]
+        mods = [op.ext[e] for e in idx]
+        psis = [int(op.psi_p[e]) if e < op.K else int(op.psi_q[e - op.K]) for e in idx]
+        a = rand_polys(mods, op.N, 975 + level)
+        for grp in (1, 3):
+            g.he_set_shape(ctx, grp, 8, 1, 0, 8, 3, 0, 0, 1)
+            t = dev(g, a)
+            g.he_step_ntt(ctx, t, idx, inverse=False)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(g, t), np.stack([oracle.ntt(a[i], mods[i], psis[i], op.logN)
+                                                        for i in range(len(idx))])), grp
+            g.he_step_ntt(ctx, t, idx, inverse=True)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(g, t), a), grp
+    finally:
+        g.he_set_shape(ctx, 4, 8, 1)
+
+
+def test_onepass_batch_and_graph_match_single(g):
+    """A batch of uneven levels and a graph replay (NTT grids resized to each
+    batch) on one-pass shapes: every result equals the job run alone."""
+    import torch
+    name = "n16"
+    ctx = ctx_for(g, name)
+    op = oracle.preset(name)
+    evk_t = dev(g, rand_evk(op, 125))
+    levels = [24, 5, 13, 2, 18]
+    try:
+        g.he_set_shape(ctx, 2, 8, 2, 15, 8, 3, 1, 0, 15)
+        graph = g.BatchGraph(ctx, 8, evk_t)
+        jobs, singles = [], []
+        for k, lv in enumerate(levels):
+            c1, c2 = rand_ct(op, lv, 600 + 2 * k), rand_ct(op, lv, 650 + 2 * k)
+            jobs.append((dev(g, c1), dev(g, c2), torch.full((2, lv - 1, op.N), -1, dtype=torch.int64, device="cuda"), lv))
+            singles.append(gpu_mul(g, ctx, c1, c2, evk_t, lv, fused=True))
+        ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
+        g.he_mul_batch(ctx, jobs, evk_t, ws)
+        torch.cuda.synchronize()
+        for (t1, t2, out, lv), single in zip(jobs, singles):
+            assert np.array_equal(host(g, out), single), lv
+            out.fill_(-1)
+        graph.launch(jobs[:3])
+        torch.cuda.synchronize()
+        for (t1, t2, out, lv), single in zip(jobs[:3], singles[:3]):
+            assert np.array_equal(host(g, out), single), lv
+        graph.close()
+    finally:
+        g.he_set_shape(ctx, 4, 8, 1)
+
+
 @pytest.mark.parametrize("name,level", [("n15", 16), ("n15", 5), ("n17", 13)])
 def test_radix8_plans_bit_identical(g, name, level):
     """Every NTT site on its radix-8 plan (the plans differ per ring size)."""
@@ -715,12 +790,12 @@ def test_autotune_batch_keeps_results(g):
     ws = torch.empty(g.he_batch_workspace_bytes(ctx, levels) // 8, dtype=torch.int64, device="cuda")
     try:
         best, tried = g.he_autotune(ctx, jobs, evk_t, ws, reps=2)
-        assert all(t[8] > 0 for t in tried) and len(set(t[:8] for t in tried)) == len(tried)
-        assert best[:8] == g.he_get_shape(ctx) and best[8] == min(t[8] for t in tried)
+        assert all(t[9] > 0 for t in tried) and len(set(t[:9] for t in tried)) == len(tried)
+        assert best[:9] == g.he_get_shape(ctx) and best[9] == min(t[9] for t in tried)
         # the first sweep gives every knob every value (N = 2^15: no pass splits
         # or small tiles); pdl with fuse and ntt_r8 with ntt_split take every pair
         for k, vals in enumerate(((1, 2, 3, 4), (4, 8, 16), (0, 1, 2), tuple(range(16)), (1, 4, 8), (0, 1, 2, 3), (0,),
-                                  (0,))):
+                                  (0,), (0,))):
             assert set(vals) <= {t[k] for t in tried}, k
         assert {(p, f) for p in range(3) for f in range(4)} <= {(t[2], t[5]) for t in tried}
         for j in jobs:
