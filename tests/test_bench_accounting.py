@@ -81,6 +81,8 @@ def test_committed_profile_lines_parse():
                 assert int(nbytes) > 0
                 assert name not in seen, f"{name} in {path} and {seen.get(name)}"
                 seen[name] = path
-    # every kernel of the event profile has a committed DRAM figure
-    for k in NTT_KERNELS + ["tensor", "modup", "inner_product", "moddown_conv"]:
+    # every kernel of the event profile of the fused, split-row step (the shape
+    # the autotuner keeps at N = 2^16) has a committed DRAM figure
+    fused = ["intt_d2.tensor_inv_pass1"] + NTT_KERNELS[1:]
+    for k in fused + ["modup", "inner_product_special", "moddown_conv_ipq"]:
         assert k in seen, k
