@@ -542,7 +542,7 @@ def run_ours(args):
     # (or fixed by --shape, e.g. for a profiler run)
     if args.shape:
         given = [int(v) for v in args.shape.split(",")]
-        shape = (given + [0, 8, 3, 0, 0, 0][len(given) - 3:])[:9]
+        shape = (given + [0, 8, 7, 0, 0, 0][len(given) - 3:])[:9]
         g.he_set_shape(ctx, *shape)
         tune_best, tune_tried = tuple(shape) + (0.0,), []
     else:

@@ -468,7 +468,7 @@ int he_nr_rescale(he_nr_plan *plan, const uint64_t *ct, int logq, uint64_t *out,
  * the special limbs, 3 the NTT of the ModDown limbs) use the radix-8 plan
  * (rounds of at most three stages, 256 threads per tile) instead of the
  * radix-16 one (128 threads per tile).  Speed only: every shape gives
- * bit-identical results.  Default {4, 8, 1, 0, 8, 3, 0, 0, 0}.  A batch graph keeps the
+ * bit-identical results.  Default {4, 8, 1, 0, 8, 7, 0, 0, 0}.  A batch graph keeps the
  * shape it was captured with, except the limb-group cap. */
 typedef struct {
     int group_cap;
@@ -485,7 +485,10 @@ typedef struct {
                     the key-switch sums of Fig. 2 region 2 are split: those of the special primes and of
                     q_{level-1} (the next iNTT's inputs) first, those of the other q primes (read only by
                     the final additions) in the same launch as the ModDown conversion, so the key stream
-                    overlaps the conversion's arithmetic.  0..3 */
+                    overlaps the conversion's arithmetic.  bit 2 (with bit 1, unseeded keys): the sums of
+                    the special primes and of q_{level-1} are formed by the first pass of their own
+                    inverse NTT, which computes its tile from U, d2 and the key instead of loading it (one
+                    launch and one write and read of those limbs fewer).  0..7 */
     int ntt_split; /* the stages each pass of every NTT covers (Algo 3 split into a strided pass over the
                     first stages and a contiguous pass over the last ones): 0 the default (2^16: 8 + 8;
                     2^17: 9 + 8), 1 one stage more in the contiguous pass (7 + 9; 8 + 9), 2 one more in the

@@ -411,7 +411,7 @@ def _shape_tuple(sh) -> tuple:
 
 
 def he_set_shape(ctx, group_cap: int, modup_chunk: int, pdl: int = 1, ntt_r8: int = 0, ip_jobs: int = 8,
-                 fuse: int = 3, ntt_split: int = 0, ntt_small: int = 0, ntt_onepass: int = 0):
+                 fuse: int = 7, ntt_split: int = 0, ntt_small: int = 0, ntt_onepass: int = 0):
     sh = he_shape(group_cap, modup_chunk, pdl, ntt_r8, ip_jobs, fuse, ntt_split, ntt_small, ntt_onepass, 0.0)
     _check(lib().he_set_shape(ctx.ptr, ctypes.byref(sh)), "he_set_shape")
 

@@ -135,17 +135,27 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
     // beside the ModDown conversion: the sums of the special limbs and the
     // last q limb (the next iNTT's inputs) come first
     const bool split = (c->fuse & 2) && !S.ipg && !R.items && mode != kTailPlain && moddown_ipq_fits(c);
+    // with the split, the sums of the special limbs and the last q limb may
+    // instead be formed by the first pass of their own iNTT (unseeded keys)
+    bool seeded = false;
+    for (const auto &k : c->seeded) seeded = seeded || k.ptr == evk;
+    const bool ip_in_ntt = split && (c->fuse & 4) && !seeded;
     if (S.ipg) {
         capture_tag = kTagIpGroups;
         HE_TRY(run_inner_product_shared(c, R, S.ipg, S.n_ipg, cnt ? cnt + 4 : nullptr, evk, st));
-    } else {
+        prof_mark(c, st, "inner_product");
+    } else if (!ip_in_ntt) {
         capture_tag = kTagJobs;
         HE_TRY(run_inner_product(c, R, evk, st, split ? kIpSpecialLastRows : kIpAllRows));
+        prof_mark(c, st, split ? "inner_product_special" : "inner_product");
     }
-    prof_mark(c, st, split ? "inner_product_special" : "inner_product");
     // ModDown: iNTT of the special limbs (times N^-1 Phat^-1), conversion, NTT
     capture_tag = kTagNtt0 + 2;
-    HE_TRY(launch_ntt(c, ntt_base, S.intt2, S.n_intt2, true, st, "intt_special", cnt ? cnt + 2 : nullptr, r8(2)));
+    if (ip_in_ntt)
+        HE_TRY(launch_ntt_ip(c, ntt_base, S.intt2, S.n_intt2, R, evk, st, "intt_special", cnt ? cnt + 2 : nullptr,
+                             r8(2)));
+    else
+        HE_TRY(launch_ntt(c, ntt_base, S.intt2, S.n_intt2, true, st, "intt_special", cnt ? cnt + 2 : nullptr, r8(2)));
     capture_tag = kTagJobs;
     if (split) {
         HE_TRY(run_moddown_ipq(c, R, mode, evk, st));
@@ -658,7 +668,7 @@ int he_set_shape(he_ctx *c, const he_shape *sh)
     if (sh->pdl < 0 || sh->pdl > 2) return HE_EINVAL;
     if (sh->ntt_r8 < 0 || sh->ntt_r8 > 15) return HE_EINVAL;
     if (sh->ip_jobs != 1 && sh->ip_jobs != 4 && sh->ip_jobs != 8) return HE_EINVAL;
-    if (sh->fuse < 0 || sh->fuse > 3) return HE_EINVAL;
+    if (sh->fuse < 0 || sh->fuse > 7) return HE_EINVAL;
     if (sh->ntt_split < 0 || sh->ntt_split > 2) return HE_EINVAL;
     if (sh->ntt_small < 0 || sh->ntt_small > 15) return HE_EINVAL;
     if (sh->ntt_onepass < 0 || sh->ntt_onepass > 15) return HE_EINVAL;
@@ -740,6 +750,7 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
                a.ntt_small == b.ntt_small && a.ntt_onepass == b.ntt_onepass;
     };
     auto try_shape = [&](he_shape sh) -> int {
+        if ((sh.fuse & 4) && !(sh.fuse & 2)) return HE_OK;  // bit 2 acts with bit 1 only
         for (const he_shape &t : seen)
             if (same(t, sh)) return HE_OK;
         seen.push_back(sh);
@@ -755,7 +766,7 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
         switch (knob) {
         case 0: return kGroupMax;
         case 1: return 3;
-        case 2: return 3 * 4;
+        case 2: return 3 * 8;
         case 3: return 16 * nsplit;
         case 4: return batch ? 3 : 0;
         case 5: return nsplit > 1 ? 16 : 0;           // 1024-element tiles: 2^16 and 2^17
@@ -773,7 +784,7 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
                     switch (knob) {
                     case 0: sh.group_cap = v + 1; break;
                     case 1: sh.modup_chunk = v == 0 ? 4 : v == 1 ? 8 : 16; break;
-                    case 2: sh.pdl = v / 4; sh.fuse = v % 4; break;
+                    case 2: sh.pdl = v / 8; sh.fuse = v % 8; break;
                     case 3: sh.ntt_r8 = v % 16; sh.ntt_split = v / 16; break;
                     case 4: sh.ip_jobs = v == 0 ? 1 : v == 1 ? 4 : 8; break;
                     case 5: sh.ntt_small = v; break;
@@ -794,7 +805,7 @@ int he_autotune(he_ctx *c, const he_job *jobs, int count, const uint64_t *evk, v
         const int masks[3] = {base.ntt_r8, 0, 15};
         for (int m = 0; m < 3 && rc == HE_OK; m++)
             for (int pdl = 0; pdl < 3 && rc == HE_OK; pdl++)
-                for (int fz = 0; fz < 4 && rc == HE_OK; fz++)
+                for (int fz = 0; fz < 8 && rc == HE_OK; fz++)
                     for (int sp = 0; sp < nsplit && rc == HE_OK; sp++) {
                         he_shape sh = base;
                         sh.ntt_r8 = masks[m];

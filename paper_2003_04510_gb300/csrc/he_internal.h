@@ -145,8 +145,9 @@ struct he_ctx {
     int ntt_small = 0;                   // bit s: 1024-element NTT tiles at pipeline NTT site s (2^16, 2^17)
     int ntt_onepass = 0;                 // bit s: one-pass cluster transform at pipeline NTT site s (2^16)
     int ip_jobs = he::kIpJobsMax;        // batches: jobs sharing one CTA's key words in the inner product (1: none)
-    int fuse = 3;                        // bit 0: the tensor product inside the first inverse NTT pass of d2;
-                                         // bit 1: the q limbs' key-switch sums beside the ModDown conversion
+    int fuse = 7;                        // bit 0: the tensor product inside the first inverse NTT pass of d2;
+                                         // bit 1: the q limbs' key-switch sums beside the ModDown conversion;
+                                         // bit 2: the special limbs' sums inside their iNTT's first pass
     std::vector<u64> ext;                // moduli, ext order
     std::vector<u64> psi;                // smallest primitive 2N-th roots, ext order
     // host tables (for the host NTT used by keygen / encrypt / decrypt)
@@ -309,6 +310,11 @@ cudaError_t launch_ntt_combine(const he_ctx *ctx, u64 *base, const NttGroup *gro
 cudaError_t launch_ntt_tensor(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
                               cudaStream_t st, const char *tag = nullptr, const int *dev_count = nullptr,
                               int plan = 0);
+// The special limbs' inverse NTT whose first pass computes its input, the
+// key-switch sums KS_h[e] of the group limbs (ci = e | h << 16) from U, d2
+// and the (unseeded) evaluation key, instead of loading it.
+cudaError_t launch_ntt_ip(const he_ctx *ctx, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
+                          const u64 *evk, cudaStream_t st, const char *tag, const int *dev_count, int plan);
 // Number of final stages (the contiguous pass's last round) whose twiddle
 // runs the device table stores transposed; 0 for an unsupported logN.
 int ntt_direct_stages(int logN);

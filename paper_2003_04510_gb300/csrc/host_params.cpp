@@ -249,13 +249,15 @@ int build_context(he_ctx *c, const he_params *p, bool device)
             for (int k = 0; k < K; k++) {
                 u64 pk = c->ext[k];
                 u64 sc = mul(c->ninv[k], c->phat_inv[k].x, pk);
+                // ci: the key-switch row and half (the first pass that computes the sums itself)
                 H.intt2.push_back(NttJob{(unsigned)(W.ks + (size_t)h * El + k), (unsigned)(W.ys + (size_t)h * K + k),
-                                         (unsigned)k, 0, sc, shoup(sc, pk)});
+                                         (unsigned)k, 0, sc, shoup(sc, pk), 0, (unsigned)k | ((unsigned)h << 16), 0, 0});
             }
         H.intt2f = H.intt2;
         for (int h = 0; h < 2; h++)
             H.intt2f.push_back(NttJob{(unsigned)(W.ks + (size_t)h * El + K + l - 1), (unsigned)(W.r + 2 + h),
-                                      (unsigned)(K + l - 1), 0, c->ninv[K + l - 1], c->ninv_sh[K + l - 1]});
+                                      (unsigned)(K + l - 1), 0, c->ninv[K + l - 1], c->ninv_sh[K + l - 1], 0,
+                                      (unsigned)(K + l - 1) | ((unsigned)h << 16), 0, 0});
         // one division by M = P q_{l-1}: y_k = x_k [Mhat_k^-1]_{p_k}, Mhat_k = Phat_k q_{l-1};
         // the conversion constants [Mhat_k P^-1]_{q_i} = [Phat_k P^-1 q_{l-1}]_{q_i}
         for (int h = 0; h < 2; h++)
@@ -263,7 +265,8 @@ int build_context(he_ctx *c, const he_params *p, bool device)
                 u64 pk = c->ext[k];
                 u64 sc = mul(mul(c->ninv[k], c->phat_inv[k].x, pk), inv(ql % pk, pk), pk);
                 H.intt2pq.push_back(NttJob{(unsigned)(W.ks + (size_t)h * El + k),
-                                           (unsigned)(W.ys + (size_t)h * K + k), (unsigned)k, 0, sc, shoup(sc, pk)});
+                                           (unsigned)(W.ys + (size_t)h * K + k), (unsigned)k, 0, sc, shoup(sc, pk), 0,
+                                           (unsigned)k | ((unsigned)h << 16), 0, 0});
             }
         for (int h = 0; h < 2; h++) H.intt2pq.push_back(H.intt2f[(size_t)2 * K + h]);
         H.pbpq.assign((size_t)std::max(l - 1, 1) * c->KP, 0);

@@ -57,6 +57,10 @@ struct NttArgs {
     JobRef R;
     const DevLevel *levels;
     const ulonglong2 *pinv;
+    // fused key-switch sums (kFuseIp passes only): the evaluation key
+    // [dnum][2][EL][N], EL = K + L
+    const u64 *evk;
+    int EL;
 };
 
 // 16-byte read-only load that does not allocate in L1 (twiddles read once).
@@ -291,6 +295,64 @@ __device__ __forceinline__ void tensor_tile(const NttArgs &P, const NttGroup &G,
     }
 }
 
+// The key-switch sum KS_h[e] = sum_j U_j[e] evk_{j,h}[e] mod q_e (Fig. 2
+// region 2, the inner product with the evaluation key in the NTT domain) of
+// the contiguous tile `tile` of one special limb (or q_{l-1}), as the tile
+// load of the inverse contiguous first pass that takes it out of the NTT
+// domain: the group's limb k carries the job (job[k]) and ci[k] = e | h << 16.
+// U_j[e] is row e of digit j's ModUp output, or row e - K of d2 for the
+// digit's own limbs; the products of up to kIpFuseDigits digits are summed in
+// 128 bits and reduced once (below 4 q^2 < 2^112).  The sums are not stored:
+// only this transform reads them.
+constexpr int kIpFuseDigits = 4;
+
+template <int TE, int NT>
+__device__ __forceinline__ void ip_tile(const NttArgs &P, const NttGroup &G, int k, int tile, const DevPrime &pr,
+                                        u64 *b)
+{
+    const int lg = P.logN;
+    const BatchItem it = job_item(P.R, (int)G.job[k]);
+    const unsigned spec = G.ci[k];
+    const int e = (int)(spec & 0xffffu), h = (int)((spec >> 16) & 1u);
+    const DevLevel &lv = P.levels[it.level];
+    const int beta = lv.beta, E = lv.E, K = lv.E - it.level;
+    // per digit: the limb of U_j[e] in the workspace (or of d2's row for the
+    // digit's own limbs) and the key's limb, as limb indices
+    unsigned uo[kIpFuseDigits], ko[kIpFuseDigits];
+#pragma unroll
+    for (int j = 0; j < kIpFuseDigits; j++) {
+        const int jj = j < beta ? j : 0;
+        const int lo = lv.dig_lo[jj], nj = lv.dig_n[jj];
+        const bool own = e >= K && e - K >= lo && e - K < lo + nj;
+        uo[j] = own ? lv.o_d2 + (unsigned)(e - K) : lv.o_u + (unsigned)(jj * E + e);
+        ko[j] = (unsigned)((2 * jj + h) * P.EL + e);
+    }
+    const u64 *ws = it.ws + (size_t)tile * TE, *kb = P.evk + (size_t)tile * TE;
+    const u64 pol = l2_policy_stream();  // U and the key are read once
+    constexpr int PAIRS = TE / 2 / NT;
+    constexpr int UNROLL = NT >= 256 ? 1 : 2;  // registers: the 256-thread tiles run at 64
+#pragma unroll UNROLL
+    for (int s = 0; s < PAIRS; s++) {
+        const int x = 2 * (threadIdx.x + s * NT);
+        ulonglong2 u[kIpFuseDigits], w[kIpFuseDigits];
+#pragma unroll
+        for (int j = 0; j < kIpFuseDigits; j++)
+            if (j < beta) {
+                u[j] = ld2_hint(ws + ((size_t)uo[j] << lg) + x, pol);
+                w[j] = ld2_hint(kb + ((size_t)ko[j] << lg) + x, pol);
+            }
+        U128 ax = {0, 0}, ay = {0, 0};
+#pragma unroll
+        for (int j = 0; j < kIpFuseDigits; j++)
+            if (j < beta) {
+                mac(ax, u[j].x, w[j].x);
+                mac(ay, u[j].y, w[j].y);
+            }
+        b[padi(x)] = barrett128(ax, pr.q, pr.mu, pr.s);
+        b[padi(x + 1)] = barrett128(ay, pr.q, pr.mu, pr.s);
+    }
+}
+
 // Final combine in place of a forward last pass's store: for limb i of the
 // group (ModDown output (h, ci) of job G.job[i]),
 // out[h][ci] = (d_h[ci] + KS_h[K+ci] P^-1 - z) q_{l-1}^-1 with z the
@@ -389,15 +451,18 @@ __host__ __device__ constexpr int ntt_min_blocks(int nt, int logm, bool inv)
 // forward contiguous last pass (ModDown + rescale limbs); kFuseTensor, the
 // tensor product computed in place of the inverse contiguous first pass's
 // tile load (d2 limbs and the rescale limbs of d0, d1).
-enum { kFuseNone = 0, kFuseCombine = 1, kFuseTensor = 2 };
+// kFuseIp, the key-switch sums of Fig. 2 region 2 computed in place of the
+// tile load of the special limbs' inverse contiguous first pass.
+enum { kFuseNone = 0, kFuseCombine = 1, kFuseTensor = 2, kFuseIp = 3 };
 
 template <int LOGM, int RA, int RB, int RC, bool STRIDED, bool INV, bool FIRST, bool LAST, int TE, int FUSE = kFuseNone>
 __global__ void __launch_bounds__(TE >> cmax(RA, cmax(RB, RC)), ntt_min_blocks(TE >> cmax(RA, cmax(RB, RC)), LOGM, INV))
 k_ntt_pass(const NttArgs P)
 {
-    constexpr bool COMBINE = FUSE == kFuseCombine, TENSOR = FUSE == kFuseTensor;
+    constexpr bool COMBINE = FUSE == kFuseCombine, TENSOR = FUSE == kFuseTensor, IPF = FUSE == kFuseIp;
+    constexpr bool COMPUTED = TENSOR || IPF;  // the tile load computes its words
     static_assert(!COMBINE || (LAST && !INV && !STRIDED), "the combine follows a forward contiguous last pass");
-    static_assert(!TENSOR || (FIRST && INV && !STRIDED), "the tensor product feeds an inverse contiguous first pass");
+    static_assert(!COMPUTED || (FIRST && INV && !STRIDED), "computed tiles feed an inverse contiguous first pass");
     constexpr int NT = TE >> cmax(RA, cmax(RB, RC));
     constexpr int RL = RC ? RC : RB;  // last round in forward order
     constexpr int L0 = LOGM - RL;     // its first stage
@@ -437,6 +502,8 @@ k_ntt_pass(const NttArgs P)
     auto load_tile = [&](int i, u64 *b) {
         if constexpr (TENSOR) {
             tensor_tile<TE, NT>(P, G, i, tile, pr, b);
+        } else if constexpr (IPF) {
+            ip_tile<TE, NT>(P, G, i, tile, pr, b);
         } else {
             const u64 *src = (FIRST ? P.src + ((size_t)G.src[i] << P.logN) : P.dst + ((size_t)G.dst[i] << P.logN)) + g1;
             u64 *d = b + padi(threadIdx.x);
@@ -497,8 +564,8 @@ k_ntt_pass(const NttArgs P)
         u64 *sm = buf + (i & 1) * Gm::DATA;
         TwReg<RL, SPT> TR;
         // the inverse starts with the direct round (its twiddles are loaded
-        // after the next limb's tensor product, which needs the registers)
-        if (DIRECT && INV && !TENSOR) load_direct(TR);
+        // after the next limb's computed tile, which needs the registers)
+        if (DIRECT && INV && !COMPUTED) load_direct(TR);
         if (i + 1 < nl) {
             load_tile(i + 1, buf + ((i + 1) & 1) * Gm::DATA);
             __pipeline_commit();
@@ -506,7 +573,7 @@ k_ntt_pass(const NttArgs P)
         } else {
             __pipeline_wait_prior(0);
         }
-        if (DIRECT && INV && TENSOR) load_direct(TR);
+        if (DIRECT && INV && COMPUTED) load_direct(TR);
         __syncthreads();
         if (!INV) {
             ntt_round<LOGM, TE, RA, STRIDED, false, NT, false>(sm, tw, TR, 0, nq, pr.q4);
@@ -1021,43 +1088,67 @@ cudaError_t combine_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st
     }
 }
 
-// Inverse transform whose first pass forms its input with the tensor product.
-template <int LOGN, class P, int TE = 2048>
-cudaError_t tensor_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag)
+// Inverse transform whose first pass computes its input: the tensor
+// product (kFuseTensor) or the key-switch sums (kFuseIp).
+template <int LOGN, class P, int FUSE, int TE = 2048>
+cudaError_t computed_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag)
 {
     a.tiles = (1 << LOGN) / TE;
-    if (ngroups == 0) return run_pass<P::S2, P::A2, P::B2, P::C2, false, true, true, false, TE, kFuseTensor>(a, 0, st);
-    cudaError_t e = run_pass<P::S2, P::A2, P::B2, P::C2, false, true, true, false, TE, kFuseTensor>(a, ngroups, st);
+    if (ngroups == 0) return run_pass<P::S2, P::A2, P::B2, P::C2, false, true, true, false, TE, FUSE>(a, 0, st);
+    cudaError_t e = run_pass<P::S2, P::A2, P::B2, P::C2, false, true, true, false, TE, FUSE>(a, ngroups, st);
     if (e != cudaSuccess) return e;
-    prof_mark(c, st, tag, ".tensor_inv_pass1");
+    prof_mark(c, st, tag, FUSE == kFuseTensor ? ".tensor_inv_pass1" : ".ip_inv_pass1");
     e = run_pass<P::S1, P::A1, P::B1, P::C1, true, true, false, true, TE>(a, ngroups, st);
     prof_mark(c, st, tag, ".inv_pass2");
     return e;
 }
 
-template <int LOGN>
-cudaError_t tensor_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, int plan)
+// The plans of computed_plan (the one-pass cluster transform takes the
+// tensor product only; with the key-switch sums that bit is ignored).
+template <int LOGN, int FUSE>
+cudaError_t computed_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, int plan)
 {
-    if (LOGN == kClLogN && (plan & kPlanOnePass)) return onepass_tensor(c, a, ngroups, st, tag);
+    if (FUSE == kFuseTensor && LOGN == kClLogN && (plan & kPlanOnePass)) return onepass_tensor(c, a, ngroups, st, tag);
     // bit 3: 1024-element tiles (2^16 and 2^17; a pass over 2^10 stages keeps 2048)
     constexpr bool SMALL_OK = LOGN == 16 || LOGN == 17;
+    constexpr int TS = SMALL_OK ? 1024 : 2048;
     if (SMALL_OK && (plan & 8)) {
         switch (plan & 7) {
-        case 1: return tensor_plan<LOGN, Plan8<LOGN>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, st, tag);
-        case 2: return tensor_plan<LOGN, PlanV<LOGN, 1, false>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, st, tag);
-        case 3: return tensor_plan<LOGN, PlanV<LOGN, 1, true>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, st, tag);
-        case 4: return tensor_plan<LOGN, PlanV<LOGN, 2, false>, small_te<PlanV<LOGN, 2, false>>()>(c, a, ngroups, st, tag);
-        case 5: return tensor_plan<LOGN, PlanV<LOGN, 2, true>, small_te<PlanV<LOGN, 2, true>>()>(c, a, ngroups, st, tag);
-        default: return tensor_plan<LOGN, Plan<LOGN>, SMALL_OK ? 1024 : 2048>(c, a, ngroups, st, tag);
+        case 1: return computed_plan<LOGN, Plan8<LOGN>, FUSE, TS>(c, a, ngroups, st, tag);
+        case 2: return computed_plan<LOGN, PlanV<LOGN, 1, false>, FUSE, TS>(c, a, ngroups, st, tag);
+        case 3: return computed_plan<LOGN, PlanV<LOGN, 1, true>, FUSE, TS>(c, a, ngroups, st, tag);
+        case 4: return computed_plan<LOGN, PlanV<LOGN, 2, false>, FUSE, small_te<PlanV<LOGN, 2, false>>()>(c, a, ngroups, st, tag);
+        case 5: return computed_plan<LOGN, PlanV<LOGN, 2, true>, FUSE, small_te<PlanV<LOGN, 2, true>>()>(c, a, ngroups, st, tag);
+        default: return computed_plan<LOGN, Plan<LOGN>, FUSE, TS>(c, a, ngroups, st, tag);
         }
     }
     switch (plan & 7) {
-    case 1: return tensor_plan<LOGN, Plan8<LOGN>>(c, a, ngroups, st, tag);
-    case 2: return tensor_plan<LOGN, PlanV<LOGN, 1, false>>(c, a, ngroups, st, tag);
-    case 3: return tensor_plan<LOGN, PlanV<LOGN, 1, true>>(c, a, ngroups, st, tag);
-    case 4: return tensor_plan<LOGN, PlanV<LOGN, 2, false>>(c, a, ngroups, st, tag);
-    case 5: return tensor_plan<LOGN, PlanV<LOGN, 2, true>>(c, a, ngroups, st, tag);
-    default: return tensor_plan<LOGN, Plan<LOGN>>(c, a, ngroups, st, tag);
+    case 1: return computed_plan<LOGN, Plan8<LOGN>, FUSE>(c, a, ngroups, st, tag);
+    case 2: return computed_plan<LOGN, PlanV<LOGN, 1, false>, FUSE>(c, a, ngroups, st, tag);
+    case 3: return computed_plan<LOGN, PlanV<LOGN, 1, true>, FUSE>(c, a, ngroups, st, tag);
+    case 4: return computed_plan<LOGN, PlanV<LOGN, 2, false>, FUSE>(c, a, ngroups, st, tag);
+    case 5: return computed_plan<LOGN, PlanV<LOGN, 2, true>, FUSE>(c, a, ngroups, st, tag);
+    default: return computed_plan<LOGN, Plan<LOGN>, FUSE>(c, a, ngroups, st, tag);
+    }
+}
+
+// An inverse transform with a computed first pass, at the context's ring size.
+cudaError_t launch_computed(const he_ctx *c, const NttArgs &a, int ngroups, cudaStream_t st, const char *tag, int plan,
+                            bool ip)
+{
+    switch (c->logN) {
+    case 12: {
+        cudaError_t e = ip ? run_pass<12, 4, 4, 4, false, true, true, true, 4096, kFuseIp>(a, ngroups, st)
+                           : run_pass<12, 4, 4, 4, false, true, true, true, 4096, kFuseTensor>(a, ngroups, st);
+        if (ngroups) prof_mark(c, st, tag, ip ? ".ip_inv" : ".tensor_inv");
+        return e;
+    }
+    case 13: return ip ? computed_any<13, kFuseIp>(c, a, ngroups, st, tag, plan) : computed_any<13, kFuseTensor>(c, a, ngroups, st, tag, plan);
+    case 14: return ip ? computed_any<14, kFuseIp>(c, a, ngroups, st, tag, plan) : computed_any<14, kFuseTensor>(c, a, ngroups, st, tag, plan);
+    case 15: return ip ? computed_any<15, kFuseIp>(c, a, ngroups, st, tag, plan) : computed_any<15, kFuseTensor>(c, a, ngroups, st, tag, plan);
+    case 16: return ip ? computed_any<16, kFuseIp>(c, a, ngroups, st, tag, plan) : computed_any<16, kFuseTensor>(c, a, ngroups, st, tag, plan);
+    case 17: return ip ? computed_any<17, kFuseIp>(c, a, ngroups, st, tag, plan) : computed_any<17, kFuseTensor>(c, a, ngroups, st, tag, plan);
+    default: return cudaErrorInvalidValue;
     }
 }
 
@@ -1081,19 +1172,29 @@ cudaError_t launch_ntt_tensor(const he_ctx *c, u64 *base, const NttGroup *groups
     a.R = R;
     a.levels = c->d_levels;
     a.pinv = c->d_pinv;
-    switch (c->logN) {
-    case 12: {
-        cudaError_t e = run_pass<12, 4, 4, 4, false, true, true, true, 4096, kFuseTensor>(a, ngroups, st);
-        if (ngroups) prof_mark(c, st, tag, ".tensor_inv");
-        return e;
-    }
-    case 13: return tensor_any<13>(c, a, ngroups, st, tag, plan);
-    case 14: return tensor_any<14>(c, a, ngroups, st, tag, plan);
-    case 15: return tensor_any<15>(c, a, ngroups, st, tag, plan);
-    case 16: return tensor_any<16>(c, a, ngroups, st, tag, plan);
-    case 17: return tensor_any<17>(c, a, ngroups, st, tag, plan);
-    default: return cudaErrorInvalidValue;
-    }
+    return launch_computed(c, a, ngroups, st, tag, plan, false);
+}
+
+cudaError_t launch_ntt_ip(const he_ctx *c, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
+                          const u64 *evk, cudaStream_t st, const char *tag, const int *dev_count, int plan)
+{
+    if (ngroups < 0) return cudaSuccess;  // ngroups == 0: configure the kernels only
+    NttArgs a;
+    memset(&a, 0, sizeof(a));
+    a.src = base;
+    a.dst = base;
+    a.groups = groups;
+    a.primes = c->d_primes;
+    a.logN = c->logN;
+    a.ts = c->logN - ntt_direct_stages(c->logN);
+    a.tiles = 1;
+    a.count = dev_count;
+    a.pdl = c->pdl;
+    a.R = R;
+    a.levels = c->d_levels;
+    a.evk = evk;
+    a.EL = c->K + c->L;
+    return launch_computed(c, a, ngroups, st, tag, plan, true);
 }
 
 cudaError_t launch_ntt_combine(const he_ctx *c, u64 *base, const NttGroup *groups, int ngroups, const JobRef &R,
@@ -1193,6 +1294,8 @@ cudaError_t configure_ntt(const he_ctx *c)
         e = launch_ntt_combine(c, nullptr, nullptr, 0, R, nullptr, nullptr, nullptr, plan);
         if (e != cudaSuccess) return e;
         e = launch_ntt_tensor(c, nullptr, nullptr, 0, R, nullptr, nullptr, nullptr, plan);
+        if (e != cudaSuccess) return e;
+        e = launch_ntt_ip(c, nullptr, nullptr, 0, R, nullptr, nullptr, nullptr, nullptr, plan);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

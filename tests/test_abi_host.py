@@ -130,9 +130,9 @@ def test_host_seeded_key_matches_oracle_n12(g):
 
 def test_shape_setters(g):
     ctx = g.Context(g.PRESETS["n12"][0], device=False)
-    assert g.he_get_shape(ctx) == (4, 8, 1, 0, 8, 3, 0, 0, 0)
+    assert g.he_get_shape(ctx) == (4, 8, 1, 0, 8, 7, 0, 0, 0)
     g.he_set_shape(ctx, 2, 16, 0)
-    assert g.he_get_shape(ctx) == (2, 16, 0, 0, 8, 3, 0, 0, 0)
+    assert g.he_get_shape(ctx) == (2, 16, 0, 0, 8, 7, 0, 0, 0)
     g.he_set_shape(ctx, 2, 16, 0, 5, 4, 0)
     assert g.he_get_shape(ctx) == (2, 16, 0, 5, 4, 0, 0, 0, 0)
     g.he_set_shape(ctx, 2, 16, 2, 5, 4, 0, 2, 9)
@@ -143,7 +143,7 @@ def test_shape_setters(g):
     for bad in ((0, 8, 1, 0, 8, 1), (5, 8, 1, 0, 8, 1), (4, 6, 1, 0, 8, 1), (4, 32, 1, 0, 8, 1), (4, 8, 3, 0, 8, 1),
                 (4, 8, -1, 0, 8, 1),
                 (4, 8, 1, 16, 8, 1), (4, 8, 1, -1, 8, 1), (4, 8, 1, 0, 0, 1), (4, 8, 1, 0, 2, 1), (4, 8, 1, 0, 9, 1),
-                (4, 8, 1, 0, 8, 4), (4, 8, 1, 0, 8, -1), (4, 8, 1, 0, 8, 1, 3), (4, 8, 1, 0, 8, 1, -1),
+                (4, 8, 1, 0, 8, 8), (4, 8, 1, 0, 8, -1), (4, 8, 1, 0, 8, 1, 3), (4, 8, 1, 0, 8, 1, -1),
                 (4, 8, 1, 0, 8, 1, 0, 16), (4, 8, 1, 0, 8, 1, 0, -1), (4, 8, 1, 0, 8, 1, 0, 0, 16),
                 (4, 8, 1, 0, 8, 1, 0, 0, -1)):
         with pytest.raises(g.HeError) as e:

@@ -237,7 +237,13 @@ def test_he_mul_rescale_n17_full(g):
     ct1, ct2 = rand_ct(op, level, 91), rand_ct(op, level, 93)
     evk = rand_evk(op, 100)
     want = oracle.rescale(op, oracle.he_mul(op, ct1, ct2, evk, level), level)
-    assert np.array_equal(gpu_mul(g, ctx, ct1, ct2, dev(g, evk), level, fused=True), want)
+    evk_t = dev(g, evk)
+    assert np.array_equal(gpu_mul(g, ctx, ct1, ct2, evk_t, level, fused=True), want)
+    try:  # four digits: the special rows' sums inside their iNTT's first pass
+        g.he_set_shape(ctx, 1, 16, 1, 9, 8, 7, 1)
+        assert np.array_equal(gpu_mul(g, ctx, ct1, ct2, evk_t, level, fused=True), want)
+    finally:
+        g.he_set_shape(ctx, 4, 8, 1)
 
 
 def test_batch_matches_single_and_oracle(g):
@@ -634,7 +640,8 @@ def test_every_shape_is_bit_identical_n16(g):
     try:
         for shape in ((1, 4, 1, 15), (2, 16, 0, 5), (3, 8, 1, 10), (4, 16, 0, 0), (4, 8, 1, 0), (1, 8, 1, 3),
                       (1, 8, 1, 8, 8, 0), (3, 4, 0, 1, 8, 0), (2, 8, 1, 15, 8, 0), (1, 8, 2, 9, 8, 1),
-                      (4, 16, 2, 0, 8, 0), (1, 8, 2, 9, 8, 2), (2, 16, 1, 6, 8, 3), (1, 4, 0, 0, 8, 2)):
+                      (4, 16, 2, 0, 8, 0), (1, 8, 2, 9, 8, 2), (2, 16, 1, 6, 8, 3), (1, 4, 0, 0, 8, 2),
+                      (1, 8, 2, 15, 8, 7, 1, 1), (3, 8, 1, 0, 8, 6), (2, 16, 0, 5, 8, 7, 2), (1, 8, 1, 15, 8, 5)):
             g.he_set_shape(ctx, *shape)
             assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want), shape
         want_plain = oracle.he_mul(op, c1, c2, evk, level)
@@ -663,7 +670,8 @@ def test_ntt_pass_splits_bit_identical(g, name, level, split):
     try:
         for r8 in (0, 15, 5):
             for small in (0, 15, 10):
-                g.he_set_shape(ctx, 1, 8, 1, r8, 8, 3, split, small)
+                fz = 7 if small == 10 else 3  # and the special rows' sums inside their iNTT
+                g.he_set_shape(ctx, 1, 8, 1, r8, 8, fz, split, small)
                 assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want), (split, r8, small)
         E = op.K + op.L
         idx = [0, op.K, E - 1]
@@ -836,6 +844,9 @@ def test_seeded_key_he_mul_bit_exact(g, name, levels):
             assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_b, level, fused=False), want), level
             got = gpu_mul(g, ctx, c1, c2, evk_b, level, fused=True)
             assert np.array_equal(got, oracle.rescale(op, want, level)), level
+            g.he_set_shape(ctx, 4, 8, 1, 0, 8, 7)  # a seeded key keeps its own sums kernel
+            assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_b, level, fused=True), got), level
+            g.he_set_shape(ctx, 4, 8, 1)
         z = oracle.decrypt(op, sk, got, levels[-1] - 1, sc * sc / int(op.q[levels[-1] - 1]))
         assert np.abs(z - m1 * m2).max() < (2.0 ** -14 if name == "n12" else 2.0 ** -24)
         # the same jobs batched

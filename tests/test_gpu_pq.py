@@ -45,7 +45,7 @@ def test_pq_n16_real_keys(g, level):
     c1, c2 = cut(ct1, level), cut(ct2, level)
     want = oracle.he_mul_rescale_pq(op, c1, c2, evk, level)
     try:
-        for shape in ((1, 8, 1, 0), (2, 16, 1, 15)):
+        for shape in ((1, 8, 1, 0), (2, 16, 1, 15), (1, 8, 2, 15, 8, 7, 1, 1)):
             g.he_set_shape(ctx, *shape)
             assert np.array_equal(gpu_pq(g, ctx, c1, c2, evk_t, level), want), shape
     finally:
