@@ -601,9 +601,10 @@ def run_ours(args):
     value = job_rate(args.steps, wsz, elapsed_ms * 1e-3)
     # the final combine runs inside the last NTT pass; with fuse bit 0 the
     # tensor product runs inside the first one (bit 1 moves the q rows of the
-    # inner product into the ModDown launch: the launch count stays)
+    # inner product into the ModDown launch: the launch count stays; bit 2
+    # with it moves the other rows into the special limbs' iNTT: one fewer)
     fz = g.he_get_shape(ctx)[5]
-    launches_per_step = (12 if prm.logN > 12 else 8) - (1 if fz & 1 else 0)
+    launches_per_step = (12 if prm.logN > 12 else 8) - (1 if fz & 1 else 0) - (1 if (fz & 6) == 6 else 0)
 
     # ---- end to end: host buffers through he_mul_rescale_host ----
     hws = torch.empty(g.he_host_workspace_bytes(ctx, level) // 8, dtype=torch.int64, device=dev)
