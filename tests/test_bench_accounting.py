@@ -81,8 +81,9 @@ def test_committed_profile_lines_parse():
                 assert int(nbytes) > 0
                 assert name not in seen, f"{name} in {path} and {seen.get(name)}"
                 seen[name] = path
-    # every kernel of the event profile of the fused, split-row step (the shape
-    # the autotuner keeps at N = 2^16) has a committed DRAM figure
-    fused = ["intt_d2.tensor_inv_pass1"] + NTT_KERNELS[1:]
-    for k in fused + ["modup", "inner_product_special", "moddown_conv_ipq"]:
+    # every kernel of the event profile of the fused step (the shape the
+    # autotuner keeps at N = 2^16: tensor product and special rows' sums inside
+    # their iNTTs, q rows beside the ModDown conversion) has a committed DRAM figure
+    fused = ["intt_d2.tensor_inv_pass1"] + NTT_KERNELS[1:4] + ["intt_special.ip_inv_pass1"] + NTT_KERNELS[5:]
+    for k in fused + ["modup", "moddown_conv_ipq"]:
         assert k in seen, k
