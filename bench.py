@@ -856,6 +856,17 @@ def run_ours(args):
     conv_width = {"modup": kernel_width(prm.alpha), "moddown_conv": kernel_width(prm.K)}
     conv_peak = {k: g.he_probe_conversion_rate(w, 152 * 8, max(64, 4096 // w), stream) for k, w in conv_width.items()}
     probe = {"butterfly_per_s": bfly_peak, "conversion_mac_per_s": conv_peak, "conversion_width": conv_width}
+    # the CUDA-core remainder of a byte-split tensor-core conversion (planes ->
+    # 128 bits -> reduction) against the whole CUDA-core conversion, per output
+    recomb = g.he_probe_recombine_rate(152 * 8, 1024, stream)
+    probe["byte_split_tensor_conversion"] = {
+        "recombine_outputs_per_s": recomb,
+        "cuda_core_outputs_per_s": {k: conv_peak[k] / w for k, w in conv_width.items()},
+        "what": "outputs/s of the CUDA-core work left per output by a byte-split tensor-core conversion (13 fp32 "
+                "planes to 128 bits, lazy Barrett; MMA not counted) beside the outputs/s of the whole CUDA-core "
+                "conversion at the kernels' widths: below 1 means the tensor-core form cannot be faster"}
+    probe["byte_split_tensor_conversion"]["ratio"] = {
+        k: recomb / v for k, v in probe["byte_split_tensor_conversion"]["cuda_core_outputs_per_s"].items()}
     for k, d in per_kernel.items():
         if d["kind"] == "alu":
             d["frac_of_probe"] = d["Gbutterfly_s"] * 1e9 / bfly_peak

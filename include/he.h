@@ -550,6 +550,17 @@ int he_probe_butterfly_rate(int blocks, int iters, double *bfly_per_s, void *str
  * outputs x `iters`.  The ALU ceiling the ModUp and ModDown conversions are
  * compared against.  HE_EINVAL for another width or a non-positive count. */
 int he_probe_conversion_rate(int width, int blocks, int iters, double *mac_per_s, void *stream);
+/* Measurement helper: rate (outputs per second) of the work a byte-split
+ * tensor-core base conversion would still leave on the CUDA cores per output
+ * (the north star's "exact byte-split form" of the conversion's matrix
+ * product, Sec. 7's base conversion): the MMA's 13 fp32 byte-diagonal planes,
+ * each an exact integer below 2^23, turned into integers, shifted and added
+ * into 128 bits, then one lazy Barrett reduction; register-resident, MMA not
+ * counted; `blocks` x 256 threads x 16 outputs x `iters`.  Compare with
+ * he_probe_conversion_rate / width, the outputs per second of the CUDA-core
+ * conversion itself.  HE_EINVAL for a non-positive count or iters above
+ * 2^18. */
+int he_probe_recombine_rate(int blocks, int iters, double *out_per_s, void *stream);
 
 const char *he_strerror(int code);
 /* Name of the CUDA error behind the calling thread's last HE_ECUDA. */

@@ -128,6 +128,7 @@ _SIGS = {
     "he_probe_butterfly_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "he_probe_conversion_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.c_void_p]),
+    "he_probe_recombine_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "he_galois_elt": (ctypes.c_uint64, [ctypes.c_void_p, ctypes.c_int]),
     "he_conj_elt": (ctypes.c_uint64, [ctypes.c_void_p]),
     "he_nr_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
@@ -631,6 +632,15 @@ def he_probe_conversion_rate(width: int, blocks: int, iters: int, stream=None) -
     r = ctypes.c_double()
     _check(lib().he_probe_conversion_rate(width, blocks, iters, ctypes.byref(r), _stream_ptr(stream)),
            "he_probe_conversion_rate")
+    return r.value
+
+
+def he_probe_recombine_rate(blocks: int, iters: int, stream=None) -> float:
+    """Outputs/s of a byte-split tensor-core conversion's CUDA-core remainder
+    (13 fp32 planes -> 128 bits -> lazy Barrett), register-resident."""
+    r = ctypes.c_double()
+    _check(lib().he_probe_recombine_rate(blocks, iters, ctypes.byref(r), _stream_ptr(stream)),
+           "he_probe_recombine_rate")
     return r.value
 
 

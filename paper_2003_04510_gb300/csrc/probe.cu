@@ -80,6 +80,53 @@ __global__ void __launch_bounds__(256) k_probe_conv(u64 *out, const u64 *rows, u
     out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
 }
 
+// The recombination a byte-split tensor-core base conversion would need per
+// output.  Such a conversion (residues and constants cut into 8-bit pieces,
+// exact in bf16, products summed in fp32 by the MMA) leaves, per output, 13
+// fp32 planes S_d = sum over byte pairs (a, b) with a + b = d, each an exact
+// integer below 2^23 for up to 16 terms; the output is
+// (sum_d S_d 2^(8 d)) mod q.  Here each plane is turned into an integer by
+// the cheapest exact route (adding 2^23 and masking the significand), the
+// shifted planes are added into a 128-bit value and reduced lazily into
+// [0, 2q) (no final subtraction): the least a tensor-core conversion must
+// still execute on the CUDA cores per output, MMA not counted.  Every output
+// shifts every plane by a loop-carried count (folded into the magic 2^23), so
+// nothing is hoisted out of the loop.
+constexpr int kPlanes = 13;
+
+__global__ void __launch_bounds__(256) k_probe_recombine(u64 *out, u64 q, u64 mu, unsigned sh, int iters)
+{
+    float S[kPlanes];
+#pragma unroll
+    for (int d = 0; d < kPlanes; d++)
+        S[d] = (float)((threadIdx.x * 2654435761u + d * 40503u + blockIdx.x * 977u) & 0x3FFFFFu);  // < 2^22
+    u64 acc = 0;
+    float t = 8388608.0f;  // 2^23 + the output count (below 2^22)
+    for (int it = 0; it < iters; it++) {
+#pragma unroll 2
+        for (int o = 0; o < kRows; o++) {
+            U128 v = {0, 0};
+#pragma unroll
+            for (int d = 0; d < kPlanes; d++) {
+                const u64 p = (u64)(__float_as_uint(S[d] + t) & 0x7FFFFFu);  // exact: S_d + count < 2^23
+                const int shl = 8 * d;
+                const u64 lo = shl < 64 ? p << shl : 0ull;
+                const u64 hi = shl == 0 ? 0ull : shl < 64 ? p >> (64 - shl) : p << (shl - 64);
+                v.lo += lo;
+                v.hi += hi + (v.lo < lo ? 1ull : 0ull);
+            }
+            const uint32_t l0 = (uint32_t)v.lo, l1 = (uint32_t)(v.lo >> 32), h0 = (uint32_t)v.hi,
+                           h1 = (uint32_t)(v.hi >> 32);
+            const bool up = sh >= 32;
+            const uint32_t w0 = up ? l1 : l0, w1 = up ? h0 : l1, w2 = up ? h1 : h0;
+            const u64 u = ((u64)__funnelshift_r(w1, w2, sh) << 32) | __funnelshift_r(w0, w1, sh);
+            acc ^= v.lo - __umul64hi(u, mu) * q;
+            t += 1.0f;
+        }
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
 // q_0 of the N = 2^16 chain (54 bits) and its Barrett constants as the
 // context computes them (s = bitlen(q) - 2, mu = floor(2^(64+s) / q)).
 constexpr u64 kProbeQ = 18014398506729473ull;
@@ -166,5 +213,25 @@ extern "C" int he_probe_conversion_rate(int width, int blocks, int iters, double
     if (rc != HE_OK) return rc;
     // per thread and trip: kRows outputs on two coefficients, `width` terms each
     *mac_per_s = (double)blocks * 256.0 * kRows * 2.0 * width * (double)iters / (ms * 1e-3);
+    return HE_OK;
+}
+
+extern "C" int he_probe_recombine_rate(int blocks, int iters, double *out_per_s, void *stream)
+{
+    // the count folded into the planes stays below 2^22 (exact in fp32)
+    if (blocks < 1 || iters < 1 || iters > (1 << 22) / kRows || !out_per_s) return HE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const u64 q = kProbeQ;
+    const unsigned sh = 64 - __builtin_clzll(q) - 2;
+    const u64 mu = (u64)(((unsigned __int128)1 << (64 + sh)) / q);
+    u64 *out = nullptr;
+    if (cudaMallocAsync((void **)&out, sizeof(u64) * blocks * 256, st) != cudaSuccess) return HE_ECUDA;
+    float ms = 0;
+    const int rc = time_launch(st, [&](bool warm) {
+        k_probe_recombine<<<blocks, 256, 0, st>>>(out, q, mu, sh, warm ? iters / 10 + 1 : iters);
+    }, &ms);
+    cudaFreeAsync(out, st);
+    if (rc != HE_OK) return rc;
+    *out_per_s = (double)blocks * 256.0 * kRows * (double)iters / (ms * 1e-3);
     return HE_OK;
 }

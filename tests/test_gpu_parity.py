@@ -864,3 +864,20 @@ def test_seeded_key_he_mul_bit_exact(g, name, levels):
             assert np.array_equal(host(g, j[2]), w)
     finally:
         g.he_evk_unregister(ctx, evk_b)
+
+
+# ---------------------------------------------------------------------------
+# measurement probes (the ALU ceilings the bench grades kernels against)
+# ---------------------------------------------------------------------------
+def test_probes_run_and_reject_bad_arguments(g):
+    bfly = g.he_probe_butterfly_rate(152, 64)
+    conv = g.he_probe_conversion_rate(8, 152, 64)
+    recomb = g.he_probe_recombine_rate(152, 64)
+    # GB300 at any clock: between 10^10 and 10^14 per second
+    for r in (bfly, conv, recomb):
+        assert 1e10 < r < 1e14, r
+    for bad in ((0, 64), (152, 0), (152, 1 << 20)):
+        with pytest.raises(g.HeError):
+            g.he_probe_recombine_rate(*bad)
+    with pytest.raises(g.HeError):
+        g.he_probe_conversion_rate(3, 152, 64)
