@@ -313,12 +313,13 @@ def hbm_peak_gbs() -> float:
 
 def inner_product_alone(g, ctx, step, level, steps=10):
     """The key-switch inner product as its own kernel (all K + l rows; the
-    shape's split and fused-sum bits off for these steps only), timed in the
-    event profile: its HBM rate against the measured copy rate.  With the
-    autotuned shape the same sums run inside the ModDown launch and the
-    special limbs' first iNTT pass, where no kernel has them alone."""
+    shape's split and fused-sum bits off and programmatic launch off for these
+    steps only, so no neighbouring kernel shares its SMs), timed in the event
+    profile: its HBM rate against the measured copy rate.  With the autotuned
+    shape the same sums run inside the ModDown launch and the special limbs'
+    first iNTT pass, where no kernel has them alone."""
     shape = g.he_get_shape(ctx)
-    g.he_set_shape(ctx, *(shape[:5] + (shape[5] & 1,) + shape[6:]))
+    g.he_set_shape(ctx, *(shape[:2] + (0,) + shape[3:5] + (shape[5] & 1,) + shape[6:]))
     try:
         for k in range(3):
             step(k)
@@ -336,7 +337,8 @@ def inner_product_alone(g, ctx, step, level, steps=10):
     ach = b / (us * 1e-6) / 1e9
     peak = hbm_peak_gbs()
     return {"us": us, "bytes": b, "achieved_gbs": ach, "peak_gbs": peak, "frac": ach / peak,
-            "what": "the inner product with the evaluation key (all rows) as its own kernel, same shape otherwise"}
+            "what": "the inner product with the evaluation key (all rows) as its own kernel, no programmatic "
+                    "launch, same shape otherwise"}
 
 
 def run_batched(g, ctx, evk_t, dev, stream, wsz, count=64, reps=20):
