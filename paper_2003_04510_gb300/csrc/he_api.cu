@@ -139,7 +139,7 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
     // instead be formed by the first pass of their own iNTT (unseeded keys)
     bool seeded = false;
     for (const auto &k : c->seeded) seeded = seeded || k.ptr == evk;
-    const bool ip_in_ntt = split && (c->fuse & 4) && !seeded;
+    const bool ip_in_ntt = split && (c->fuse & 4) && !seeded && c->dnum <= kIpFuseDigits;
     if (S.ipg) {
         capture_tag = kTagIpGroups;
         HE_TRY(run_inner_product_shared(c, R, S.ipg, S.n_ipg, cnt ? cnt + 4 : nullptr, evk, st));

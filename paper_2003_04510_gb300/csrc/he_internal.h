@@ -16,6 +16,8 @@ typedef uint64_t u64;
 namespace he {
 
 constexpr int kMaxDigits = 16;
+// digits the fused key-switch sums of an NTT pass's tile load take (ip_tile)
+constexpr int kIpFuseDigits = 4;
 constexpr int kMaxK = 16;
 constexpr int kMaxL = 64;
 

@@ -303,8 +303,7 @@ __device__ __forceinline__ void tensor_tile(const NttArgs &P, const NttGroup &G,
 // U_j[e] is row e of digit j's ModUp output, or row e - K of d2 for the
 // digit's own limbs; the products of up to kIpFuseDigits digits are summed in
 // 128 bits and reduced once (below 4 q^2 < 2^112).  The sums are not stored:
-// only this transform reads them.
-constexpr int kIpFuseDigits = 4;
+// only this transform reads them.  At most kIpFuseDigits digits.
 
 template <int TE, int NT>
 __device__ __forceinline__ void ip_tile(const NttArgs &P, const NttGroup &G, int k, int tile, const DevPrime &pr,

@@ -692,6 +692,26 @@ def test_ntt_pass_splits_bit_identical(g, name, level, split):
         g.he_set_shape(ctx, 4, 8, 1)
 
 
+@pytest.mark.parametrize("name,levels", [("n16", (2, 3, 8, 9)), ("n15", (2, 5)), ("n12", (2, 3))])
+def test_fused_special_sums_low_levels(g, name, levels):
+    """The special rows' key-switch sums inside their iNTT's first pass (fuse
+    bit 2) at the lowest levels and at digit boundaries (a short last digit,
+    q_{l-1} in the first digit), on every ring size's plans: the oracle's words."""
+    op = oracle.preset(name)
+    ctx = ctx_for(g, name)
+    evk = rand_evk(op, 1010)
+    evk_t = dev(g, evk)
+    try:
+        for level in levels:
+            c1, c2 = rand_ct(op, level, 1020 + level), rand_ct(op, level, 1040 + level)
+            want = oracle.rescale(op, oracle.he_mul(op, c1, c2, evk, level), level)
+            for shape in ((1, 8, 2, 15, 8, 7), (3, 4, 1, 0, 8, 7)):
+                g.he_set_shape(ctx, *shape)
+                assert np.array_equal(gpu_mul(g, ctx, c1, c2, evk_t, level, fused=True), want), (level, shape)
+    finally:
+        g.he_set_shape(ctx, 4, 8, 1)
+
+
 @pytest.mark.parametrize("level", [24, 3])
 def test_onepass_cluster_bit_identical(g, level):
     """The one-pass transforms over a cluster of 8 CTAs (N = 2^16) at every
