@@ -1204,6 +1204,7 @@ cudaError_t launch_ntt_combine(const he_ctx *c, u64 *base, const NttGroup *group
 {
     if (ngroups < 0) return cudaSuccess;  // ngroups == 0: configure the kernels only
     NttArgs a;
+    memset(&a, 0, sizeof(a));
     a.src = base;
     a.dst = base;
     a.groups = groups;
@@ -1236,6 +1237,7 @@ cudaError_t launch_ntt2(const he_ctx *c, const u64 *src, u64 *dst, const NttGrou
 {
     if (ngroups < 0) return cudaSuccess;  // ngroups == 0: configure the kernels only
     NttArgs a;
+    memset(&a, 0, sizeof(a));
     a.src = src;
     a.dst = dst;
     a.groups = groups;
