@@ -134,7 +134,7 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
     // a single job's q-limb sums (read only by the final combine) may run
     // beside the ModDown conversion: the sums of the special limbs and the
     // last q limb (the next iNTT's inputs) come first
-    const bool split = (c->fuse & 2) && !S.ipg && !R.items && mode != kTailPlain && moddown_ipq_fits(c);
+    const bool split = (c->fuse & 2) && !S.ipg && !R.items && moddown_ipq_fits(c);
     // with the split, the sums of the special limbs and the last q limb may
     // instead be formed by the first pass of their own iNTT (unseeded keys)
     bool seeded = false;
@@ -146,7 +146,8 @@ int run_keyswitch(he_ctx *c, const JobRef &R, u64 *ntt_base, const Stages &S, co
         prof_mark(c, st, "inner_product");
     } else if (!ip_in_ntt) {
         capture_tag = kTagJobs;
-        HE_TRY(run_inner_product(c, R, evk, st, split ? kIpSpecialLastRows : kIpAllRows));
+        HE_TRY(run_inner_product(c, R, evk, st,
+                                 !split ? kIpAllRows : mode == kTailPlain ? kIpSpecialRows : kIpSpecialLastRows));
         prof_mark(c, st, split ? "inner_product_special" : "inner_product");
     }
     // ModDown: iNTT of the special limbs (times N^-1 Phat^-1), conversion, NTT

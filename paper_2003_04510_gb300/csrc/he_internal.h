@@ -330,7 +330,7 @@ cudaError_t run_elementwise(const he_ctx *c, int op, const u64 *x, const u64 *y,
 cudaError_t run_automorph(const he_ctx *c, const u64 *ct, u64 *ws, int l, u64 g, cudaStream_t st);
 // rows (IpRows in keyswitch.cu): 0 every ext limb; 1 the special limbs and the
 // last q limb; 2 the special limbs; 3 the q limbs but the last; 4 the q limbs.
-enum { kIpAllRows = 0, kIpSpecialLastRows = 1 };
+enum { kIpAllRows = 0, kIpSpecialLastRows = 1, kIpSpecialRows = 2 };
 cudaError_t run_inner_product(const he_ctx *c, const JobRef &R, const u64 *evk, cudaStream_t st,
                               int rows = kIpAllRows);
 // The ModDown conversion (rescaling tails) and the key-switch sums of the q

@@ -799,10 +799,10 @@ bool moddown_ipq_fits(const he_ctx *c)
 
 cudaError_t run_moddown_ipq(const he_ctx *c, const JobRef &R, int mode, const u64 *evk, cudaStream_t st)
 {
-    if (!moddown_ipq_fits(c) || mode == kTailPlain) return cudaErrorInvalidValue;
+    if (!moddown_ipq_fits(c)) return cudaErrorInvalidValue;
     const int chunks = (R.lmax + kModdownChunk - 1) / kModdownChunk;
     dim3 g = grid_x(c->N);
-    g.y = 2 * chunks + R.lmax - 1;
+    g.y = 2 * chunks + (mode == kTailPlain ? R.lmax : R.lmax - 1);  // the q rows the final additions read
     g.z = R.B;
     const int K = c->K, bm = (c->L + c->alpha - 1) / c->alpha;
     bool seeded;
@@ -820,6 +820,7 @@ cudaError_t run_moddown_ipq(const he_ctx *c, const JobRef &R, int mode, const u6
 #define HE_MDQ_M(KK)                                                                                                 \
     do {                                                                                                             \
         if (mode == kTailRescale) HE_MDQ_B(KK, kTailRescale);                                                        \
+        else if (mode == kTailPlain) HE_MDQ_B(KK, kTailPlain);                                                       \
         else HE_MDQ_B(KK, kTailRescalePQ);                                                                           \
     } while (0)
     if (c->KP == 1) HE_MDQ_M(1);
