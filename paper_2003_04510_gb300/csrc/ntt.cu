@@ -710,28 +710,32 @@ __device__ __forceinline__ void cross_inv(u64 (&a)[8], const ulonglong2 (&w)[7],
     }
 }
 
-template <int R0, int R1, int R2, int R3>
+// Local rounds R0..R4 in forward order (R4 = 0: four rounds); the last one
+// is the direct round.  NT threads: one set of the widest round each.
+template <int R0, int R1, int R2, int R3, int R4>
 struct ClGeom {
-    static constexpr int RMAX = cmax(cmax(R0, R1), cmax(R2, R3));
+    static constexpr int RMAX = cmax(cmax(cmax(R0, R1), cmax(R2, R3)), R4);
     static constexpr int NT = kClTE >> RMAX;
-    using Gm = Geometry<kClLogM, kClTE, false, R3>;
+    static constexpr int RL = R4 ? R4 : R3;
+    using Gm = Geometry<kClLogM, kClTE, false, RL>;
     static constexpr size_t SMEM = sizeof(ulonglong2) * Gm::TWN + sizeof(u64) * Gm::DATA;  // one data buffer
 };
 
-template <int R0, int R1, int R2, int R3, bool INV, int FUSE>
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(ClGeom<R0, R1, R2, R3>::NT, 1)
+template <int R0, int R1, int R2, int R3, int R4, bool INV, int FUSE>
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(ClGeom<R0, R1, R2, R3, R4>::NT, 1)
 k_ntt_cluster(const NttArgs P)
 {
     constexpr bool COMBINE = FUSE == kFuseCombine, TENSOR = FUSE == kFuseTensor;
     static_assert(!COMBINE || !INV, "the combine follows a forward transform");
     static_assert(!TENSOR || INV, "the tensor product feeds an inverse transform");
-    using CG = ClGeom<R0, R1, R2, R3>;
+    using CG = ClGeom<R0, R1, R2, R3, R4>;
     using Gm = typename CG::Gm;
-    constexpr int LOGM = kClLogM, TE = kClTE, NT = CG::NT, RL = R3, L0 = LOGM - RL;
-    static_assert(R0 + R1 + R2 + R3 == LOGM, "rounds must cover the local stages");
+    constexpr int LOGM = kClLogM, TE = kClTE, NT = CG::NT, RL = CG::RL, L0 = LOGM - RL;
+    static_assert(R0 + R1 + R2 + R3 + R4 == LOGM, "rounds must cover the local stages");
     static_assert(Gm::NG == 1, "one group per chunk");
-    constexpr int CK = TE / kCl;  // cross-round offsets per CTA
-    static_assert(CK == 2 * NT, "two consecutive offsets per thread in the cross round");
+    constexpr int CK = TE / kCl;    // cross-round offsets per CTA
+    constexpr int CPT = CK / NT;    // per thread: consecutive offsets k0 .. k0 + CPT - 1
+    static_assert(CPT * NT == CK && (CPT == 1 || CPT == 2), "one or two offsets per thread in the cross round");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ulonglong2 *tw = reinterpret_cast<ulonglong2 *>(smem_raw);
     u64 *sm = reinterpret_cast<u64 *>(smem_raw + sizeof(ulonglong2) * Gm::TWN);
@@ -759,10 +763,11 @@ k_ntt_cluster(const NttArgs P)
     }
     __pipeline_commit();
     prefetch_direct_tw<LOGM, TE, RL, NT>(twg, tile, s0, P.ts);
-    // this thread's two cross-round offsets k0, k0 + 1 and their words in
-    // every CTA's shared memory
-    const int k0 = tile * CK + 2 * threadIdx.x;
-    const uint32_t ko0 = 8u * (uint32_t)padi(k0), ko1 = 8u * (uint32_t)padi(k0 + 1);
+    // this thread's cross-round offsets and their words in every CTA's shared memory
+    const int k0 = tile * CK + CPT * threadIdx.x;
+    uint32_t ko[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; c++) ko[c] = 8u * (uint32_t)padi(k0 + c);
     uint32_t rb[kCl];
 #pragma unroll
     for (int v = 0; v < kCl; v++) rb[v] = cl_map(sm, (unsigned)v);
@@ -793,21 +798,24 @@ k_ntt_cluster(const NttArgs P)
         for (int t = 0; t < 7; t++) cw[t] = ld_tw(twg + 1 + t);
         if (!INV) {
             const u64 *src = P.src + ((size_t)G.src[i] << P.logN);
-            u64 a[8], b[8];
+            u64 a[CPT][8];
 #pragma unroll
             for (int v = 0; v < 8; v++) {
-                const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(src + (size_t)v * TE + k0);
-                a[v] = x.x;
-                b[v] = x.y;
+                if constexpr (CPT == 2) {
+                    const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(src + (size_t)v * TE + k0);
+                    a[0][v] = x.x;
+                    a[CPT - 1][v] = x.y;
+                } else {
+                    a[0][v] = src[(size_t)v * TE + k0];
+                }
             }
-            cross_fwd(a, cw, nq, pr.q4);
-            cross_fwd(b, cw, nq, pr.q4);
+#pragma unroll
+            for (int c = 0; c < CPT; c++) cross_fwd(a[c], cw, nq, pr.q4);
             cl_sync();  // every CTA of the cluster runs and is done with its previous chunk
 #pragma unroll
-            for (int v = 0; v < 8; v++) {
-                cl_st(rb[v] + ko0, a[v]);
-                cl_st(rb[v] + ko1, b[v]);
-            }
+            for (int v = 0; v < 8; v++)
+#pragma unroll
+                for (int c = 0; c < CPT; c++) cl_st(rb[v] + ko[c], a[c][v]);
             __pipeline_wait_prior(0);  // this thread's staged twiddles
             cl_sync();                 // every chunk complete, the twiddles visible
             ntt_round<LOGM, TE, R0, false, false, NT, false>(sm, tw, TR, 0, nq, pr.q4);
@@ -815,9 +823,13 @@ k_ntt_cluster(const NttArgs P)
             ntt_round<LOGM, TE, R1, false, false, NT, false>(sm, tw, TR, R0, nq, pr.q4);
             __syncthreads();
             ntt_round<LOGM, TE, R2, false, false, NT, false>(sm, tw, TR, R0 + R1, nq, pr.q4);
+            if constexpr (R4 != 0) {
+                __syncthreads();
+                ntt_round<LOGM, TE, R3, false, false, NT, false>(sm, tw, TR, R0 + R1 + R2, nq, pr.q4);
+            }
             load_direct(TR);
             __syncthreads();
-            ntt_round<LOGM, TE, R3, false, false, NT, true>(sm, tw, TR, L0, nq, pr.q4);
+            ntt_round<LOGM, TE, RL, false, false, NT, true>(sm, tw, TR, L0, nq, pr.q4);
             __syncthreads();
             if (COMBINE) combine_store<TE, NT>(P, G, i, sm, g2, gs2, pr, nq);
             else final_store<TE, NT, true, false>(P, G, i, sm, g2, gs2, pr, nq);
@@ -839,39 +851,46 @@ k_ntt_cluster(const NttArgs P)
             load_direct(TR);
             __pipeline_wait_prior(0);
             __syncthreads();
-            ntt_round<LOGM, TE, R3, false, true, NT, true>(sm, tw, TR, L0, nq, pr.q4);
+            ntt_round<LOGM, TE, RL, false, true, NT, true>(sm, tw, TR, L0, nq, pr.q4);
             __syncthreads();
+            if constexpr (R4 != 0) {
+                ntt_round<LOGM, TE, R3, false, true, NT, false>(sm, tw, TR, R0 + R1 + R2, nq, pr.q4);
+                __syncthreads();
+            }
             ntt_round<LOGM, TE, R2, false, true, NT, false>(sm, tw, TR, R0 + R1, nq, pr.q4);
             __syncthreads();
             ntt_round<LOGM, TE, R1, false, true, NT, false>(sm, tw, TR, R0, nq, pr.q4);
             __syncthreads();
             ntt_round<LOGM, TE, R0, false, true, NT, false>(sm, tw, TR, 0, nq, pr.q4);
             cl_sync();  // every chunk transformed
-            u64 a[8], b[8];
+            u64 a[CPT][8];
 #pragma unroll
-            for (int v = 0; v < 8; v++) {
-                a[v] = cl_ld(rb[v] + ko0);
-                b[v] = cl_ld(rb[v] + ko1);
-            }
-            cross_inv(a, cw, nq, pr.q4);
-            cross_inv(b, cw, nq, pr.q4);
+            for (int v = 0; v < 8; v++)
+#pragma unroll
+                for (int c = 0; c < CPT; c++) a[c][v] = cl_ld(rb[v] + ko[c]);
+#pragma unroll
+            for (int c = 0; c < CPT; c++) cross_inv(a[c], cw, nq, pr.q4);
             u64 *dst = P.dst + ((size_t)G.dst[i] << P.logN) + k0;
             const u64 sc = G.scale[i], scs = G.scale_sh[i];
 #pragma unroll
-            for (int v = 0; v < 8; v++)
-                *reinterpret_cast<ulonglong2 *>(dst + (size_t)v * TE) =
-                    make_ulonglong2(shoup_canon(a[v], sc, scs, pr.q, nq), shoup_canon(b[v], sc, scs, pr.q, nq));
+            for (int v = 0; v < 8; v++) {
+                if constexpr (CPT == 2)
+                    *reinterpret_cast<ulonglong2 *>(dst + (size_t)v * TE) = make_ulonglong2(
+                        shoup_canon(a[0][v], sc, scs, pr.q, nq), shoup_canon(a[CPT - 1][v], sc, scs, pr.q, nq));
+                else
+                    dst[(size_t)v * TE] = shoup_canon(a[0][v], sc, scs, pr.q, nq);
+            }
         }
     }
     if (INV) cl_sync();  // no CTA leaves while a peer still reads its shared memory
 }
 
 // ngroups == 0 only sets the kernel's shared-memory limit (no launch).
-template <int R0, int R1, int R2, int R3, bool INV, int FUSE = kFuseNone>
+template <int R0, int R1, int R2, int R3, int R4, bool INV, int FUSE = kFuseNone>
 cudaError_t run_cluster(const NttArgs &a, int ngroups, cudaStream_t st)
 {
-    using CG = ClGeom<R0, R1, R2, R3>;
-    auto kern = k_ntt_cluster<R0, R1, R2, R3, INV, FUSE>;
+    using CG = ClGeom<R0, R1, R2, R3, R4>;
+    auto kern = k_ntt_cluster<R0, R1, R2, R3, R4, INV, FUSE>;
     static bool configured = false;  // once per instantiation
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG::SMEM);
@@ -987,36 +1006,56 @@ cudaError_t two_pass(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cuda
     return e;
 }
 
-// One-pass transforms over a cluster: local rounds (3, 3, 3, 4), which are
-// free of shared-memory bank conflicts with the one-word-per-16 padding and
-// keep the direct round inside the table's transposed region.
-#define HE_CL_ROUNDS 3, 3, 3, 4
-cudaError_t onepass(const he_ctx *c, const NttArgs &a, int ngroups, bool inverse, cudaStream_t st, const char *tag)
+// One-pass transforms over a cluster.  Local rounds (3, 3, 3, 4), 512
+// threads, free of shared-memory bank conflicts with the one-word-per-16
+// padding; with the plan's radix-8 bit, (3, 3, 2, 2, 3), 1024 threads at most
+// 64 registers (a 2-way conflict in the fourth round).  Both keep the direct
+// round inside the table's transposed region.
+#define HE_CL16 3, 3, 3, 4, 0
+#define HE_CL8 3, 3, 2, 2, 3
+cudaError_t onepass(const he_ctx *c, const NttArgs &a, int ngroups, bool inverse, cudaStream_t st, const char *tag,
+                    int plan)
 {
     if (ngroups == 0) {  // configure only
-        cudaError_t e = run_cluster<HE_CL_ROUNDS, false>(a, 0, st);
-        return e == cudaSuccess ? run_cluster<HE_CL_ROUNDS, true>(a, 0, st) : e;
+        cudaError_t e = run_cluster<HE_CL16, false>(a, 0, st);
+        if (e == cudaSuccess) e = run_cluster<HE_CL16, true>(a, 0, st);
+        if (e == cudaSuccess) e = run_cluster<HE_CL8, false>(a, 0, st);
+        return e == cudaSuccess ? run_cluster<HE_CL8, true>(a, 0, st) : e;
     }
-    const cudaError_t e = inverse ? run_cluster<HE_CL_ROUNDS, true>(a, ngroups, st)
-                                  : run_cluster<HE_CL_ROUNDS, false>(a, ngroups, st);
+    cudaError_t e;
+    if (plan & 1) e = inverse ? run_cluster<HE_CL8, true>(a, ngroups, st) : run_cluster<HE_CL8, false>(a, ngroups, st);
+    else e = inverse ? run_cluster<HE_CL16, true>(a, ngroups, st) : run_cluster<HE_CL16, false>(a, ngroups, st);
     prof_mark(c, st, tag, inverse ? ".inv_onepass" : ".fwd_onepass");
     return e;
 }
 
-cudaError_t onepass_combine(const he_ctx *c, const NttArgs &a, int ngroups, cudaStream_t st, const char *tag)
+cudaError_t onepass_combine(const he_ctx *c, const NttArgs &a, int ngroups, cudaStream_t st, const char *tag,
+                            int plan)
 {
-    const cudaError_t e = run_cluster<HE_CL_ROUNDS, false, kFuseCombine>(a, ngroups, st);
-    if (ngroups) prof_mark(c, st, tag, ".fwd_onepass_combine");
+    if (ngroups == 0) {
+        const cudaError_t e = run_cluster<HE_CL16, false, kFuseCombine>(a, 0, st);
+        return e == cudaSuccess ? run_cluster<HE_CL8, false, kFuseCombine>(a, 0, st) : e;
+    }
+    const cudaError_t e = (plan & 1) ? run_cluster<HE_CL8, false, kFuseCombine>(a, ngroups, st)
+                                     : run_cluster<HE_CL16, false, kFuseCombine>(a, ngroups, st);
+    prof_mark(c, st, tag, ".fwd_onepass_combine");
     return e;
 }
 
-cudaError_t onepass_tensor(const he_ctx *c, const NttArgs &a, int ngroups, cudaStream_t st, const char *tag)
+cudaError_t onepass_tensor(const he_ctx *c, const NttArgs &a, int ngroups, cudaStream_t st, const char *tag,
+                           int plan)
 {
-    const cudaError_t e = run_cluster<HE_CL_ROUNDS, true, kFuseTensor>(a, ngroups, st);
-    if (ngroups) prof_mark(c, st, tag, ".tensor_inv_onepass");
+    if (ngroups == 0) {
+        const cudaError_t e = run_cluster<HE_CL16, true, kFuseTensor>(a, 0, st);
+        return e == cudaSuccess ? run_cluster<HE_CL8, true, kFuseTensor>(a, 0, st) : e;
+    }
+    const cudaError_t e = (plan & 1) ? run_cluster<HE_CL8, true, kFuseTensor>(a, ngroups, st)
+                                     : run_cluster<HE_CL16, true, kFuseTensor>(a, ngroups, st);
+    prof_mark(c, st, tag, ".tensor_inv_onepass");
     return e;
 }
-#undef HE_CL_ROUNDS
+#undef HE_CL16
+#undef HE_CL8
 
 template <int LOGN, class P = Plan<LOGN>, int TE = 2048>
 cudaError_t two_pass_plan(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag)
@@ -1027,7 +1066,7 @@ cudaError_t two_pass_plan(const he_ctx *c, NttArgs a, int ngroups, bool inverse,
 template <int LOGN>
 cudaError_t two_pass_any(const he_ctx *c, NttArgs a, int ngroups, bool inverse, cudaStream_t st, const char *tag, int plan)
 {
-    if (LOGN == kClLogN && (plan & kPlanOnePass)) return onepass(c, a, ngroups, inverse, st, tag);
+    if (LOGN == kClLogN && (plan & kPlanOnePass)) return onepass(c, a, ngroups, inverse, st, tag, plan);
     // bit 3: 1024-element tiles (2^16 and 2^17; a pass over 2^10 stages keeps 2048)
     constexpr bool SMALL_OK = LOGN == 16 || LOGN == 17;
     if (SMALL_OK && (plan & 8)) {
@@ -1067,7 +1106,7 @@ cudaError_t combine_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t s
 template <int LOGN>
 cudaError_t combine_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, int plan)
 {
-    if (LOGN == kClLogN && (plan & kPlanOnePass)) return onepass_combine(c, a, ngroups, st, tag);
+    if (LOGN == kClLogN && (plan & kPlanOnePass)) return onepass_combine(c, a, ngroups, st, tag, plan);
     // bit 3: 1024-element tiles (2^16 and 2^17; a pass over 2^10 stages keeps 2048)
     constexpr bool SMALL_OK = LOGN == 16 || LOGN == 17;
     if (SMALL_OK && (plan & 8)) {
@@ -1110,7 +1149,7 @@ cudaError_t computed_plan(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t 
 template <int LOGN, int FUSE>
 cudaError_t computed_any(const he_ctx *c, NttArgs a, int ngroups, cudaStream_t st, const char *tag, int plan)
 {
-    if (FUSE == kFuseTensor && LOGN == kClLogN && (plan & kPlanOnePass)) return onepass_tensor(c, a, ngroups, st, tag);
+    if (FUSE == kFuseTensor && LOGN == kClLogN && (plan & kPlanOnePass)) return onepass_tensor(c, a, ngroups, st, tag, plan);
     // bit 3: 1024-element tiles (2^16 and 2^17; a pass over 2^10 stages keeps 2048)
     constexpr bool SMALL_OK = LOGN == 16 || LOGN == 17;
     constexpr int TS = SMALL_OK ? 1024 : 2048;
