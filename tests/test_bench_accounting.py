@@ -87,3 +87,27 @@ def test_committed_profile_lines_parse():
     fused = ["intt_d2.tensor_inv_pass1"] + NTT_KERNELS[1:4] + ["intt_special.ip_inv_pass1"] + NTT_KERNELS[5:]
     for k in fused + ["modup", "moddown_conv_ipq"]:
         assert k in seen, k
+
+
+@pytest.mark.parametrize("name,level,split", [("n16", 24, 1), ("n17", 44, 1), ("n16", 9, 0)])
+def test_fused_and_onepass_profile_names(name, level, split):
+    """The profile names of the fused and one-pass launches count the same
+    butterflies as the plain passes they replace."""
+    prm = oracle.preset(name)
+    plain = bench.kernel_work("intt_special.inv_pass1", prm, level, split)
+    assert bench.kernel_work("intt_special.ip_inv_pass1", prm, level, split) == plain
+    assert bench.kernel_work("intt_d2.tensor_inv_pass1", prm, level, split) == \
+        bench.kernel_work("intt_d2.inv_pass1", prm, level, split)
+    for site in ("intt_d2", "ntt_modup", "intt_special", "ntt_moddown"):
+        two = sum(bench.kernel_work(f"{site}.{d}_pass{k}", prm, level, split)[1]
+                  for d in ("fwd", "inv") for k in (1, 2)) // 2
+        kind, one = bench.kernel_work(f"{site}.{'fwd' if site.startswith('ntt') else 'inv'}_onepass", prm, level, split)
+        assert kind == "alu" and one == two, site
+
+
+def test_shape_dict_round_trip():
+    t = (1, 8, 2, 15, 8, 7, 1, 1, 4, 0.25)
+    d = bench.shape_dict(t)
+    assert d == {"group_cap": 1, "modup_chunk": 8, "pdl": 2, "ntt_r8": 15, "ip_jobs": 8, "fuse": 7,
+                 "ntt_split": 1, "ntt_small": 1, "ntt_onepass": 4, "ms": 0.25}
+    assert "ms" not in bench.shape_dict(t[:9])
