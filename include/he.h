@@ -554,8 +554,8 @@ int he_probe_butterfly_rate(int blocks, int iters, double *bfly_per_s, void *str
 int he_probe_conversion_rate(int width, int blocks, int iters, double *mac_per_s, void *stream);
 /* Measurement helper: rate (outputs per second) of the work a byte-split
  * tensor-core base conversion would still leave on the CUDA cores per output
- * (the north star's "exact byte-split form" of the conversion's matrix
- * product, Sec. 7's base conversion): the MMA's 13 fp32 byte-diagonal planes,
+ * (the conversion's matrix product, Sec. 7's base conversion, cut into 8-bit
+ * pieces exact in bf16 and summed in fp32): the MMA's 13 byte-diagonal planes,
  * each an exact integer below 2^23, turned into integers, shifted and added
  * into 128 bits, then one lazy Barrett reduction; register-resident, MMA not
  * counted; `blocks` x 256 threads x 16 outputs x `iters`.  Compare with
