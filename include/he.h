@@ -519,8 +519,10 @@ int he_get_shape(const he_ctx *ctx, he_shape *shape);
  * count == 1 times he_mul_rescale on jobs[0] (ws of he_workspace_bytes),
  * count > 1 times he_mul_batch on the jobs (ws of he_batch_workspace_bytes),
  * `reps` calls per shape after one warm-up call, CUDA events on `stream`.
- * The jobs' outputs are overwritten.  best: the shape kept; tried (optional,
- * max_tried entries): every shape with its time, *n_tried set. */
+ * The four fastest are then timed again, interleaved, in three rounds of
+ * 2 x `reps` calls, and the best median is kept.  The jobs' outputs are
+ * overwritten.  best: the shape kept, with that median; tried (optional,
+ * max_tried entries): every shape of the search with its time, *n_tried set. */
 int he_autotune(he_ctx *ctx, const he_job *jobs, int count, const uint64_t *evk_dev, void *ws, size_t ws_bytes,
                 int reps, void *stream, he_shape *best, he_shape *tried, int max_tried, int *n_tried);
 

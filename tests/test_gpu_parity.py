@@ -819,7 +819,9 @@ def test_autotune_batch_keeps_results(g):
     try:
         best, tried = g.he_autotune(ctx, jobs, evk_t, ws, reps=2)
         assert all(t[9] > 0 for t in tried) and len(set(t[:9] for t in tried)) == len(tried)
-        assert best[:9] == g.he_get_shape(ctx) and best[9] == min(t[9] for t in tried)
+        # the kept shape is one of the four fastest of the search, re-timed
+        fastest = sorted(tried, key=lambda t: t[9])[:4]
+        assert best[:9] == g.he_get_shape(ctx) and best[:9] in {t[:9] for t in fastest} and best[9] > 0
         # the first sweep gives every knob every value (N = 2^15: no pass splits
         # or small tiles); pdl with fuse and ntt_r8 with ntt_split take every pair
         for k, vals in enumerate(((1, 2, 3, 4), (4, 8, 16), (0, 1, 2), tuple(range(16)), (1, 4, 8), (0, 1, 2, 3), (0,),
