@@ -500,7 +500,9 @@ typedef struct {
     int ntt_onepass; /* bit s (the sites of ntt_r8), N = 2^16 only: that site's transform runs in one pass
                     over memory (Algo 3 whole), each limb on a cluster of 8 CTAs that hold one eighth of it
                     each in shared memory and exchange the first three stages through the cluster's
-                    distributed shared memory; else the two passes of ntt_split.  Site 2 keeps two
+                    distributed shared memory; else the two passes of ntt_split.  The site's ntt_r8 bit
+                    picks the local rounds: radix-8 and radix-4 on 1024 threads, else radix-16 on 512.
+                    Site 2 keeps two
                     passes when fuse bits 1 and 2 put the key-switch sums into its first pass.
                     0..15 */
     double ms;   /* he_autotune: measured milliseconds per call; else 0 */
