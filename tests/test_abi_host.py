@@ -170,3 +170,15 @@ def test_argument_errors_are_status_codes(g):
         g.he_encrypt_poly(ctx, np.zeros((2, 3, 4096), np.uint64), np.zeros(4096, np.int64), 4, 1)
     assert e.value.code == g.HE_ELEVEL
     assert g.lib().he_strerror(g.HE_ETIMEOUT) == b"bounded device wait gave up"
+
+
+def test_probe_argument_errors_need_no_gpu(g):
+    """The probes check their arguments before any CUDA call."""
+    st = 0  # a stream handle the calls never reach
+    for call in (lambda: g.he_probe_recombine_rate(0, 64, st), lambda: g.he_probe_recombine_rate(152, 0, st),
+                 lambda: g.he_probe_recombine_rate(152, 1 << 20, st),
+                 lambda: g.he_probe_conversion_rate(3, 152, 64, st), lambda: g.he_probe_conversion_rate(8, 0, 64, st),
+                 lambda: g.he_probe_butterfly_rate(0, 64, st)):
+        with pytest.raises(g.HeError) as e:
+            call()
+        assert e.value.code == g.HE_EINVAL
